@@ -1,0 +1,519 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+published known-answer vectors, closed forms, library routines, geometric
+invariants and brute force.  Each test names the passage of the paper it
+checks (arxiv 2602.10114) or the outside source of its expected values."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, stats
+from scipy.spatial.distance import cdist
+from scipy.spatial.transform import Rotation
+
+from paper_2602_10114_gb300 import scenarios as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+def tiny_scenario(arms, K=None, H=None, world=None, aabb=None, **params):
+    p = dict(S.DEFAULT_PARAMS)
+    p.update(params)
+    A = len(arms)
+    for a in arms:
+        a.K = a.K if K is None else K
+        a.H = a.H if H is None else H
+    return S.Scenario(
+        "tiny", arms, p,
+        np.zeros((0, 4), np.float32) if world is None else np.asarray(world, np.float32),
+        None, np.zeros((0, 6), np.float32) if aabb is None else np.asarray(aabb, np.float32),
+        [np.zeros(a.dof, np.float32) for a in arms], [np.zeros(a.dof, np.float32) for a in arms],
+        [np.zeros(a.dof, np.float32) for a in arms], np.zeros((A, 3), np.float32), cycles=1)
+
+
+def point_arm(base_xyz, radius, K=8, H=4):
+    """One revolute joint with a=d=alpha=0 and a single sphere at the frame-1
+    origin, i.e. at the base position whatever q is."""
+    return S.Arm(dof=1, n_spheres=1, K=K, H=H, dh=np.zeros((1, 4), np.float32),
+                 q_lo=np.full(1, -2.8, np.float32), q_hi=np.full(1, 2.8, np.float32),
+                 qd_max=np.full(1, 2.0, np.float32), sphere_body=np.array([1], np.int32),
+                 sphere_xyzr=np.array([[0, 0, 0, radius]], np.float32),
+                 base_pose=np.array([*base_xyz, 1, 0, 0, 0], np.float32))
+
+
+def dh_arm(dh, spheres=None, bodies=None, base=(0, 0, 0, 1, 0, 0, 0), K=8, H=4):
+    dh = np.asarray(dh, np.float32)
+    d = len(dh)
+    if spheres is None:
+        spheres = np.array([[0, 0, 0, 0.01]], np.float32)
+        bodies = np.array([d], np.int32)
+    return S.Arm(dof=d, n_spheres=len(spheres), K=K, H=H, dh=dh,
+                 q_lo=np.full(d, -2.8, np.float32), q_hi=np.full(d, 2.8, np.float32),
+                 qd_max=np.full(d, 2.0, np.float32),
+                 sphere_body=np.asarray(bodies, np.int32),
+                 sphere_xyzr=np.asarray(spheres, np.float32),
+                 base_pose=np.asarray(base, np.float32))
+
+
+def goals_of(orc, sc):
+    gp, gR = zip(*[orc.goal_pose(a, sc.goal_q[a]) for a in range(sc.n_arms)])
+    return np.asarray(gp), np.asarray(gR)
+
+
+# ---------------------------------------------------------------------------
+# sampling (Sec. III-A Optimize: eps ~ N(0, Sigma_h))
+
+def test_philox_known_answer_vectors(oracle_mod):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert oracle_mod.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_uniform23_is_open_interval_and_float32_exact(oracle_mod):
+    rng = np.random.default_rng(0)
+    lo, hi = oracle_mod.uniform23(0), oracle_mod.uniform23(0xFFFFFFFF)
+    assert lo == 0.5 / 2 ** 23 and hi == 1 - 0.5 / 2 ** 23
+    for x in [0x12345678, 0xdeadbeef, 0x80000000, *rng.integers(0, 2**32, 1000)]:
+        u = oracle_mod.uniform23(x)
+        assert float(np.float32(u)) == u and 0 < u < 1
+
+
+def test_normals_moments_and_independence(oracle_mod):
+    d, N = 8, 125_000
+    Z = np.array([oracle_mod.normals(7, 1, 3, 0, n % 5000, n // 5000, d) for n in range(N)])
+    z = Z.ravel()
+    M = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(M)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / M)
+    assert abs(stats.skew(z)) < 5 * math.sqrt(6 / M)
+    assert abs(stats.kurtosis(z)) < 5 * math.sqrt(24 / M)
+    assert stats.kstest(z[:200_000], "norm").pvalue > 1e-4
+    corr = np.corrcoef(Z.T)
+    off = corr[~np.eye(d, dtype=bool)]
+    assert np.abs(off).max() < 5 / math.sqrt(N)
+
+
+def test_normals_depend_on_every_counter_field(oracle_mod):
+    base = oracle_mod.normals(1, 0, 0, 0, 0, 0, 9)
+    for args in [(2, 0, 0, 0, 0, 0), (1, 1, 0, 0, 0, 0), (1, 0, 1, 0, 0, 0), (1, 0, 0, 1, 0, 0),
+                 (1, 0, 0, 0, 1, 0), (1, 0, 0, 0, 0, 1)]:
+        z = oracle_mod.normals(*args, 9)
+        assert np.all(z != base)
+    # joints 4..7 come from a different Philox block than 0..3
+    assert len(set(np.round(base, 12))) == 9
+
+
+def test_cholesky_matches_library(oracle_mod):
+    rng = np.random.default_rng(0)
+    for d in (1, 6, 7, 9):
+        X = rng.normal(size=(d, d))
+        Sg = X @ X.T + 0.1 * np.eye(d)
+        L = oracle_mod.cholesky(Sg, jitter=1e-8)
+        assert np.allclose(np.triu(L, 1), 0)
+        ref = np.linalg.cholesky(Sg + 1e-8 * np.eye(d))
+        assert np.allclose(L, ref, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# kinematics (Sec. IV-A: link frames by forward kinematics, spheres at
+# constant transforms from the links)
+
+def test_fk_planar_two_link_closed_form(oracle_mod):
+    from oracle.oracle import Oracle
+    a1, a2 = 0.4, 0.3
+    arm = dh_arm([[a1, 0, 0, 0], [a2, 0, 0, 0]])
+    orc = Oracle(tiny_scenario([arm]))
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        q = rng.uniform(-2.8, 2.8, 2)
+        F, _ = orc.fk(0, q)
+        ee = F[-1][:3, 3]
+        exp = [a1 * math.cos(q[0]) + a2 * math.cos(q[0] + q[1]),
+               a1 * math.sin(q[0]) + a2 * math.sin(q[0] + q[1]), 0.0]
+        assert np.allclose(ee, exp, atol=1e-14)
+        # planar: the end-effector heading is q1 + q2 about z
+        R = F[-1][:3, :3]
+        assert np.allclose(R, Rotation.from_euler("z", q[0] + q[1]).as_matrix(), atol=1e-14)
+
+
+def _random_arm(seed, dof=7):
+    rng = np.random.default_rng(seed)
+    geo = S.random_geometry(rng, dof, per_link=5, tool_spheres=5)
+    base = np.array([0.3, -0.2, 0.1, *Rotation.from_euler("zyx", [0.4, 0.2, -0.3]).as_quat(
+        scalar_first=True)], np.float32)
+    return S.Arm(dof=dof, n_spheres=len(geo["sphere_body"]), K=8, H=4, dh=geo["dh"],
+                 q_lo=np.full(dof, -2.8, np.float32), q_hi=np.full(dof, 2.8, np.float32),
+                 qd_max=np.full(dof, 2.0, np.float32), sphere_body=geo["sphere_body"],
+                 sphere_xyzr=geo["sphere_xyzr"], base_pose=base)
+
+
+def test_fk_frames_rigid_and_link_lengths(oracle_mod):
+    from oracle.oracle import Oracle
+    arm = _random_arm(3)
+    orc = Oracle(tiny_scenario([arm]))
+    dh = arm.dh.astype(np.float64)
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        F, _ = orc.fk(0, rng.uniform(-2.8, 2.8, 7))
+        for i in range(8):
+            R = F[i][:3, :3]
+            assert np.allclose(R @ R.T, np.eye(3), atol=1e-13)
+            assert abs(np.linalg.det(R) - 1) < 1e-13
+            assert np.allclose(F[i][3], [0, 0, 0, 1])
+        for i in range(1, 8):
+            step = np.linalg.norm(F[i][:3, 3] - F[i - 1][:3, 3])
+            assert abs(step - math.hypot(dh[i - 1, 0], dh[i - 1, 1])) < 1e-13
+
+
+def test_fk_joint_i_rotates_downstream_about_axis_z_im1(oracle_mod):
+    """Joint i turns everything after it about the z axis of frame i-1 through
+    the frame-(i-1) origin, by exactly the change of q_i (right-hand rule)."""
+    from oracle.oracle import Oracle
+    arm = _random_arm(4)
+    orc = Oracle(tiny_scenario([arm]))
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        q = rng.uniform(-2, 2, 7)
+        F0, S0 = orc.fk(0, q)
+        i = int(rng.integers(1, 8))
+        dq = float(rng.uniform(-0.7, 0.7))
+        q1 = q.copy()
+        q1[i - 1] += dq
+        F1, S1 = orc.fk(0, q1)
+        axis = F0[i - 1][:3, 2]
+        o = F0[i - 1][:3, 3]
+        rot = Rotation.from_rotvec(axis * dq).as_matrix()
+        down = arm.sphere_body >= i
+        moved = (S0[down, :3] - o) @ rot.T + o
+        assert np.allclose(S1[down, :3], moved, atol=1e-13)
+        assert np.allclose(S1[~down, :3], S0[~down, :3], atol=0)
+        assert np.allclose(F1[-1][:3, :3], rot @ F0[-1][:3, :3], atol=1e-13)
+
+
+def test_link_sphere_end_points_sit_on_frame_origins(oracle_mod):
+    """The generator puts t=0 of link i at the frame-i origin and t=1 at the
+    frame-(i-1) origin; FK must place them there."""
+    from oracle.oracle import Oracle
+    arm = _random_arm(6)
+    orc = Oracle(tiny_scenario([arm]))
+    F, Sph = orc.fk(0, np.linspace(-1, 1, 7))
+    for i in range(1, 8):
+        idx = np.where(arm.sphere_body == i)[0]
+        assert np.allclose(Sph[idx[0], :3], F[i][:3, 3], atol=1e-6)
+        assert np.allclose(Sph[idx[-1], :3], F[i - 1][:3, 3], atol=1e-6)
+
+
+def test_fk_base_pose_is_a_rigid_motion(oracle_mod):
+    from oracle.oracle import Oracle
+    arm = _random_arm(7)
+    arm0 = _random_arm(7)
+    arm0.base_pose = np.array([0, 0, 0, 1, 0, 0, 0], np.float32)
+    o1 = Oracle(tiny_scenario([arm]))
+    o0 = Oracle(tiny_scenario([arm0]))
+    q = np.linspace(-1.3, 0.9, 7)
+    _, s1 = o1.fk(0, q)
+    _, s0 = o0.fk(0, q)
+    bp = arm.base_pose.astype(np.float64)
+    R = Rotation.from_quat(bp[3:], scalar_first=True).as_matrix()
+    assert np.allclose(s1[:, :3], s0[:, :3] @ R.T + bp[:3], atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# distances (Sec. IV-A rho_b)
+
+def test_sphere_distances_brute_force(oracle_mod):
+    rng = np.random.default_rng(8)
+    A = rng.uniform(-1, 1, (20, 4))
+    B = rng.uniform(-1, 1, (30, 4))
+    A[:, 3] = np.abs(A[:, 3]) * 0.1
+    B[:, 3] = np.abs(B[:, 3]) * 0.1
+    ref = cdist(A[:, :3], B[:, :3]) - A[:, 3:4] - B[:, 3][None, :]
+    got = np.array([[oracle_mod.sphere_sphere(a, b) for b in B] for a in A])
+    assert np.allclose(got, ref, atol=1e-14)
+
+
+def test_sphere_aabb_analytic_points(oracle_mod):
+    box = [0.1, 0.2, 0.3, 0.2, 0.1, 0.05]
+    c, h = np.array(box[:3]), np.array(box[3:])
+    r = 0.02
+    # centre inside: nearest face is the z face at 0.05
+    assert math.isclose(oracle_mod.sphere_aabb([*c, r], box), -0.05 - r, abs_tol=1e-15)
+    dlt = 0.07
+    face = c + np.array([h[0] + dlt, 0, 0])
+    assert math.isclose(oracle_mod.sphere_aabb([*face, r], box), dlt - r, abs_tol=1e-14)
+    edge = c + np.array([h[0] + dlt, h[1] + dlt, 0])
+    assert math.isclose(oracle_mod.sphere_aabb([*edge, r], box), dlt * math.sqrt(2) - r,
+                        abs_tol=1e-14)
+    corner = c - h - dlt
+    assert math.isclose(oracle_mod.sphere_aabb([*corner, r], box), dlt * math.sqrt(3) - r,
+                        abs_tol=1e-14)
+    # random outside points: distance to the nearest point of the box
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        p = rng.uniform(-1, 1, 3)
+        near = np.clip(p, c - h, c + h)
+        if np.all(near == p):
+            continue
+        assert math.isclose(oracle_mod.sphere_aabb([*p, r], box), np.linalg.norm(p - near) - r,
+                            abs_tol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# stage-cost terms (Eq. 5) and the coordination ramp (Sec. IV-A)
+
+def test_pose_cost_closed_forms(oracle_mod):
+    rng = np.random.default_rng(10)
+    R = Rotation.random(random_state=3).as_matrix()
+    p = np.array([0.3, -0.1, 0.5])
+    T = np.eye(4)
+    T[:3, :3], T[:3, 3] = R, p
+    assert abs(oracle_mod.pose_cost(T, p, R, 0.5)) < 1e-15
+    v = rng.normal(size=3) * 0.2
+    assert math.isclose(oracle_mod.pose_cost(T, p + v, R, 0.5), np.linalg.norm(v), rel_tol=1e-14)
+    for th in (0.1, 1.0, math.pi):
+        Rg = Rotation.from_rotvec(th * np.array([0.6, 0.0, 0.8])).as_matrix() @ R
+        assert math.isclose(oracle_mod.pose_cost(T, p, Rg, 0.5), 0.5 * (1 - math.cos(th)),
+                            abs_tol=1e-14)
+
+
+def test_stop_and_joint_cost_closed_forms(oracle_mod):
+    qmax = np.array([2.0, 2.0, 2.0])
+    assert oracle_mod.stop_cost([1.9, -2.0, 0.0], qmax) == 0.0
+    assert math.isclose(oracle_mod.stop_cost([2.5, -3.0, 0.0], qmax), 0.25 + 1.0)
+    lo, hi = np.full(2, -2.8), np.full(2, 2.8)
+    assert oracle_mod.joint_cost([2.65, -2.65], lo, hi, 0.1) == 0.0
+    assert math.isclose(oracle_mod.joint_cost([2.9, -3.0], lo, hi, 0.1), 0.2 ** 2 + 0.3 ** 2)
+
+
+def test_ramp_closed_forms(oracle_mod):
+    B = 0.03
+    assert oracle_mod.ramp(B, B) == 0.0
+    assert oracle_mod.ramp(0.5, B) == 0.0
+    assert math.isclose(oracle_mod.ramp(B / 2, B), 0.5)
+    assert oracle_mod.ramp(0.0, B) == 1.0
+    assert oracle_mod.ramp(-0.01, B) > 1.0
+
+
+def test_priority_rule(oracle_mod):
+    """Sec. IV-B: tau = 0 disables priority; alpha^(j,i) alpha^(i,j) = 1;
+    the arm closer to its goal gets the smaller weight."""
+    for e1, e2 in [(0.2, 0.5), (0.01, 1.0), (0.3, 0.3)]:
+        assert oracle_mod.priority(e1, e2, 0.0) == 1.0
+        assert math.isclose(oracle_mod.priority(e1, e2, 3.0) * oracle_mod.priority(e2, e1, 3.0),
+                            1.0, rel_tol=1e-14)
+    assert oracle_mod.priority(0.1, 0.5, 3.0) < 1.0 < oracle_mod.priority(0.5, 0.1, 3.0)
+    assert math.isclose(oracle_mod.priority(2 - 1e-4, 1 - 1e-4, 3.0), 8.0, rel_tol=1e-14)
+
+
+def test_weights_softmax(oracle_mod):
+    """Eq. 2: positive, sum to one, invariant to a common shift, equal to the
+    library softmax of -C/lambda."""
+    rng = np.random.default_rng(11)
+    Cn = rng.uniform(0, 200, 257)
+    w = oracle_mod.weights(Cn, 10.0)
+    assert np.all(w > 0) and abs(w.sum() - 1) < 1e-12
+    assert np.allclose(w, special.softmax(-Cn / 10.0), rtol=1e-12, atol=1e-300)
+    assert np.allclose(oracle_mod.weights(Cn + 1e4, 10.0), w, rtol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# rollout (Sec. III-A f, Eq. 1)
+
+def _single(world=None, **params):
+    from oracle.oracle import Oracle
+    arm = _random_arm(12)
+    sc = tiny_scenario([arm], K=16, H=8, world=world, **params)
+    return sc, Oracle(sc)
+
+
+def test_integration_closed_form_constant_acceleration(oracle_mod):
+    sc, orc = _single(dt=0.02)
+    a = np.linspace(-0.5, 0.7, 7)
+    q0 = np.linspace(-1, 1, 7)
+    qd0 = np.linspace(0.2, -0.3, 7)
+    gp, gR = goals_of(orc, sc)
+    H, dt = 8, 0.02
+    _, _, _, qtraj = orc.rollout(0, [q0], [qd0], gp, gR, np.tile(a, (H, 1)))
+    for h in range(1, H + 1):
+        exp = q0 + h * dt * qd0 + a * dt * dt * h * (h + 1) / 2
+        assert np.allclose(qtraj[h - 1], exp, atol=1e-14)
+
+
+def test_discounted_sum_of_constant_stage_cost(oracle_mod):
+    """Eq. 1 with gamma < 1: a rollout standing still scores the same stage cost
+    c at every step, so C = c (1 - gamma^H) / (1 - gamma)."""
+    sc, orc = _single(gamma=0.9)
+    gp, gR = goals_of(orc, sc)
+    gp = gp + 0.1
+    q0, qd0 = np.linspace(-1, 1, 7), np.zeros(7)
+    tot, stage, _, _ = orc.rollout(0, [q0], [qd0], gp, gR, np.zeros((8, 7)))
+    c = stage[0]
+    assert c > 0 and np.allclose(stage, c, rtol=1e-14)
+    assert math.isclose(tot, c * (1 - 0.9 ** 8) / (1 - 0.9), rel_tol=1e-13)
+
+
+def test_colliding_pose_exceeds_threshold(oracle_mod):
+    """A world sphere placed on a link sphere: the world term is above its
+    unweighted threshold 1, i.e. the stage cost exceeds w_c."""
+    from oracle.oracle import Oracle
+    arm = _random_arm(13)
+    q0 = np.linspace(-0.5, 0.5, 7)
+    probe = Oracle(tiny_scenario([arm]))
+    _, sph = probe.fk(0, q0)
+    world = [[*sph[20, :3], 0.05]]
+    sc = tiny_scenario([arm], H=3, world=world, w_pose=0, w_stop=0, w_joint=0, w_self=0)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    _, stage, _, _ = orc.rollout(0, [q0], [np.zeros(7)], gp, gR, np.zeros((3, 7)))
+    o = sc.world[0].astype(np.float64)
+    dmin = (cdist(sph[:, :3], o[None, :3])[:, 0] - sph[:, 3] - o[3]).min()
+    assert dmin <= -(sph[20, 3] + 0.05) + 1e-6
+    exp = 1 - dmin / 0.03
+    assert stage[0] > sc.params["w_coll"]
+    assert math.isclose(stage[0], sc.params["w_coll"] * exp, rel_tol=1e-12)
+
+
+def _two_points(gap, tau=0.0, H_other=4):
+    """Arm 0 and arm 1 are single spheres of radius 1/16 whose surfaces are
+    `gap` apart (up to float32 rounding of the input position); arm 1's plan is published; only the coordination term is on."""
+    from oracle.oracle import Oracle
+    r = 0.0625
+    a0 = point_arm((0, 0, 0), r, H=4)
+    a1 = point_arm((2 * r + gap, 0, 0), r, H=H_other)
+    sc = tiny_scenario([a0, a1], w_pose=0, w_stop=0, w_joint=0, w_coll=0, w_self=0,
+                       w_dyn=1.0, tau=tau)
+    orc = Oracle(sc)
+    # publish both plans: run one cycle (plans = the spheres, which never move)
+    gp = np.zeros((2, 3))
+    gR = np.tile(np.eye(3).ravel(), (2, 1))
+    orc.cycle([np.zeros(1)] * 2, [np.zeros(1)] * 2, gp, gR)
+    return sc, orc, gp, gR
+
+
+@pytest.mark.parametrize("gap,expected", [(0.0301, 0.0), (0.2, 0.0), (0.015, 0.5), (0.0, 1.0),
+                                          (-0.02, 1.0)])
+def test_coordination_cost_closed_forms(oracle_mod, gap, expected):
+    """Sec. IV-A: C_dyn = max(0, 1 - rho_b / B): zero at rho_b >= B, one half at
+    B/2, one at contact and under overlap (rho_b is a distance, >= 0)."""
+    sc, orc, gp, gR = _two_points(gap)
+    _, stage, _, _ = orc.rollout(0, [np.zeros(1)] * 2, [np.zeros(1)] * 2, gp, gR,
+                                 np.zeros((4, 1)), alpha_row=np.array([0.0, 1.0]))
+    # float32 rounding of the input position moves the gap by < 1e-8 m
+    assert np.allclose(stage, expected, atol=1e-6)
+    if expected in (0.0, 1.0):
+        assert np.all(stage == expected)
+
+
+def test_min_horizon_rule(oracle_mod):
+    """Sec. IV-C: an arm uses min(H_j, H_i) steps of a received plan."""
+    sc, orc, gp, gR = _two_points(0.0, H_other=2)
+    _, stage, _, _ = orc.rollout(0, [np.zeros(1)] * 2, [np.zeros(1)] * 2, gp, gR,
+                                 np.zeros((4, 1)), alpha_row=np.array([0.0, 1.0]))
+    assert np.allclose(stage, [1, 1, 0, 0], atol=1e-12)
+
+
+def test_missing_plans_are_ignored_and_query_count(oracle_mod):
+    """Sec. IV-C: neighbours without a published plan are ignored (first
+    cycle); afterwards every rollout step queries N_S^(j) * sum_i N_S^(i)
+    sphere pairs (Sec. IV-A complexity)."""
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(2), K=16, H=6)
+    orc = Oracle(sc, threads=4)
+    gp, gR = goals_of(orc, sc)
+    o1 = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    assert np.all(o1["n_queries"] == 0) and np.all(o1["alpha"] == 0)
+    o2 = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    for a in range(sc.n_arms):
+        assert o2["n_queries"][a] == orc.query_count(a) == 6 * 16 * 40 * 120
+
+
+def test_zero_noise_rollout_reproduces_the_plan(oracle_mod):
+    """Sec. IV-A: ToPlan applies f to the means; a rollout of U = mu gives the
+    published sphere trajectory and joint plan."""
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(2), K=16, H=6)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    out = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    for a in range(sc.n_arms):
+        mu = orc.split(out["mean_plan"], "hd", a)
+        q = [sc.q0[i] for i in range(sc.n_arms)]
+        _, _, sph, qt = orc.rollout(a, q, sc.qd0, gp, gR, mu)
+        assert np.array_equal(sph, orc.split(out["plan_spheres"], "hs", a))
+        assert np.array_equal(qt, orc.split(out["plan_q"], "hd", a))
+
+
+def test_update_one_hot_weights_recover_best_sample(oracle_mod):
+    """Eqs. 2-4 with lambda -> 0 and alpha_mu = alpha_Sigma = 1: the weights are
+    one-hot on n*, so mu_1 = U_{n*,1} (= the executed U_*) and Sigma_1 = 0."""
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(1), K=32, H=5)
+    sc.params.update(lam=1e-9, alpha_mu=1.0, alpha_sigma=1.0)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    out = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    mu = orc.split(out["mean_plan"], "hd", 0)
+    assert np.allclose(mu[0], out["u_star"], atol=1e-15)
+    assert np.abs(orc.split(out["Sigma"], "hdd", 0)[0]).max() < 1e-20
+    costs = out["costs"]
+    assert out["n_star"][0] == int(np.argmin(costs))
+
+
+def test_update_uniform_weights_give_sample_moments(oracle_mod):
+    """Eqs. 3-4 with lambda -> infinity: uniform weights, so mu~ and Sigma~ are
+    the sample mean and the (biased) sample covariance of the drawn U."""
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(1), K=64, H=3)
+    sc.params.update(lam=1e30, alpha_mu=1.0, alpha_sigma=1.0)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    out = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    d, K, s2 = 7, 64, 0.3 ** 2
+    L = oracle_mod.cholesky(s2 * np.eye(d), 1e-8)
+    for h in range(3):
+        U = np.array([L @ oracle_mod.normals(sc.params["seed"], 0, 0, 0, n, h, d)
+                      for n in range(K)])
+        assert np.allclose(orc.split(out["mean_plan"], "hd", 0)[h], U.mean(0), atol=1e-14)
+        assert np.allclose(orc.split(out["Sigma"], "hdd", 0)[h], np.cov(U.T, bias=True),
+                           atol=1e-14)
+
+
+def test_shift_moves_phi_one_step(oracle_mod):
+    """Sec. III-A left-shifting at the start of each cycle: phi_h <- phi_{h+1};
+    with alpha_mu = alpha_Sigma = 0 the update keeps the shifted values."""
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(1), K=16, H=5)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    o1 = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    orc.sc.params.update(alpha_mu=0.0, alpha_sigma=0.0)
+    orc.cfg.alpha_mu = 0.0
+    orc.cfg.alpha_sigma = 0.0
+    o2 = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    mu1, mu2 = orc.split(o1["mean_plan"], "hd", 0), orc.split(o2["mean_plan"], "hd", 0)
+    S1, S2 = orc.split(o1["Sigma"], "hdd", 0), orc.split(o2["Sigma"], "hdd", 0)
+    assert np.array_equal(mu2[:-1], mu1[1:]) and np.array_equal(mu2[-1], mu1[-1])
+    assert np.array_equal(S2[:-1], S1[1:]) and np.array_equal(S2[-1], 0.09 * np.eye(7))
+
+
+def test_priority_uses_own_sensed_and_neighbours_published_distance(oracle_mod):
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(2), K=8, H=4)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    o1 = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    e_pub = o1["dist_to_goal"].copy()
+    q2 = [q + 0.1 for q in sc.q0]
+    o2 = orc.cycle(q2, sc.qd0, gp, gR)
+    A = sc.n_arms
+    al = o2["alpha"].reshape(A, A)
+    for j in range(A):
+        for i in range(A):
+            exp = 0.0 if i == j else oracle_mod.priority(o2["dist_to_goal"][j], e_pub[i], 3.0)
+            assert al[j, i] == exp
