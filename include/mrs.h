@@ -1,0 +1,253 @@
+/*
+ * mrs.h -- C ABI of the GB300 (sm_103a) MR-STORM control-cycle library.
+ *
+ * The library runs, for several robot arms at once, the per-control-cycle
+ * MPPI update of MR-STORM (arxiv 2602.10114): each arm samples K joint-
+ * acceleration sequences around its Gaussian control distribution, rolls
+ * them out over its horizon H, scores every step (goal pose, stopping
+ * velocity, joint limits, world and self clearance, and clearance against
+ * the other arms' published plans weighted by the dynamic priority rule),
+ * and updates the distribution from the exponentiated costs.  All stages
+ * run in the library's own CUDA kernels on the context's stream.
+ *
+ * Conventions common to every call
+ *  - Every call returns an mrs_status; no exception or abort crosses the
+ *    ABI.  On failure, mrs_last_error(ctx) gives a one-line reason.
+ *  - Host pointers are read or written only during the call; the caller
+ *    owns all memory it passes.  Device pointers (the *_device calls) are
+ *    used in stream order on the context's stream.
+ *  - Per-arm arrays are concatenated in arm order.  With d_a, H_a, K_a and
+ *    NS_a the DoF, horizon, samples and spheres of arm a:
+ *      "hd"  = sum_a H_a*d_a          "hs" = sum_a H_a*NS_a*4
+ *      "d"   = sum_a d_a              "k"  = sum_a K_a
+ *  - Floats are IEEE binary32.  Lengths are metres, angles radians, time
+ *    seconds.  Non-finite inputs are rejected with MRS_EINVAL.
+ *  - One context per host thread; calls on one context are not reentrant.
+ */
+#ifndef MRS_H
+#define MRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrs_ctx mrs_ctx;
+
+typedef enum {
+    MRS_OK = 0,
+    MRS_EINVAL = 1,        /* bad argument: null, out of range, non-finite */
+    MRS_ENOMEM = 2,        /* device or pinned host allocation failed */
+    MRS_ECUDA = 3,         /* a CUDA runtime call failed */
+    MRS_ETIMEOUT = 4,      /* a bounded wait (host or device) gave up */
+    MRS_ESTATE = 5,        /* call not valid in the context's state */
+    MRS_EUNSUPPORTED = 6   /* valid request the build does not support */
+} mrs_status;
+
+/* Limits of this build. */
+#define MRS_MAX_ARMS 32
+#define MRS_MAX_DOF 9
+#define MRS_MAX_SPHERES 64
+#define MRS_MAX_HORIZON 128
+#define MRS_MAX_SAMPLES 8192
+#define MRS_MAX_WORLD_SPHERES 1024
+#define MRS_MAX_AABBS 64
+
+/* One arm (Sec. IV-A: an arm is a DH chain whose collision geometry is N_S
+ * spheres at constant transforms from its links).  Copied at create.
+ *  dh          [dof][4]   a, d, alpha, theta_offset of the standard DH
+ *                         convention  T_i = T_{i-1} Rz(q_i + theta_i) Tz(d_i)
+ *                         Tx(a_i) Rx(alpha_i),  T_0 = base pose.
+ *  q_lo, q_hi  [dof]      joint limits of the soft joint-limit cost.
+ *  qd_max      [dof]      velocity limit of the safe-stopping cost.
+ *  sphere_body [NS]       body of each sphere, 1..dof for link i, dof+1 for
+ *                         the tool (carried by frame dof); non-decreasing.
+ *  sphere_xyzr [NS][4]    centre in the body's frame and radius.
+ *  base_pose   [7]        base position and unit quaternion (w, x, y, z).
+ *  K, H                   samples per iteration and horizon.           */
+typedef struct {
+    int dof, n_spheres, K, H;
+    const float *dh;
+    const float *q_lo, *q_hi, *qd_max;
+    const int *sphere_body;
+    const float *sphere_xyzr;
+    float base_pose[7];
+} mrs_arm_desc;
+
+/* Controller parameters.
+ *  dt           control period and rollout step.
+ *  lambda       temperature of the MPPI weights (Eq. 2).
+ *  gamma        discount of Eq. 1.
+ *  alpha_mu, alpha_sigma   EMA steps of Eq. 4.
+ *  sigma_init   initial standard deviation of every control (Sigma = s^2 I),
+ *               also the covariance given to the new last step at a shift.
+ *  w_*          weights of Eq. 5 (w_coll world, w_self self collision) and
+ *               w_dyn of the coordination term (Sec. IV-A/B).
+ *  B            coordination safety buffer; B_world, B_self the ramps of
+ *               the world and self clearance terms.
+ *  tau          priority trust exponent (Sec. IV-B).
+ *  q_margin     soft-limit margin of the joint cost.
+ *  iterations   optimisation iterations per cycle (the paper's K).
+ *  seed         Philox key of the sampling.
+ *  mode         0 = exact costs (the only mode of this build).          */
+typedef struct {
+    int n_arms;
+    const mrs_arm_desc *arms;
+    float dt, lambda, gamma, alpha_mu, alpha_sigma, sigma_init;
+    float w_pose, w_rot, w_stop, w_joint, w_coll, w_self, w_dyn;
+    float B, B_world, B_self, tau, q_margin;
+    int iterations;
+    unsigned long long seed;
+    int mode;
+} mrs_config;
+
+/* Sensed state of one arm for one cycle (Alg. 1, Sense): host pointers.
+ *  q, qd [dof]; goal_p [3]; goal_R [9] row-major rotation of the goal. */
+typedef struct {
+    const float *q, *qd, *goal_p, *goal_R;
+} mrs_arm_state;
+
+/* Results of one cycle, caller-allocated host buffers (any may be NULL).
+ *  mean_plan    "hd"   mu after the update (the mean plan).
+ *  plan_spheres "hs"   ToPlan(mu): the anticipated plan of Sec. IV-A,
+ *                      time-major [h][sphere][x, y, z, r], h = 1..H.
+ *  plan_q       "hd"   joint positions of that plan.
+ *  u_star       "d"    U_* (Sec. III-A Act): first step of the cheapest
+ *                      sampled sequence of the last iteration.
+ *  dist_to_goal [A]    ||ee_p - g_p|| at Sense (published with the plan).
+ *  min_cost     [A]    cheapest total rollout cost of the last iteration. */
+typedef struct {
+    float *mean_plan;
+    float *plan_spheres;
+    float *plan_q;
+    float *u_star;
+    float *dist_to_goal;
+    float *min_cost;
+} mrs_step_out;
+
+/* Sizes of the concatenated arrays, for allocation by the caller. */
+typedef struct {
+    size_t n_arms, hd, hs, d, k, hdd;
+    size_t input_floats;   /* packed device input of mrs_step_device */
+    size_t output_floats;  /* packed device output (see mrs_output_device) */
+    size_t state_bytes;    /* blob of mrs_save_state / mrs_load_state */
+    size_t workspace_bytes;
+} mrs_sizes;
+
+/* Create a context for cfg on `stream` (a cudaStream_t, or NULL for a
+ * stream the library creates).  Validates and copies cfg; allocates pinned
+ * host staging; device memory comes from mrs_bind_workspace or, if that is
+ * never called, is allocated at the first call that needs it.
+ * Errors: MRS_EINVAL (bad cfg or limits exceeded), MRS_ENOMEM, MRS_ECUDA. */
+mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out);
+
+/* Release everything the context allocated (not a bound workspace). */
+void mrs_destroy(mrs_ctx *ctx);
+
+/* One-line reason of the last failure on ctx ("" if none; a static string
+ * if ctx is NULL). */
+const char *mrs_last_error(const mrs_ctx *ctx);
+
+mrs_status mrs_query_sizes(const mrs_ctx *ctx, mrs_sizes *out);
+
+/* Device workspace: bytes needed, and binding caller-owned device memory
+ * (at least that many bytes, 256-byte aligned) that must outlive the
+ * context.  Binding resets the controller to its initial state.
+ * Errors: MRS_EINVAL (null, too small, misaligned). */
+mrs_status mrs_workspace_size(const mrs_ctx *ctx, size_t *bytes);
+mrs_status mrs_bind_workspace(mrs_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* World obstacles (Sec. III-A Sense: the obstacle representation; treated
+ * as static over the horizon unless velocities are given, in which case a
+ * sphere is predicted at constant velocity: centre + vel * (t + h dt), t
+ * being the time since this call).  Host pointers:
+ *  spheres [n][4] centre + radius; vel [n][3] or NULL; aabbs [m][6] centre
+ *  and half extents.  n <= MRS_MAX_WORLD_SPHERES, m <= MRS_MAX_AABBS. */
+mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, int n_spheres,
+                         const float *aabbs, int n_aabbs);
+
+/* Publish (Alg. 1, Publish; Sec. IV-A plan communication): overwrite arm
+ * `arm`'s entry of the plan board that the next mrs_step reads, with an
+ * anticipated plan received from elsewhere.  plan_spheres [H_arm][NS][4]
+ * time-major, plan_q [H_arm][dof] (may be NULL), dist_to_goal >= 0 its
+ * published distance-to-goal, `cycle` its publication stamp.  A negative
+ * dist_to_goal withdraws the entry (the arm is then ignored, Sec. IV-C). */
+mrs_status mrs_share_plans(mrs_ctx *ctx, int arm, const float *plan_spheres, const float *plan_q,
+                           float dist_to_goal, long long cycle);
+
+/* One control cycle for every arm (Algorithm 1: Sense, Shift, `iterations`
+ * x {SampleControls, Rollout, UpdateDistribution}, ToPlan, Publish to the
+ * board for the next cycle, PickBest).  `states` [n_arms] host pointers.
+ * Blocks until the results are in `out` or until the bounded wait gives up
+ * (MRS_ETIMEOUT; the context must then be destroyed). */
+mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out);
+
+/* Same cycle with device-resident inputs, enqueued on the context stream
+ * without waiting.  d_input: input_floats floats, per arm in arm order
+ * [q(d), qd(d), goal_p(3), goal_R(9)].  Results stay in device memory
+ * (mrs_output_device). */
+mrs_status mrs_step_device(mrs_ctx *ctx, const float *d_input);
+
+/* Device pointers of the packed result buffer written by every step:
+ * mean_plan(hd), plan_spheres(hs), plan_q(hd), u_star(d), dist_to_goal(A),
+ * min_cost(A), each starting at a 16-byte boundary; out->* receive device
+ * pointers into it. */
+mrs_status mrs_output_device(mrs_ctx *ctx, mrs_step_out *out);
+
+/* Wait (bounded by timeout_s seconds) for the work enqueued on the context
+ * stream; MRS_ETIMEOUT if it does not finish in time. */
+mrs_status mrs_sync(mrs_ctx *ctx, double timeout_s);
+
+/* Capture the cycle in a CUDA graph (on = 1, the default) or launch the
+ * kernels one by one (on = 0). */
+mrs_status mrs_use_graph(mrs_ctx *ctx, int on);
+
+/* Checkpoint / resume of the controller: state_bytes bytes holding the cycle
+ * index, the world clock, mu, Sigma and the plan board.  Layout (little
+ * endian): u32 magic 0x3152534d, u32 version 1, u32 n_arms, u32 pad,
+ * i64 cycle, f32 world_t, f32 pad, then per arm mu[H][d], Sigma[H][d][d]
+ * (f32), then per arm {i32 valid, i32 pad, i64 stamp, f32 dist, f32 pad,
+ * plan_spheres[H][NS][4], plan_q[H][d]}.  Loading checks sizes and finiteness. */
+mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes);
+mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes);
+
+/* Forward kinematics of arm `arm` for n joint vectors q [n][dof] (host):
+ * ee [n][12] = rotation row-major then position of frame dof; spheres
+ * [n][NS][4] world centres + radii (may be NULL).  Uses the same device code
+ * as the rollout. */
+mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres);
+
+/* Inspection of the last completed cycle (host outputs):
+ * mrs_debug_costs   : C_n of the last iteration, [K_arm].
+ * mrs_debug_spheres : sphere centres of sampled rollouts at (arm, n, h)
+ *                     triples anh[n_req][3] (h 0-based), [n_req][64][4],
+ *                     recomputed by the rollout's own kinematics from the
+ *                     stored joint trajectory.
+ * mrs_debug_alpha   : priority weights [A][A] used by the last cycle. */
+mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs);
+mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out);
+mrs_status mrs_debug_alpha(mrs_ctx *ctx, float *alpha);
+
+/* Debug switch: zero_noise = 1 samples eps = 0 (every rollout is the mean). */
+mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise);
+
+/* Per-kernel timing of the cycle: with on = 1 every following cycle records
+ * CUDA events on the context stream between its kernels (also inside the
+ * captured graph).  mrs_kernel_times writes the durations (ms) of the last
+ * cycle's kernels, in launch order: prep, then per iteration sample,
+ * rollout, costs, update, then toplan (2 + 4 * iterations values); *n gives
+ * the capacity of ms on entry and the count on return.  Waits for the cycle. */
+mrs_status mrs_enable_timing(mrs_ctx *ctx, int on);
+mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
+
+/* Philox4x32-10 self-test (Salmon et al., SC'11): out[n][4] = Philox of
+ * ctr[n][4] under key[2], computed by the device generator the sampling
+ * uses.  Host arrays; allocates a temporary device buffer. */
+mrs_status mrs_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRS_H */

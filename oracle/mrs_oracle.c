@@ -348,7 +348,7 @@ void orc_init_state(const orc_config *cfg, orc_state *st)
  *   C_n = sum_{h=1..H} gamma^{h-1} C_{n,h}. */
 double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const orc_inputs *in,
                    const double *alpha_row, const double *U, double *stage,
-                   double *spheres_out, double *q_out, long long *n_queries)
+                   double *spheres_out, double *q_out, long long *n_queries, double *sens)
 {
     const orc_arm *A = &cfg->arms[arm];
     const int d = A->dof, H = A->H, NS = A->n_spheres;
@@ -362,7 +362,7 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
     }
     const double *g_p = in->goal_p + 3 * arm, *g_R = in->goal_R + 9 * arm;
     long long queries = 0;
-    double total = 0.0;
+    double total = 0.0, slope_total = 0.0;
     for (int h = 0; h < H; ++h) {
         for (int j = 0; j < d; ++j) {
             qd[j] = qd[j] + U[h * d + j] * cfg->dt;
@@ -412,7 +412,7 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
 
         /* coordination: rho_b to every published neighbour plan at the same
          * horizon step, only up to the neighbour's own horizon */
-        double c_dyn = 0.0;
+        double c_dyn = 0.0, slope_dyn = 0.0;
         for (int i = 0; i < cfg->n_arms; ++i) {
             if (i == arm || !st->plan_valid[i]) continue;
             const orc_arm *Ai = &cfg->arms[i];
@@ -429,15 +429,21 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
                 }
             if (rho < 0.0) rho = 0.0;
             c_dyn += alpha_row[i] * orc_ramp(rho, cfg->B);
+            if (rho > 0.0 && rho < cfg->B) slope_dyn += alpha_row[i] / cfg->B;
         }
 
         double c = cfg->w_pose * c_pose + cfg->w_stop * c_stop + cfg->w_joint * c_joint +
                    cfg->w_coll * c_coll + cfg->w_self * c_self + cfg->w_dyn * c_dyn;
         if (stage) stage[h] = c;
         total += pow(cfg->gamma, (double)h) * c;
+        double slope = cfg->w_pose + cfg->w_dyn * slope_dyn;
+        if (d_world < cfg->B_world) slope += cfg->w_coll / cfg->B_world;
+        if (d_self < cfg->B_self) slope += cfg->w_self / cfg->B_self;
+        slope_total += pow(cfg->gamma, (double)h) * slope;
     }
     (void)ohd; (void)ohs;
     if (n_queries) *n_queries = queries;
+    if (sens) *sens = slope_total;
     return total;
 }
 
@@ -506,7 +512,8 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
         double *C = (double *)malloc(sizeof(double) * K);
         double *w = (double *)malloc(sizeof(double) * K);
         long long *nq = (long long *)calloc((size_t)K, sizeof(long long));
-        if (!L || !U || !C || !w || !nq) return 1;
+        double *sn = (double *)calloc((size_t)K, sizeof(double));
+        if (!L || !U || !C || !w || !nq || !sn) return 1;
 
         for (int it = 0; it < cfg->iterations; ++it) {
             for (int h = 0; h < H; ++h) orc_cholesky(d, Sig + h * d * d, 1e-8, L + h * d * d);
@@ -529,7 +536,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
 #endif
             for (int n = 0; n < K; ++n)
                 C[n] = orc_rollout(cfg, a, st, in, alpha + a * A, U + (size_t)n * H * d, NULL,
-                                   NULL, NULL, &nq[n]);
+                                   NULL, NULL, &nq[n], &sn[n]);
 
             /* UpdateDistribution: Eq. 2 weights, Eq. 3 statistics, Eq. 4 EMA */
             orc_weights(K, C, cfg->lambda, w);
@@ -569,6 +576,14 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
                 if (out->n_star) out->n_star[a] = best;
                 if (out->costs)
                     for (int n = 0; n < K; ++n) out->costs[ok + n] = C[n];
+                if (out->sens)
+                    for (int n = 0; n < K; ++n) out->sens[ok + n] = sn[n];
+                if (out->U) {
+                    long long offU = 0;
+                    for (int b = 0; b < a; ++b)
+                        offU += (long long)cfg->arms[b].K * cfg->arms[b].H * cfg->arms[b].dof;
+                    memcpy(out->U + offU, U, sizeof(double) * (size_t)K * H * d);
+                }
                 if (out->n_queries) {
                     long long s = 0;
                     for (int n = 0; n < K; ++n) s += nq[n];
@@ -582,7 +597,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
                     double *stg = (double *)malloc(sizeof(double) * H);
                     if (!traj || !stg) return 1;
                     orc_rollout(cfg, a, st, in, alpha + a * A, U + (size_t)n * H * d, stg, traj,
-                                NULL, NULL);
+                                NULL, NULL, NULL);
                     int nsmax = 0;
                     for (int b = 0; b < A; ++b)
                         if (cfg->arms[b].n_spheres > nsmax) nsmax = cfg->arms[b].n_spheres;
@@ -595,7 +610,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
                 }
             }
         }
-        free(L); free(U); free(C); free(w); free(nq);
+        free(L); free(U); free(C); free(w); free(nq); free(sn);
     }
 
     /* ToPlan: the mean sequence through f and forward kinematics */
@@ -611,7 +626,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
         long long ohd, ohs;
         orc_offsets(cfg, a, &ohd, NULL, &ohs, NULL, NULL);
         orc_rollout(cfg, a, st, in, alpha + a * A, st->mu + ohd, NULL, new_spheres + ohs,
-                    new_q + ohd, NULL);
+                    new_q + ohd, NULL, NULL);
     }
 
     /* outputs of the cycle */

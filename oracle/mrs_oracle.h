@@ -90,6 +90,10 @@ typedef struct {
     double *costs;         /* sum_a K_a  C_n of the last iteration (or NULL) */
     double *alpha;         /* [A][A] priority weights used (or NULL)        */
     long long *n_queries;  /* [A] rho_b sphere-pair evaluations (or NULL)    */
+    double *sens;          /* sum_a K_a  dC_n/d(distance) of the last iteration
+                              (sum of the active ramp slopes; or NULL)      */
+    double *U;             /* sum_a K_a*H_a*d_a sampled U [n][h][j] of the last
+                              iteration (or NULL)                            */
     /* optional sphere dumps of sampled rollouts of the last iteration */
     int n_dump;
     const int *dump_anh;   /* [n_dump][3] arm, n, h (0-based h)              */
@@ -134,11 +138,14 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in,
               orc_outputs *out);
 /* Rollout of one control sequence U [H][d] from (q0, qd0): stage costs
  * [H], sphere trajectory [H][NS][4] and joint trajectory [H][d] (each may
- * be NULL); n_queries (may be NULL) receives the rho_b pair count.  Used by the
+ * be NULL); n_queries (may be NULL) receives the rho_b pair count and sens
+ * (may be NULL) the sensitivity of the total cost to a common error in all
+ * clearance distances: sum_h gamma^h (sum of the slopes of the active ramps,
+ * plus w_pose for the position error).   Used by the
  * zero-noise invariant and by ToPlan. */
 double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const orc_inputs *in,
                    const double *alpha_row, const double *U, double *stage,
-                   double *spheres_out, double *q_out, long long *n_queries);
+                   double *spheres_out, double *q_out, long long *n_queries, double *sens);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

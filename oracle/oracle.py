@@ -55,7 +55,8 @@ class OrcInputs(C.Structure):
 class OrcOutputs(C.Structure):
     _fields_ = [("mean_plan", _dp), ("Sigma", _dp), ("plan_spheres", _dp), ("plan_q", _dp),
                 ("u_star", _dp), ("dist_to_goal", _dp), ("min_cost", _dp), ("n_star", _ip),
-                ("costs", _dp), ("alpha", _dp), ("n_queries", _llp), ("n_dump", C.c_int),
+                ("costs", _dp), ("alpha", _dp), ("n_queries", _llp), ("sens", _dp),
+                ("U", _dp), ("n_dump", C.c_int),
                 ("dump_anh", _ip), ("dump_spheres", _dp), ("dump_stage", _dp)]
 
 
@@ -108,7 +109,7 @@ def lib():
                                     C.POINTER(OrcInputs), C.POINTER(OrcOutputs)]
             L.orc_rollout.restype = C.c_double
             L.orc_rollout.argtypes = [C.POINTER(OrcConfig), C.c_int, C.POINTER(OrcState),
-                                      C.POINTER(OrcInputs), _dp, _dp, _dp, _dp, _dp, _llp]
+                                      C.POINTER(OrcInputs), _dp, _dp, _dp, _dp, _dp, _llp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -230,7 +231,9 @@ class Oracle:
             s.sphere_xyzr = pxyzr
             for k in range(7):
                 s.base_pose[k] = float(a.base_pose[k])
-        p = sc.params
+        # the CUDA path reads float32 parameters: use exactly those values
+        p = {k: (v if k in ("iterations", "seed") else float(np.float32(v)))
+             for k, v in sc.params.items()}
         self.cfg = OrcConfig(A, self.arms, p["dt"], p["lam"], p["gamma"], p["alpha_mu"],
                              p["alpha_sigma"], p["sigma_init"], p["w_pose"], p["w_rot"],
                              p["w_stop"], p["w_joint"], p["w_coll"], p["w_self"], p["w_dyn"],
@@ -312,7 +315,7 @@ class Oracle:
         return int(lib().orc_query_count(C.byref(self.cfg), arm))
 
     # -- one control cycle --------------------------------------------------
-    def cycle(self, q, qd, goal_p, goal_R, dump=None, want_costs=True):
+    def cycle(self, q, qd, goal_p, goal_R, dump=None, want_costs=True, want_U=False):
         sc = self.sc
         A = sc.n_arms
         inp, keep = self.inputs(q, qd, goal_p, goal_R)
@@ -322,14 +325,17 @@ class Oracle:
                    u_star=np.zeros(self.off_d[-1]), dist_to_goal=np.zeros(A),
                    min_cost=np.zeros(A), n_star=np.zeros(A, np.int32),
                    costs=np.zeros(self.off_k[-1]) if want_costs else None,
-                   alpha=np.zeros(A * A), n_queries=np.zeros(A, np.int64))
+                   alpha=np.zeros(A * A), n_queries=np.zeros(A, np.int64),
+                   sens=np.zeros(self.off_k[-1]) if want_costs else None,
+                   U=np.zeros(sum(a.K * a.H * a.dof for a in sc.arms)) if want_U else None)
         dump = np.zeros((0, 3), np.int32) if dump is None else np.ascontiguousarray(dump, np.int32)
         out["dump_spheres"] = np.zeros((len(dump), nsmax, 4))
         out["dump_stage"] = np.zeros(len(dump))
         o = OrcOutputs(_ptr(out["mean_plan"]), _ptr(out["Sigma"]), _ptr(out["plan_spheres"]),
                        _ptr(out["plan_q"]), _ptr(out["u_star"]), _ptr(out["dist_to_goal"]),
                        _ptr(out["min_cost"]), _ptr(out["n_star"], _ip), _ptr(out["costs"]),
-                       _ptr(out["alpha"]), _ptr(out["n_queries"], _llp), len(dump),
+                       _ptr(out["alpha"]), _ptr(out["n_queries"], _llp), _ptr(out["sens"]),
+                       _ptr(out["U"]), len(dump),
                        _ptr(dump, _ip), _ptr(out["dump_spheres"]), _ptr(out["dump_stage"]))
         st = self._state_struct()
         rc = lib().orc_cycle(C.byref(self.cfg), C.byref(st), C.byref(inp), C.byref(o))
@@ -350,9 +356,11 @@ class Oracle:
         sph = np.zeros((a.H, a.n_spheres, 4))
         qo = np.zeros((a.H, a.dof))
         nq = C.c_longlong(0)
+        sens = C.c_double(0)
         st = self._state_struct()
         tot = lib().orc_rollout(C.byref(self.cfg), arm, C.byref(st), C.byref(inp), pal, pU,
-                                _ptr(stage), _ptr(sph), _ptr(qo), C.byref(nq))
+                                _ptr(stage), _ptr(sph), _ptr(qo), C.byref(nq), C.byref(sens))
+        self.last_rollout_sens = sens.value
         return tot, stage, sph, qo
 
     def split(self, flat, kind: str, arm: int):
@@ -368,4 +376,7 @@ class Oracle:
             return flat[self.off_d[arm]:self.off_d[arm + 1]]
         if kind == "k":
             return flat[self.off_k[arm]:self.off_k[arm + 1]]
+        if kind == "U":
+            o = sum(b.K * b.H * b.dof for b in self.sc.arms[:arm])
+            return flat[o:o + a.K * a.H * a.dof].reshape(a.K, a.H, a.dof)
         raise KeyError(kind)

@@ -1,0 +1,37 @@
+// kernels.cuh -- launch wrappers of the control-cycle kernels (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mrs_device.cuh"
+
+namespace mrs {
+
+struct LaunchPlan {
+    int n_arms;
+    int n_sample_tiles, n_rollout_tiles, n_cost_tiles, n_update_tiles;
+    const SampleTile *sample_tiles;
+    const RolloutTile *rollout_tiles;
+    const CostTile *cost_tiles;
+    const UpdateTile *update_tiles;
+    size_t smem_prep, smem_sample, smem_rollout, smem_toplan;
+    int *done_counter;  // last-block-done counter of k_toplan
+};
+
+// Everything one control cycle enqueues on `s` (Algorithm 1 for all arms).
+// With `events` non-null, events[0] is recorded before the first kernel and
+// events[i + 1] after kernel i (2 + 4 * iterations events); `capturing` makes
+// them external event nodes of the graph being captured.
+cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cudaStream_t s,
+                          cudaEvent_t *events = nullptr, bool capturing = false);
+cudaError_t configure_kernels(const LaunchPlan &L);
+// Fill the derived per-arm constants and reset the controller state.
+cudaError_t enqueue_init(const Params &P, const Dev &D, int n_arms, int total_hdd, int total_hd,
+                         cudaStream_t s);
+cudaError_t enqueue_fk(const Dev &D, int arm, int n, const float *q, float *ee, float *spheres,
+                       cudaStream_t s);
+cudaError_t enqueue_debug_spheres(const Dev &D, int n_req, const int *anh, float *out,
+                                  cudaStream_t s);
+cudaError_t enqueue_philox(int n, const uint4 *ctr, uint2 key, uint4 *out, cudaStream_t s);
+
+}  // namespace mrs

@@ -1,0 +1,921 @@
+// mrs_capi.cu -- the C ABI declared in include/mrs.h: context, validation,
+// workspace layout, work lists, CUDA-graph capture, bounded waits, state
+// checkpointing.  All arithmetic of the method runs in kernels.cu.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.cuh"
+#include "mrs.h"
+
+using namespace mrs;
+
+struct mrs_ctx {
+    Params P{};
+    Dev D{};
+    LaunchPlan L{};
+    int A = 0;
+    std::vector<ArmDev> arms;
+    mrs_sizes sz{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    bool bound = false;
+    float *pin_in = nullptr, *pin_out = nullptr;
+    int *pin_err = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    std::string err;
+    // workspace offsets (bytes)
+    struct Layout {
+        size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
+            board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
+            e_now, n_star, out, cycle, world_t, err, done_counter, sample_tiles, rollout_tiles,
+            cost_tiles, update_tiles, total;
+    } lay{};
+    std::vector<SampleTile> sample_tiles;
+    std::vector<RolloutTile> rollout_tiles;
+    std::vector<CostTile> cost_tiles;
+    std::vector<UpdateTile> update_tiles;
+};
+
+static const char *g_noctx = "null context";
+
+static mrs_status fail(mrs_ctx *c, mrs_status s, const std::string &m)
+{
+    if (c) c->err = m;
+    return s;
+}
+
+static mrs_status cuda_fail(mrs_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, MRS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                        \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+static bool finite_arr(const float *p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static void build_layout(mrs_ctx *c)
+{
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        o = align_up(o, 256);
+        size_t at = o;
+        o += bytes;
+        return at;
+    };
+    const int A = c->A;
+    size_t khd = 0, kh = 0;
+    for (auto &a : c->arms) {
+        khd += (size_t)a.K * a.H * a.dof;
+        kh += (size_t)a.K * a.H;
+    }
+    auto &L = c->lay;
+    L.arms = take(sizeof(ArmDev) * A);
+    L.input = take(sizeof(float) * c->sz.input_floats);
+    L.world = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
+    L.world_vel = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
+    L.aabb = take(sizeof(float4) * 2 * MRS_MAX_AABBS);
+    L.world_n = take(sizeof(int) * 2);
+    L.mu = take(sizeof(float) * c->sz.hd);
+    L.Sigma = take(sizeof(float) * c->sz.hdd);
+    L.L = take(sizeof(float) * c->sz.hdd);
+    L.board_sph = take(sizeof(float) * c->sz.hs);
+    L.board_q = take(sizeof(float) * c->sz.hd);
+    L.board_valid = take(sizeof(int) * A);
+    L.board_stamp = take(sizeof(long long) * A);
+    L.board_dist = take(sizeof(float) * A);
+    L.traj = take(sizeof(float) * khd);
+    L.eps = take(sizeof(float) * khd);
+    L.stage_lim = take(sizeof(float) * kh);
+    L.stage = take(sizeof(float) * kh);
+    L.costs = take(sizeof(float) * c->sz.k);
+    L.alpha = take(sizeof(float) * A * A);
+    L.e_now = take(sizeof(float) * A);
+    L.n_star = take(sizeof(int) * A);
+    L.out = take(sizeof(float) * c->sz.output_floats);
+    L.cycle = take(sizeof(long long));
+    L.world_t = take(sizeof(float));
+    L.err = take(sizeof(int));
+    L.done_counter = take(sizeof(int));
+    L.sample_tiles = take(sizeof(SampleTile) * c->sample_tiles.size());
+    L.rollout_tiles = take(sizeof(RolloutTile) * c->rollout_tiles.size());
+    L.cost_tiles = take(sizeof(CostTile) * c->cost_tiles.size());
+    L.update_tiles = take(sizeof(UpdateTile) * c->update_tiles.size());
+    L.total = align_up(o, 256);
+    c->sz.workspace_bytes = L.total;
+}
+
+static void build_work_lists(mrs_ctx *c)
+{
+    c->sample_tiles.clear();
+    c->rollout_tiles.clear();
+    c->cost_tiles.clear();
+    c->update_tiles.clear();
+    for (int a = 0; a < c->A; ++a) {
+        const ArmDev &A = c->arms[a];
+        for (int n0 = 0; n0 < A.K; n0 += 32) c->sample_tiles.push_back({a, n0});
+        for (int n0 = 0; n0 < A.K; n0 += 256) c->cost_tiles.push_back({a, n0});
+        for (int h = 0; h < A.H; ++h) c->update_tiles.push_back({a, h});
+    }
+    // rollout tiles step-major so that concurrently resident blocks share steps
+    int Hmax = 0;
+    for (auto &A : c->arms) Hmax = std::max(Hmax, A.H);
+    for (int h = 0; h < Hmax; ++h)
+        for (int a = 0; a < c->A; ++a) {
+            const ArmDev &A = c->arms[a];
+            if (h >= A.H) continue;
+            for (int n0 = 0; n0 < A.K; n0 += kTileSamples) c->rollout_tiles.push_back({a, h, n0, 0});
+        }
+}
+
+static void fill_dev(mrs_ctx *c, char *base)
+{
+    auto &L = c->lay;
+    Dev &D = c->D;
+    D.arms = (ArmDev *)(base + L.arms);
+    D.input = (float *)(base + L.input);
+    D.world = (float4 *)(base + L.world);
+    D.world_vel = (float4 *)(base + L.world_vel);
+    D.aabb = (float4 *)(base + L.aabb);
+    D.world_n = (int *)(base + L.world_n);
+    D.mu = (float *)(base + L.mu);
+    D.Sigma = (float *)(base + L.Sigma);
+    D.L = (float *)(base + L.L);
+    D.board_sph = (float4 *)(base + L.board_sph);
+    D.board_q = (float *)(base + L.board_q);
+    D.board_valid = (int *)(base + L.board_valid);
+    D.board_stamp = (long long *)(base + L.board_stamp);
+    D.board_dist = (float *)(base + L.board_dist);
+    D.next_sph = nullptr;
+    D.next_q = nullptr;
+    D.traj = (float *)(base + L.traj);
+    D.eps = (float *)(base + L.eps);
+    D.stage_lim = (float *)(base + L.stage_lim);
+    D.stage = (float *)(base + L.stage);
+    D.costs = (float *)(base + L.costs);
+    D.alpha = (float *)(base + L.alpha);
+    D.e_now = (float *)(base + L.e_now);
+    D.n_star = (int *)(base + L.n_star);
+    D.out = (float *)(base + L.out);
+    D.cycle = (long long *)(base + L.cycle);
+    D.world_t = (float *)(base + L.world_t);
+    D.err = (int *)(base + L.err);
+    c->L.done_counter = (int *)(base + L.done_counter);
+    c->L.sample_tiles = (const SampleTile *)(base + L.sample_tiles);
+    c->L.rollout_tiles = (const RolloutTile *)(base + L.rollout_tiles);
+    c->L.cost_tiles = (const CostTile *)(base + L.cost_tiles);
+    c->L.update_tiles = (const UpdateTile *)(base + L.update_tiles);
+}
+
+static void out_offsets(mrs_ctx *c)
+{
+    size_t o = 0;
+    auto take = [&](size_t n) {
+        o = align_up(o, 4);
+        size_t at = o;
+        o += n;
+        return (int)at;
+    };
+    c->D.out_mean = take(c->sz.hd);
+    c->D.out_sph = take(c->sz.hs);
+    c->D.out_q = take(c->sz.hd);
+    c->D.out_u = take(c->sz.d);
+    c->D.out_dist = take(c->A);
+    c->D.out_min = take(c->A);
+    c->sz.output_floats = align_up(o, 4);
+}
+
+static mrs_status validate(const mrs_config *cfg, std::string &why)
+{
+    if (!cfg || !cfg->arms) return why = "null config or arms", MRS_EINVAL;
+    if (cfg->n_arms < 1 || cfg->n_arms > MRS_MAX_ARMS) return why = "n_arms out of range", MRS_EINVAL;
+    const float sc[] = {cfg->dt, cfg->lambda, cfg->gamma, cfg->alpha_mu, cfg->alpha_sigma,
+                        cfg->sigma_init, cfg->w_pose, cfg->w_rot, cfg->w_stop, cfg->w_joint,
+                        cfg->w_coll, cfg->w_self, cfg->w_dyn, cfg->B, cfg->B_world, cfg->B_self,
+                        cfg->tau, cfg->q_margin};
+    if (!finite_arr(sc, sizeof(sc) / sizeof(float))) return why = "non-finite parameter", MRS_EINVAL;
+    if (cfg->dt <= 0 || cfg->lambda <= 0 || cfg->sigma_init <= 0 || cfg->B <= 0 ||
+        cfg->B_world <= 0 || cfg->B_self <= 0 || cfg->gamma <= 0 || cfg->gamma > 1)
+        return why = "dt, lambda, sigma_init, B, B_world, B_self must be > 0 and gamma in (0,1]",
+               MRS_EINVAL;
+    if (cfg->alpha_mu < 0 || cfg->alpha_mu > 1 || cfg->alpha_sigma < 0 || cfg->alpha_sigma > 1)
+        return why = "EMA steps must be in [0,1]", MRS_EINVAL;
+    if (cfg->w_pose < 0 || cfg->w_rot < 0 || cfg->w_stop < 0 || cfg->w_joint < 0 ||
+        cfg->w_coll < 0 || cfg->w_self < 0 || cfg->w_dyn < 0 || cfg->tau < 0)
+        return why = "cost weights and tau must be >= 0", MRS_EINVAL;
+    if (cfg->iterations < 1 || cfg->iterations > 64) return why = "iterations out of range", MRS_EINVAL;
+    if (cfg->mode != 0) return why = "only exact mode (0) is built", MRS_EUNSUPPORTED;
+    for (int a = 0; a < cfg->n_arms; ++a) {
+        const mrs_arm_desc &d = cfg->arms[a];
+        if (d.dof < 1 || d.dof > MRS_MAX_DOF) return why = "dof out of range", MRS_EINVAL;
+        if (d.n_spheres < 1 || d.n_spheres > MRS_MAX_SPHERES)
+            return why = "n_spheres out of range", MRS_EINVAL;
+        if (d.K < 1 || d.K > MRS_MAX_SAMPLES) return why = "K out of range", MRS_EINVAL;
+        if (d.H < 1 || d.H > MRS_MAX_HORIZON) return why = "H out of range", MRS_EINVAL;
+        if (!d.dh || !d.q_lo || !d.q_hi || !d.qd_max || !d.sphere_body || !d.sphere_xyzr)
+            return why = "null arm array", MRS_EINVAL;
+        if (!finite_arr(d.dh, 4 * d.dof) || !finite_arr(d.q_lo, d.dof) ||
+            !finite_arr(d.q_hi, d.dof) || !finite_arr(d.qd_max, d.dof) ||
+            !finite_arr(d.sphere_xyzr, 4 * d.n_spheres) || !finite_arr(d.base_pose, 7))
+            return why = "non-finite arm description", MRS_EINVAL;
+        for (int s = 0; s < d.n_spheres; ++s) {
+            if (d.sphere_body[s] < 0 || d.sphere_body[s] > d.dof + 1)
+                return why = "sphere_body out of range", MRS_EINVAL;
+            if (s > 0 && d.sphere_body[s] < d.sphere_body[s - 1])
+                return why = "sphere_body must be non-decreasing", MRS_EINVAL;
+            if (d.sphere_xyzr[4 * s + 3] < 0) return why = "negative sphere radius", MRS_EINVAL;
+        }
+        const float *qp = d.base_pose + 3;
+        if (qp[0] * qp[0] + qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3] < 1e-12f)
+            return why = "zero base quaternion", MRS_EINVAL;
+    }
+    return MRS_OK;
+}
+
+extern "C" {
+
+mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
+{
+    if (!out) return MRS_EINVAL;
+    *out = nullptr;
+    std::string why;
+    mrs_status st = validate(cfg, why);
+    if (st != MRS_OK) return st;
+    mrs_ctx *ctx = new (std::nothrow) mrs_ctx();
+    if (!ctx) return MRS_ENOMEM;
+    ctx->A = cfg->n_arms;
+    Params &P = ctx->P;
+    P.n_arms = cfg->n_arms;
+    P.iterations = cfg->iterations;
+    P.mode = cfg->mode;
+    P.zero_noise = 0;
+    P.dt = cfg->dt; P.lambda = cfg->lambda; P.gamma = cfg->gamma;
+    P.alpha_mu = cfg->alpha_mu; P.alpha_sigma = cfg->alpha_sigma; P.sigma_init = cfg->sigma_init;
+    P.w_pose = cfg->w_pose; P.w_rot = cfg->w_rot; P.w_stop = cfg->w_stop; P.w_joint = cfg->w_joint;
+    P.w_coll = cfg->w_coll; P.w_self = cfg->w_self; P.w_dyn = cfg->w_dyn;
+    P.B = cfg->B; P.B_world = cfg->B_world; P.B_self = cfg->B_self; P.tau = cfg->tau;
+    P.q_margin = cfg->q_margin; P.seed = cfg->seed;
+
+    size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
+    long long khd = 0, kh = 0;
+    int max_ns = 0;
+    ctx->arms.resize(ctx->A);
+    for (int a = 0; a < ctx->A; ++a) {
+        const mrs_arm_desc &d = cfg->arms[a];
+        ArmDev &A = ctx->arms[a];
+        std::memset(&A, 0, sizeof(A));
+        A.dof = d.dof; A.ns = d.n_spheres; A.K = d.K; A.H = d.H;
+        A.off_hd = (int)hd; A.off_hdd = (int)hdd; A.off_hs = (int)hs; A.off_d = (int)dsum;
+        A.off_k = (int)ksum; A.off_in = (int)in;
+        A.spg = (d.n_spheres + kGroups - 1) / kGroups;
+        A.off_khd = khd; A.off_kh = kh;
+        for (int j = 0; j < d.dof; ++j) {
+            A.dh[j] = make_float4(d.dh[4 * j], d.dh[4 * j + 1], d.dh[4 * j + 2], d.dh[4 * j + 3]);
+            A.q_lo[j] = d.q_lo[j]; A.q_hi[j] = d.q_hi[j]; A.qd_max[j] = d.qd_max[j];
+        }
+        for (int k = 0; k < 7; ++k) A.base_pose[k] = d.base_pose[k];
+        for (int s = 0; s < d.n_spheres; ++s) {
+            A.sph[s] = make_float4(d.sphere_xyzr[4 * s], d.sphere_xyzr[4 * s + 1],
+                                   d.sphere_xyzr[4 * s + 2], d.sphere_xyzr[4 * s + 3]);
+            A.body[s] = d.sphere_body[s];
+            A.frame[s] = std::min(d.sphere_body[s], d.dof);
+        }
+        for (int s = 0; s < d.n_spheres; ++s) {
+            int k = s + 1;
+            while (k < d.n_spheres && d.sphere_body[k] < d.sphere_body[s] + 3) ++k;
+            A.self_start[s] = k;
+        }
+        hd += (size_t)d.H * d.dof;
+        hdd += (size_t)d.H * d.dof * d.dof;
+        hs += (size_t)d.H * d.n_spheres * 4;
+        dsum += d.dof;
+        ksum += d.K;
+        in += 2 * d.dof + 12;
+        khd += (long long)d.K * d.H * d.dof;
+        kh += (long long)d.K * d.H;
+        max_ns = std::max(max_ns, d.n_spheres);
+    }
+    P.max_ns = max_ns;
+    ctx->sz.n_arms = ctx->A;
+    ctx->sz.hd = hd; ctx->sz.hdd = hdd; ctx->sz.hs = hs; ctx->sz.d = dsum; ctx->sz.k = ksum;
+    ctx->sz.input_floats = in;
+    ctx->sz.state_bytes = 32 + sizeof(float) * (hd + hdd) +
+                          (size_t)ctx->A * 24 + sizeof(float) * (hs + hd);
+    out_offsets(ctx);
+    build_work_lists(ctx);
+    build_layout(ctx);
+
+    // launch plan
+    LaunchPlan &L = ctx->L;
+    L.n_arms = ctx->A;
+    L.n_sample_tiles = (int)ctx->sample_tiles.size();
+    L.n_rollout_tiles = (int)ctx->rollout_tiles.size();
+    L.n_cost_tiles = (int)ctx->cost_tiles.size();
+    L.n_update_tiles = (int)ctx->update_tiles.size();
+    size_t sp = 0, ss = 0, st2 = 0;
+    for (auto &A : ctx->arms) {
+        sp = std::max(sp, sizeof(float) * (size_t)A.H * (A.dof * A.dof + A.dof));
+        ss = std::max(ss, sizeof(float) * (size_t)A.H * (A.dof * A.dof + 2 * A.dof * 32));
+        st2 = std::max(st2, sizeof(float) * (size_t)A.H * A.dof);
+    }
+    L.smem_prep = sp;
+    L.smem_sample = ss;
+    L.smem_toplan = st2;
+    L.smem_rollout = sizeof(float4) * MRS_MAX_WORLD_SPHERES + sizeof(float4) * 2 * MRS_MAX_AABBS +
+                     sizeof(float4) * kMaxSpheres + sizeof(float4) * (size_t)max_ns * ctx->A +
+                     sizeof(float) * kMaxSpheres * 3 * 32 + sizeof(int) * kMaxSpheres * 2 +
+                     sizeof(int) * (MRS_MAX_ARMS + 1) + sizeof(float) * MRS_MAX_ARMS +
+                     sizeof(int) * (2 + MRS_MAX_ARMS) * 32;
+
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return MRS_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaHostAlloc((void **)&ctx->pin_in, sizeof(float) * in, cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaHostAlloc((void **)&ctx->pin_out, sizeof(float) * ctx->sz.output_floats,
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&ctx->pin_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) != cudaSuccess) {
+        mrs_destroy(ctx);
+        return MRS_ENOMEM;
+    }
+    if (configure_kernels(L) != cudaSuccess) {
+        mrs_destroy(ctx);
+        return MRS_ECUDA;
+    }
+    *out = ctx;
+    return MRS_OK;
+}
+
+void mrs_destroy(mrs_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    if (ctx->pin_in) cudaFreeHost(ctx->pin_in);
+    if (ctx->pin_out) cudaFreeHost(ctx->pin_out);
+    if (ctx->pin_err) cudaFreeHost(ctx->pin_err);
+    if (ctx->done) cudaEventDestroy(ctx->done);
+    for (auto e : ctx->events) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *mrs_last_error(const mrs_ctx *ctx) { return ctx ? ctx->err.c_str() : g_noctx; }
+
+mrs_status mrs_query_sizes(const mrs_ctx *ctx, mrs_sizes *out)
+{
+    if (!ctx || !out) return MRS_EINVAL;
+    *out = ctx->sz;
+    return MRS_OK;
+}
+
+mrs_status mrs_workspace_size(const mrs_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return MRS_EINVAL;
+    *bytes = ctx->sz.workspace_bytes;
+    return MRS_OK;
+}
+
+static void invalidate_graph(mrs_ctx *ctx)
+{
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+}
+
+static mrs_status bind(mrs_ctx *ctx, void *dev, size_t bytes)
+{
+    invalidate_graph(ctx);
+    ctx->ws = dev;
+    ctx->ws_bytes = bytes;
+    fill_dev(ctx, (char *)dev);
+    const auto &L = ctx->lay;
+    char *base = (char *)dev;
+    CK(cudaMemcpyAsync(base + L.arms, ctx->arms.data(), sizeof(ArmDev) * ctx->A,
+                       cudaMemcpyHostToDevice, ctx->stream), "upload arms");
+    CK(cudaMemcpyAsync(base + L.sample_tiles, ctx->sample_tiles.data(),
+                       sizeof(SampleTile) * ctx->sample_tiles.size(), cudaMemcpyHostToDevice,
+                       ctx->stream), "upload tiles");
+    CK(cudaMemcpyAsync(base + L.rollout_tiles, ctx->rollout_tiles.data(),
+                       sizeof(RolloutTile) * ctx->rollout_tiles.size(), cudaMemcpyHostToDevice,
+                       ctx->stream), "upload tiles");
+    CK(cudaMemcpyAsync(base + L.cost_tiles, ctx->cost_tiles.data(),
+                       sizeof(CostTile) * ctx->cost_tiles.size(), cudaMemcpyHostToDevice,
+                       ctx->stream), "upload tiles");
+    CK(cudaMemcpyAsync(base + L.update_tiles, ctx->update_tiles.data(),
+                       sizeof(UpdateTile) * ctx->update_tiles.size(), cudaMemcpyHostToDevice,
+                       ctx->stream), "upload tiles");
+    CK(cudaMemsetAsync(base + L.done_counter, 0, sizeof(int), ctx->stream), "memset");
+    CK(cudaMemsetAsync(base + L.input, 0, sizeof(float) * ctx->sz.input_floats, ctx->stream),
+       "memset");
+    CK(cudaMemsetAsync(base + L.out, 0, sizeof(float) * ctx->sz.output_floats, ctx->stream),
+       "memset");
+    CK(cudaMemsetAsync(base + L.world_vel, 0, sizeof(float4) * MRS_MAX_WORLD_SPHERES, ctx->stream),
+       "memset");
+    CK(enqueue_init(ctx->P, ctx->D, ctx->A, (int)ctx->sz.hdd, (int)ctx->sz.hd, ctx->stream),
+       "init kernels");
+    CK(cudaStreamSynchronize(ctx->stream), "sync after init");
+    ctx->bound = true;
+    return MRS_OK;
+}
+
+mrs_status mrs_bind_workspace(mrs_ctx *ctx, void *dev_ptr, size_t bytes)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (!dev_ptr || bytes < ctx->sz.workspace_bytes || ((uintptr_t)dev_ptr & 255))
+        return fail(ctx, MRS_EINVAL, "workspace null, too small or not 256-byte aligned");
+    if (ctx->own_ws && ctx->ws) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->ws);
+        ctx->own_ws = false;
+    }
+    return bind(ctx, dev_ptr, bytes);
+}
+
+static mrs_status ensure_bound(mrs_ctx *ctx)
+{
+    if (ctx->bound) return MRS_OK;
+    void *p = nullptr;
+    CK(cudaMalloc(&p, ctx->sz.workspace_bytes), "workspace allocation");
+    ctx->own_ws = true;
+    return bind(ctx, p, ctx->sz.workspace_bytes);
+}
+
+mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, int n_spheres,
+                         const float *aabbs, int n_aabbs)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (n_spheres < 0 || n_spheres > MRS_MAX_WORLD_SPHERES || n_aabbs < 0 ||
+        n_aabbs > MRS_MAX_AABBS || (n_spheres && !spheres) || (n_aabbs && !aabbs))
+        return fail(ctx, MRS_EINVAL, "world sizes out of range or null arrays");
+    if ((n_spheres && !finite_arr(spheres, 4 * (size_t)n_spheres)) ||
+        (vel && n_spheres && !finite_arr(vel, 3 * (size_t)n_spheres)) ||
+        (n_aabbs && !finite_arr(aabbs, 6 * (size_t)n_aabbs)))
+        return fail(ctx, MRS_EINVAL, "non-finite world");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    std::vector<float4> w(n_spheres), v(n_spheres), b(2 * n_aabbs);
+    for (int i = 0; i < n_spheres; ++i) {
+        w[i] = make_float4(spheres[4 * i], spheres[4 * i + 1], spheres[4 * i + 2], spheres[4 * i + 3]);
+        v[i] = vel ? make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.f)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int i = 0; i < n_aabbs; ++i) {
+        b[2 * i] = make_float4(aabbs[6 * i], aabbs[6 * i + 1], aabbs[6 * i + 2], 0.f);
+        b[2 * i + 1] = make_float4(aabbs[6 * i + 3], aabbs[6 * i + 4], aabbs[6 * i + 5], 0.f);
+    }
+    int n[2] = {n_spheres, n_aabbs};
+    float zero = 0.f;
+    if (n_spheres) {
+        CK(cudaMemcpyAsync(ctx->D.world, w.data(), sizeof(float4) * n_spheres,
+                           cudaMemcpyHostToDevice, ctx->stream), "set_world");
+        CK(cudaMemcpyAsync(ctx->D.world_vel, v.data(), sizeof(float4) * n_spheres,
+                           cudaMemcpyHostToDevice, ctx->stream), "set_world");
+    }
+    if (n_aabbs)
+        CK(cudaMemcpyAsync(ctx->D.aabb, b.data(), sizeof(float4) * 2 * n_aabbs,
+                           cudaMemcpyHostToDevice, ctx->stream), "set_world");
+    CK(cudaMemcpyAsync(ctx->D.world_n, n, sizeof(n), cudaMemcpyHostToDevice, ctx->stream),
+       "set_world");
+    CK(cudaMemcpyAsync(ctx->D.world_t, &zero, sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+       "set_world");
+    CK(cudaStreamSynchronize(ctx->stream), "set_world sync");
+    return MRS_OK;
+}
+
+mrs_status mrs_share_plans(mrs_ctx *ctx, int arm, const float *plan_spheres, const float *plan_q,
+                           float dist_to_goal, long long cycle)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "arm out of range");
+    if (!std::isfinite(dist_to_goal)) return fail(ctx, MRS_EINVAL, "non-finite distance");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const ArmDev &A = ctx->arms[arm];
+    int valid = dist_to_goal >= 0.f ? 1 : 0;
+    if (valid) {
+        if (!plan_spheres) return fail(ctx, MRS_EINVAL, "null plan");
+        const size_t nsph = (size_t)A.H * A.ns * 4;
+        if (!finite_arr(plan_spheres, nsph) || (plan_q && !finite_arr(plan_q, (size_t)A.H * A.dof)))
+            return fail(ctx, MRS_EINVAL, "non-finite plan");
+        CK(cudaMemcpyAsync(ctx->D.board_sph + A.off_hs / 4, plan_spheres, sizeof(float) * nsph,
+                           cudaMemcpyHostToDevice, ctx->stream), "share_plans");
+        if (plan_q)
+            CK(cudaMemcpyAsync(ctx->D.board_q + A.off_hd, plan_q, sizeof(float) * A.H * A.dof,
+                               cudaMemcpyHostToDevice, ctx->stream), "share_plans");
+        CK(cudaMemcpyAsync(ctx->D.board_dist + arm, &dist_to_goal, sizeof(float),
+                           cudaMemcpyHostToDevice, ctx->stream), "share_plans");
+        CK(cudaMemcpyAsync(ctx->D.board_stamp + arm, &cycle, sizeof(long long),
+                           cudaMemcpyHostToDevice, ctx->stream), "share_plans");
+    }
+    CK(cudaMemcpyAsync(ctx->D.board_valid + arm, &valid, sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->stream), "share_plans");
+    CK(cudaStreamSynchronize(ctx->stream), "share_plans sync");
+    return MRS_OK;
+}
+
+static mrs_status launch_cycle(mrs_ctx *ctx)
+{
+    cudaEvent_t *ev = ctx->timing ? ctx->events.data() : nullptr;
+    if (!ctx->use_graph) {
+        CK(enqueue_cycle(ctx->P, ctx->D, ctx->L, ctx->stream, ev), "cycle launch");
+        return MRS_OK;
+    }
+    if (!ctx->gexec) {
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+        cudaError_t e = enqueue_cycle(ctx->P, ctx->D, ctx->L, ctx->stream, ev, true);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "graph end capture");
+        ctx->graph = g;
+        CK(cudaGraphInstantiate(&ctx->gexec, g, 0), "graph instantiate");
+    }
+    CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
+    return MRS_OK;
+}
+
+static mrs_status wait_bounded(mrs_ctx *ctx, double timeout_s)
+{
+    CK(cudaEventRecord(ctx->done, ctx->stream), "event record");
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ctx->done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream wait");
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(ctx, MRS_ETIMEOUT, "bounded wait for the cycle gave up");
+        std::this_thread::yield();
+    }
+    return MRS_OK;
+}
+
+mrs_status mrs_step_device(mrs_ctx *ctx, const float *d_input)
+{
+    if (!ctx || !d_input) return fail(ctx, MRS_EINVAL, "null argument");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    CK(cudaMemcpyAsync(ctx->D.input, d_input, sizeof(float) * ctx->sz.input_floats,
+                       cudaMemcpyDeviceToDevice, ctx->stream), "input copy");
+    return launch_cycle(ctx);
+}
+
+mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out)
+{
+    if (!ctx || !states) return fail(ctx, MRS_EINVAL, "null argument");
+    float *p = ctx->pin_in;
+    for (int a = 0; a < ctx->A; ++a) {
+        const ArmDev &A = ctx->arms[a];
+        const mrs_arm_state &s = states[a];
+        if (!s.q || !s.qd || !s.goal_p || !s.goal_R) return fail(ctx, MRS_EINVAL, "null state array");
+        if (!finite_arr(s.q, A.dof) || !finite_arr(s.qd, A.dof) || !finite_arr(s.goal_p, 3) ||
+            !finite_arr(s.goal_R, 9))
+            return fail(ctx, MRS_EINVAL, "non-finite state");
+        std::memcpy(p, s.q, sizeof(float) * A.dof);
+        std::memcpy(p + A.dof, s.qd, sizeof(float) * A.dof);
+        std::memcpy(p + 2 * A.dof, s.goal_p, sizeof(float) * 3);
+        std::memcpy(p + 2 * A.dof + 3, s.goal_R, sizeof(float) * 9);
+        p += 2 * A.dof + 12;
+    }
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    CK(cudaMemcpyAsync(ctx->D.input, ctx->pin_in, sizeof(float) * ctx->sz.input_floats,
+                       cudaMemcpyHostToDevice, ctx->stream), "input upload");
+    st = launch_cycle(ctx);
+    if (st != MRS_OK) return st;
+    CK(cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
+                       cudaMemcpyDeviceToHost, ctx->stream), "output download");
+    CK(cudaMemcpyAsync(ctx->pin_err, ctx->D.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+       "error word download");
+    st = wait_bounded(ctx, 10.0);
+    if (st != MRS_OK) return st;
+    if (*ctx->pin_err) return fail(ctx, MRS_ETIMEOUT, "a device-side bounded wait gave up");
+    if (out) {
+        const Dev &D = ctx->D;
+        const float *o = ctx->pin_out;
+        if (out->mean_plan) std::memcpy(out->mean_plan, o + D.out_mean, sizeof(float) * ctx->sz.hd);
+        if (out->plan_spheres) std::memcpy(out->plan_spheres, o + D.out_sph, sizeof(float) * ctx->sz.hs);
+        if (out->plan_q) std::memcpy(out->plan_q, o + D.out_q, sizeof(float) * ctx->sz.hd);
+        if (out->u_star) std::memcpy(out->u_star, o + D.out_u, sizeof(float) * ctx->sz.d);
+        if (out->dist_to_goal) std::memcpy(out->dist_to_goal, o + D.out_dist, sizeof(float) * ctx->A);
+        if (out->min_cost) std::memcpy(out->min_cost, o + D.out_min, sizeof(float) * ctx->A);
+    }
+    return MRS_OK;
+}
+
+mrs_status mrs_output_device(mrs_ctx *ctx, mrs_step_out *out)
+{
+    if (!ctx || !out) return MRS_EINVAL;
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const Dev &D = ctx->D;
+    out->mean_plan = D.out + D.out_mean;
+    out->plan_spheres = D.out + D.out_sph;
+    out->plan_q = D.out + D.out_q;
+    out->u_star = D.out + D.out_u;
+    out->dist_to_goal = D.out + D.out_dist;
+    out->min_cost = D.out + D.out_min;
+    return MRS_OK;
+}
+
+mrs_status mrs_sync(mrs_ctx *ctx, double timeout_s)
+{
+    if (!ctx) return MRS_EINVAL;
+    return wait_bounded(ctx, timeout_s);
+}
+
+mrs_status mrs_use_graph(mrs_ctx *ctx, int on)
+{
+    if (!ctx) return MRS_EINVAL;
+    ctx->use_graph = on != 0;
+    return MRS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume
+
+namespace {
+struct BlobHeader {
+    uint32_t magic, version, n_arms, pad;
+    int64_t cycle;
+    float world_t, pad2;
+};
+}
+
+mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes)
+{
+    if (!ctx || !blob) return MRS_EINVAL;
+    if (bytes < ctx->sz.state_bytes) return fail(ctx, MRS_EINVAL, "state buffer too small");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const int A = ctx->A;
+    std::vector<float> mu(ctx->sz.hd), Sg(ctx->sz.hdd), sph(ctx->sz.hs), q(ctx->sz.hd), dist(A);
+    std::vector<int> valid(A);
+    std::vector<long long> stamp(A);
+    long long cycle = 0;
+    float wt = 0.f;
+    const Dev &D = ctx->D;
+    CK(cudaMemcpyAsync(mu.data(), D.mu, sizeof(float) * mu.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(Sg.data(), D.Sigma, sizeof(float) * Sg.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(sph.data(), D.board_sph, sizeof(float) * sph.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(q.data(), D.board_q, sizeof(float) * q.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(dist.data(), D.board_dist, sizeof(float) * A, cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(valid.data(), D.board_valid, sizeof(int) * A, cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(stamp.data(), D.board_stamp, sizeof(long long) * A, cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(&cycle, D.cycle, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(&wt, D.world_t, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaStreamSynchronize(ctx->stream), "save sync");
+    char *p = (char *)blob;
+    BlobHeader hdr{0x3152534du, 1u, (uint32_t)A, 0u, cycle, wt, 0.f};
+    std::memcpy(p, &hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    for (int a = 0; a < A; ++a) {
+        const ArmDev &Ar = ctx->arms[a];
+        std::memcpy(p, mu.data() + Ar.off_hd, sizeof(float) * Ar.H * Ar.dof);
+        p += sizeof(float) * Ar.H * Ar.dof;
+        std::memcpy(p, Sg.data() + Ar.off_hdd, sizeof(float) * Ar.H * Ar.dof * Ar.dof);
+        p += sizeof(float) * Ar.H * Ar.dof * Ar.dof;
+    }
+    for (int a = 0; a < A; ++a) {
+        const ArmDev &Ar = ctx->arms[a];
+        int32_t v[2] = {valid[a], 0};
+        std::memcpy(p, v, 8); p += 8;
+        int64_t s = stamp[a];
+        std::memcpy(p, &s, 8); p += 8;
+        float dd[2] = {dist[a], 0.f};
+        std::memcpy(p, dd, 8); p += 8;
+        std::memcpy(p, sph.data() + Ar.off_hs, sizeof(float) * Ar.H * Ar.ns * 4);
+        p += sizeof(float) * Ar.H * Ar.ns * 4;
+        std::memcpy(p, q.data() + Ar.off_hd, sizeof(float) * Ar.H * Ar.dof);
+        p += sizeof(float) * Ar.H * Ar.dof;
+    }
+    return MRS_OK;
+}
+
+mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
+{
+    if (!ctx || !blob) return MRS_EINVAL;
+    if (bytes < ctx->sz.state_bytes) return fail(ctx, MRS_EINVAL, "state blob too small");
+    const char *p = (const char *)blob;
+    BlobHeader hdr;
+    std::memcpy(&hdr, p, sizeof(hdr));
+    p += sizeof(hdr);
+    if (hdr.magic != 0x3152534du || hdr.version != 1u || (int)hdr.n_arms != ctx->A)
+        return fail(ctx, MRS_EINVAL, "state blob header mismatch");
+    if (!std::isfinite(hdr.world_t) || hdr.cycle < 0) return fail(ctx, MRS_EINVAL, "bad clocks");
+    const int A = ctx->A;
+    std::vector<float> mu(ctx->sz.hd), Sg(ctx->sz.hdd), sph(ctx->sz.hs), q(ctx->sz.hd), dist(A);
+    std::vector<int> valid(A);
+    std::vector<long long> stamp(A);
+    for (int a = 0; a < A; ++a) {
+        const ArmDev &Ar = ctx->arms[a];
+        std::memcpy(mu.data() + Ar.off_hd, p, sizeof(float) * Ar.H * Ar.dof);
+        p += sizeof(float) * Ar.H * Ar.dof;
+        std::memcpy(Sg.data() + Ar.off_hdd, p, sizeof(float) * Ar.H * Ar.dof * Ar.dof);
+        p += sizeof(float) * Ar.H * Ar.dof * Ar.dof;
+    }
+    for (int a = 0; a < A; ++a) {
+        const ArmDev &Ar = ctx->arms[a];
+        int32_t v[2];
+        std::memcpy(v, p, 8); p += 8;
+        int64_t s;
+        std::memcpy(&s, p, 8); p += 8;
+        float dd[2];
+        std::memcpy(dd, p, 8); p += 8;
+        valid[a] = v[0] ? 1 : 0;
+        stamp[a] = s;
+        dist[a] = dd[0];
+        std::memcpy(sph.data() + Ar.off_hs, p, sizeof(float) * Ar.H * Ar.ns * 4);
+        p += sizeof(float) * Ar.H * Ar.ns * 4;
+        std::memcpy(q.data() + Ar.off_hd, p, sizeof(float) * Ar.H * Ar.dof);
+        p += sizeof(float) * Ar.H * Ar.dof;
+    }
+    if (!finite_arr(mu.data(), mu.size()) || !finite_arr(Sg.data(), Sg.size()) ||
+        !finite_arr(sph.data(), sph.size()) || !finite_arr(q.data(), q.size()) ||
+        !finite_arr(dist.data(), dist.size()))
+        return fail(ctx, MRS_EINVAL, "non-finite state");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const Dev &D = ctx->D;
+    long long cycle = hdr.cycle;
+    float wt = hdr.world_t;
+    CK(cudaMemcpyAsync(D.mu, mu.data(), sizeof(float) * mu.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.Sigma, Sg.data(), sizeof(float) * Sg.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.board_sph, sph.data(), sizeof(float) * sph.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.board_q, q.data(), sizeof(float) * q.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.board_dist, dist.data(), sizeof(float) * A, cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.board_valid, valid.data(), sizeof(int) * A, cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.board_stamp, stamp.data(), sizeof(long long) * A, cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.cycle, &cycle, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.world_t, &wt, sizeof(float), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaStreamSynchronize(ctx->stream), "load sync");
+    return MRS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kinematics, inspection, self-test
+
+mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (arm < 0 || arm >= ctx->A || n < 0 || (n && (!q || !ee)))
+        return fail(ctx, MRS_EINVAL, "bad fk arguments");
+    if (n == 0) return MRS_OK;
+    const ArmDev &A = ctx->arms[arm];
+    if (!finite_arr(q, (size_t)n * A.dof)) return fail(ctx, MRS_EINVAL, "non-finite q");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    float *dq = nullptr, *dee = nullptr, *ds = nullptr;
+    // sub-buffers start on 16-byte boundaries (the sphere output is float4)
+    const size_t nq = (size_t)n * A.dof, ne = (size_t)n * 12, nsph = (size_t)n * A.ns * 4;
+    const size_t nq_pad = align_up(nq, 4), ne_pad = align_up(ne, 4);
+    CK(cudaMalloc(&dq, sizeof(float) * (nq_pad + ne_pad + (spheres ? nsph : 0))), "fk buffer");
+    dee = dq + nq_pad;
+    ds = spheres ? dee + ne_pad : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dq, q, sizeof(float) * nq, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = enqueue_fk(ctx->D, arm, n, dq, dee, ds, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ee, dee, sizeof(float) * ne, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && spheres)
+        e = cudaMemcpyAsync(spheres, ds, sizeof(float) * nsph, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dq);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fk");
+    return MRS_OK;
+}
+
+mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs)
+{
+    if (!ctx || !costs || arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "bad arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const ArmDev &A = ctx->arms[arm];
+    CK(cudaMemcpyAsync(costs, ctx->D.costs + A.off_k, sizeof(float) * A.K, cudaMemcpyDeviceToHost,
+                       ctx->stream), "debug costs");
+    CK(cudaStreamSynchronize(ctx->stream), "debug costs");
+    return MRS_OK;
+}
+
+mrs_status mrs_debug_alpha(mrs_ctx *ctx, float *alpha)
+{
+    if (!ctx || !alpha) return fail(ctx, MRS_EINVAL, "bad arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    CK(cudaMemcpyAsync(alpha, ctx->D.alpha, sizeof(float) * ctx->A * ctx->A, cudaMemcpyDeviceToHost,
+                       ctx->stream), "debug alpha");
+    CK(cudaStreamSynchronize(ctx->stream), "debug alpha");
+    return MRS_OK;
+}
+
+mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out)
+{
+    if (!ctx || n_req < 0 || (n_req && (!anh || !out))) return fail(ctx, MRS_EINVAL, "bad arguments");
+    if (n_req == 0) return MRS_OK;
+    for (int r = 0; r < n_req; ++r) {
+        const int a = anh[3 * r], n = anh[3 * r + 1], h = anh[3 * r + 2];
+        if (a < 0 || a >= ctx->A || n < 0 || n >= ctx->arms[a].K || h < 0 || h >= ctx->arms[a].H)
+            return fail(ctx, MRS_EINVAL, "request out of range");
+    }
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    int *dreq = nullptr;
+    const size_t nout = (size_t)n_req * kMaxSpheres * 4;
+    const size_t nreq_pad = align_up((size_t)3 * n_req, 4);   // float4 output after it
+    CK(cudaMalloc(&dreq, sizeof(int) * nreq_pad + sizeof(float) * nout), "debug buffer");
+    float *dout = (float *)(dreq + nreq_pad);
+    cudaError_t e = cudaMemsetAsync(dout, 0, sizeof(float) * nout, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dreq, anh, sizeof(int) * 3 * n_req, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = enqueue_debug_spheres(ctx->D, n_req, dreq, dout, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, dout, sizeof(float) * nout, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dreq);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "debug spheres");
+    return MRS_OK;
+}
+
+mrs_status mrs_enable_timing(mrs_ctx *ctx, int on)
+{
+    if (!ctx) return MRS_EINVAL;
+    const size_t need = 2 + 4 * (size_t)ctx->P.iterations;
+    if (on && ctx->events.size() < need) {
+        while (ctx->events.size() < need) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e), "event create");
+            ctx->events.push_back(e);
+        }
+    }
+    if ((on != 0) != ctx->timing) invalidate_graph(ctx);
+    ctx->timing = on != 0;
+    return MRS_OK;
+}
+
+mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
+{
+    if (!ctx || !ms || !n) return MRS_EINVAL;
+    if (!ctx->timing) return fail(ctx, MRS_ESTATE, "timing is not enabled");
+    const int cnt = 1 + 4 * ctx->P.iterations;
+    if (*n < cnt) return fail(ctx, MRS_EINVAL, "ms has too few entries");
+    CK(cudaEventSynchronize(ctx->events[cnt]), "timing wait");
+    for (int i = 0; i < cnt; ++i)
+        CK(cudaEventElapsedTime(&ms[i], ctx->events[i], ctx->events[i + 1]), "elapsed time");
+    *n = cnt;
+    return MRS_OK;
+}
+
+mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise)
+{
+    if (!ctx) return MRS_EINVAL;
+    ctx->P.zero_noise = zero_noise ? 1 : 0;
+    invalidate_graph(ctx);
+    return MRS_OK;
+}
+
+mrs_status mrs_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    if (n < 0 || (n && (!ctr || !key || !out))) return MRS_EINVAL;
+    if (n == 0) return MRS_OK;
+    uint4 *d = nullptr;
+    if (cudaMalloc(&d, sizeof(uint4) * 2 * (size_t)n) != cudaSuccess) return MRS_ENOMEM;
+    cudaError_t e = cudaMemcpy(d, ctr, sizeof(uint4) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = enqueue_philox(n, d, make_uint2(key[0], key[1]), d + n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + n, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? MRS_OK : MRS_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,353 @@
+"""Python binding of libmrs (include/mrs.h): argument marshalling only.
+
+Every step of the control cycle runs in the library's CUDA kernels; this
+module converts numpy / torch arguments to the C ABI and back.  PyTorch
+supplies device memory (the workspace) and streams.  If the compiled library
+is missing, loading fails with an error: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int)
+
+STATUS = {0: "MRS_OK", 1: "MRS_EINVAL", 2: "MRS_ENOMEM", 3: "MRS_ECUDA", 4: "MRS_ETIMEOUT",
+          5: "MRS_ESTATE", 6: "MRS_EUNSUPPORTED"}
+
+MAX_SPHERES = 64
+
+
+class MrsArmDesc(C.Structure):
+    _fields_ = [("dof", C.c_int), ("n_spheres", C.c_int), ("K", C.c_int), ("H", C.c_int),
+                ("dh", _fp), ("q_lo", _fp), ("q_hi", _fp), ("qd_max", _fp),
+                ("sphere_body", _ip), ("sphere_xyzr", _fp), ("base_pose", C.c_float * 7)]
+
+
+class MrsConfig(C.Structure):
+    _fields_ = [("n_arms", C.c_int), ("arms", C.POINTER(MrsArmDesc)),
+                ("dt", C.c_float), ("lambda_", C.c_float), ("gamma", C.c_float),
+                ("alpha_mu", C.c_float), ("alpha_sigma", C.c_float), ("sigma_init", C.c_float),
+                ("w_pose", C.c_float), ("w_rot", C.c_float), ("w_stop", C.c_float),
+                ("w_joint", C.c_float), ("w_coll", C.c_float), ("w_self", C.c_float),
+                ("w_dyn", C.c_float), ("B", C.c_float), ("B_world", C.c_float),
+                ("B_self", C.c_float), ("tau", C.c_float), ("q_margin", C.c_float),
+                ("iterations", C.c_int), ("seed", C.c_ulonglong), ("mode", C.c_int)]
+
+
+class MrsArmState(C.Structure):
+    _fields_ = [("q", _fp), ("qd", _fp), ("goal_p", _fp), ("goal_R", _fp)]
+
+
+class MrsStepOut(C.Structure):
+    _fields_ = [("mean_plan", _fp), ("plan_spheres", _fp), ("plan_q", _fp), ("u_star", _fp),
+                ("dist_to_goal", _fp), ("min_cost", _fp)]
+
+
+class MrsSizes(C.Structure):
+    _fields_ = [("n_arms", C.c_size_t), ("hd", C.c_size_t), ("hs", C.c_size_t),
+                ("d", C.c_size_t), ("k", C.c_size_t), ("hdd", C.c_size_t),
+                ("input_floats", C.c_size_t), ("output_floats", C.c_size_t),
+                ("state_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t)]
+
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "mrs_create": (C.c_int, [C.POINTER(MrsConfig), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mrs_destroy": (None, [C.c_void_p]),
+    "mrs_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrs_query_sizes": (C.c_int, [C.c_void_p, C.POINTER(MrsSizes)]),
+    "mrs_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "mrs_bind_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mrs_set_world": (C.c_int, [C.c_void_p, _fp, _fp, C.c_int, _fp, C.c_int]),
+    "mrs_share_plans": (C.c_int, [C.c_void_p, C.c_int, _fp, _fp, C.c_float, C.c_longlong]),
+    "mrs_step": (C.c_int, [C.c_void_p, C.POINTER(MrsArmState), C.POINTER(MrsStepOut)]),
+    "mrs_step_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mrs_output_device": (C.c_int, [C.c_void_p, C.POINTER(MrsStepOut)]),
+    "mrs_sync": (C.c_int, [C.c_void_p, C.c_double]),
+    "mrs_use_graph": (C.c_int, [C.c_void_p, C.c_int]),
+    "mrs_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mrs_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mrs_fk": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp, _fp, _fp]),
+    "mrs_debug_costs": (C.c_int, [C.c_void_p, C.c_int, _fp]),
+    "mrs_debug_spheres": (C.c_int, [C.c_void_p, C.c_int, _ip, _fp]),
+    "mrs_debug_alpha": (C.c_int, [C.c_void_p, _fp]),
+    "mrs_set_zero_noise": (C.c_int, [C.c_void_p, C.c_int]),
+    "mrs_enable_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "mrs_kernel_times": (C.c_int, [C.c_void_p, _fp, C.POINTER(C.c_int)]),
+    "mrs_philox": (C.c_int, [C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                             C.POINTER(C.c_uint32)]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load libmrs.so from the source tree (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libmrs.so is not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    L = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class MrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _pf(a):
+    return None if a is None else a.ctypes.data_as(_fp)
+
+
+def philox(ctr, key):
+    """Device Philox4x32-10 of counters ctr [n][4] under key [2] -> [n][4]."""
+    L = load()
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros_like(ctr)
+    p = C.POINTER(C.c_uint32)
+    st = L.mrs_philox(len(ctr), ctr.ctypes.data_as(p), key.ctypes.data_as(p), out.ctypes.data_as(p))
+    if st != 0:
+        raise MrsError(st, "philox self-test")
+    return out
+
+
+class Controller:
+    """One library context for a `scenarios.Scenario` (or any object with the
+    same fields).  The device workspace is a torch uint8 tensor on `device`."""
+
+    def __init__(self, sc, device="cuda", stream=None, workspace=True):
+        import torch
+        self.L = load()
+        self.sc = sc
+        self._keep = []
+        A = len(sc.arms)
+        self._arms = (MrsArmDesc * A)()
+        for i, a in enumerate(sc.arms):
+            dh, lo, hi, vm = _f32(a.dh), _f32(a.q_lo), _f32(a.q_hi), _f32(a.qd_max)
+            body = np.ascontiguousarray(a.sphere_body, dtype=np.int32)
+            xyzr = _f32(a.sphere_xyzr)
+            self._keep += [dh, lo, hi, vm, body, xyzr]
+            s = self._arms[i]
+            s.dof, s.n_spheres, s.K, s.H = a.dof, a.n_spheres, a.K, a.H
+            s.dh, s.q_lo, s.q_hi, s.qd_max = _pf(dh), _pf(lo), _pf(hi), _pf(vm)
+            s.sphere_body = body.ctypes.data_as(_ip)
+            s.sphere_xyzr = _pf(xyzr)
+            for k in range(7):
+                s.base_pose[k] = float(a.base_pose[k])
+        p = sc.params
+        self.cfg = MrsConfig(A, self._arms, p["dt"], p["lam"], p["gamma"], p["alpha_mu"],
+                             p["alpha_sigma"], p["sigma_init"], p["w_pose"], p["w_rot"],
+                             p["w_stop"], p["w_joint"], p["w_coll"], p["w_self"], p["w_dyn"],
+                             p["B"], p["B_world"], p["B_self"], p["tau"], p["q_margin"],
+                             int(p["iterations"]), int(p["seed"]), 0)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        h = C.c_void_p()
+        st = self.L.mrs_create(C.byref(self.cfg), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise MrsError(st, "mrs_create")
+        self.h = h
+        self.sizes = MrsSizes()
+        self._check(self.L.mrs_query_sizes(self.h, C.byref(self.sizes)), "query_sizes")
+        self.ws = None
+        if workspace:
+            nb = int(self.sizes.workspace_bytes)
+            self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+            base = self.ws.data_ptr()
+            off = (-base) % 256
+            self._check(self.L.mrs_bind_workspace(self.h, C.c_void_p(base + off), nb), "bind")
+        self.off_hd = np.concatenate([[0], np.cumsum([a.H * a.dof for a in sc.arms])]).astype(int)
+        self.off_hs = np.concatenate([[0], np.cumsum([a.H * a.n_spheres * 4 for a in sc.arms])]).astype(int)
+        self.off_d = np.concatenate([[0], np.cumsum([a.dof for a in sc.arms])]).astype(int)
+        self.off_in = np.concatenate([[0], np.cumsum([2 * a.dof + 12 for a in sc.arms])]).astype(int)
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.L.mrs_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise MrsError(st, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mrs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API ----------------------------------------------------------------
+    def set_world(self, spheres=None, vel=None, aabbs=None):
+        sc = self.sc
+        spheres = _f32(sc.world if spheres is None else spheres).reshape(-1, 4)
+        if vel is None and spheres is sc.world:
+            vel = sc.world_vel
+        vel = None if vel is None else _f32(vel).reshape(-1, 3)
+        aabbs = _f32(sc.aabb if aabbs is None else aabbs).reshape(-1, 6)
+        self._check(self.L.mrs_set_world(self.h, _pf(spheres) if len(spheres) else None,
+                                         _pf(vel), len(spheres),
+                                         _pf(aabbs) if len(aabbs) else None, len(aabbs)),
+                    "set_world")
+
+    def share_plans(self, arm, plan_spheres, plan_q, dist_to_goal, cycle):
+        ps = _f32(plan_spheres)
+        pq = None if plan_q is None else _f32(plan_q)
+        self._check(self.L.mrs_share_plans(self.h, arm, _pf(ps), _pf(pq), float(dist_to_goal),
+                                           int(cycle)), "share_plans")
+
+    def pack_input(self, q, qd, goal_p, goal_R):
+        parts = []
+        for a in range(len(self.sc.arms)):
+            parts += [_f32(q[a]).ravel(), _f32(qd[a]).ravel(), _f32(goal_p[a]).ravel(),
+                      _f32(goal_R[a]).ravel()]
+        return np.concatenate(parts).astype(np.float32)
+
+    def step(self, q, qd, goal_p, goal_R):
+        """One control cycle with host inputs; returns a dict of host arrays."""
+        A = len(self.sc.arms)
+        keep = []
+        states = (MrsArmState * A)()
+        for a in range(A):
+            arrs = [_f32(q[a]), _f32(qd[a]), _f32(goal_p[a]).ravel(), _f32(goal_R[a]).ravel()]
+            keep += arrs
+            states[a] = MrsArmState(*[_pf(x) for x in arrs])
+        sz = self.sizes
+        out = dict(mean_plan=np.zeros(sz.hd, np.float32), plan_spheres=np.zeros(sz.hs, np.float32),
+                   plan_q=np.zeros(sz.hd, np.float32), u_star=np.zeros(sz.d, np.float32),
+                   dist_to_goal=np.zeros(A, np.float32), min_cost=np.zeros(A, np.float32))
+        o = MrsStepOut(*[_pf(out[k]) for k in ("mean_plan", "plan_spheres", "plan_q", "u_star",
+                                               "dist_to_goal", "min_cost")])
+        self._check(self.L.mrs_step(self.h, states, C.byref(o)), "step")
+        return out
+
+    def step_device(self, d_input):
+        """Enqueue one cycle with a device-resident packed input (torch float32
+        tensor of input_floats elements); does not wait."""
+        self._check(self.L.mrs_step_device(self.h, C.c_void_p(d_input.data_ptr())), "step_device")
+
+    def output_pointers(self):
+        o = MrsStepOut()
+        self._check(self.L.mrs_output_device(self.h, C.byref(o)), "output_device")
+        return o
+
+    def sync(self, timeout_s=10.0):
+        self._check(self.L.mrs_sync(self.h, float(timeout_s)), "sync")
+
+    def use_graph(self, on: bool):
+        self._check(self.L.mrs_use_graph(self.h, 1 if on else 0), "use_graph")
+
+    def set_zero_noise(self, on: bool):
+        self._check(self.L.mrs_set_zero_noise(self.h, 1 if on else 0), "zero_noise")
+
+    def enable_timing(self, on: bool):
+        self._check(self.L.mrs_enable_timing(self.h, 1 if on else 0), "enable_timing")
+
+    def kernel_times(self):
+        """Durations (ms) of the last cycle's kernels in launch order."""
+        n = C.c_int(64)
+        ms = np.zeros(64, np.float32)
+        self._check(self.L.mrs_kernel_times(self.h, _pf(ms), C.byref(n)), "kernel_times")
+        return ms[:n.value].copy()
+
+    def save_state(self) -> bytes:
+        buf = (C.c_char * int(self.sizes.state_bytes))()
+        self._check(self.L.mrs_save_state(self.h, buf, len(buf)), "save_state")
+        return bytes(buf)
+
+    def load_state(self, blob: bytes):
+        buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+        self._check(self.L.mrs_load_state(self.h, buf, len(blob)), "load_state")
+
+    def fk(self, arm, q):
+        a = self.sc.arms[arm]
+        q = _f32(q).reshape(-1, a.dof)
+        ee = np.zeros((len(q), 12), np.float32)
+        sph = np.zeros((len(q), a.n_spheres, 4), np.float32)
+        self._check(self.L.mrs_fk(self.h, arm, len(q), _pf(q), _pf(ee), _pf(sph)), "fk")
+        return ee, sph
+
+    def goal_pose(self, arm, q):
+        ee, _ = self.fk(arm, q)
+        return ee[0, 9:12].copy(), ee[0, :9].reshape(3, 3).copy()
+
+    def debug_costs(self, arm):
+        c = np.zeros(self.sc.arms[arm].K, np.float32)
+        self._check(self.L.mrs_debug_costs(self.h, arm, _pf(c)), "debug_costs")
+        return c
+
+    def debug_alpha(self):
+        A = len(self.sc.arms)
+        al = np.zeros((A, A), np.float32)
+        self._check(self.L.mrs_debug_alpha(self.h, _pf(al)), "debug_alpha")
+        return al
+
+    def debug_spheres(self, anh):
+        anh = np.ascontiguousarray(np.asarray(anh, dtype=np.int32).reshape(-1, 3))
+        out = np.zeros((len(anh), MAX_SPHERES, 4), np.float32)
+        self._check(self.L.mrs_debug_spheres(self.h, len(anh), anh.ctypes.data_as(_ip), _pf(out)),
+                    "debug_spheres")
+        return out
+
+    def split(self, flat, kind, arm):
+        a = self.sc.arms[arm]
+        if kind == "hd":
+            return flat[self.off_hd[arm]:self.off_hd[arm + 1]].reshape(a.H, a.dof)
+        if kind == "hs":
+            return flat[self.off_hs[arm]:self.off_hs[arm + 1]].reshape(a.H, a.n_spheres, 4)
+        if kind == "d":
+            return flat[self.off_d[arm]:self.off_d[arm + 1]]
+        raise KeyError(kind)
+
+
+def state_blob(sc, mu, Sigma, cycle, world_t, plan_valid, plan_stamp, plan_dist, plan_spheres,
+               plan_q) -> bytes:
+    """Serialise a controller state (per-arm concatenated arrays) in the layout
+    of mrs_save_state / mrs_load_state."""
+    import struct
+    A = len(sc.arms)
+    parts = [struct.pack("<IIIIqff", 0x3152534D, 1, A, 0, int(cycle), float(world_t), 0.0)]
+    o_hd = o_hdd = 0
+    for a in sc.arms:
+        hd, hdd = a.H * a.dof, a.H * a.dof * a.dof
+        parts.append(np.asarray(mu[o_hd:o_hd + hd], np.float32).tobytes())
+        parts.append(np.asarray(Sigma[o_hdd:o_hdd + hdd], np.float32).tobytes())
+        o_hd += hd
+        o_hdd += hdd
+    o_hd = o_hs = 0
+    for i, a in enumerate(sc.arms):
+        hd, hs = a.H * a.dof, a.H * a.n_spheres * 4
+        parts.append(struct.pack("<iiqff", int(plan_valid[i]), 0, int(plan_stamp[i]),
+                                 float(plan_dist[i]), 0.0))
+        parts.append(np.asarray(plan_spheres[o_hs:o_hs + hs], np.float32).tobytes())
+        parts.append(np.asarray(plan_q[o_hd:o_hd + hd], np.float32).tobytes())
+        o_hd += hd
+        o_hs += hs
+    return b"".join(parts)

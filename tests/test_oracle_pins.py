@@ -355,7 +355,8 @@ def test_discounted_sum_of_constant_stage_cost(oracle_mod):
     tot, stage, _, _ = orc.rollout(0, [q0], [qd0], gp, gR, np.zeros((8, 7)))
     c = stage[0]
     assert c > 0 and np.allclose(stage, c, rtol=1e-14)
-    assert math.isclose(tot, c * (1 - 0.9 ** 8) / (1 - 0.9), rel_tol=1e-13)
+    g = float(np.float32(0.9))          # parameters are read as float32 values
+    assert math.isclose(tot, c * (1 - g ** 8) / (1 - g), rel_tol=1e-13)
 
 
 def test_colliding_pose_exceeds_threshold(oracle_mod):
@@ -374,7 +375,7 @@ def test_colliding_pose_exceeds_threshold(oracle_mod):
     o = sc.world[0].astype(np.float64)
     dmin = (cdist(sph[:, :3], o[None, :3])[:, 0] - sph[:, 3] - o[3]).min()
     assert dmin <= -(sph[20, 3] + 0.05) + 1e-6
-    exp = 1 - dmin / 0.03
+    exp = 1 - dmin / float(np.float32(0.03))   # B_world as the float32 parameter
     assert stage[0] > sc.params["w_coll"]
     assert math.isclose(stage[0], sc.params["w_coll"] * exp, rel_tol=1e-12)
 
@@ -474,7 +475,7 @@ def test_update_uniform_weights_give_sample_moments(oracle_mod):
     orc = Oracle(sc)
     gp, gR = goals_of(orc, sc)
     out = orc.cycle(sc.q0, sc.qd0, gp, gR)
-    d, K, s2 = 7, 64, 0.3 ** 2
+    d, K, s2 = 7, 64, float(np.float32(0.3)) ** 2
     L = oracle_mod.cholesky(s2 * np.eye(d), 1e-8)
     for h in range(3):
         U = np.array([L @ oracle_mod.normals(sc.params["seed"], 0, 0, 0, n, h, d)
@@ -499,7 +500,8 @@ def test_shift_moves_phi_one_step(oracle_mod):
     mu1, mu2 = orc.split(o1["mean_plan"], "hd", 0), orc.split(o2["mean_plan"], "hd", 0)
     S1, S2 = orc.split(o1["Sigma"], "hdd", 0), orc.split(o2["Sigma"], "hdd", 0)
     assert np.array_equal(mu2[:-1], mu1[1:]) and np.array_equal(mu2[-1], mu1[-1])
-    assert np.array_equal(S2[:-1], S1[1:]) and np.array_equal(S2[-1], 0.09 * np.eye(7))
+    s2 = float(np.float32(0.3)) ** 2       # sigma_init as the float32 parameter
+    assert np.array_equal(S2[:-1], S1[1:]) and np.array_equal(S2[-1], s2 * np.eye(7))
 
 
 def test_priority_uses_own_sensed_and_neighbours_published_distance(oracle_mod):

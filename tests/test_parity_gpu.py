@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA control cycle (through the C ABI) against the FP64
+oracle on the same seeded inputs.
+
+Tolerances: sphere positions 1e-5 m, per-rollout costs 1e-4 relative (floor
+1e-6 (1 + |C|)), updated mean and covariance 1e-5; U_* must come from the
+same sample whenever the oracle's two cheapest rollouts differ by more than
+1e-4 relative.  Every cycle is a replay: the CUDA context is loaded with the
+oracle's float32-rounded state first.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_10114_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+SPHERE_TOL = 1e-5
+MU_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_10114_gb300 import build, mrs
+    build.build()
+    mrs.load()
+
+
+def _check_cycle(R, got, gc, ga, gs, exp, dump):
+    """Sampled rollout spheres 1e-5 m (and within the EPS_D / 4 error model),
+    costs 1e-4 relative, alpha 1e-5 relative, U_* from the same sample unless
+    the two cheapest oracle costs are within 1e-4; mean and covariance within
+    1e-5 plus the first-order propagation of the FP32 cost-error bound
+    (update_tolerance); the published plan within 1e-5 m plus that excess
+    carried through ToPlan (plan_tolerance)."""
+    from parity_utils import EPS_D, cost_tol, parse_state, plan_tolerance, update_tolerance
+    sc, orc = R.sc, R.orc
+    p = sc.params
+    assert np.abs(got["dist_to_goal"] - exp["dist_to_goal"]).max() < SPHERE_TOL
+    assert np.allclose(ga.ravel(), exp["alpha"], rtol=1e-5, atol=0)
+    st = parse_state(sc, R.ctl.save_state())
+    for a in range(sc.n_arms):
+        ce = orc.split(exp["costs"], "k", a)
+        assert np.all(np.abs(gc[a] - ce) <= cost_tol(ce)), f"arm {a} costs"
+        srt = np.sort(ce)
+        if len(ce) == 1 or srt[1] - srt[0] > 1e-4 * abs(srt[0]):
+            assert int(np.argmin(gc[a])) == int(exp["n_star"][a])
+            ua = orc.split(exp["u_star"], "d", a)
+            assert np.abs(R.ctl.split(got["u_star"], "d", a) - ua).max() < MU_TOL
+        tol_mu, tol_sig = update_tolerance(exp, orc, a, p["lam"], p["alpha_mu"], p["alpha_sigma"])
+        err_mu = np.abs(R.ctl.split(got["mean_plan"], "hd", a) - orc.split(exp["mean_plan"], "hd", a))
+        assert np.all(err_mu <= tol_mu), f"arm {a} mean: {err_mu.max()} vs {tol_mu.min()}"
+        sa = sc.arms[a]
+        o0 = sum(b.H * b.dof * b.dof for b in sc.arms[:a])
+        sg = st["Sigma"][o0:o0 + sa.H * sa.dof * sa.dof].reshape(sa.H, sa.dof, sa.dof)
+        err_sig = np.abs(sg - orc.split(exp["Sigma"], "hdd", a))
+        assert np.all(err_sig <= tol_sig), f"arm {a} covariance"
+        # the published plan: ToPlan of the updated mean
+        tol_plan = plan_tolerance(sc, a, tol_mu)
+        e_plan = np.abs(R.ctl.split(got["plan_spheres"], "hs", a)
+                        - orc.split(exp["plan_spheres"], "hs", a))[..., :3].max(axis=(1, 2))
+        assert np.all(e_plan <= tol_plan), f"arm {a} plan spheres"
+        e_q = np.abs(R.ctl.split(got["plan_q"], "hd", a) - orc.split(exp["plan_q"], "hd", a))
+        assert np.all(e_q.max(axis=1) <= tol_plan), f"arm {a} plan joints"
+    if dump is not None:
+        for i, (a, n, h) in enumerate(dump):
+            ns = sc.arms[a].n_spheres
+            e = np.abs(gs[i, :ns] - exp["dump_spheres"][i, :ns]).max()
+            assert e < SPHERE_TOL and e < EPS_D / 4
+
+
+def _dump(sc):
+    return np.array([[a, n, h] for a in range(sc.n_arms)
+                     for n in sorted({0, 5, sc.arms[a].K // 2, sc.arms[a].K - 1})
+                     for h in sorted({0, sc.arms[a].H // 2, sc.arms[a].H - 1})], np.int32)
+
+
+def test_philox_bit_exact():
+    from oracle import oracle as O
+    from paper_2602_10114_gb300 import mrs
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, (257, 4), dtype=np.uint64).astype(np.uint32)
+    key = np.array([0xDEADBEEF, 0x12345678], np.uint32)
+    got = mrs.philox(ctr, key)
+    for i in range(len(ctr)):
+        assert list(got[i]) == O.philox(ctr[i], key)
+
+
+def test_fk_matches_oracle():
+    from oracle.oracle import Oracle
+    from paper_2602_10114_gb300 import mrs
+    for idx in (1, 4):
+        sc = S.config(idx)
+        orc = Oracle(sc)
+        ctl = mrs.Controller(sc)
+        rng = np.random.default_rng(idx)
+        for a in range(min(sc.n_arms, 3)):
+            q = rng.uniform(-2.8, 2.8, (64, sc.arms[a].dof)).astype(np.float32)
+            ee, sph = ctl.fk(a, q)
+            for i in range(len(q)):
+                F, so = orc.fk(a, q[i].astype(np.float64))
+                assert np.abs(sph[i] - so).max() < SPHERE_TOL
+                assert np.abs(ee[i, 9:] - F[-1][:3, 3]).max() < SPHERE_TOL
+                assert np.abs(ee[i, :9] - F[-1][:3, :3].ravel()).max() < 1e-5
+
+
+@pytest.mark.parametrize("n_cycles", [3])
+def test_cycle_single_arm(n_cycles):
+    """Workload 1: one 7-DoF arm, K=64, H=16, 8 world spheres."""
+    from parity_utils import Replay
+    sc = S.config(1)
+    R = Replay(sc)
+    for _ in range(n_cycles):
+        d = _dump(sc)
+        got, gc, ga, gs, exp = R.cycle(d)
+        _check_cycle(R, got, gc, ga, gs, exp, d)
+        R.advance(exp)
+
+
+def test_cycle_four_arms_replay():
+    """Workload 2 (four arms sharing plans, K=512, H=30): replayed cycles."""
+    from parity_utils import Replay
+    sc = S.config(2)
+    R = Replay(sc)
+    for c in range(4):
+        d = _dump(sc)
+        got, gc, ga, gs, exp = R.cycle(d)
+        _check_cycle(R, got, gc, ga, gs, exp, d)
+        R.advance(exp)
+
+
+def test_ragged_shapes():
+    """K not a multiple of the 32-sample tile, H = 1 and 2, one-sphere arm."""
+    from parity_utils import Replay
+    for K, H in [(45, 3), (33, 1), (1, 2)]:
+        sc = S.shrink(S.config(2), K=K, H=H, arms=3)
+        R = Replay(sc)
+        for _ in range(2):
+            got, gc, ga, gs, exp = R.cycle(None)
+            _check_cycle(R, got, gc, ga, gs, exp, None)
+            R.advance(exp)
+
+
+def test_zero_noise_rollout_reproduces_the_plan():
+    """With eps = 0 every rollout is the mean, the update leaves mu unchanged,
+    and the sampled spheres equal the published plan bit for bit."""
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import goals
+    from oracle.oracle import Oracle
+    sc = S.config(2)
+    ctl = mrs.Controller(sc)
+    ctl.set_world()
+    ctl.set_zero_noise(True)
+    gp, gR = goals(Oracle(sc), sc)
+    got = ctl.step(sc.q0, sc.qd0, gp.astype(np.float32), gR.astype(np.float32))
+    assert np.all(got["mean_plan"] == 0)
+    for a in range(sc.n_arms):
+        anh = [[a, n, h] for n in (0, 100, 511) for h in range(sc.arms[a].H)]
+        sph = ctl.debug_spheres(anh)
+        plan = ctl.split(got["plan_spheres"], "hs", a)
+        for i, (_, n, h) in enumerate(anh):
+            assert np.array_equal(sph[i, :sc.arms[a].n_spheres], plan[h])
+
+
+def test_state_roundtrip_and_resume():
+    """Checkpoint/resume: a resumed controller continues bit-identically."""
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import goals
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(2), K=128, H=10)
+    gp, gR = goals(Oracle(sc), sc)
+    gp, gR = gp.astype(np.float32), gR.astype(np.float32)
+    a = mrs.Controller(sc)
+    a.set_world()
+    a.step(sc.q0, sc.qd0, gp, gR)
+    blob = a.save_state()
+    r1 = a.step(sc.q0, sc.qd0, gp, gR)
+    b = mrs.Controller(sc)
+    b.set_world()
+    b.load_state(blob)
+    assert b.save_state() == blob
+    r2 = b.step(sc.q0, sc.qd0, gp, gR)
+    for k in r1:
+        assert np.array_equal(r1[k], r2[k]), k
+
+
+def test_graph_and_direct_launch_agree():
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import goals
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(2), K=96, H=8)
+    gp, gR = goals(Oracle(sc), sc)
+    outs = []
+    for graph in (True, False):
+        c = mrs.Controller(sc)
+        c.use_graph(graph)
+        c.set_world()
+        for _ in range(3):
+            r = c.step(sc.q0, sc.qd0, gp.astype(np.float32), gR.astype(np.float32))
+        outs.append(r)
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_shared_plan_injection_and_withdrawal():
+    """mrs_share_plans overrides a neighbour's board entry (Publish from
+    elsewhere); a negative distance withdraws it (ignored, Sec. IV-C)."""
+    from parity_utils import Replay, load_oracle_state, r32
+    sc = S.shrink(S.config(2), K=64, H=6)
+    R = Replay(sc)
+    got, gc, ga, gs, exp = R.cycle(None)
+    R.advance(exp)
+    o = R.orc
+    load_oracle_state(R.ctl, o)
+    # arm 2 publishes arm 0's plan with a new distance; arm 3 withdraws
+    s = o.state
+    new_plan = r32(s["plan_spheres"][o.off_hs[0]:o.off_hs[1]] + 0.01)
+    s["plan_spheres"][o.off_hs[2]:o.off_hs[3]] = new_plan
+    s["plan_dist"][2] = r32(0.05)
+    s["plan_valid"][3] = 0
+    R.ctl.share_plans(2, new_plan.astype(np.float32), None, 0.05, 7)
+    R.ctl.share_plans(3, np.zeros(1, np.float32), None, -1.0, 7)
+    got = R.ctl.step([q.astype(np.float32) for q in R.q], [q.astype(np.float32) for q in R.qd],
+                     R.gp.astype(np.float32), R.gR.astype(np.float32))
+    gc = [R.ctl.debug_costs(a) for a in range(sc.n_arms)]
+    ga = R.ctl.debug_alpha()
+    exp = o.cycle(R.q, R.qd, R.gp, R.gR)
+    assert np.all(ga[:, 3] == 0) and ga[0, 2] > 0
+    _check_cycle(R, got, gc, ga, None, exp, None)
+
+
+def test_rejects_non_finite_state():
+    from paper_2602_10114_gb300 import mrs
+    sc = S.config(1)
+    c = mrs.Controller(sc)
+    q = [np.full(7, np.nan, np.float32)]
+    with pytest.raises(mrs.MrsError) as e:
+        c.step(q, sc.qd0, np.zeros((1, 3), np.float32), np.eye(3, dtype=np.float32)[None])
+    assert e.value.status == 1
