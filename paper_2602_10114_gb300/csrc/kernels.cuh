@@ -20,7 +20,7 @@ struct LaunchPlan {
 
 // Everything one control cycle enqueues on `s` (Algorithm 1 for all arms).
 // With `events` non-null, events[0] is recorded before the first kernel and
-// events[i + 1] after kernel i (2 + 4 * iterations events); `capturing` makes
+// events[i + 1] after kernel i (3 + 4 * iterations events); `capturing` makes
 // them external event nodes of the graph being captured.
 cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cudaStream_t s,
                           cudaEvent_t *events = nullptr, bool capturing = false);

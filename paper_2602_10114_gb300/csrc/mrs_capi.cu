@@ -871,7 +871,7 @@ mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out
 mrs_status mrs_enable_timing(mrs_ctx *ctx, int on)
 {
     if (!ctx) return MRS_EINVAL;
-    const size_t need = 2 + 4 * (size_t)ctx->P.iterations;
+    const size_t need = 3 + 4 * (size_t)ctx->P.iterations;   // one more than the kernels
     if (on && ctx->events.size() < need) {
         while (ctx->events.size() < need) {
             cudaEvent_t e;
@@ -888,7 +888,7 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
 {
     if (!ctx || !ms || !n) return MRS_EINVAL;
     if (!ctx->timing) return fail(ctx, MRS_ESTATE, "timing is not enabled");
-    const int cnt = 1 + 4 * ctx->P.iterations;
+    const int cnt = 2 + 4 * ctx->P.iterations;                 // kernels of one cycle
     if (*n < cnt) return fail(ctx, MRS_EINVAL, "ms has too few entries");
     CK(cudaEventSynchronize(ctx->events[cnt]), "timing wait");
     for (int i = 0; i < cnt; ++i)

@@ -226,7 +226,7 @@ def test_shared_plan_injection_and_withdrawal():
                      R.gp.astype(np.float32), R.gR.astype(np.float32))
     gc = [R.ctl.debug_costs(a) for a in range(sc.n_arms)]
     ga = R.ctl.debug_alpha()
-    exp = o.cycle(R.q, R.qd, R.gp, R.gR)
+    exp = o.cycle(R.q, R.qd, R.gp, R.gR, want_U=True)
     assert np.all(ga[:, 3] == 0) and ga[0, 2] > 0
     _check_cycle(R, got, gc, ga, None, exp, None)
 
