@@ -219,6 +219,27 @@ mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes);
  * as the rollout. */
 mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres);
 
+/* Forward kinematics like mrs_fk, for callers that cannot allocate device
+ * memory (the paper has no counterpart; this is a library service).  A
+ * control loop with a hard period cannot afford cudaMalloc/cudaFree, which may
+ * block and synchronise the device, and a process whose device memory belongs
+ * to another allocator may not call them at all; mrs_fk does both on every
+ * call.  This call stages q and its results in one file-scope static device
+ * array of 2^20 floats (4 MiB) that every GPU loading the library holds until
+ * the process exits, and calls no allocating routine.
+ *  - Limit: round_up(n * dof, 4) + 12 n + 4 n N_S <= 1048576 floats; larger
+ *    requests fail with MRS_EINVAL before any device work.
+ *  - The context must have a bound workspace (MRS_ESTATE otherwise: binding
+ *    on demand would allocate).
+ *  - The first call on each device looks up the array's device address on
+ *    that device; make that first call before any stream capture.
+ *  - All calls in the process share the one array and it keeps the last
+ *    call's contents (nothing in it needs to start at zero: every value
+ *    returned is written by the call).  Calls that overlap on the GPU, from
+ *    several threads or contexts, race on it: serialise them.
+ * Blocks until ee [n][12] and spheres [n][NS][4] (may be NULL) are written. */
+mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres);
+
 /* Inspection of the last completed cycle (host outputs):
  * mrs_debug_costs   : C_n of the last iteration, [K_arm].
  * mrs_debug_spheres : sphere centres of sampled rollouts at (arm, n, h)

@@ -817,6 +817,25 @@ mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float
     return MRS_OK;
 }
 
+mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (arm < 0 || arm >= ctx->A || n < 0 || (n && (!q || !ee)))
+        return fail(ctx, MRS_EINVAL, "bad fk arguments");
+    if (n == 0) return MRS_OK;
+    if (!ctx->bound)
+        return fail(ctx, MRS_ESTATE, "bind a workspace first: mrs_fk_static allocates nothing");
+    const ArmDev &A = ctx->arms[arm];
+    if (!finite_arr(q, (size_t)n * A.dof)) return fail(ctx, MRS_EINVAL, "non-finite q");
+    std::string why;
+    bool too_large = false;
+    cudaError_t e = fk_static(ctx->D, arm, A.dof, A.ns, n, q, ee, spheres, ctx->stream, why,
+                              too_large);
+    if (too_large) return fail(ctx, MRS_EINVAL, why);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, ("mrs_fk_static: " + why).c_str());
+    return MRS_OK;
+}
+
 mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs)
 {
     if (!ctx || !costs || arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "bad arguments");

@@ -74,6 +74,7 @@ SIGNATURES = {
     "mrs_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mrs_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mrs_fk": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp, _fp, _fp]),
+    "mrs_fk_static": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp, _fp, _fp]),
     "mrs_debug_costs": (C.c_int, [C.c_void_p, C.c_int, _fp]),
     "mrs_debug_spheres": (C.c_int, [C.c_void_p, C.c_int, _ip, _fp]),
     "mrs_debug_alpha": (C.c_int, [C.c_void_p, _fp]),
@@ -292,6 +293,17 @@ class Controller:
         ee = np.zeros((len(q), 12), np.float32)
         sph = np.zeros((len(q), a.n_spheres, 4), np.float32)
         self._check(self.L.mrs_fk(self.h, arm, len(q), _pf(q), _pf(ee), _pf(sph)), "fk")
+        return ee, sph
+
+    def fk_static(self, arm, q):
+        """mrs_fk_static: forward kinematics staged in the library's static
+        device scratch, for callers that cannot allocate device memory."""
+        a = self.sc.arms[arm]
+        q = _f32(q).reshape(-1, a.dof)
+        ee = np.zeros((len(q), 12), np.float32)
+        sph = np.zeros((len(q), a.n_spheres, 4), np.float32)
+        self._check(self.L.mrs_fk_static(self.h, arm, len(q), _pf(q), _pf(ee), _pf(sph)),
+                    "fk_static")
         return ee, sph
 
     def goal_pose(self, arm, q):
