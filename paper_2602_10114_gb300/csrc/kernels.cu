@@ -113,28 +113,31 @@ __global__ void k_prep(Params P, Dev D)
     const long long cycle = *D.cycle;
     float *Sig = D.Sigma + A.off_hdd;
     float *mu = D.mu + A.off_hd;
+    float *sS = sm, *sL = sm + H * dd, *sM = sm + 2 * H * dd;
 
     // Shift (not before the first cycle): phi_h <- phi_{h+1}; the last step
-    // keeps its mean and restarts from sigma_init^2 I.
-    if (cycle > 0) {
-        float *sS = sm, *sM = sm + H * dd;
-        for (int i = threadIdx.x; i < H * dd; i += blockDim.x) sS[i] = Sig[i];
-        for (int i = threadIdx.x; i < H * d; i += blockDim.x) sM[i] = mu[i];
-        __syncthreads();
-        const float s2 = P.sigma_init * P.sigma_init;
-        for (int i = threadIdx.x; i < H * dd; i += blockDim.x) {
-            const int h = i / dd, k = i % dd;
-            Sig[i] = (h + 1 < H) ? sS[i + dd] : ((k % (d + 1) == 0) ? s2 : 0.f);
-        }
-        for (int i = threadIdx.x; i < H * d; i += blockDim.x) {
-            const int h = i / d;
-            mu[i] = (h + 1 < H) ? sM[i + d] : sM[i];
-        }
-        __syncthreads();
+    // keeps its mean and restarts from sigma_init^2 I.  Staged in shared memory.
+    const bool shift = cycle > 0;
+    const float s2 = P.sigma_init * P.sigma_init;
+    for (int i = threadIdx.x; i < H * dd; i += blockDim.x) {
+        const int h = i / dd, k = i % dd;
+        sS[i] = !shift ? Sig[i] : (h + 1 < H ? Sig[i + dd] : ((k % (d + 1) == 0) ? s2 : 0.f));
     }
-    // Cholesky factor of every step's covariance.
-    for (int h = threadIdx.x; h < H; h += blockDim.x)
-        cholesky_fp32(d, Sig + h * dd, D.L + A.off_hdd + h * dd);
+    for (int i = threadIdx.x; i < H * d; i += blockDim.x) {
+        const int h = i / d;
+        sM[i] = (shift && h + 1 < H) ? mu[i + d] : mu[i];
+    }
+    if (a == 0)   // rollout tile counters of this cycle's iterations
+        for (int i = threadIdx.x; i < P.iterations; i += blockDim.x) D.work[i] = 0;
+    __syncthreads();
+    if (shift) {
+        for (int i = threadIdx.x; i < H * dd; i += blockDim.x) Sig[i] = sS[i];
+        for (int i = threadIdx.x; i < H * d; i += blockDim.x) mu[i] = sM[i];
+    }
+    // Cholesky factor of every step's covariance (in shared memory).
+    for (int h = threadIdx.x; h < H; h += blockDim.x) cholesky_fp32(d, sS + h * dd, sL + h * dd);
+    __syncthreads();
+    for (int i = threadIdx.x; i < H * dd; i += blockDim.x) D.L[A.off_hdd + i] = sL[i];
 
     // Sense: distance of the end effector to the goal, from the measured q.
     __shared__ float e_self;
@@ -161,7 +164,7 @@ __global__ void k_prep(Params P, Dev D)
 // ---------------------------------------------------------------------------
 // SampleControls + integration (one block per (arm, 32 samples))
 
-__global__ void __launch_bounds__(256) k_sample(Params P, Dev D, const SampleTile *tiles, int iter)
+__global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTile *tiles, int iter)
 {
     extern __shared__ float sm[];
     const SampleTile T = tiles[blockIdx.x];
@@ -230,236 +233,6 @@ __global__ void __launch_bounds__(256) k_sample(Params P, Dev D, const SampleTil
 }
 
 // ---------------------------------------------------------------------------
-// Rollout costs (one block per (arm, step h, 32 samples); warp g owns sphere
-// group g = spheres [g*spg, (g+1)*spg) of those 32 rollout steps)
-
-struct RolloutSmem {
-    float4 *sph;      // [ns] local centre + radius
-    int *frame;       // [ns]
-    int *start;       // [ns] self-pair start
-    float4 *world;    // [n_world] at the step's time
-    float4 *aabb;     // [2 * n_aabb]
-    float4 *plan;     // neighbours' plan spheres at step h, concatenated
-    int *nb_start;    // [n_nb + 1]
-    float *nb_alpha;  // [n_nb]
-    float *own;       // [ns][3][32] own sphere centres
-    int *red;         // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
-};
-
-// Candidate test of one pair: only pairs within the ramp of the cost
-// (centre distance < r1 + r2 + B) can change it; those get the exact
-// distance.  m is the running minimum of the signed distance.
-__device__ __forceinline__ void pair_min(float3 c, float rB, float r, float4 p, float &m)
-{
-    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
-    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float t = __fadd_rn(rB, p.w);
-    if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
-}
-
-template <int SPG>
-__device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmDev &A,
-                                              const RolloutSmem &S, int h, int n, bool valid,
-                                              int g, int lane, int n_world, int n_aabb, int n_nb,
-                                              float *pose_out)
-{
-    const int d = A.dof, ns = A.ns, K = A.K;
-    const int s0 = g * SPG;
-    const int cnt = max(0, min(SPG, ns - s0));
-    // joint positions of this rollout step, read per frame (coalesced over n)
-    const float *qh = D.traj + A.off_khd + (long long)h * d * K + (valid ? n : 0);
-
-    // DH chain up to the last frame this group needs (the last group always
-    // runs to the end effector for the pose cost).
-    float cx[SPG], cy[SPG], cz[SPG], rr[SPG];
-    Frame F;
-    frame_base(A, F);
-    int f = 0;
-#pragma unroll
-    for (int s = 0; s < SPG; ++s) {
-        if (s < cnt) {
-            const int fs = S.frame[s0 + s];
-            while (f < fs) {
-                frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
-                ++f;
-            }
-            const float4 p = S.sph[s0 + s];
-            const float3 c = sphere_centre(F, p);
-            cx[s] = c.x; cy[s] = c.y; cz[s] = c.z; rr[s] = p.w;
-            S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
-            S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
-            S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
-        } else {
-            cx[s] = cy[s] = cz[s] = 1e15f;
-            rr[s] = 0.f;
-        }
-    }
-    if (g == kGroups - 1) {
-        while (f < d) {
-            frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
-            ++f;
-        }
-        const float *in = D.input + A.off_in;
-        *pose_out = pose_cost(F, in + 2 * d, in + 2 * d + 3, P.w_rot);
-    }
-
-    // world clearance: spheres, then boxes
-    if (cnt > 0) {
-        float m = kInf;
-        float rB[SPG];
-#pragma unroll
-        for (int s = 0; s < SPG; ++s) rB[s] = __fadd_rn(rr[s], P.B_world);
-        for (int k = 0; k < n_world; ++k) {
-            const float4 o = S.world[k];
-#pragma unroll
-            for (int s = 0; s < SPG; ++s) pair_min(make_float3(cx[s], cy[s], cz[s]), rB[s], rr[s], o, m);
-        }
-        for (int b = 0; b < n_aabb; ++b) {
-            const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
-#pragma unroll
-            for (int s = 0; s < SPG; ++s)
-                if (s < cnt) m = fminf(m, sphere_aabb(make_float3(cx[s], cy[s], cz[s]), rr[s], bc, bh));
-        }
-        if (m < P.B_world) atomicMin(&S.red[0 * 32 + lane], float_to_ordered(m));
-
-        // coordination: every published neighbour plan at this step
-#pragma unroll
-        for (int s = 0; s < SPG; ++s) rB[s] = __fadd_rn(rr[s], P.B);
-        for (int nb = 0; nb < n_nb; ++nb) {
-            float mn = kInf;
-            const int k1 = S.nb_start[nb + 1];
-            for (int k = S.nb_start[nb]; k < k1; ++k) {
-                const float4 p = S.plan[k];
-#pragma unroll
-                for (int s = 0; s < SPG; ++s) pair_min(make_float3(cx[s], cy[s], cz[s]), rB[s], rr[s], p, mn);
-            }
-            if (mn < P.B) atomicMin(&S.red[(2 + nb) * 32 + lane], float_to_ordered(mn));
-        }
-    }
-    __syncthreads();   // own sphere centres of all groups are in shared memory
-
-    // self collision: own spheres against later spheres on bodies >= 3 apart
-    if (cnt > 0) {
-        float m = kInf;
-#pragma unroll
-        for (int s = 0; s < SPG; ++s) {
-            if (s < cnt) {
-                const float rB = __fadd_rn(rr[s], P.B_self);
-                const float3 c = make_float3(cx[s], cy[s], cz[s]);
-                for (int k = S.start[s0 + s]; k < ns; ++k) {
-                    const float4 p = make_float4(S.own[(k * 3 + 0) * 32 + lane],
-                                                 S.own[(k * 3 + 1) * 32 + lane],
-                                                 S.own[(k * 3 + 2) * 32 + lane], S.sph[k].w);
-                    pair_min(c, rB, rr[s], p, m);
-                }
-            }
-        }
-        if (m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
-    }
-}
-
-__global__ void __launch_bounds__(kRolloutThreads) k_rollout(Params P, Dev D,
-                                                             const RolloutTile *tiles, int iter)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const RolloutTile T = tiles[blockIdx.x];
-    const ArmDev &A = D.arms[T.arm];
-    const int ns = A.ns, h = T.h;
-    const int n_world = D.world_n[0], n_aabb = D.world_n[1];
-    const int NA = P.n_arms;
-
-    // shared-memory carve (sizes bounded by the build limits)
-    RolloutSmem S;
-    unsigned char *p = smraw;
-    S.world = (float4 *)p;  p += sizeof(float4) * kMaxWorld;
-    S.aabb = (float4 *)p;   p += sizeof(float4) * 2 * kMaxAabb;
-    S.sph = (float4 *)p;    p += sizeof(float4) * kMaxSpheres;
-    S.plan = (float4 *)p;   p += sizeof(float4) * (size_t)P.max_ns * NA;
-    S.own = (float *)p;     p += sizeof(float) * kMaxSpheres * 3 * 32;
-    S.frame = (int *)p;     p += sizeof(int) * kMaxSpheres;
-    S.start = (int *)p;     p += sizeof(int) * kMaxSpheres;
-    S.nb_start = (int *)p;  p += sizeof(int) * (MRS_MAX_ARMS + 1);
-    S.nb_alpha = (float *)p; p += sizeof(float) * MRS_MAX_ARMS;
-    S.red = (int *)p;
-
-    __shared__ int s_nb_arm[MRS_MAX_ARMS];
-    __shared__ int s_nnb;
-    if (threadIdx.x == 0) {
-        int nnb = 0, tot = 0;
-        for (int i = 0; i < NA; ++i) {
-            if (i == T.arm || !D.board_valid[i]) continue;
-            const ArmDev &Ai = D.arms[i];
-            if (h >= Ai.H) continue;                 // min(H_j, H_i) rule
-            s_nb_arm[nnb] = i;
-            S.nb_start[nnb] = tot;
-            S.nb_alpha[nnb] = D.alpha[T.arm * NA + i];
-            tot += Ai.ns;
-            ++nnb;
-        }
-        S.nb_start[nnb] = tot;
-        s_nnb = nnb;
-    }
-    const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
-    for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
-        const float4 o = D.world[k], v = D.world_vel[k];
-        S.world[k] = make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
-                                 __fmaf_rn(v.z, t_h, o.z), o.w);
-    }
-    for (int k = threadIdx.x; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-        S.sph[k] = A.sph[k];
-        S.frame[k] = A.frame[k];
-        S.start[k] = A.self_start[k];
-    }
-    __syncthreads();
-    const int n_nb = s_nnb;
-    for (int nb = 0; nb < n_nb; ++nb) {
-        const ArmDev &Ai = D.arms[s_nb_arm[nb]];
-        const float4 *src = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
-        for (int k = threadIdx.x; k < Ai.ns; k += blockDim.x) S.plan[S.nb_start[nb] + k] = src[k];
-    }
-    for (int k = threadIdx.x; k < (2 + n_nb) * 32; k += blockDim.x) S.red[k] = float_to_ordered(kInf);
-    __syncthreads();
-
-    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = T.n0 + lane;
-    const bool valid = n < A.K;
-    __shared__ float s_pose[32];
-    float pose = 0.f;
-    switch (A.spg) {
-        case 1: rollout_group<1>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        case 2: rollout_group<2>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        case 3: rollout_group<3>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        case 4: rollout_group<4>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        case 5: rollout_group<5>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        case 6: rollout_group<6>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        case 7: rollout_group<7>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        default: rollout_group<8>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-    }
-    if (g == kGroups - 1) s_pose[lane] = pose;
-    __syncthreads();
-
-    // stage cost of Eq. 5 plus the prioritised coordination term
-    if (g == 0 && valid) {
-        const long long idx = A.off_kh + (long long)h * A.K + n;
-        const float dw = ordered_to_float(S.red[0 * 32 + lane]);
-        const float dsf = ordered_to_float(S.red[1 * 32 + lane]);
-        float dyn = 0.f;
-        for (int nb = 0; nb < n_nb; ++nb) {
-            const float rho = fmaxf(ordered_to_float(S.red[(2 + nb) * 32 + lane]), 0.f);
-            dyn = __fmaf_rn(S.nb_alpha[nb], ramp(rho, P.B), dyn);
-        }
-        float c = __fmul_rn(P.w_pose, s_pose[lane]);
-        c = __fadd_rn(c, D.stage_lim[idx]);
-        c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
-        c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
-        c = __fmaf_rn(P.w_dyn, dyn, c);
-        D.stage[idx] = c;
-    }
-    (void)iter;
-}
-
-// ---------------------------------------------------------------------------
 // Eq. 1: C_n = sum_h gamma^h C_{n,h}, compensated (Kahan) summation.
 
 __global__ void __launch_bounds__(256) k_costs(Params P, Dev D, const CostTile *tiles)
@@ -470,12 +243,20 @@ __global__ void __launch_bounds__(256) k_costs(Params P, Dev D, const CostTile *
     if (n >= A.K) return;
     const float *st = D.stage + A.off_kh;
     float s = 0.f, c = 0.f;
-    for (int h = 0; h < A.H; ++h) {
-        const float gh = (P.gamma == 1.f) ? 1.f : powf(P.gamma, (float)h);
-        const float y = __fsub_rn(__fmul_rn(gh, st[(long long)h * A.K + n]), c);
-        const float t = __fadd_rn(s, y);
-        c = __fsub_rn(__fsub_rn(t, s), y);
-        s = t;
+    for (int h0 = 0; h0 < A.H; h0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)       // loads first, then the ordered sum
+            v[u] = (h0 + u < A.H) ? st[(long long)(h0 + u) * A.K + n] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (h0 + u >= A.H) break;
+            const float gh = (P.gamma == 1.f) ? 1.f : powf(P.gamma, (float)(h0 + u));
+            const float y = __fsub_rn(__fmul_rn(gh, v[u]), c);
+            const float t = __fadd_rn(s, y);
+            c = __fsub_rn(__fsub_rn(t, s), y);
+            s = t;
+        }
     }
     D.costs[A.off_k + n] = s;
 }
@@ -496,23 +277,26 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_update(Params P, Dev D, const UpdateTile *tiles, int last)
+__global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTile *tiles, int last)
 {
+    constexpr int NT = 128;
+    constexpr int kM2 = kMoments - kMaxDof;
     const UpdateTile T = tiles[blockIdx.x];
     const ArmDev &A = D.arms[T.arm];
     const int d = A.dof, K = A.K, h = T.h, dd = d * d;
     const float *C = D.costs + A.off_k;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT >> 5;
     __shared__ float s_v[32];
     __shared__ int s_i[32];
     __shared__ float s_beta, s_Z;
     __shared__ int s_best;
-    __shared__ float s_mom[8][kMoments];
+    __shared__ float s_part[kMoments + 1][NT + 1];   // per-thread partial moments and Z
+    __shared__ float s_mom[kMoments + 1];
 
     // minimum cost and its lowest index
     float bv = kInf;
     int bi = 0x7fffffff;
-    for (int n = threadIdx.x; n < K; n += blockDim.x) {
+    for (int n = threadIdx.x; n < K; n += NT) {
         const float v = C[n];
         if (v < bv || (v == bv && n < bi)) { bv = v; bi = n; }
     }
@@ -536,15 +320,16 @@ __global__ void __launch_bounds__(256) k_update(Params P, Dev D, const UpdateTil
     const float beta = s_beta;
     const float inv_lambda = __frcp_rn(P.lambda);
 
-    // normaliser Z = sum_n exp(-(C_n - beta)/lambda) and the moments of eps
+    // per-thread partial normaliser Z = sum_n exp(-(C_n - beta)/lambda) and
+    // weighted moments of eps at this step
     float z = 0.f;
-    float m1[kMaxDof], m2[kMoments - kMaxDof];
+    float m1[kMaxDof], m2[kM2];
 #pragma unroll
     for (int j = 0; j < kMaxDof; ++j) m1[j] = 0.f;
 #pragma unroll
-    for (int k = 0; k < kMoments - kMaxDof; ++k) m2[k] = 0.f;
+    for (int k = 0; k < kM2; ++k) m2[k] = 0.f;
     const float *eps = D.eps + A.off_khd + (long long)h * d * K;
-    for (int n = threadIdx.x; n < K; n += blockDim.x) {
+    for (int n = threadIdx.x; n < K; n += NT) {
         const float w = expf(-__fmul_rn(__fsub_rn(C[n], beta), inv_lambda));
         z = __fadd_rn(z, w);
         float e[kMaxDof];
@@ -562,58 +347,60 @@ __global__ void __launch_bounds__(256) k_update(Params P, Dev D, const UpdateTil
             }
         }
     }
-    z = warp_sum(z);
-    if (lane == 0) s_v[warp] = z;
+    // block reduction through shared memory, in a fixed order
 #pragma unroll
-    for (int j = 0; j < kMaxDof; ++j) {
-        const float v = warp_sum(m1[j]);
-        if (lane == 0) s_mom[warp][j] = v;
-    }
+    for (int j = 0; j < kMaxDof; ++j) s_part[j][threadIdx.x] = m1[j];
 #pragma unroll
-    for (int k = 0; k < kMoments - kMaxDof; ++k) {
-        const float v = warp_sum(m2[k]);
-        if (lane == 0) s_mom[warp][kMaxDof + k] = v;
+    for (int k = 0; k < kM2; ++k) s_part[kMaxDof + k][threadIdx.x] = m2[k];
+    s_part[kMoments][threadIdx.x] = z;
+    __syncthreads();
+    for (int c = warp; c <= kMoments; c += nw) {
+        float v = 0.f;
+        for (int t = lane; t < NT; t += 32) v = __fadd_rn(v, s_part[c][t]);
+        v = warp_sum(v);
+        if (lane == 0) s_mom[c] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float Z = 0.f;
-        for (int w = 0; w < nw; ++w) Z = __fadd_rn(Z, s_v[w]);
-        s_Z = Z;
-    }
-    if (threadIdx.x < kMoments) {
-        float v = 0.f;
-        for (int w = 0; w < nw; ++w) v = __fadd_rn(v, s_mom[w][threadIdx.x]);
-        s_mom[0][threadIdx.x] = v;
-    }
+    if (threadIdx.x == 0) s_Z = s_mom[kMoments];
     __syncthreads();
 
-    if (threadIdx.x == 0) {
-        const float invZ = __frcp_rn(s_Z);
-        float *mu = D.mu + A.off_hd + h * d;
-        float *Sig = D.Sigma + A.off_hdd + h * dd;
-        float delta[kMaxDof];
-        for (int j = 0; j < d; ++j) delta[j] = __fmul_rn(s_mom[0][j], invZ);
-        // PickBest on the last iteration: U_* = mu_1 + eps_{n*,1} (old mean)
-        if (last && h == 0) {
-            const float *e0 = D.eps + A.off_khd;
-            for (int j = 0; j < d; ++j)
-                D.out[D.out_u + A.off_d + j] = __fadd_rn(mu[j], e0[(long long)j * K + s_best]);
+    const float invZ = __frcp_rn(s_Z);
+    float *mu = D.mu + A.off_hd + h * d;
+    float *Sig = D.Sigma + A.off_hdd + h * dd;
+    // PickBest on the last iteration: U_* = mu_1 + eps_{n*,1} (before the update)
+    if (last && h == 0 && threadIdx.x < d) {
+        const int j = threadIdx.x;
+        const float *e0 = D.eps + A.off_khd;
+        D.out[D.out_u + A.off_d + j] = __fadd_rn(mu[j], e0[(long long)j * K + s_best]);
+        if (j == 0) {
             D.out[D.out_min + T.arm] = beta;
             D.n_star[T.arm] = s_best;
         }
-        for (int j = 0; j < d; ++j) mu[j] = __fmaf_rn(P.alpha_mu, delta[j], mu[j]);
-        int k = 0;
-        for (int j = 0; j < d; ++j)
-            for (int c = 0; c <= j; ++c) {
-                const float st = __fsub_rn(__fmul_rn(s_mom[0][kMaxDof + k], invZ),
-                                           __fmul_rn(delta[j], delta[c]));
-                const float nv = __fmaf_rn(P.alpha_sigma, st,
-                                           __fmul_rn(1.f - P.alpha_sigma, Sig[j * d + c]));
-                Sig[j * d + c] = nv;
-                Sig[c * d + j] = nv;
-                ++k;
-            }
-        if (!last) cholesky_fp32(d, Sig, D.L + A.off_hdd + h * dd);
+    }
+    __syncthreads();
+    // Eq. 4 with Eq. 3 written through eps: delta = S1/Z, Sigma~ = S2/Z - delta delta^T
+    if (threadIdx.x < d) {
+        const int j = threadIdx.x;
+        mu[j] = __fmaf_rn(P.alpha_mu, __fmul_rn(s_mom[j], invZ), mu[j]);
+    }
+    for (int t = threadIdx.x; t < d * (d + 1) / 2; t += NT) {
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int c = t - j * (j + 1) / 2;
+        const float dj = __fmul_rn(s_mom[j], invZ), dc = __fmul_rn(s_mom[c], invZ);
+        const float st = __fsub_rn(__fmul_rn(s_mom[kMaxDof + t], invZ), __fmul_rn(dj, dc));
+        const float nv = __fmaf_rn(P.alpha_sigma, st, __fmul_rn(1.f - P.alpha_sigma, Sig[j * d + c]));
+        Sig[j * d + c] = nv;
+        Sig[c * d + j] = nv;
+    }
+    if (!last) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float S[kMaxDof * kMaxDof], Lh[kMaxDof * kMaxDof];
+            for (int k = 0; k < dd; ++k) S[k] = Sig[k];
+            cholesky_fp32(d, S, Lh);
+            for (int k = 0; k < dd; ++k) D.L[A.off_hdd + h * dd + k] = Lh[k];
+        }
     }
 }
 
@@ -624,16 +411,19 @@ __global__ void __launch_bounds__(256) k_update(Params P, Dev D, const UpdateTil
 
 __global__ void k_toplan(Params P, Dev D, int *done_counter)
 {
-    extern __shared__ float sq[];   // [H][d]
+    extern __shared__ float sq[];   // [H][d] plan joints, then [H][d] mean
     const int a = blockIdx.x;
     const ArmDev &A = D.arms[a];
     const int d = A.dof, H = A.H, ns = A.ns;
+    float *smu = sq + H * d;
     const float *mu = D.mu + A.off_hd;
     const float *in = D.input + A.off_in;
+    for (int i = threadIdx.x; i < H * d; i += blockDim.x) smu[i] = mu[i];
+    __syncthreads();
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         float q = in[j], qd = in[d + j];
         for (int h = 0; h < H; ++h) {
-            integrate(q, qd, mu[h * d + j], P.dt);
+            integrate(q, qd, smu[h * d + j], P.dt);
             sq[h * d + j] = q;
         }
     }
@@ -641,15 +431,19 @@ __global__ void k_toplan(Params P, Dev D, int *done_counter)
     for (int i = threadIdx.x; i < H * d; i += blockDim.x) {
         D.board_q[A.off_hd + i] = sq[i];
         D.out[D.out_q + A.off_hd + i] = sq[i];
-        D.out[D.out_mean + A.off_hd + i] = mu[i];
+        D.out[D.out_mean + A.off_hd + i] = smu[i];
     }
+    // kinematics: one thread per (step, group of 8 spheres), the same chain
+    // and sphere arithmetic as the rollout
     float4 *board = D.board_sph + (A.off_hs >> 2);
     float4 *outs = (float4 *)(D.out + D.out_sph) + (A.off_hs >> 2);
-    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+    const int ng = (ns + 7) / 8;
+    for (int t = threadIdx.x; t < H * ng; t += blockDim.x) {
+        const int h = t / ng, s0 = (t % ng) * 8, s1 = min(ns, s0 + 8);
         Frame F;
         frame_base(A, F);
         int f = 0;
-        for (int s = 0; s < ns; ++s) {
+        for (int s = s0; s < s1; ++s) {
             const int fs = A.frame[s];
             while (f < fs) {
                 frame_step(F, sq[h * d + f], A.dh[f], A.twist[f]);
@@ -746,9 +540,7 @@ __global__ void k_philox(int n, const uint4 *ctr, uint2 key, uint4 *out)
 cudaError_t configure_kernels(const LaunchPlan &L)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)L.smem_rollout)) != cudaSuccess)
-        return e;
+    if ((e = configure_rollout(L)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)L.smem_sample)) != cudaSuccess)
         return e;
@@ -777,21 +569,20 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
                         : cudaEventRecord(events[ev++], s);
     };
     mark();
-    k_prep<<<L.n_arms, 256, L.smem_prep, s>>>(P, D);
+    k_prep<<<L.n_arms, 128, L.smem_prep, s>>>(P, D);
     mark();
     for (int it = 0; it < P.iterations; ++it) {
         const int last = (it == P.iterations - 1);
-        k_sample<<<L.n_sample_tiles, 256, L.smem_sample, s>>>(P, D, L.sample_tiles, it);
+        k_sample<<<L.n_sample_tiles, 512, L.smem_sample, s>>>(P, D, L.sample_tiles, it);
         mark();
-        k_rollout<<<L.n_rollout_tiles, kRolloutThreads, L.smem_rollout, s>>>(P, D, L.rollout_tiles,
-                                                                            it);
+        if ((rec = launch_rollout(P, D, L, it, s)) != cudaSuccess) return rec;
         mark();
         k_costs<<<L.n_cost_tiles, 256, 0, s>>>(P, D, L.cost_tiles);
         mark();
-        k_update<<<L.n_update_tiles, 256, 0, s>>>(P, D, L.update_tiles, last);
+        k_update<<<L.n_update_tiles, 128, 0, s>>>(P, D, L.update_tiles, last);
         mark();
     }
-    k_toplan<<<L.n_arms, 128, L.smem_toplan, s>>>(P, D, L.done_counter);
+    k_toplan<<<L.n_arms, 256, L.smem_toplan, s>>>(P, D, L.done_counter);
     mark();
     if (rec != cudaSuccess) return rec;
     return cudaGetLastError();

@@ -17,8 +17,17 @@ struct LaunchPlan {
     const CostTile *cost_tiles;
     const UpdateTile *update_tiles;
     size_t smem_prep, smem_sample, smem_rollout, smem_toplan;
+    int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)
     int *done_counter;  // last-block-done counter of k_toplan
 };
+
+// The rollout kernel (rollout.cu): shared-memory size for the given
+// capacities, attribute set-up and launch.
+size_t rollout_smem_bytes(const Params &P, int n_arms);
+cudaError_t configure_rollout(const LaunchPlan &L);
+int rollout_blocks_per_sm(size_t smem);
+cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
+                           cudaStream_t s);
 
 // Everything one control cycle enqueues on `s` (Algorithm 1 for all arms).
 // With `events` non-null, events[0] is recorded before the first kernel and

@@ -1,7 +1,9 @@
 // mrs_capi.cu -- the C ABI declared in include/mrs.h: context, validation,
 // workspace layout, work lists, CUDA-graph capture, bounded waits, state
 // checkpointing.  All arithmetic of the method runs in kernels.cu.
+#include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -40,12 +42,14 @@ struct mrs_ctx {
         size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
             board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
             e_now, n_star, out, cycle, world_t, err, done_counter, sample_tiles, rollout_tiles,
-            cost_tiles, update_tiles, total;
+            cost_tiles, update_tiles, self_pairs, work, total;
     } lay{};
     std::vector<SampleTile> sample_tiles;
     std::vector<RolloutTile> rollout_tiles;
     std::vector<CostTile> cost_tiles;
     std::vector<UpdateTile> update_tiles;
+    std::vector<int> self_pairs;
+    int num_sms = 0;
 };
 
 static const char *g_noctx = "null context";
@@ -123,6 +127,8 @@ static void build_layout(mrs_ctx *c)
     L.rollout_tiles = take(sizeof(RolloutTile) * c->rollout_tiles.size());
     L.cost_tiles = take(sizeof(CostTile) * c->cost_tiles.size());
     L.update_tiles = take(sizeof(UpdateTile) * c->update_tiles.size());
+    L.self_pairs = take(sizeof(int) * std::max<size_t>(1, c->self_pairs.size()));
+    L.work = take(sizeof(int) * 64);
     L.total = align_up(o, 256);
     c->sz.workspace_bytes = L.total;
 }
@@ -187,6 +193,8 @@ static void fill_dev(mrs_ctx *c, char *base)
     c->L.rollout_tiles = (const RolloutTile *)(base + L.rollout_tiles);
     c->L.cost_tiles = (const CostTile *)(base + L.cost_tiles);
     c->L.update_tiles = (const UpdateTile *)(base + L.update_tiles);
+    D.self_pairs = (int *)(base + L.self_pairs);
+    D.work = (int *)(base + L.work);
 }
 
 static void out_offsets(mrs_ctx *c)
@@ -254,6 +262,14 @@ static mrs_status validate(const mrs_config *cfg, std::string &why)
     return MRS_OK;
 }
 
+static void invalidate_graph(mrs_ctx *ctx)
+{
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+}
+
 extern "C" {
 
 mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
@@ -280,7 +296,8 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
 
     size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
     long long khd = 0, kh = 0;
-    int max_ns = 0;
+    int max_ns = 0, max_pairs = 0;
+    float ws_radius = 0.f;
     ctx->arms.resize(ctx->A);
     for (int a = 0; a < ctx->A; ++a) {
         const mrs_arm_desc &d = cfg->arms[a];
@@ -302,11 +319,24 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
             A.body[s] = d.sphere_body[s];
             A.frame[s] = std::min(d.sphere_body[s], d.dof);
         }
-        for (int s = 0; s < d.n_spheres; ++s) {
-            int k = s + 1;
-            while (k < d.n_spheres && d.sphere_body[k] < d.sphere_body[s] + 3) ++k;
-            A.self_start[s] = k;
+        // self-collision pairs: bodies at least three apart
+        A.self_off = (int)ctx->self_pairs.size();
+        for (int s1 = 0; s1 < d.n_spheres; ++s1)
+            for (int s2 = s1 + 1; s2 < d.n_spheres; ++s2)
+                if (std::abs(d.sphere_body[s1] - d.sphere_body[s2]) >= 3)
+                    ctx->self_pairs.push_back(s1 | (s2 << 8));
+        A.n_self = (int)ctx->self_pairs.size() - A.self_off;
+        max_pairs = std::max(max_pairs, A.n_self);
+        // workspace radius for the cancellation margin of the pair pre-test
+        float reach = 0.f, tool = 0.f;
+        for (int j = 0; j < d.dof; ++j) reach += std::fabs(d.dh[4 * j]) + std::fabs(d.dh[4 * j + 1]);
+        for (int s2 = 0; s2 < d.n_spheres; ++s2) {
+            const float *v = d.sphere_xyzr + 4 * s2;
+            tool = std::max(tool, std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + v[3]);
         }
+        const float *b = d.base_pose;
+        ws_radius = std::max(ws_radius, std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]) +
+                                            reach + tool + 0.3f);
         hd += (size_t)d.H * d.dof;
         hdd += (size_t)d.H * d.dof * d.dof;
         hs += (size_t)d.H * d.n_spheres * 4;
@@ -318,6 +348,13 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         max_ns = std::max(max_ns, d.n_spheres);
     }
     P.max_ns = max_ns;
+    P.max_pairs = std::max(max_pairs, 1);
+    P.world_cap = 64;
+    P.aabb_cap = 8;
+    // The expanded pre-test g = |c-p|^2 - t^2 carries rounding of order
+    // 2^-24 times the squared coordinates (<= ws_radius^2, four FMAs and two
+    // precomputed terms); 64 units of it is a safe margin.
+    P.eps_g = std::max(1e-6f, 64.f * 5.9604645e-8f * ws_radius * ws_radius);
     ctx->sz.n_arms = ctx->A;
     ctx->sz.hd = hd; ctx->sz.hdd = hdd; ctx->sz.hs = hs; ctx->sz.d = dsum; ctx->sz.k = ksum;
     ctx->sz.input_floats = in;
@@ -336,18 +373,14 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     L.n_update_tiles = (int)ctx->update_tiles.size();
     size_t sp = 0, ss = 0, st2 = 0;
     for (auto &A : ctx->arms) {
-        sp = std::max(sp, sizeof(float) * (size_t)A.H * (A.dof * A.dof + A.dof));
+        sp = std::max(sp, sizeof(float) * (size_t)A.H * (2 * A.dof * A.dof + A.dof));
         ss = std::max(ss, sizeof(float) * (size_t)A.H * (A.dof * A.dof + 2 * A.dof * 32));
-        st2 = std::max(st2, sizeof(float) * (size_t)A.H * A.dof);
+        st2 = std::max(st2, sizeof(float) * (size_t)A.H * 2 * A.dof);
     }
     L.smem_prep = sp;
     L.smem_sample = ss;
     L.smem_toplan = st2;
-    L.smem_rollout = sizeof(float4) * MRS_MAX_WORLD_SPHERES + sizeof(float4) * 2 * MRS_MAX_AABBS +
-                     sizeof(float4) * kMaxSpheres + sizeof(float4) * (size_t)max_ns * ctx->A +
-                     sizeof(float) * kMaxSpheres * 3 * 32 + sizeof(int) * kMaxSpheres * 2 +
-                     sizeof(int) * (MRS_MAX_ARMS + 1) + sizeof(float) * MRS_MAX_ARMS +
-                     sizeof(int) * (2 + MRS_MAX_ARMS) * 32;
+    L.smem_rollout = rollout_smem_bytes(P, ctx->A);
 
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
@@ -368,10 +401,14 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         mrs_destroy(ctx);
         return MRS_ENOMEM;
     }
-    if (configure_kernels(L) != cudaSuccess) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        configure_kernels(L) != cudaSuccess) {
         mrs_destroy(ctx);
         return MRS_ECUDA;
     }
+    L.rollout_grid = rollout_blocks_per_sm(L.smem_rollout) * ctx->num_sms;
     *out = ctx;
     return MRS_OK;
 }
@@ -408,14 +445,6 @@ mrs_status mrs_workspace_size(const mrs_ctx *ctx, size_t *bytes)
     return MRS_OK;
 }
 
-static void invalidate_graph(mrs_ctx *ctx)
-{
-    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-    if (ctx->graph) cudaGraphDestroy(ctx->graph);
-    ctx->gexec = nullptr;
-    ctx->graph = nullptr;
-}
-
 static mrs_status bind(mrs_ctx *ctx, void *dev, size_t bytes)
 {
     invalidate_graph(ctx);
@@ -438,7 +467,12 @@ static mrs_status bind(mrs_ctx *ctx, void *dev, size_t bytes)
     CK(cudaMemcpyAsync(base + L.update_tiles, ctx->update_tiles.data(),
                        sizeof(UpdateTile) * ctx->update_tiles.size(), cudaMemcpyHostToDevice,
                        ctx->stream), "upload tiles");
+    if (!ctx->self_pairs.empty())
+        CK(cudaMemcpyAsync(base + L.self_pairs, ctx->self_pairs.data(),
+                           sizeof(int) * ctx->self_pairs.size(), cudaMemcpyHostToDevice,
+                           ctx->stream), "upload self pairs");
     CK(cudaMemsetAsync(base + L.done_counter, 0, sizeof(int), ctx->stream), "memset");
+    CK(cudaMemsetAsync(base + L.work, 0, sizeof(int) * 64, ctx->stream), "memset");
     CK(cudaMemsetAsync(base + L.input, 0, sizeof(float) * ctx->sz.input_floats, ctx->stream),
        "memset");
     CK(cudaMemsetAsync(base + L.out, 0, sizeof(float) * ctx->sz.output_floats, ctx->stream),
@@ -487,6 +521,17 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
         return fail(ctx, MRS_EINVAL, "non-finite world");
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
+    if (n_spheres > ctx->P.world_cap || n_aabbs > ctx->P.aabb_cap) {
+        // grow the rollout's shared-memory world capacity (powers of two)
+        while (ctx->P.world_cap < n_spheres) ctx->P.world_cap *= 2;
+        while (ctx->P.aabb_cap < n_aabbs) ctx->P.aabb_cap *= 2;
+        ctx->P.world_cap = std::min(ctx->P.world_cap, MRS_MAX_WORLD_SPHERES);
+        ctx->P.aabb_cap = std::min(ctx->P.aabb_cap, MRS_MAX_AABBS);
+        ctx->L.smem_rollout = rollout_smem_bytes(ctx->P, ctx->A);
+        CK(configure_rollout(ctx->L), "rollout shared memory");
+        ctx->L.rollout_grid = rollout_blocks_per_sm(ctx->L.smem_rollout) * ctx->num_sms;
+        invalidate_graph(ctx);
+    }
     std::vector<float4> w(n_spheres), v(n_spheres), b(2 * n_aabbs);
     for (int i = 0; i < n_spheres; ++i) {
         w[i] = make_float4(spheres[4 * i], spheres[4 * i + 1], spheres[4 * i + 2], spheres[4 * i + 3]);

@@ -24,7 +24,8 @@ constexpr float kInf = __builtin_inff();
 struct __align__(16) ArmDev {
     int dof, ns, K, H;
     int off_hd, off_hdd, off_hs, off_d;   // offsets into concatenated arrays
-    int off_k, off_in, spg, pad0;         // spg: spheres per group (ceil(ns/8))
+    int off_k, off_in, spg, self_off;     // spg: spheres per group (ceil(ns/8))
+    int n_self, pad1, pad2, pad3;         // self-collision pairs at self_off in Dev::self_pairs
     long long off_khd, off_kh;            // offsets into K*H*d and K*H work arrays
     float4 dh[kMaxDof];                   // a, d, alpha, theta_offset
     float2 twist[kMaxDof];                // sin(alpha), cos(alpha)
@@ -34,7 +35,6 @@ struct __align__(16) ArmDev {
     float4 sph[kMaxSpheres];              // centre in body frame, radius
     int frame[kMaxSpheres];               // frame carrying the sphere: min(body, dof)
     int body[kMaxSpheres];
-    int self_start[kMaxSpheres];          // first sphere with body >= body + 3
 };
 
 struct Params {
@@ -43,7 +43,10 @@ struct Params {
     float w_pose, w_rot, w_stop, w_joint, w_coll, w_self, w_dyn;
     float B, B_world, B_self, tau, q_margin;
     unsigned long long seed;
-    int max_ns, pad;
+    int max_ns, max_pairs;        // largest sphere and self-pair counts of any arm
+    int world_cap, aabb_cap;      // shared-memory capacity of the rollout for the world
+    float eps_g;                  // cancellation margin of the expanded pair pre-test (m^2)
+    int pad;
 };
 
 // Device pointers into the workspace.
@@ -74,6 +77,8 @@ struct Dev {
     long long *cycle;      // completed cycles
     float *world_t;        // seconds since the world was set
     int *err;              // device error word (bounded waits)
+    int *self_pairs;       // per arm, packed s1 | s2 << 8, bodies >= 3 apart
+    int *work;             // rollout tile counters, one per iteration
     int out_mean, out_sph, out_q, out_u, out_dist, out_min;  // offsets in out (floats)
 };
 

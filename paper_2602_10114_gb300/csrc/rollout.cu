@@ -1,0 +1,335 @@
+// rollout.cu -- the Rollout step of Algorithm 1 for every arm: kinematics of
+// the collision spheres at each sampled state and the stage cost of Eq. 5
+// with the prioritised coordination term of Eq. 9 (Sec. IV-A/B).
+//
+// Work unit (tile): (arm, step h, 32 samples).  A persistent grid of 256-thread
+// blocks takes tiles from an atomic counter.  Warp g of a block owns sphere
+// group g (spheres [g*spg, (g+1)*spg), spg = ceil(N_S / 8)) of the tile's 32
+// rollout steps, one sample per lane; its centres stay in registers.
+//
+// Pair test.  A pair (own sphere c, radius r; other sphere p, radius r_p) can
+// change a ramp cost max(0, 1 - dist/B) only if |c - p| < r + r_p + B.  With
+//   g = |c - p|^2 - (r + B + r_p)^2
+//     = [|p|^2 - r_p^2] - 2 c.p - 2 (r + B) r_p + [|c|^2 - (r + B)^2]
+// the bracketed per-sphere terms are precomputed, so the inner loop is four
+// FMAs and a min per pair, without branches.  An own sphere whose minimum g
+// falls below eps_g (the FP32 cancellation margin of this expansion over the
+// workspace) gets an exact pass: direct squared distance, and the square root
+// only for pairs inside the ramp.  Since the cost is zero outside the ramp,
+// the result equals the brute-force minimum of Eq. 6 restricted to the ramp.
+#include "kernels.cuh"
+
+namespace mrs {
+
+struct RolloutSmem {
+    float4 *other;     // world spheres at the step's time, then neighbours' plan spheres
+    float *other_w;    // |p|^2 - r_p^2 of each
+    float4 *aabb;      // [2 * n_aabb] centre, half extents
+    float4 *sph;       // [ns] local centre + radius
+    int *frame;        // [ns]
+    int *pairs;        // [n_self] s1 | s2 << 8
+    float *own;        // [ns][3][32] own sphere centres of the tile
+    int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
+    int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
+    float *nb_alpha;   // [n_nb]
+};
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// exact distance of a candidate pair, as in the oracle: sqrt(d2) - r - r_p
+__device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p, float &m)
+{
+    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const float t = __fadd_rn(rB, p.w);
+    if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
+}
+
+// Minimum signed distance, inside the ramp of buffer B, between the warp's
+// own spheres and other[k0, k1).  Returns +inf when no pair is in the ramp.
+template <int SPG>
+__device__ __forceinline__ float clearance_pass(const RolloutSmem &S, int k0, int k1, float B,
+                                                float eps_g, int s0, int cnt,
+                                                const float (&mx)[SPG], const float (&my)[SPG],
+                                                const float (&mz)[SPG])
+{
+    float mr[SPG], gmin[SPG];
+#pragma unroll
+    for (int s = 0; s < SPG; ++s) {
+        mr[s] = (s < cnt) ? -2.f * __fadd_rn(S.sph[s0 + s].w, B) : 0.f;
+        gmin[s] = kInf;
+    }
+    for (int k = k0; k < k1; ++k) {
+        const float4 p = S.other[k];
+        const float w = S.other_w[k];
+#pragma unroll
+        for (int s = 0; s < SPG; ++s) {
+            const float g = __fmaf_rn(mx[s], p.x, __fmaf_rn(my[s], p.y,
+                            __fmaf_rn(mz[s], p.z, __fmaf_rn(mr[s], p.w, w))));
+            gmin[s] = fminf(gmin[s], g);
+        }
+    }
+    float m = kInf;
+#pragma unroll
+    for (int s = 0; s < SPG; ++s) {
+        if (s < cnt) {
+            // g = gmin + |c|^2 - (r + B)^2 with c = -m/2
+            const float r = S.sph[s0 + s].w;
+            const float rB = __fadd_rn(r, B);
+            const float3 c = make_float3(-0.5f * mx[s], -0.5f * my[s], -0.5f * mz[s]);
+            const float ac = __fmaf_rn(c.z, c.z, __fmaf_rn(c.y, c.y,
+                             __fmaf_rn(c.x, c.x, -__fmul_rn(rB, rB))));
+            if (__fadd_rn(gmin[s], ac) < eps_g)
+                for (int k = k0; k < k1; ++k) pair_exact(c, rB, r, S.other[k], m);
+        }
+    }
+    return m;
+}
+
+template <int SPG>
+__device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmDev &A,
+                                              const RolloutSmem &S, int h, int n, bool valid,
+                                              int g, int lane, int n_world, int n_aabb, int n_nb,
+                                              float *pose_out)
+{
+    const int d = A.dof, K = A.K;
+    const int s0 = g * SPG;
+    const int cnt = max(0, min(SPG, A.ns - s0));
+    const float *qh = D.traj + A.off_khd + (long long)h * d * K + (valid ? n : 0);
+
+    // DH chain up to the last frame this group needs; the last warp always
+    // runs to the end effector for the pose cost.
+    float mx[SPG], my[SPG], mz[SPG];
+    Frame F;
+    frame_base(A, F);
+    int f = 0;
+#pragma unroll
+    for (int s = 0; s < SPG; ++s) {
+        if (s < cnt) {
+            const int fs = S.frame[s0 + s];
+            while (f < fs) {
+                frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+                ++f;
+            }
+            const float4 p = S.sph[s0 + s];
+            const float3 c = sphere_centre(F, p);
+            mx[s] = -2.f * c.x; my[s] = -2.f * c.y; mz[s] = -2.f * c.z;
+            S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
+            S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
+            S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
+        } else {
+            mx[s] = my[s] = mz[s] = -2e15f;   // padding: never tested
+        }
+    }
+    if (g == kGroups - 1) {
+        while (f < d) {
+            frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+            ++f;
+        }
+        const float *in = D.input + A.off_in;
+        *pose_out = pose_cost(F, in + 2 * d, in + 2 * d + 3, P.w_rot);
+    }
+
+    if (cnt > 0) {
+        // world clearance: spheres (pre-tested), boxes (exact)
+        float m = clearance_pass<SPG>(S, 0, n_world, P.B_world, P.eps_g, s0, cnt, mx, my, mz);
+        for (int b = 0; b < n_aabb; ++b) {
+            const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
+#pragma unroll
+            for (int s = 0; s < SPG; ++s)
+                if (s < cnt)
+                    m = fminf(m, sphere_aabb(make_float3(-0.5f * mx[s], -0.5f * my[s],
+                                                         -0.5f * mz[s]), S.sph[s0 + s].w, bc, bh));
+        }
+        if (m < P.B_world) atomicMin(&S.red[0 * 32 + lane], float_to_ordered(m));
+        // coordination: each published neighbour plan at this step
+        for (int nb = 0; nb < n_nb; ++nb) {
+            const float mn = clearance_pass<SPG>(S, S.nb_start[nb], S.nb_start[nb + 1], P.B,
+                                                 P.eps_g, s0, cnt, mx, my, mz);
+            if (mn < P.B) atomicMin(&S.red[(2 + nb) * 32 + lane], float_to_ordered(mn));
+        }
+    }
+    __syncthreads();   // every group's centres are in shared memory
+
+    // self collision: the arm's pair list, split evenly over the 8 warps
+    {
+        const int np = A.n_self;
+        const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
+        float m = kInf;
+        for (int i = p0; i < p1; ++i) {
+            const int pr = S.pairs[i];
+            const int a1 = pr & 0xff, a2 = pr >> 8;
+            const float3 c = make_float3(S.own[(a1 * 3 + 0) * 32 + lane],
+                                         S.own[(a1 * 3 + 1) * 32 + lane],
+                                         S.own[(a1 * 3 + 2) * 32 + lane]);
+            const float4 q = make_float4(S.own[(a2 * 3 + 0) * 32 + lane],
+                                         S.own[(a2 * 3 + 1) * 32 + lane],
+                                         S.own[(a2 * 3 + 2) * 32 + lane], S.sph[a2].w);
+            const float r1 = S.sph[a1].w;
+            pair_exact(c, __fadd_rn(r1, P.B_self), r1, q, m);
+        }
+        if (m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
+    }
+}
+
+__global__ void __launch_bounds__(kRolloutThreads, 3) k_rollout(Params P, Dev D,
+                                                             const RolloutTile *tiles, int n_tiles,
+                                                             int iter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int NA = P.n_arms;
+    RolloutSmem S;
+    {
+        unsigned char *p = smraw;
+        const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * NA;
+        S.other = (float4 *)p;     p += align16(sizeof(float4) * n_other);
+        S.aabb = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.aabb_cap);
+        S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
+        S.own = (float *)p;        p += align16(sizeof(float) * P.max_ns * 3 * 32);
+        S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
+        S.frame = (int *)p;        p += align16(sizeof(int) * P.max_ns);
+        S.pairs = (int *)p;        p += align16(sizeof(int) * P.max_pairs);
+        S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
+        S.nb_alpha = (float *)p;   p += align16(sizeof(float) * MRS_MAX_ARMS);
+        S.red = (int *)p;
+    }
+    __shared__ int s_nb_arm[MRS_MAX_ARMS];
+    __shared__ int s_nnb, s_tile;
+    __shared__ float s_pose[32];
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_world = D.world_n[0], n_aabb = D.world_n[1];
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&D.work[iter], 1);
+        __syncthreads();
+        const int ti = s_tile;
+        if (ti >= n_tiles) break;
+        const RolloutTile T = tiles[ti];
+        const ArmDev &A = D.arms[T.arm];
+        const int h = T.h;
+
+        // stage the tile's inputs: neighbour list (published plans whose
+        // horizon reaches step h), world at the step's time, arm constants
+        if (threadIdx.x == 0) {
+            int nnb = 0, tot = n_world;
+            for (int i = 0; i < NA; ++i) {
+                if (i == T.arm || !D.board_valid[i]) continue;
+                const ArmDev &Ai = D.arms[i];
+                if (h >= Ai.H) continue;                 // min(H_j, H_i) rule
+                s_nb_arm[nnb] = i;
+                S.nb_start[nnb] = tot;
+                S.nb_alpha[nnb] = D.alpha[T.arm * NA + i];
+                tot += Ai.ns;
+                ++nnb;
+            }
+            S.nb_start[nnb] = tot;
+            s_nnb = nnb;
+        }
+        const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
+        for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
+            const float4 o = D.world[k], v = D.world_vel[k];
+            const float4 w = make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
+                                         __fmaf_rn(v.z, t_h, o.z), o.w);
+            S.other[k] = w;
+            S.other_w[k] = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
+                                     -__fmul_rn(w.w, w.w))));
+        }
+        for (int k = threadIdx.x; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
+        for (int k = threadIdx.x; k < A.ns; k += blockDim.x) {
+            S.sph[k] = A.sph[k];
+            S.frame[k] = A.frame[k];
+        }
+        for (int k = threadIdx.x; k < A.n_self; k += blockDim.x)
+            S.pairs[k] = D.self_pairs[A.self_off + k];
+        __syncthreads();
+        const int n_nb = s_nnb;
+        for (int nb = 0; nb < n_nb; ++nb) {
+            const ArmDev &Ai = D.arms[s_nb_arm[nb]];
+            const float4 *src = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
+            const int o = S.nb_start[nb];
+            for (int k = threadIdx.x; k < Ai.ns; k += blockDim.x) {
+                const float4 w = src[k];
+                S.other[o + k] = w;
+                S.other_w[o + k] = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
+                                             -__fmul_rn(w.w, w.w))));
+            }
+        }
+        for (int k = threadIdx.x; k < (2 + n_nb) * 32; k += blockDim.x)
+            S.red[k] = float_to_ordered(kInf);
+        __syncthreads();
+
+        const int n = T.n0 + lane;
+        const bool valid = n < A.K;
+        float pose = 0.f;
+        switch (A.spg) {
+            case 1: rollout_group<1>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            case 2: rollout_group<2>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            case 3: rollout_group<3>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            case 4: rollout_group<4>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            case 5: rollout_group<5>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            case 6: rollout_group<6>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            case 7: rollout_group<7>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            default: rollout_group<8>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+        }
+        if (g == kGroups - 1) s_pose[lane] = pose;
+        __syncthreads();
+
+        // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
+        if (g == 0 && valid) {
+            const long long idx = A.off_kh + (long long)h * A.K + n;
+            const float dw = ordered_to_float(S.red[0 * 32 + lane]);
+            const float dsf = ordered_to_float(S.red[1 * 32 + lane]);
+            float dyn = 0.f;
+            for (int nb = 0; nb < n_nb; ++nb) {
+                const float rho = fmaxf(ordered_to_float(S.red[(2 + nb) * 32 + lane]), 0.f);
+                dyn = __fmaf_rn(S.nb_alpha[nb], ramp(rho, P.B), dyn);
+            }
+            float c = __fmul_rn(P.w_pose, s_pose[lane]);
+            c = __fadd_rn(c, D.stage_lim[idx]);
+            c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
+            c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
+            c = __fmaf_rn(P.w_dyn, dyn, c);
+            D.stage[idx] = c;
+        }
+        __syncthreads();   // shared memory is reused by the next tile
+    }
+}
+
+size_t rollout_smem_bytes(const Params &P, int n_arms)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * n_arms;
+    return a16(sizeof(float4) * n_other) + a16(sizeof(float4) * 2 * P.aabb_cap) +
+           a16(sizeof(float4) * P.max_ns) + a16(sizeof(float) * P.max_ns * 3 * 32) +
+           a16(sizeof(float) * n_other) + a16(sizeof(int) * P.max_ns) +
+           a16(sizeof(int) * P.max_pairs) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +
+           a16(sizeof(float) * MRS_MAX_ARMS) + sizeof(int) * (2 + MRS_MAX_ARMS) * 32;
+}
+
+cudaError_t configure_rollout(const LaunchPlan &L)
+{
+    return cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)L.smem_rollout);
+}
+
+int rollout_blocks_per_sm(size_t smem)
+{
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rollout, kRolloutThreads, smem) !=
+            cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
+                           cudaStream_t s)
+{
+    const int grid = L.n_rollout_tiles < L.rollout_grid ? L.n_rollout_tiles : L.rollout_grid;
+    k_rollout<<<grid, kRolloutThreads, L.smem_rollout, s>>>(P, D, L.rollout_tiles,
+                                                            L.n_rollout_tiles, iter);
+    return cudaGetLastError();
+}
+
+}  // namespace mrs
