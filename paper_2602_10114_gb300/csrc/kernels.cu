@@ -104,6 +104,35 @@ __device__ void cholesky_fp32(int d, const float *S, float *L)
         for (int j = i + 1; j < d; ++j) L[i * d + j] = 0.f;
 }
 
+// The same factorisation with the factor in registers (indices unrolled to
+// the build's DoF limit): identical operations in identical order, without
+// a memory round trip on the dependent chain.
+__device__ __forceinline__ void cholesky_unrolled(int d, const float *S, float *Lout)
+{
+    float L[kMaxDof][kMaxDof];
+#pragma unroll
+    for (int i = 0; i < kMaxDof; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            L[i][j] = 0.f;
+            if (i < d) {
+                float s = S[i * d + j];
+                if (i == j) s = __fadd_rn(s, 1e-8f);
+#pragma unroll
+                for (int k = 0; k < j; ++k) s = __fmaf_rn(-L[i][k], L[j][k], s);
+                if (i == j)
+                    L[i][i] = sqrtf(s > 1e-12f ? s : 1e-12f);
+                else
+                    L[i][j] = __fdiv_rn(s, L[j][j]);
+            }
+        }
+#pragma unroll
+    for (int i = 0; i < kMaxDof; ++i)
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j)
+            if (i < d && j < d) Lout[i * d + j] = (j <= i) ? L[i][j] : 0.f;
+}
+
 __global__ void k_prep(Params P, Dev D)
 {
     extern __shared__ float sm[];
@@ -114,9 +143,18 @@ __global__ void k_prep(Params P, Dev D)
     float *Sig = D.Sigma + A.off_hdd;
     float *mu = D.mu + A.off_hd;
     float *sS = sm, *sL = sm + H * dd, *sM = sm + 2 * H * dd;
+    __shared__ float s_in[2 * kMaxDof + 12];
+    __shared__ float4 s_dh[kMaxDof];
+    __shared__ float2 s_tw[kMaxDof];
+    __shared__ float s_base[12];
+    __shared__ float s_bdist[MRS_MAX_ARMS];
+    __shared__ int s_bvalid[MRS_MAX_ARMS];
+    __shared__ float e_self;
 
-    // Shift (not before the first cycle): phi_h <- phi_{h+1}; the last step
-    // keeps its mean and restarts from sigma_init^2 I.  Staged in shared memory.
+    // one parallel wave of loads: the shifted distribution (Shift, Sec. III-A:
+    // phi_h <- phi_{h+1}, the last step keeps its mean and restarts from
+    // sigma_init^2 I; not before the first cycle), the sensed input, the arm's
+    // kinematic constants and the board's published distances
     const bool shift = cycle > 0;
     const float s2 = P.sigma_init * P.sigma_init;
     for (int i = threadIdx.x; i < H * dd; i += blockDim.x) {
@@ -127,38 +165,46 @@ __global__ void k_prep(Params P, Dev D)
         const int h = i / d;
         sM[i] = (shift && h + 1 < H) ? mu[i + d] : mu[i];
     }
+    const int t = threadIdx.x;
+    if (t < 2 * d + 12) s_in[t] = D.input[A.off_in + t];
+    if (t < d) {
+        s_dh[t] = A.dh[t];
+        s_tw[t] = A.twist[t];
+    }
+    if (t < 9) s_base[t] = A.base_R[t];
+    else if (t < 12) s_base[t] = A.base_t[t - 9];
+    if (t < P.n_arms) {
+        s_bvalid[t] = D.board_valid[t];
+        s_bdist[t] = D.board_dist[t];
+    }
     if (a == 0)   // rollout tile counters of this cycle's iterations
-        for (int i = threadIdx.x; i < P.iterations; i += blockDim.x) D.work[i] = 0;
+        for (int i = t; i < P.iterations; i += blockDim.x) D.work[i] = 0;
     __syncthreads();
     if (shift) {
-        for (int i = threadIdx.x; i < H * dd; i += blockDim.x) Sig[i] = sS[i];
-        for (int i = threadIdx.x; i < H * d; i += blockDim.x) mu[i] = sM[i];
+        for (int i = t; i < H * dd; i += blockDim.x) Sig[i] = sS[i];
+        for (int i = t; i < H * d; i += blockDim.x) mu[i] = sM[i];
     }
-    // Cholesky factor of every step's covariance (in shared memory).
-    for (int h = threadIdx.x; h < H; h += blockDim.x) cholesky_fp32(d, sS + h * dd, sL + h * dd);
-    __syncthreads();
-    for (int i = threadIdx.x; i < H * dd; i += blockDim.x) D.L[A.off_hdd + i] = sL[i];
-
-    // Sense: distance of the end effector to the goal, from the measured q.
-    __shared__ float e_self;
-    if (threadIdx.x == 0) {
-        const float *in = D.input + A.off_in;
+    // Cholesky factor of every step's covariance (in shared memory), and, on
+    // the last thread, Sense: the end effector's distance to the goal
+    for (int h = t; h < H; h += blockDim.x) cholesky_unrolled(d, sS + h * dd, sL + h * dd);
+    if (t == blockDim.x - 1) {
         Frame F;
-        frame_base(A, F);
-        for (int i = 0; i < d; ++i) frame_step(F, in[i], A.dh[i], A.twist[i]);
-        const float *gp = in + 2 * d;
+        for (int k = 0; k < 9; ++k) F.R[k] = s_base[k];
+        for (int k = 0; k < 3; ++k) F.t[k] = s_base[9 + k];
+        for (int i = 0; i < d; ++i) frame_step(F, s_in[i], s_dh[i], s_tw[i]);
+        const float *gp = s_in + 2 * d;
         const float dx = __fsub_rn(F.t[0], gp[0]), dy = __fsub_rn(F.t[1], gp[1]),
                     dz = __fsub_rn(F.t[2], gp[2]);
         e_self = sqrtf(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
         D.e_now[a] = e_self;
     }
     __syncthreads();
+    for (int i = t; i < H * dd; i += blockDim.x) D.L[A.off_hdd + i] = sL[i];
     // Priority of every neighbour with a published plan (Sec. IV-B), from the
     // own sensed distance and the neighbour's published one.
-    for (int i = threadIdx.x; i < P.n_arms; i += blockDim.x)
-        D.alpha[a * P.n_arms + i] = (i != a && D.board_valid[i])
-                                        ? priority(e_self, D.board_dist[i], P.tau)
-                                        : 0.f;
+    for (int i = t; i < P.n_arms; i += blockDim.x)
+        D.alpha[a * P.n_arms + i] =
+            (i != a && s_bvalid[i]) ? priority(e_self, s_bdist[i], P.tau) : 0.f;
 }
 
 // ---------------------------------------------------------------------------

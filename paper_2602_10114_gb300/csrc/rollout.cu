@@ -12,18 +12,32 @@
 //   g = |c - p|^2 - (r + B + r_p)^2
 //     = [|p|^2 - r_p^2] - 2 c.p - 2 (r + B) r_p + [|c|^2 - (r + B)^2]
 // the bracketed per-sphere terms are precomputed, so the inner loop is four
-// FMAs and a min per pair, without branches.  An own sphere whose minimum g
+// FMAs and a min per pair, without branches, issued as packed f32x2
+// instructions on two own spheres at a time.  An own sphere whose minimum g
 // falls below eps_g (the FP32 cancellation margin of this expansion over the
 // workspace) gets an exact pass: direct squared distance, and the square root
 // only for pairs inside the ramp.  Since the cost is zero outside the ramp,
 // the result equals the brute-force minimum of Eq. 6 restricted to the ramp.
 #include "kernels.cuh"
 
+// tuning knobs of the rollout kernel (set at build time)
+#ifndef MRS_ROLLOUT_MIN_BLOCKS
+#define MRS_ROLLOUT_MIN_BLOCKS 3
+#endif
+#ifndef MRS_PRETEST_UNROLL
+#define MRS_PRETEST_UNROLL 2
+#endif
+
 namespace mrs {
+
+constexpr int kPretestUnroll = MRS_PRETEST_UNROLL;
 
 struct RolloutSmem {
     float4 *other;     // world spheres at the step's time, then neighbours' plan spheres
     float *other_w;    // |p|^2 - r_p^2 of each
+    ulonglong2 *pa;    // packed pairs for the f32x2 pre-test: (x, x), (y, y)
+    ulonglong2 *pb;    //                                      (z, z), (r, r)
+    unsigned long long *pc;   //                               (w, w)
     float4 *aabb;      // [2 * n_aabb] centre, half extents
     float4 *sph;       // [ns] local centre + radius
     int *frame;        // [ns]
@@ -36,6 +50,38 @@ struct RolloutSmem {
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// packed binary32 pairs (Blackwell f32x2 FMA: two lanes, each rounded exactly
+// like the scalar instruction)
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// store one other sphere (and its |p|^2 - r^2) in every layout the passes read
+__device__ __forceinline__ void put_other(const RolloutSmem &S, int k, float4 w)
+{
+    const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
+                                -__fmul_rn(w.w, w.w))));
+    S.other[k] = w;
+    S.other_w[k] = pw;
+    S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
+    S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
+    S.pc[k] = pack2(pw, pw);
+}
+
 // exact distance of a candidate pair, as in the oracle: sqrt(d2) - r - r_p
 __device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p, float &m)
 {
@@ -47,43 +93,87 @@ __device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p
 
 // Minimum signed distance, inside the ramp of buffer B, between the warp's
 // own spheres and other[k0, k1).  Returns +inf when no pair is in the ramp.
-template <int SPG>
+// Own sphere centres arrive packed in pairs as -2c (NP = ceil(SPG / 2)); the
+// pre-test runs on both spheres of a pair with one f32x2 FMA chain.
+template <int NP>
 __device__ __forceinline__ float clearance_pass(const RolloutSmem &S, int k0, int k1, float B,
-                                                float eps_g, int s0, int cnt,
-                                                const float (&mx)[SPG], const float (&my)[SPG],
-                                                const float (&mz)[SPG])
+                                                float eps_g, int s0, int cnt, int lane,
+                                                const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
+                                                const f32x2 (&MZ)[NP])
 {
-    float mr[SPG], gmin[SPG];
+    f32x2 MR[NP];
+    float gmin[2 * NP];
 #pragma unroll
-    for (int s = 0; s < SPG; ++s) {
-        mr[s] = (s < cnt) ? -2.f * __fadd_rn(S.sph[s0 + s].w, B) : 0.f;
-        gmin[s] = kInf;
+    for (int q = 0; q < NP; ++q) {
+        const int a = 2 * q, b = 2 * q + 1;
+        const float ra = (a < cnt) ? -2.f * __fadd_rn(S.sph[s0 + a].w, B) : 0.f;
+        const float rb = (b < cnt) ? -2.f * __fadd_rn(S.sph[s0 + b].w, B) : 0.f;
+        MR[q] = pack2(ra, rb);
+        gmin[a] = gmin[b] = kInf;
     }
+#pragma unroll kPretestUnroll
     for (int k = k0; k < k1; ++k) {
-        const float4 p = S.other[k];
-        const float w = S.other_w[k];
+        const ulonglong2 A = S.pa[k], Bv = S.pb[k];
+        const f32x2 W = S.pc[k];
 #pragma unroll
-        for (int s = 0; s < SPG; ++s) {
-            const float g = __fmaf_rn(mx[s], p.x, __fmaf_rn(my[s], p.y,
-                            __fmaf_rn(mz[s], p.z, __fmaf_rn(mr[s], p.w, w))));
-            gmin[s] = fminf(gmin[s], g);
+        for (int q = 0; q < NP; ++q) {
+            float g0, g1;
+            unpack2(fma2(MX[q], A.x, fma2(MY[q], A.y, fma2(MZ[q], Bv.x, fma2(MR[q], Bv.y, W)))),
+                    g0, g1);
+            gmin[2 * q] = fminf(gmin[2 * q], g0);
+            gmin[2 * q + 1] = fminf(gmin[2 * q + 1], g1);
         }
     }
-    float m = kInf;
+    // own spheres whose pre-test minimum is within the margin of the ramp
+    unsigned flagged = 0u;
 #pragma unroll
-    for (int s = 0; s < SPG; ++s) {
+    for (int s = 0; s < 2 * NP; ++s) {
         if (s < cnt) {
             // g = gmin + |c|^2 - (r + B)^2 with c = -m/2
-            const float r = S.sph[s0 + s].w;
-            const float rB = __fadd_rn(r, B);
-            const float3 c = make_float3(-0.5f * mx[s], -0.5f * my[s], -0.5f * mz[s]);
-            const float ac = __fmaf_rn(c.z, c.z, __fmaf_rn(c.y, c.y,
-                             __fmaf_rn(c.x, c.x, -__fmul_rn(rB, rB))));
-            if (__fadd_rn(gmin[s], ac) < eps_g)
-                for (int k = k0; k < k1; ++k) pair_exact(c, rB, r, S.other[k], m);
+            float x0, x1, y0, y1, z0, z1;
+            unpack2(MX[s / 2], x0, x1);
+            unpack2(MY[s / 2], y0, y1);
+            unpack2(MZ[s / 2], z0, z1);
+            const float cx = -0.5f * ((s & 1) ? x1 : x0), cy = -0.5f * ((s & 1) ? y1 : y0),
+                        cz = -0.5f * ((s & 1) ? z1 : z0);
+            const float rB = __fadd_rn(S.sph[s0 + s].w, B);
+            const float ac = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmaf_rn(cx, cx, -__fmul_rn(rB, rB))));
+            if (__fadd_rn(gmin[s], ac) < eps_g) flagged |= 1u << s;
         }
     }
+    // exact pass (rare): one loop for all flagged spheres, centres read back
+    // from the warp's shared-memory copy
+    float m = kInf;
+    unsigned any = __ballot_sync(0xffffffffu, flagged != 0u);
+    while (any) {
+        unsigned bits = flagged;
+        flagged = 0u;
+        if (bits) {
+            const int s = __ffs(bits) - 1;
+            flagged = bits & (bits - 1u);
+            const float3 c = make_float3(S.own[((s0 + s) * 3 + 0) * 32 + lane],
+                                         S.own[((s0 + s) * 3 + 1) * 32 + lane],
+                                         S.own[((s0 + s) * 3 + 2) * 32 + lane]);
+            const float r = S.sph[s0 + s].w;
+            const float rB = __fadd_rn(r, B);
+            for (int k = k0; k < k1; ++k) pair_exact(c, rB, r, S.other[k], m);
+        }
+        any = __ballot_sync(0xffffffffu, flagged != 0u);
+    }
     return m;
+}
+
+// centre of own sphere s from the packed -2c registers
+template <int NP>
+__device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
+                                             const f32x2 (&MZ)[NP], int s)
+{
+    float x0, x1, y0, y1, z0, z1;
+    unpack2(MX[s / 2], x0, x1);
+    unpack2(MY[s / 2], y0, y1);
+    unpack2(MZ[s / 2], z0, z1);
+    return make_float3(-0.5f * ((s & 1) ? x1 : x0), -0.5f * ((s & 1) ? y1 : y0),
+                       -0.5f * ((s & 1) ? z1 : z0));
 }
 
 template <int SPG>
@@ -98,28 +188,37 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     const float *qh = D.traj + A.off_khd + (long long)h * d * K + (valid ? n : 0);
 
     // DH chain up to the last frame this group needs; the last warp always
-    // runs to the end effector for the pose cost.
-    float mx[SPG], my[SPG], mz[SPG];
+    // runs to the end effector for the pose cost.  Own centres are kept as
+    // packed pairs of -2c (padding far away, never tested).
+    constexpr int NP = (SPG + 1) / 2;
+    f32x2 MX[NP], MY[NP], MZ[NP];
     Frame F;
     frame_base(A, F);
     int f = 0;
 #pragma unroll
-    for (int s = 0; s < SPG; ++s) {
-        if (s < cnt) {
-            const int fs = S.frame[s0 + s];
-            while (f < fs) {
-                frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
-                ++f;
+    for (int q = 0; q < NP; ++q) {
+        float cx[2], cy[2], cz[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = 2 * q + u;
+            if (s < cnt) {
+                const int fs = S.frame[s0 + s];
+                while (f < fs) {
+                    frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+                    ++f;
+                }
+                const float3 c = sphere_centre(F, S.sph[s0 + s]);
+                cx[u] = -2.f * c.x; cy[u] = -2.f * c.y; cz[u] = -2.f * c.z;
+                S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
+                S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
+                S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
+            } else {
+                cx[u] = cy[u] = cz[u] = -2e15f;
             }
-            const float4 p = S.sph[s0 + s];
-            const float3 c = sphere_centre(F, p);
-            mx[s] = -2.f * c.x; my[s] = -2.f * c.y; mz[s] = -2.f * c.z;
-            S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
-            S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
-            S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
-        } else {
-            mx[s] = my[s] = mz[s] = -2e15f;   // padding: never tested
         }
+        MX[q] = pack2(cx[0], cx[1]);
+        MY[q] = pack2(cy[0], cy[1]);
+        MZ[q] = pack2(cz[0], cz[1]);
     }
     if (g == kGroups - 1) {
         while (f < d) {
@@ -131,22 +230,26 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     }
 
     if (cnt > 0) {
-        // world clearance: spheres (pre-tested), boxes (exact)
-        float m = clearance_pass<SPG>(S, 0, n_world, P.B_world, P.eps_g, s0, cnt, mx, my, mz);
+        // world boxes (exact), then one pre-tested pass per sphere set: the
+        // world spheres (slot 0, buffer B_world) and each published neighbour
+        // plan at this step (slot 2 + nb, buffer B)
+        float mbox = kInf;
         for (int b = 0; b < n_aabb; ++b) {
             const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
 #pragma unroll
             for (int s = 0; s < SPG; ++s)
                 if (s < cnt)
-                    m = fminf(m, sphere_aabb(make_float3(-0.5f * mx[s], -0.5f * my[s],
-                                                         -0.5f * mz[s]), S.sph[s0 + s].w, bc, bh));
+                    mbox = fminf(mbox, sphere_aabb(own_centre<NP>(MX, MY, MZ, s), S.sph[s0 + s].w,
+                                                   bc, bh));
         }
-        if (m < P.B_world) atomicMin(&S.red[0 * 32 + lane], float_to_ordered(m));
-        // coordination: each published neighbour plan at this step
-        for (int nb = 0; nb < n_nb; ++nb) {
-            const float mn = clearance_pass<SPG>(S, S.nb_start[nb], S.nb_start[nb + 1], P.B,
-                                                 P.eps_g, s0, cnt, mx, my, mz);
-            if (mn < P.B) atomicMin(&S.red[(2 + nb) * 32 + lane], float_to_ordered(mn));
+        for (int ps = 0; ps <= n_nb; ++ps) {
+            const bool world = ps == 0;
+            const int k0 = world ? 0 : S.nb_start[ps - 1];
+            const int k1 = world ? n_world : S.nb_start[ps];
+            const float Bp = world ? P.B_world : P.B;
+            float m = clearance_pass<NP>(S, k0, k1, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ);
+            if (world) m = fminf(m, mbox);
+            if (m < Bp) atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
         }
     }
     __syncthreads();   // every group's centres are in shared memory
@@ -172,7 +275,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     }
 }
 
-__global__ void __launch_bounds__(kRolloutThreads, 3) k_rollout(Params P, Dev D,
+__global__ void __launch_bounds__(kRolloutThreads, MRS_ROLLOUT_MIN_BLOCKS) k_rollout(Params P, Dev D,
                                                              const RolloutTile *tiles, int n_tiles,
                                                              int iter)
 {
@@ -187,6 +290,9 @@ __global__ void __launch_bounds__(kRolloutThreads, 3) k_rollout(Params P, Dev D,
         S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
         S.own = (float *)p;        p += align16(sizeof(float) * P.max_ns * 3 * 32);
         S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
+        S.pa = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
+        S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
+        S.pc = (unsigned long long *)p; p += align16(sizeof(unsigned long long) * n_other);
         S.frame = (int *)p;        p += align16(sizeof(int) * P.max_ns);
         S.pairs = (int *)p;        p += align16(sizeof(int) * P.max_pairs);
         S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
@@ -210,29 +316,50 @@ __global__ void __launch_bounds__(kRolloutThreads, 3) k_rollout(Params P, Dev D,
 
         // stage the tile's inputs: neighbour list (published plans whose
         // horizon reaches step h), world at the step's time, arm constants
-        if (threadIdx.x == 0) {
-            int nnb = 0, tot = n_world;
-            for (int i = 0; i < NA; ++i) {
-                if (i == T.arm || !D.board_valid[i]) continue;
-                const ArmDev &Ai = D.arms[i];
-                if (h >= Ai.H) continue;                 // min(H_j, H_i) rule
-                s_nb_arm[nnb] = i;
-                S.nb_start[nnb] = tot;
-                S.nb_alpha[nnb] = D.alpha[T.arm * NA + i];
-                tot += Ai.ns;
-                ++nnb;
+        if (g == 0) {
+            // lane i decides whether arm i's published plan reaches step h
+            const int i = lane;
+            bool ok = false;
+            int ns_i = 0;
+            float al = 0.f;
+            if (i < NA && i != T.arm && D.board_valid[i] && h < D.arms[i].H) {   // min(H_j, H_i)
+                ok = true;
+                ns_i = D.arms[i].ns;
+                al = D.alpha[T.arm * NA + i];
             }
-            S.nb_start[nnb] = tot;
-            s_nnb = nnb;
+            const unsigned mask = __ballot_sync(0xffffffffu, ok);
+            int incl = ns_i;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int pos = __popc(mask & ((1u << lane) - 1u));
+            if (ok) {
+                s_nb_arm[pos] = i;
+                S.nb_start[pos] = n_world + incl - ns_i;
+                S.nb_alpha[pos] = al;
+            }
+            if (lane == 31) {
+                s_nnb = __popc(mask);
+                S.nb_start[__popc(mask)] = n_world + incl;
+            }
+            __syncwarp();
+            // the same warp stages the neighbours' plan spheres at step h
+            const int nnb = __popc(mask);
+            for (int nb = 0; nb < nnb; ++nb) {
+                const ArmDev &Ai = D.arms[s_nb_arm[nb]];
+                const float4 *src = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
+                const int o = S.nb_start[nb];
+                for (int k = lane; k < Ai.ns; k += 32) put_other(S, o + k, src[k]);
+            }
+            for (int k = lane; k < (2 + nnb) * 32; k += 32) S.red[k] = float_to_ordered(kInf);
         }
         const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
         for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
             const float4 o = D.world[k], v = D.world_vel[k];
-            const float4 w = make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
-                                         __fmaf_rn(v.z, t_h, o.z), o.w);
-            S.other[k] = w;
-            S.other_w[k] = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
-                                     -__fmul_rn(w.w, w.w))));
+            put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
+                                        __fmaf_rn(v.z, t_h, o.z), o.w));
         }
         for (int k = threadIdx.x; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
         for (int k = threadIdx.x; k < A.ns; k += blockDim.x) {
@@ -243,20 +370,6 @@ __global__ void __launch_bounds__(kRolloutThreads, 3) k_rollout(Params P, Dev D,
             S.pairs[k] = D.self_pairs[A.self_off + k];
         __syncthreads();
         const int n_nb = s_nnb;
-        for (int nb = 0; nb < n_nb; ++nb) {
-            const ArmDev &Ai = D.arms[s_nb_arm[nb]];
-            const float4 *src = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
-            const int o = S.nb_start[nb];
-            for (int k = threadIdx.x; k < Ai.ns; k += blockDim.x) {
-                const float4 w = src[k];
-                S.other[o + k] = w;
-                S.other_w[o + k] = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
-                                             -__fmul_rn(w.w, w.w))));
-            }
-        }
-        for (int k = threadIdx.x; k < (2 + n_nb) * 32; k += blockDim.x)
-            S.red[k] = float_to_ordered(kInf);
-        __syncthreads();
 
         const int n = T.n0 + lane;
         const bool valid = n < A.K;
@@ -301,7 +414,8 @@ size_t rollout_smem_bytes(const Params &P, int n_arms)
     const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * n_arms;
     return a16(sizeof(float4) * n_other) + a16(sizeof(float4) * 2 * P.aabb_cap) +
            a16(sizeof(float4) * P.max_ns) + a16(sizeof(float) * P.max_ns * 3 * 32) +
-           a16(sizeof(float) * n_other) + a16(sizeof(int) * P.max_ns) +
+           a16(sizeof(float) * n_other) + 2 * a16(sizeof(ulonglong2) * n_other) +
+           a16(sizeof(unsigned long long) * n_other) + a16(sizeof(int) * P.max_ns) +
            a16(sizeof(int) * P.max_pairs) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +
            a16(sizeof(float) * MRS_MAX_ARMS) + sizeof(int) * (2 + MRS_MAX_ARMS) * 32;
 }
