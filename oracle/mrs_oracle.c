@@ -448,17 +448,13 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
 }
 
 /* ------------------------------------------------------------------------ */
-/* One control cycle, Algorithm 1, for every arm.  All arms read the plan
- * board as it stood at the start of the cycle; the new plans are written
- * after every arm has optimised (publication at the end of the cycle). */
-int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_outputs *out)
+/* Sense: current distance-to-goal of every arm from the measured q; priority
+ * weights: own current distance against the neighbour's published one
+ * (neighbours without a published plan are ignored, alpha = 0). */
+static void sense_and_priority(const orc_config *cfg, const orc_state *st, const orc_inputs *in,
+                               double *e_now, double *alpha)
 {
     const int A = cfg->n_arms;
-    double *e_now = (double *)calloc((size_t)A, sizeof(double));
-    double *alpha = (double *)calloc((size_t)A * A, sizeof(double));
-    if (!e_now || !alpha) return 1;
-
-    /* Sense: current distance-to-goal of every arm from the measured q */
     for (int a = 0; a < A; ++a) {
         const orc_arm *Aa = &cfg->arms[a];
         long long od;
@@ -470,33 +466,48 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
                dz = T[11] - in->goal_p[3 * a + 2];
         e_now[a] = sqrt(dx * dx + dy * dy + dz * dz);
     }
-    /* priority weights: own current distance against the neighbour's
-     * published one (neighbours without a published plan are ignored) */
     for (int a = 0; a < A; ++a)
         for (int i = 0; i < A; ++i)
             alpha[a * A + i] = (i != a && st->plan_valid[i])
                                    ? orc_priority(e_now[a], st->plan_dist[i], cfg->tau)
                                    : 0.0;
+}
 
-    /* Shift (Sec. III-A): phi_h <- phi_{h+1}; the last step keeps its mean and
-     * restarts from the initial covariance.  Not applied before the first cycle. */
+/* Shift (Sec. III-A) of one arm's distribution: phi_h <- phi_{h+1}; the last
+ * step keeps its mean and restarts from the initial covariance. */
+static void shift_arm(const orc_config *cfg, int a, double *mu, double *Sig)
+{
+    const orc_arm *Aa = &cfg->arms[a];
+    const int d = Aa->dof, H = Aa->H;
+    for (int h = 0; h + 1 < H; ++h) {
+        for (int j = 0; j < d; ++j) mu[h * d + j] = mu[(h + 1) * d + j];
+        for (int k = 0; k < d * d; ++k) Sig[(long long)h * d * d + k] = Sig[(long long)(h + 1) * d * d + k];
+    }
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c)
+            Sig[(long long)(H - 1) * d * d + r * d + c] =
+                (r == c) ? cfg->sigma_init * cfg->sigma_init : 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One control cycle, Algorithm 1, for every arm.  All arms read the plan
+ * board as it stood at the start of the cycle; the new plans are written
+ * after every arm has optimised (publication at the end of the cycle). */
+int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_outputs *out)
+{
+    const int A = cfg->n_arms;
+    double *e_now = (double *)calloc((size_t)A, sizeof(double));
+    double *alpha = (double *)calloc((size_t)A * A, sizeof(double));
+    if (!e_now || !alpha) return 1;
+
+    sense_and_priority(cfg, st, in, e_now, alpha);
+
+    /* Shift: not applied before the first cycle */
     if (st->cycle > 0) {
         for (int a = 0; a < A; ++a) {
-            const orc_arm *Aa = &cfg->arms[a];
-            const int d = Aa->dof, H = Aa->H;
             long long ohd, ohdd;
             orc_offsets(cfg, a, &ohd, &ohdd, NULL, NULL, NULL);
-            for (int h = 0; h + 1 < H; ++h) {
-                for (int j = 0; j < d; ++j)
-                    st->mu[ohd + h * d + j] = st->mu[ohd + (h + 1) * d + j];
-                for (int k = 0; k < d * d; ++k)
-                    st->Sigma[ohdd + (long long)h * d * d + k] =
-                        st->Sigma[ohdd + (long long)(h + 1) * d * d + k];
-            }
-            for (int r = 0; r < d; ++r)
-                for (int c = 0; c < d; ++c)
-                    st->Sigma[ohdd + (long long)(H - 1) * d * d + r * d + c] =
-                        (r == c) ? cfg->sigma_init * cfg->sigma_init : 0.0;
+            shift_arm(cfg, a, st->mu + ohd, st->Sigma + ohdd);
         }
     }
 
@@ -651,5 +662,48 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
     st->cycle += 1;
     st->world_t += cfg->dt;
     free(new_spheres); free(new_q); free(e_now); free(alpha);
+    return 0;
+}
+
+/* Costs of chosen samples of the first iteration of a cycle, one by one:
+ * Sense and priority, Shift (on a copy), Cholesky, then for each requested
+ * sample n its normals, U = mu + L z and the rollout.  The state is read,
+ * never written.  spheres_out (may be NULL): [n_req][H][NS][4]. */
+int orc_sample_costs(const orc_config *cfg, const orc_state *st, const orc_inputs *in, int arm,
+                     int n_req, const int *ns, double *costs, double *spheres_out)
+{
+    const int A = cfg->n_arms;
+    const orc_arm *Aa = &cfg->arms[arm];
+    const int d = Aa->dof, H = Aa->H, NS = Aa->n_spheres;
+    double *e_now = (double *)calloc((size_t)A, sizeof(double));
+    double *alpha = (double *)calloc((size_t)A * A, sizeof(double));
+    double *mu = (double *)malloc(sizeof(double) * H * d);
+    double *Sig = (double *)malloc(sizeof(double) * H * d * d);
+    double *L = (double *)malloc(sizeof(double) * H * d * d);
+    double *U = (double *)malloc(sizeof(double) * H * d);
+    if (!e_now || !alpha || !mu || !Sig || !L || !U) return 1;
+    sense_and_priority(cfg, st, in, e_now, alpha);
+    long long ohd, ohdd;
+    orc_offsets(cfg, arm, &ohd, &ohdd, NULL, NULL, NULL);
+    memcpy(mu, st->mu + ohd, sizeof(double) * H * d);
+    memcpy(Sig, st->Sigma + ohdd, sizeof(double) * H * d * d);
+    if (st->cycle > 0) shift_arm(cfg, arm, mu, Sig);
+    for (int h = 0; h < H; ++h) orc_cholesky(d, Sig + h * d * d, 1e-8, L + h * d * d);
+    for (int r = 0; r < n_req; ++r) {
+        const int n = ns[r];
+        for (int h = 0; h < H; ++h) {
+            double z[ORC_MAX_DOF];
+            orc_normals(cfg->seed, arm, st->cycle, 0, n, h, d, z);
+            for (int i = 0; i < d; ++i) {
+                double eps = 0.0;
+                for (int c = 0; c <= i; ++c) eps += L[h * d * d + i * d + c] * z[c];
+                U[h * d + i] = mu[h * d + i] + eps;
+            }
+        }
+        costs[r] = orc_rollout(cfg, arm, st, in, alpha + arm * A, U, NULL,
+                               spheres_out ? spheres_out + (size_t)r * H * NS * 4 : NULL, NULL, NULL,
+                               NULL);
+    }
+    free(e_now); free(alpha); free(mu); free(Sig); free(L); free(U);
     return 0;
 }

@@ -146,6 +146,11 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in,
 double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const orc_inputs *in,
                    const double *alpha_row, const double *U, double *stage,
                    double *spheres_out, double *q_out, long long *n_queries, double *sens);
+/* Costs (and optionally sphere trajectories) of chosen samples n of the
+ * first iteration of the next cycle, computed one by one without running the
+ * cycle; the state is not modified. */
+int orc_sample_costs(const orc_config *cfg, const orc_state *st, const orc_inputs *in, int arm,
+                     int n_req, const int *ns, double *costs, double *spheres_out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

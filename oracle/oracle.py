@@ -110,6 +110,9 @@ def lib():
             L.orc_rollout.restype = C.c_double
             L.orc_rollout.argtypes = [C.POINTER(OrcConfig), C.c_int, C.POINTER(OrcState),
                                       C.POINTER(OrcInputs), _dp, _dp, _dp, _dp, _dp, _llp, _dp]
+            L.orc_sample_costs.restype = C.c_int
+            L.orc_sample_costs.argtypes = [C.POINTER(OrcConfig), C.POINTER(OrcState),
+                                           C.POINTER(OrcInputs), C.c_int, C.c_int, _ip, _dp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -362,6 +365,21 @@ class Oracle:
                                 _ptr(stage), _ptr(sph), _ptr(qo), C.byref(nq), C.byref(sens))
         self.last_rollout_sens = sens.value
         return tot, stage, sph, qo
+
+    def sample_costs(self, arm, q, qd, goal_p, goal_R, ns, want_spheres=False):
+        """Costs of samples `ns` of the next cycle's first iteration, one by
+        one (the state is not modified); optionally their sphere trajectories."""
+        a = self.sc.arms[arm]
+        inp, keep = self.inputs(q, qd, goal_p, goal_R)
+        ns = np.ascontiguousarray(ns, dtype=np.int32)
+        costs = np.zeros(len(ns))
+        sph = np.zeros((len(ns), a.H, a.n_spheres, 4)) if want_spheres else None
+        st = self._state_struct()
+        rc = lib().orc_sample_costs(C.byref(self.cfg), C.byref(st), C.byref(inp), arm, len(ns),
+                                    _ptr(ns, _ip), _ptr(costs), _ptr(sph))
+        if rc != 0:
+            raise RuntimeError("oracle sample_costs failed")
+        return (costs, sph) if want_spheres else costs
 
     def split(self, flat, kind: str, arm: int):
         """Per-arm view of a concatenated state/output array."""

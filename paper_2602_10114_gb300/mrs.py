@@ -207,10 +207,12 @@ class Controller:
 
     # -- API ----------------------------------------------------------------
     def set_world(self, spheres=None, vel=None, aabbs=None):
+        """World obstacles; with no arguments, the scenario's spheres, their
+        velocities (if any) and its boxes."""
         sc = self.sc
-        spheres = _f32(sc.world if spheres is None else spheres).reshape(-1, 4)
-        if vel is None and spheres is sc.world:
-            vel = sc.world_vel
+        if spheres is None:
+            spheres, vel = sc.world, sc.world_vel if vel is None else vel
+        spheres = _f32(spheres).reshape(-1, 4)
         vel = None if vel is None else _f32(vel).reshape(-1, 3)
         aabbs = _f32(sc.aabb if aabbs is None else aabbs).reshape(-1, 6)
         self._check(self.L.mrs_set_world(self.h, _pf(spheres) if len(spheres) else None,

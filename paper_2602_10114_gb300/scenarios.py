@@ -237,11 +237,15 @@ def config(index: int, run: int = 0, **overrides) -> Scenario:
 
 
 def shrink(sc: Scenario, K: int | None = None, H: int | None = None, arms: int | None = None,
-           n_world: int | None = None) -> Scenario:
+           n_world: int | None = None, K_div: int | None = None) -> Scenario:
     """A smaller copy of a workload (fewer samples, steps, arms or obstacles)
-    for tests that must finish in seconds on the CPU oracle."""
+    for tests that must finish in seconds on the CPU oracle; K_div divides every
+    arm's sample count and keeps their ratios."""
     import copy
     s = copy.deepcopy(sc)
+    if K_div is not None:
+        for a in s.arms:
+            a.K = max(1, a.K // K_div)
     if arms is not None:
         s.arms = s.arms[:arms]
         s.q0, s.qd0, s.goal_q = s.q0[:arms], s.qd0[:arms], s.goal_q[:arms]

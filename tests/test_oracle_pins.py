@@ -519,3 +519,18 @@ def test_priority_uses_own_sensed_and_neighbours_published_distance(oracle_mod):
         for i in range(A):
             exp = 0.0 if i == j else oracle_mod.priority(o2["dist_to_goal"][j], e_pub[i], 3.0)
             assert al[j, i] == exp
+
+
+def test_sample_costs_agree_with_the_cycle(oracle_mod):
+    """The one-by-one sample scorer reproduces the cycle's own costs of
+    those samples (both follow Sense, Shift, SampleControls, Rollout)."""
+    from oracle.oracle import Oracle
+    sc = S.shrink(S.config(2), K=24, H=6)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    orc.cycle(sc.q0, sc.qd0, gp, gR)
+    ns = [0, 5, 23]
+    before = {a: orc.sample_costs(a, sc.q0, sc.qd0, gp, gR, ns) for a in range(sc.n_arms)}
+    out = orc.cycle(sc.q0, sc.qd0, gp, gR)
+    for a in range(sc.n_arms):
+        assert np.array_equal(before[a], orc.split(out["costs"], "k", a)[ns])

@@ -239,3 +239,74 @@ def test_rejects_non_finite_state():
     with pytest.raises(mrs.MrsError) as e:
         c.step(q, sc.qd0, np.zeros((1, 3), np.float32), np.eye(3, dtype=np.float32)[None])
     assert e.value.status == 1
+
+
+def test_cycle_sixteen_uneven_arms_replay():
+    """Workload 4 (16 arms, DoF 6/7/9, H 20/30/48, N_S 35/40/50, one launch for
+    all arms) with K divided by 16 so the oracle keeps up: every output of
+    two replayed cycles, the second with all plans published (min-horizon rule
+    in play)."""
+    from parity_utils import Replay
+    sc = S.shrink(S.config(4), K_div=16)
+    R = Replay(sc)
+    for c in range(2):
+        d = np.array([[a, n, h] for a in (0, 4, 8, 14) for n in (0, sc.arms[a].K - 1)
+                      for h in (0, sc.arms[a].H - 1)], np.int32)
+        got, gc, ga, gs, exp = R.cycle(d)
+        _check_cycle(R, got, gc, ga, gs, exp, d)
+        R.advance(exp)
+
+
+def test_cycle_eight_arms_moving_world_replay():
+    """Workload 5 (8 arms, H = 64, dt = 0.01, 256 spheres moving at constant
+    velocity) with K = 32: three replayed cycles, the world clock advancing."""
+    from parity_utils import Replay
+    sc = S.shrink(S.config(5), K=32)
+    R = Replay(sc)
+    for c in range(3):
+        d = np.array([[a, n, h] for a in (0, 7) for n in (0, 31) for h in (0, 40, 63)], np.int32)
+        got, gc, ga, gs, exp = R.cycle(d)
+        _check_cycle(R, got, gc, ga, gs, exp, d)
+        R.advance(exp)
+
+
+@pytest.mark.parametrize("idx", [4, 5])
+def test_full_size_sampled_rollouts(idx):
+    """Full-size workloads 4 and 5 in the benchmark's launch configuration
+    (graph, persistent rollout over all arms): the state (mean, covariance,
+    published plans) is the oracle's after one cycle, which does not depend on
+    K, so it is produced with few samples; the oracle then scores sampled
+    rollouts of the full-size cycle one by one."""
+    from oracle.oracle import Oracle
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import EPS_D, cost_tol, goals, load_oracle_state, r32
+    full = S.config(idx)
+    small = S.shrink(full, K=8)
+    orc_small = Oracle(small, threads=8)
+    gp, gR = goals(orc_small, small)
+    q = [r32(x) for x in full.q0]
+    qd = [r32(x) for x in full.qd0]
+    orc_small.cycle(q, qd, gp, gR)
+    orc_small.round_state_to_f32()
+    orc = Oracle(full, threads=8)
+    orc.state = {k: v.copy() for k, v in orc_small.state.items()}
+    orc.cycle_index, orc.world_t = orc_small.cycle_index, orc_small.world_t
+    ctl = mrs.Controller(full)
+    ctl.set_world()
+    load_oracle_state(ctl, orc)
+    ctl.step([x.astype(np.float32) for x in q], [x.astype(np.float32) for x in qd],
+             gp.astype(np.float32), gR.astype(np.float32))
+    rng = np.random.default_rng(idx)
+    arms = range(full.n_arms) if idx == 5 else (0, 1, 2, 5, 9, 15)
+    for a in arms:
+        K, H = full.arms[a].K, full.arms[a].H
+        ns = sorted({0, K - 1, *rng.integers(0, K, 3).tolist()})
+        exp, sph = orc.sample_costs(a, q, qd, gp, gR, ns, want_spheres=True)
+        got = ctl.debug_costs(a)[ns]
+        assert np.all(np.abs(got - exp) <= cost_tol(exp)), f"arm {a}"
+        hs = [0, H // 2, H - 1]
+        gs = ctl.debug_spheres([[a, n, h] for n in ns for h in hs])
+        ns_a = full.arms[a].n_spheres
+        for i, (n, h) in enumerate([(n, h) for n in range(len(ns)) for h in hs]):
+            e = np.abs(gs[i, :ns_a] - sph[n, h]).max()
+            assert e < 1e-5 and e < EPS_D / 4
