@@ -66,7 +66,12 @@ typedef enum {
  *                         the tool (carried by frame dof); non-decreasing.
  *  sphere_xyzr [NS][4]    centre in the body's frame and radius.
  *  base_pose   [7]        base position and unit quaternion (w, x, y, z).
- *  K, H                   samples per iteration and horizon.           */
+ *  K, H                   samples per iteration and horizon.
+ *  external               0: this context optimises the arm; 1: the arm is
+ *                         controlled elsewhere (another process, Sec. IV-C:
+ *                         each arm runs its own Algorithm 1) and only its
+ *                         published plan, given through mrs_share_plans,
+ *                         is used here.  Its outputs are left untouched.  */
 typedef struct {
     int dof, n_spheres, K, H;
     const float *dh;
@@ -74,6 +79,7 @@ typedef struct {
     const int *sphere_body;
     const float *sphere_xyzr;
     float base_pose[7];
+    int external;
 } mrs_arm_desc;
 
 /* Controller parameters.
@@ -91,7 +97,9 @@ typedef struct {
  *  q_margin     soft-limit margin of the joint cost.
  *  iterations   optimisation iterations per cycle (the paper's K).
  *  seed         Philox key of the sampling.
- *  mode         0 = exact costs (the only mode of this build).          */
+ *  mode         0 = exact costs (the only mode of this build).
+ *  max_plan_age a board entry older than this many cycles counts as not
+ *               published and is ignored (Sec. IV-C); 0 = no limit.     */
 typedef struct {
     int n_arms;
     const mrs_arm_desc *arms;
@@ -101,6 +109,7 @@ typedef struct {
     int iterations;
     unsigned long long seed;
     int mode;
+    int max_plan_age;
 } mrs_config;
 
 /* Sensed state of one arm for one cycle (Alg. 1, Sense): host pointers.

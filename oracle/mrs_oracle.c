@@ -339,6 +339,18 @@ void orc_init_state(const orc_config *cfg, orc_state *st)
     st->world_t = 0.0;
 }
 
+/* A neighbour's board entry is used when it was published (Sec. IV-C: arms
+ * ignore neighbours whose plans have not been published) and, with a staleness
+ * limit set, is at most that many cycles old; older entries count as missing. */
+static int plan_usable(const orc_config *cfg, const orc_state *st, int i)
+{
+    if (!st->plan_valid[i]) return 0;
+    if (cfg->max_plan_age > 0 && st->cycle - st->plan_stamp[i] > cfg->max_plan_age) return 0;
+    return 1;
+}
+
+static int arm_active(const orc_config *cfg, int a) { return !cfg->active || cfg->active[a]; }
+
 /* ------------------------------------------------------------------------ */
 /* Rollout (Sec. III-A: [C_n, X_n] = f(U_n)).  Reading of the dynamics f:
  * U are joint accelerations, integrated by semi-implicit Euler,
@@ -414,7 +426,7 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
          * horizon step, only up to the neighbour's own horizon */
         double c_dyn = 0.0, slope_dyn = 0.0;
         for (int i = 0; i < cfg->n_arms; ++i) {
-            if (i == arm || !st->plan_valid[i]) continue;
+            if (i == arm || !plan_usable(cfg, st, i)) continue;
             const orc_arm *Ai = &cfg->arms[i];
             if (h >= Ai->H) continue;
             long long ohs_i;
@@ -447,6 +459,9 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
     return total;
 }
 
+static int plan_usable(const orc_config *cfg, const orc_state *st, int i);
+static int arm_active(const orc_config *cfg, int a);
+
 /* ------------------------------------------------------------------------ */
 /* Sense: current distance-to-goal of every arm from the measured q; priority
  * weights: own current distance against the neighbour's published one
@@ -468,7 +483,7 @@ static void sense_and_priority(const orc_config *cfg, const orc_state *st, const
     }
     for (int a = 0; a < A; ++a)
         for (int i = 0; i < A; ++i)
-            alpha[a * A + i] = (i != a && st->plan_valid[i])
+            alpha[a * A + i] = (i != a && plan_usable(cfg, st, i))
                                    ? orc_priority(e_now[a], st->plan_dist[i], cfg->tau)
                                    : 0.0;
 }
@@ -505,6 +520,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
     /* Shift: not applied before the first cycle */
     if (st->cycle > 0) {
         for (int a = 0; a < A; ++a) {
+            if (!arm_active(cfg, a)) continue;
             long long ohd, ohdd;
             orc_offsets(cfg, a, &ohd, &ohdd, NULL, NULL, NULL);
             shift_arm(cfg, a, st->mu + ohd, st->Sigma + ohdd);
@@ -513,6 +529,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
 
     /* Optimize: K_paper iterations of SampleControls / Rollout / UpdateDistribution */
     for (int a = 0; a < A; ++a) {
+        if (!arm_active(cfg, a)) continue;
         const orc_arm *Aa = &cfg->arms[a];
         const int d = Aa->dof, H = Aa->H, K = Aa->K;
         long long ohd, ohdd, od, ok;
@@ -636,6 +653,13 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
     for (int a = 0; a < A; ++a) {
         long long ohd, ohs;
         orc_offsets(cfg, a, &ohd, NULL, &ohs, NULL, NULL);
+        if (!arm_active(cfg, a)) {   /* keep what the board holds for it */
+            const orc_arm *Aa = &cfg->arms[a];
+            memcpy(new_spheres + ohs, st->plan_spheres + ohs,
+                   sizeof(double) * Aa->H * Aa->n_spheres * 4);
+            memcpy(new_q + ohd, st->plan_q + ohd, sizeof(double) * Aa->H * Aa->dof);
+            continue;
+        }
         orc_rollout(cfg, a, st, in, alpha + a * A, st->mu + ohd, NULL, new_spheres + ohs,
                     new_q + ohd, NULL, NULL);
     }
@@ -655,6 +679,7 @@ int orc_cycle(const orc_config *cfg, orc_state *st, const orc_inputs *in, orc_ou
         memcpy(st->plan_q, new_q, sizeof(double) * tot_hd);
     }
     for (int a = 0; a < A; ++a) {
+        if (!arm_active(cfg, a)) continue;
         st->plan_valid[a] = 1;
         st->plan_stamp[a] = st->cycle;
         st->plan_dist[a] = e_now[a];

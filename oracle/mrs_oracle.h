@@ -47,6 +47,8 @@ typedef struct {
     double q_margin;          /* soft-limit margin of the joint cost */
     int iterations;           /* optimisation iterations per cycle (paper's K) */
     uint64_t seed;            /* Philox key */
+    int max_plan_age;         /* plans older than this many cycles are ignored (0: no limit) */
+    const int *active;        /* [A] arms this controller optimises (NULL: all) */
 } orc_config;
 
 /* Controller state carried from cycle to cycle.  Per-arm blocks are

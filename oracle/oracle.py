@@ -37,7 +37,8 @@ class OrcConfig(C.Structure):
                 ("w_stop", C.c_double), ("w_joint", C.c_double), ("w_coll", C.c_double),
                 ("w_self", C.c_double), ("w_dyn", C.c_double), ("B", C.c_double),
                 ("B_world", C.c_double), ("B_self", C.c_double), ("tau", C.c_double),
-                ("q_margin", C.c_double), ("iterations", C.c_int), ("seed", C.c_uint64)]
+                ("q_margin", C.c_double), ("iterations", C.c_int), ("seed", C.c_uint64),
+                ("max_plan_age", C.c_int), ("active", _ip)]
 
 
 class OrcState(C.Structure):
@@ -212,7 +213,7 @@ class Oracle:
     """Owns the marshalled arms/config and the controller state of one
     scenario; `cycle()` runs Algorithm 1 once for every arm."""
 
-    def __init__(self, sc, threads: int = 1):
+    def __init__(self, sc, threads: int = 1, active=None):
         self.sc = sc
         L = lib()
         L.orc_set_threads(int(threads))
@@ -241,7 +242,11 @@ class Oracle:
                              p["alpha_sigma"], p["sigma_init"], p["w_pose"], p["w_rot"],
                              p["w_stop"], p["w_joint"], p["w_coll"], p["w_self"], p["w_dyn"],
                              p["B"], p["B_world"], p["B_self"], p["tau"], p["q_margin"],
-                             int(p["iterations"]), int(p["seed"]))
+                             int(p["iterations"]), int(p["seed"]), int(p.get("max_plan_age", 0)),
+                             None)
+        if active is not None:          # arms this controller optimises
+            self._active = np.ascontiguousarray(active, dtype=np.int32)
+            self.cfg.active = self._active.ctypes.data_as(_ip)
         self.hd = [a.H * a.dof for a in sc.arms]
         self.hdd = [a.H * a.dof * a.dof for a in sc.arms]
         self.hs = [a.H * a.n_spheres * 4 for a in sc.arms]

@@ -69,6 +69,7 @@ __global__ void k_reset(Params P, Dev D, int total_hdd, int total_hd)
             D.Sigma[A.off_hdd + i] = (k % (A.dof + 1) == 0) ? s2 : 0.f;
         }
     }
+    for (int i = tid; i < P.n_arms * P.n_arms; i += stride) D.alpha[i] = 0.f;
     for (int i = tid; i < P.n_arms; i += stride) {
         D.board_valid[i] = 0;
         D.board_stamp[i] = -1;
@@ -138,6 +139,11 @@ __global__ void k_prep(Params P, Dev D)
     extern __shared__ float sm[];
     const int a = blockIdx.x;
     const ArmDev &A = D.arms[a];
+    if (A.external) {   // optimised elsewhere: only the tile counters
+        if (a == 0)
+            for (int i = threadIdx.x; i < P.iterations; i += blockDim.x) D.work[i] = 0;
+        return;
+    }
     const int d = A.dof, H = A.H, dd = d * d;
     const long long cycle = *D.cycle;
     float *Sig = D.Sigma + A.off_hdd;
@@ -148,7 +154,7 @@ __global__ void k_prep(Params P, Dev D)
     __shared__ float2 s_tw[kMaxDof];
     __shared__ float s_base[12];
     __shared__ float s_bdist[MRS_MAX_ARMS];
-    __shared__ int s_bvalid[MRS_MAX_ARMS];
+    __shared__ int s_bvalid[MRS_MAX_ARMS];   // usable: published and fresh enough
     __shared__ float e_self;
 
     // one parallel wave of loads: the shifted distribution (Shift, Sec. III-A:
@@ -174,7 +180,7 @@ __global__ void k_prep(Params P, Dev D)
     if (t < 9) s_base[t] = A.base_R[t];
     else if (t < 12) s_base[t] = A.base_t[t - 9];
     if (t < P.n_arms) {
-        s_bvalid[t] = D.board_valid[t];
+        s_bvalid[t] = plan_usable(P, D.board_valid[t], D.board_stamp[t], cycle) ? 1 : 0;
         s_bdist[t] = D.board_dist[t];
     }
     if (a == 0)   // rollout tile counters of this cycle's iterations
@@ -461,12 +467,14 @@ __global__ void k_toplan(Params P, Dev D, int *done_counter)
     const int a = blockIdx.x;
     const ArmDev &A = D.arms[a];
     const int d = A.dof, H = A.H, ns = A.ns;
+    const bool local = !A.external;   // external arms keep the plan they were given
     float *smu = sq + H * d;
     const float *mu = D.mu + A.off_hd;
     const float *in = D.input + A.off_in;
-    for (int i = threadIdx.x; i < H * d; i += blockDim.x) smu[i] = mu[i];
+    if (local)
+        for (int i = threadIdx.x; i < H * d; i += blockDim.x) smu[i] = mu[i];
     __syncthreads();
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    for (int j = threadIdx.x; local && j < d; j += blockDim.x) {
         float q = in[j], qd = in[d + j];
         for (int h = 0; h < H; ++h) {
             integrate(q, qd, smu[h * d + j], P.dt);
@@ -474,7 +482,7 @@ __global__ void k_toplan(Params P, Dev D, int *done_counter)
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < H * d; i += blockDim.x) {
+    for (int i = threadIdx.x; local && i < H * d; i += blockDim.x) {
         D.board_q[A.off_hd + i] = sq[i];
         D.out[D.out_q + A.off_hd + i] = sq[i];
         D.out[D.out_mean + A.off_hd + i] = smu[i];
@@ -484,7 +492,7 @@ __global__ void k_toplan(Params P, Dev D, int *done_counter)
     float4 *board = D.board_sph + (A.off_hs >> 2);
     float4 *outs = (float4 *)(D.out + D.out_sph) + (A.off_hs >> 2);
     const int ng = (ns + 7) / 8;
-    for (int t = threadIdx.x; t < H * ng; t += blockDim.x) {
+    for (int t = threadIdx.x; local && t < H * ng; t += blockDim.x) {
         const int h = t / ng, s0 = (t % ng) * 8, s1 = min(ns, s0 + 8);
         Frame F;
         frame_base(A, F);
@@ -504,10 +512,12 @@ __global__ void k_toplan(Params P, Dev D, int *done_counter)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        D.board_valid[a] = 1;
-        D.board_stamp[a] = *D.cycle;
-        D.board_dist[a] = D.e_now[a];
-        D.out[D.out_dist + a] = D.e_now[a];
+        if (local) {
+            D.board_valid[a] = 1;
+            D.board_stamp[a] = *D.cycle;
+            D.board_dist[a] = D.e_now[a];
+            D.out[D.out_dist + a] = D.e_now[a];
+        }
         __threadfence();
         const int prev = atomicAdd(done_counter, 1);
         if (prev == gridDim.x - 1) {

@@ -141,6 +141,7 @@ static void build_work_lists(mrs_ctx *c)
     c->update_tiles.clear();
     for (int a = 0; a < c->A; ++a) {
         const ArmDev &A = c->arms[a];
+        if (A.external) continue;   // optimised elsewhere
         for (int n0 = 0; n0 < A.K; n0 += 32) c->sample_tiles.push_back({a, n0});
         for (int n0 = 0; n0 < A.K; n0 += 256) c->cost_tiles.push_back({a, n0});
         for (int h = 0; h < A.H; ++h) c->update_tiles.push_back({a, h});
@@ -151,7 +152,7 @@ static void build_work_lists(mrs_ctx *c)
     for (int h = 0; h < Hmax; ++h)
         for (int a = 0; a < c->A; ++a) {
             const ArmDev &A = c->arms[a];
-            if (h >= A.H) continue;
+            if (h >= A.H || A.external) continue;
             for (int n0 = 0; n0 < A.K; n0 += kTileSamples) c->rollout_tiles.push_back({a, h, n0, 0});
         }
 }
@@ -234,6 +235,7 @@ static mrs_status validate(const mrs_config *cfg, std::string &why)
         cfg->w_coll < 0 || cfg->w_self < 0 || cfg->w_dyn < 0 || cfg->tau < 0)
         return why = "cost weights and tau must be >= 0", MRS_EINVAL;
     if (cfg->iterations < 1 || cfg->iterations > 64) return why = "iterations out of range", MRS_EINVAL;
+    if (cfg->max_plan_age < 0) return why = "max_plan_age must be >= 0", MRS_EINVAL;
     if (cfg->mode != 0) return why = "only exact mode (0) is built", MRS_EUNSUPPORTED;
     for (int a = 0; a < cfg->n_arms; ++a) {
         const mrs_arm_desc &d = cfg->arms[a];
@@ -293,6 +295,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     P.w_coll = cfg->w_coll; P.w_self = cfg->w_self; P.w_dyn = cfg->w_dyn;
     P.B = cfg->B; P.B_world = cfg->B_world; P.B_self = cfg->B_self; P.tau = cfg->tau;
     P.q_margin = cfg->q_margin; P.seed = cfg->seed;
+    P.max_plan_age = cfg->max_plan_age;
 
     size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
     long long khd = 0, kh = 0;
@@ -308,6 +311,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         A.off_k = (int)ksum; A.off_in = (int)in;
         A.spg = (d.n_spheres + kGroups - 1) / kGroups;
         A.off_khd = khd; A.off_kh = kh;
+        A.external = d.external ? 1 : 0;
         for (int j = 0; j < d.dof; ++j) {
             A.dh[j] = make_float4(d.dh[4 * j], d.dh[4 * j + 1], d.dh[4 * j + 2], d.dh[4 * j + 3]);
             A.q_lo[j] = d.q_lo[j]; A.q_hi[j] = d.q_hi[j]; A.qd_max[j] = d.qd_max[j];

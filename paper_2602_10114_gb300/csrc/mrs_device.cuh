@@ -25,7 +25,8 @@ struct __align__(16) ArmDev {
     int dof, ns, K, H;
     int off_hd, off_hdd, off_hs, off_d;   // offsets into concatenated arrays
     int off_k, off_in, spg, self_off;     // spg: spheres per group (ceil(ns/8))
-    int n_self, pad1, pad2, pad3;         // self-collision pairs at self_off in Dev::self_pairs
+    int n_self, external, pad2, pad3;     // self-collision pairs at self_off in Dev::self_pairs;
+                                          // external: optimised elsewhere, plan from the board
     long long off_khd, off_kh;            // offsets into K*H*d and K*H work arrays
     float4 dh[kMaxDof];                   // a, d, alpha, theta_offset
     float2 twist[kMaxDof];                // sin(alpha), cos(alpha)
@@ -46,8 +47,16 @@ struct Params {
     int max_ns, max_pairs;        // largest sphere and self-pair counts of any arm
     int world_cap, aabb_cap;      // shared-memory capacity of the rollout for the world
     float eps_g;                  // cancellation margin of the expanded pair pre-test (m^2)
-    int pad;
+    int max_plan_age;             // board entries older than this are ignored (0: no limit)
 };
+
+// A neighbour's board entry is used when it is published and, with a
+// staleness limit, at most that many cycles old (Sec. IV-C missing plans).
+__device__ __forceinline__ bool plan_usable(const Params &P, int valid, long long stamp,
+                                            long long cycle)
+{
+    return valid && (P.max_plan_age <= 0 || cycle - stamp <= P.max_plan_age);
+}
 
 // Device pointers into the workspace.
 struct Dev {

@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MRS_ROLLOUT_MIN_BLOCKS) k_rol
     __shared__ float s_pose[32];
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
+    const long long cycle = *D.cycle;
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&D.work[iter], 1);
@@ -322,7 +323,8 @@ __global__ void __launch_bounds__(kRolloutThreads, MRS_ROLLOUT_MIN_BLOCKS) k_rol
             bool ok = false;
             int ns_i = 0;
             float al = 0.f;
-            if (i < NA && i != T.arm && D.board_valid[i] && h < D.arms[i].H) {   // min(H_j, H_i)
+            if (i < NA && i != T.arm && h < D.arms[i].H &&   // min(H_j, H_i)
+                plan_usable(P, D.board_valid[i], D.board_stamp[i], cycle)) {
                 ok = true;
                 ns_i = D.arms[i].ns;
                 al = D.alpha[T.arm * NA + i];

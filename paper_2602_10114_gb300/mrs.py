@@ -26,7 +26,8 @@ MAX_SPHERES = 64
 class MrsArmDesc(C.Structure):
     _fields_ = [("dof", C.c_int), ("n_spheres", C.c_int), ("K", C.c_int), ("H", C.c_int),
                 ("dh", _fp), ("q_lo", _fp), ("q_hi", _fp), ("qd_max", _fp),
-                ("sphere_body", _ip), ("sphere_xyzr", _fp), ("base_pose", C.c_float * 7)]
+                ("sphere_body", _ip), ("sphere_xyzr", _fp), ("base_pose", C.c_float * 7),
+                ("external", C.c_int)]
 
 
 class MrsConfig(C.Structure):
@@ -37,7 +38,8 @@ class MrsConfig(C.Structure):
                 ("w_joint", C.c_float), ("w_coll", C.c_float), ("w_self", C.c_float),
                 ("w_dyn", C.c_float), ("B", C.c_float), ("B_world", C.c_float),
                 ("B_self", C.c_float), ("tau", C.c_float), ("q_margin", C.c_float),
-                ("iterations", C.c_int), ("seed", C.c_ulonglong), ("mode", C.c_int)]
+                ("iterations", C.c_int), ("seed", C.c_ulonglong), ("mode", C.c_int),
+                ("max_plan_age", C.c_int)]
 
 
 class MrsArmState(C.Structure):
@@ -142,7 +144,7 @@ class Controller:
     """One library context for a `scenarios.Scenario` (or any object with the
     same fields).  The device workspace is a torch uint8 tensor on `device`."""
 
-    def __init__(self, sc, device="cuda", stream=None, workspace=True):
+    def __init__(self, sc, device="cuda", stream=None, workspace=True, external=()):
         import torch
         self.L = load()
         self.sc = sc
@@ -161,12 +163,15 @@ class Controller:
             s.sphere_xyzr = _pf(xyzr)
             for k in range(7):
                 s.base_pose[k] = float(a.base_pose[k])
+            s.external = 1 if i in external else 0
+        self.external = set(external)
         p = sc.params
         self.cfg = MrsConfig(A, self._arms, p["dt"], p["lam"], p["gamma"], p["alpha_mu"],
                              p["alpha_sigma"], p["sigma_init"], p["w_pose"], p["w_rot"],
                              p["w_stop"], p["w_joint"], p["w_coll"], p["w_self"], p["w_dyn"],
                              p["B"], p["B_world"], p["B_self"], p["tau"], p["q_margin"],
-                             int(p["iterations"]), int(p["seed"]), 0)
+                             int(p["iterations"]), int(p["seed"]), 0,
+                             int(p.get("max_plan_age", 0)))
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         h = C.c_void_p()
