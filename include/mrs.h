@@ -277,6 +277,39 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
  * uses.  Host arrays; allocates a temporary device buffer. */
 mrs_status mrs_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
+/* ------------------------------------------------------------------------
+ * Learned clearance surrogate (not in the paper: a small MLP that stands in
+ * for the exact self-collision distance of Eq. 5, with exact fallback near
+ * contact).  in_dim inputs (joint sin/cos features; zero-padded to a multiple
+ * of 16), `layers` hidden layers of `width` units (multiple of 16, <= 256)
+ * with SiLU, one linear output.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores, FP32 master weights trained with Adam.
+ * Parameter order (mrs_mlp_get_params / set_params, FP32): per hidden layer
+ * W [width][in] row-major then b [width]; then w_out [width], b_out [1].
+ * Device pointers are used on the network's stream; batch sizes passed to
+ * mrs_mlp_grads / mrs_mlp_train_step must be multiples of 8. */
+typedef struct mrs_mlp mrs_mlp;
+mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long seed,
+                          void *stream, mrs_mlp **out);
+void mrs_mlp_destroy(mrs_mlp *m);
+const char *mrs_mlp_last_error(const mrs_mlp *m);
+mrs_status mrs_mlp_param_count(const mrs_mlp *m, size_t *n);
+mrs_status mrs_mlp_get_params(mrs_mlp *m, float *host, size_t n);
+mrs_status mrs_mlp_set_params(mrs_mlp *m, const float *host, size_t n);
+/* y [n] = network(x [n][in_dim]), device pointers. */
+mrs_status mrs_mlp_forward(mrs_mlp *m, const float *d_x, int n, float *d_y);
+/* Gradients of the mean squared error against targets t [n] clipped to
+ * [-0.1, 0.3] m (host output in parameter order, and the loss). */
+mrs_status mrs_mlp_grads(mrs_mlp *m, const float *d_x, const float *d_t, int n, float *host_grads,
+                         float *host_loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss. */
+mrs_status mrs_mlp_train_step(mrs_mlp *m, const float *d_x, const float *d_t, int n, float lr,
+                              float *host_loss);
+
+/* Tensor-core GEMM self-test: C [M][N] (FP32) = A [M][K] B [N][K]^T with A, B
+ * BF16 bit patterns (host arrays); N multiple of 16 up to 256, K multiple of 8. */
+mrs_status mrs_selftest_gemm(int M, int N, int K, const uint16_t *A, const uint16_t *B, float *C);
+
 #ifdef __cplusplus
 }
 #endif

@@ -732,3 +732,83 @@ int orc_sample_costs(const orc_config *cfg, const orc_state *st, const orc_input
     free(e_now); free(alpha); free(mu); free(Sig); free(L); free(U);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned clearance surrogate (not in the paper): an MLP with SiLU hidden
+ * layers and a linear output, and the gradient of the mean squared error
+ * against targets clipped to [-0.1, 0.3] m.  Parameter order: per hidden
+ * layer W [width][in] (row-major) then b [width]; then w_out [width], b_out.
+ * Input rows of in_dim values are zero-padded to in_pad. */
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+static double dsilu(double z)
+{
+    double s = 1.0 / (1.0 + exp(-z));
+    return s * (1.0 + z * (1.0 - s));
+}
+
+double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const double *params, int n,
+                         const double *x, const double *t, double *grad, double *y_out)
+{
+    const int L = layers;
+    double *h = (double *)malloc(sizeof(double) * (size_t)(L + 1) * (in_pad > width ? in_pad : width));
+    double *z = (double *)malloc(sizeof(double) * (size_t)L * width);
+    double *dh = (double *)malloc(sizeof(double) * (in_pad > width ? in_pad : width));
+    double *dz = (double *)malloc(sizeof(double) * width);
+    if (!h || !z || !dh || !dz) return NAN;
+    const int stride = in_pad > width ? in_pad : width;
+    long long np = 0;
+    for (int l = 0; l < L; ++l) np += (long long)width * (l == 0 ? in_pad : width) + width;
+    np += width + 1;
+    if (grad)
+        for (long long i = 0; i < np; ++i) grad[i] = 0.0;
+    double loss = 0.0;
+    for (int r = 0; r < n; ++r) {
+        for (int c = 0; c < in_pad; ++c) h[c] = c < in_dim ? x[(size_t)r * in_dim + c] : 0.0;
+        long long o = 0;
+        for (int l = 0; l < L; ++l) {
+            const int in = l == 0 ? in_pad : width;
+            const double *W = params + o, *b = params + o + (long long)width * in;
+            for (int j = 0; j < width; ++j) {
+                double s = b[j];
+                for (int i = 0; i < in; ++i) s += W[(long long)j * in + i] * h[l * stride + i];
+                z[l * width + j] = s;
+                h[(l + 1) * stride + j] = silu(s);
+            }
+            o += (long long)width * in + width;
+        }
+        const double *wo = params + o, bo = params[o + width];
+        double y = bo;
+        for (int j = 0; j < width; ++j) y += wo[j] * h[L * stride + j];
+        if (y_out) y_out[r] = y;
+        double tc = t[r] < -0.1 ? -0.1 : (t[r] > 0.3 ? 0.3 : t[r]);
+        double e = y - tc;
+        loss += e * e / n;
+        if (!grad) continue;
+        /* backward */
+        double dy = 2.0 * e / n;
+        for (int j = 0; j < width; ++j) {
+            grad[o + j] += dy * h[L * stride + j];
+            dh[j] = dy * wo[j];
+        }
+        grad[o + width] += dy;
+        long long ol = o;
+        for (int l = L - 1; l >= 0; --l) {
+            const int in = l == 0 ? in_pad : width;
+            ol -= (long long)width * in + width;
+            const double *W = params + ol;
+            double *gW = grad + ol, *gb = grad + ol + (long long)width * in;
+            for (int j = 0; j < width; ++j) {
+                dz[j] = dh[j] * dsilu(z[l * width + j]);
+                gb[j] += dz[j];
+                for (int i = 0; i < in; ++i) gW[(long long)j * in + i] += dz[j] * h[l * stride + i];
+            }
+            for (int i = 0; i < in; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < width; ++j) s += W[(long long)j * in + i] * dz[j];
+                dh[i] = s;
+            }
+        }
+    }
+    free(h); free(z); free(dh); free(dz);
+    return loss;
+}

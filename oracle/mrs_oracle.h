@@ -153,6 +153,11 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
  * cycle; the state is not modified. */
 int orc_sample_costs(const orc_config *cfg, const orc_state *st, const orc_inputs *in, int arm,
                      int n_req, const int *ns, double *costs, double *spheres_out);
+/* Learned clearance surrogate (not in the paper): loss of an MLP with SiLU
+ * hidden layers against clipped targets and, if grad != NULL, its gradient;
+ * y_out (may be NULL) receives the outputs. */
+double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const double *params, int n,
+                         const double *x, const double *t, double *grad, double *y_out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

@@ -114,6 +114,9 @@ def lib():
             L.orc_sample_costs.restype = C.c_int
             L.orc_sample_costs.argtypes = [C.POINTER(OrcConfig), C.POINTER(OrcState),
                                            C.POINTER(OrcInputs), C.c_int, C.c_int, _ip, _dp, _dp]
+            L.orc_mlp_loss_grad.restype = C.c_double
+            L.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
+                                            _dp, _dp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -204,6 +207,19 @@ def weights(Cn, lam):
     w = np.zeros(len(Cn))
     lib().orc_weights(len(Cn), p, lam, _ptr(w))
     return w
+
+
+def mlp_loss_grad(in_dim, width, layers, params, x, t, want_grad=True):
+    """FP64 loss, gradient and outputs of the surrogate MLP."""
+    in_pad = (in_dim + 15) // 16 * 16
+    p, pp = _d(params)
+    x, px = _d(x)
+    t, pt = _d(t)
+    g = np.zeros(len(p)) if want_grad else None
+    y = np.zeros(len(t))
+    loss = lib().orc_mlp_loss_grad(in_dim, in_pad, width, layers, pp, len(t), px, pt,
+                                   _ptr(g), _ptr(y))
+    return loss, g, y
 
 
 # ---------------------------------------------------------------------------

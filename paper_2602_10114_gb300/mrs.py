@@ -85,6 +85,18 @@ SIGNATURES = {
     "mrs_kernel_times": (C.c_int, [C.c_void_p, _fp, C.POINTER(C.c_int)]),
     "mrs_philox": (C.c_int, [C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                              C.POINTER(C.c_uint32)]),
+    "mrs_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "mrs_mlp_destroy": (None, [C.c_void_p]),
+    "mrs_mlp_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrs_mlp_param_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "mrs_mlp_get_params": (C.c_int, [C.c_void_p, _fp, C.c_size_t]),
+    "mrs_mlp_set_params": (C.c_int, [C.c_void_p, _fp, C.c_size_t]),
+    "mrs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mrs_mlp_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, _fp, _fp]),
+    "mrs_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, _fp]),
+    "mrs_selftest_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint16),
+                                    C.POINTER(C.c_uint16), _fp]),
 }
 
 _lib = None
@@ -370,3 +382,97 @@ def state_blob(sc, mu, Sigma, cycle, world_t, plan_valid, plan_stamp, plan_dist,
         o_hd += hd
         o_hs += hs
     return b"".join(parts)
+
+
+def selftest_gemm(A_bits, B_bits):
+    """C = A B^T on the tensor cores, for BF16 bit patterns A [M][K], B [N][K]."""
+    L = load()
+    A_bits = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B_bits = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    M, K = A_bits.shape
+    N = B_bits.shape[0]
+    C_ = np.zeros((M, N), np.float32)
+    p16 = C.POINTER(C.c_uint16)
+    st = L.mrs_selftest_gemm(M, N, K, A_bits.ctypes.data_as(p16), B_bits.ctypes.data_as(p16),
+                             _pf(C_))
+    if st != 0:
+        raise MrsError(st, "selftest_gemm")
+    return C_
+
+
+class MLP:
+    """A clearance-surrogate network on the device (mrs_mlp_*).  Inputs and
+    targets are torch float32 CUDA tensors."""
+
+    def __init__(self, in_dim, width=256, layers=3, seed=0, stream=None):
+        import torch
+        self.L = load()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        st = self.L.mrs_mlp_create(in_dim, width, layers, seed, C.c_void_p(self.stream.cuda_stream),
+                                   C.byref(h))
+        if st != 0:
+            raise MrsError(st, "mrs_mlp_create")
+        self.h = h
+        self.in_dim, self.width, self.layers = in_dim, width, layers
+        n = C.c_size_t()
+        self.L.mrs_mlp_param_count(self.h, C.byref(n))
+        self.n_params = n.value
+
+    def _check(self, st, what):
+        if st != 0:
+            raise MrsError(st, f"{what}: {self.L.mrs_mlp_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mrs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        self._check(self.L.mrs_mlp_get_params(self.h, _pf(p), self.n_params), "get_params")
+        return p
+
+    def set_params(self, p):
+        p = _f32(p)
+        self._check(self.L.mrs_mlp_set_params(self.h, _pf(p), len(p)), "set_params")
+
+    def forward(self, x):
+        import torch
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        self._check(self.L.mrs_mlp_forward(self.h, C.c_void_p(x.data_ptr()), x.shape[0],
+                                           C.c_void_p(y.data_ptr())), "forward")
+        return y
+
+    def grads(self, x, t):
+        g = np.zeros(self.n_params, np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(self.L.mrs_mlp_grads(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                         x.shape[0], _pf(g), _pf(loss)), "grads")
+        return g, float(loss[0])
+
+    def train_step(self, x, t, lr):
+        loss = np.zeros(1, np.float32)
+        self._check(self.L.mrs_mlp_train_step(self.h, C.c_void_p(x.data_ptr()),
+                                              C.c_void_p(t.data_ptr()), x.shape[0], float(lr),
+                                              _pf(loss)), "train_step")
+        return float(loss[0])
+
+    def unpack(self, p):
+        """Split a flat parameter vector into [(W, b), ...], (w_out, b_out)."""
+        out, o = [], 0
+        in_pad = (self.in_dim + 15) // 16 * 16
+        for l in range(self.layers):
+            fan = in_pad if l == 0 else self.width
+            W = p[o:o + self.width * fan].reshape(self.width, fan)
+            o += self.width * fan
+            b = p[o:o + self.width]
+            o += self.width
+            out.append((W, b))
+        return out, (p[o:o + self.width], p[o + self.width:o + self.width + 1])

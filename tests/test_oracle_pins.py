@@ -534,3 +534,43 @@ def test_sample_costs_agree_with_the_cycle(oracle_mod):
     out = orc.cycle(sc.q0, sc.qd0, gp, gR)
     for a in range(sc.n_arms):
         assert np.array_equal(before[a], orc.split(out["costs"], "k", a)[ns])
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate (not in the paper): FP64 MLP gradient
+
+def test_mlp_gradient_matches_central_differences(oracle_mod):
+    rng = np.random.default_rng(21)
+    in_dim, width, layers = 14, 16, 3
+    in_pad = 16
+    n_par = width * in_pad + width + 2 * (width * width + width) + width + 1
+    p = rng.normal(scale=0.4, size=n_par)
+    x = rng.normal(size=(9, in_dim))
+    t = rng.uniform(-0.2, 0.4, 9)          # some targets beyond the clip range
+    loss, g, _ = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, t)
+    idx = rng.choice(n_par, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        if (i % (width * in_pad + width)) < width * in_pad and i < width * in_pad + width \
+                and (i % in_pad) >= in_dim:
+            continue          # weights on padding inputs: zero gradient
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (oracle_mod.mlp_loss_grad(in_dim, width, layers, pp, x, t, False)[0]
+              - oracle_mod.mlp_loss_grad(in_dim, width, layers, pm, x, t, False)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_forward_closed_form(oracle_mod):
+    """One hidden unit layer per layer with known weights: y = w_out silu(...)."""
+    in_dim, width, layers = 1, 16, 1
+    p = np.zeros(16 * 16 + 16 + 16 + 1)
+    p[0] = 2.0                              # W[0][0]
+    p[256 + 0] = 0.5                        # b[0]
+    p[256 + 16 + 0] = 3.0                   # w_out[0]
+    p[-1] = -0.25                           # b_out
+    x = np.array([[0.7]])
+    _, _, y = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, np.zeros(1), False)
+    z = 2.0 * 0.7 + 0.5
+    assert math.isclose(y[0], 3.0 * z / (1 + math.exp(-z)) - 0.25, rel_tol=1e-14)
