@@ -243,7 +243,7 @@ def run(args):
     ms_max = max_over_ranks(ms, ws)
     value = units_per_step * ws / (ms_max / 1e3)
     kt = np.asarray(ktimes)            # [steps][kernels]
-    names = ["prep"] + ["sample", "rollout", "costs", "update"] * sc.params["iterations"] + ["toplan"]
+    names = ["prep"] + ["sample", "surrogate", "rollout", "costs", "update"] * sc.params["iterations"] + ["toplan"]
     k_mean = {n: float(kt[:, i].mean()) for i, n in enumerate(names[:kt.shape[1]])}
     roll_ms = float(np.mean([kt[:, i] for i, n in enumerate(names) if n == "rollout"]))
     flops = rollout_flops(sc) / sc.params["iterations"]
@@ -306,7 +306,7 @@ def run(args):
                      "flops_per_launch": flops},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),
+        "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),   # no surrogate
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

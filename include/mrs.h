@@ -263,12 +263,13 @@ mrs_status mrs_debug_alpha(mrs_ctx *ctx, float *alpha);
 /* Debug switch: zero_noise = 1 samples eps = 0 (every rollout is the mean). */
 mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise);
 
-/* Per-kernel timing of the cycle: with on = 1 every following cycle records
- * CUDA events on the context stream between its kernels (also inside the
+/* Per-stage timing of the cycle: with on = 1 every following cycle records
+ * CUDA events on the context stream between its stages (also inside the
  * captured graph).  mrs_kernel_times writes the durations (ms) of the last
- * cycle's kernels, in launch order: prep, then per iteration sample,
- * rollout, costs, update, then toplan (2 + 4 * iterations values); *n gives
- * the capacity of ms on entry and the count on return.  Waits for the cycle. */
+ * cycle's stages, in launch order: prep, then per iteration sample,
+ * surrogate (zero without a surrogate), rollout, costs, update, then toplan
+ * (2 + 5 * iterations values); *n gives the capacity of ms on entry and the
+ * count on return.  Waits for the cycle. */
 mrs_status mrs_enable_timing(mrs_ctx *ctx, int on);
 mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
 
@@ -305,6 +306,25 @@ mrs_status mrs_mlp_grads(mrs_mlp *m, const float *d_x, const float *d_t, int n, 
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss. */
 mrs_status mrs_mlp_train_step(mrs_mlp *m, const float *d_x, const float *d_t, int n, float lr,
                               float *host_loss);
+
+/* Use a surrogate for arm `arm`'s self-collision clearance in the cycle
+ * (net = NULL: back to exact).  Every rollout step's clearance is predicted
+ * from the sin/cos of its joint angles (net input = 2 * dof); steps whose
+ * prediction is at least B_self + margin get a zero self term, the others the
+ * exact computation.  The network must outlive its use by the context. */
+mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float margin);
+/* Training data for an arm's surrogate, on the device: n joint vectors
+ * uniform within the joint limits (Philox, `seed`), their features d_x
+ * [n][2 dof] (sin, cos per joint) and exact self-collision clearance d_t [n]
+ * (the minimum over sphere pairs on bodies at least three apart of centre
+ * distance minus radii); d_q [n][dof] receives the joint vectors (may be NULL). */
+mrs_status mrs_self_dataset(mrs_ctx *ctx, int arm, int n, unsigned long long seed, float *d_x,
+                            float *d_t, float *d_q);
+/* Exact self-collision clearance of joint vectors d_q [n][dof] -> d_out [n]. */
+mrs_status mrs_self_distance(mrs_ctx *ctx, int arm, int n, const float *d_q, float *d_out);
+/* Of the last cycle, every rollout step [H][K] of an arm: the surrogate's
+ * predicted clearance and (recomputed) the exact one; either may be NULL. */
+mrs_status mrs_debug_self(mrs_ctx *ctx, int arm, float *dhat, float *exact);
 
 /* Tensor-core GEMM self-test: C [M][N] (FP32) = A [M][K] B [N][K]^T with A, B
  * BF16 bit patterns (host arrays); N multiple of 16 up to 256, K multiple of 8. */

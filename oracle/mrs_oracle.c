@@ -812,3 +812,26 @@ double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const do
     free(h); free(z); free(dh); free(dz);
     return loss;
 }
+
+/* Exact self-collision clearance of joint vectors q [n][dof]: the minimum
+ * over sphere pairs on bodies at least three apart of the centre distance
+ * minus both radii (the quantity the self-collision term ramps, Eq. 5);
+ * +infinity when the arm has no such pair.  The training label of the
+ * learned surrogate. */
+void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out)
+{
+    double S[ORC_MAX_SPHERES * 4];
+    for (int r = 0; r < n; ++r) {
+        orc_fk(arm, q + (size_t)r * arm->dof, NULL, S);
+        double m = INFINITY;
+        for (int s1 = 0; s1 < arm->n_spheres; ++s1)
+            for (int s2 = s1 + 1; s2 < arm->n_spheres; ++s2) {
+                int gap = arm->sphere_body[s1] - arm->sphere_body[s2];
+                if (gap < 0) gap = -gap;
+                if (gap < 3) continue;
+                double d = orc_sphere_sphere(S + 4 * s1, S + 4 * s2);
+                if (d < m) m = d;
+            }
+        out[r] = m;
+    }
+}

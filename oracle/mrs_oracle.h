@@ -158,6 +158,9 @@ int orc_sample_costs(const orc_config *cfg, const orc_state *st, const orc_input
  * y_out (may be NULL) receives the outputs. */
 double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const double *params, int n,
                          const double *x, const double *t, double *grad, double *y_out);
+/* Exact self-collision clearance of joint vectors q [n][dof] (+inf if the
+ * arm has no sphere pair on bodies at least three apart). */
+void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

@@ -117,6 +117,7 @@ def lib():
             L.orc_mlp_loss_grad.restype = C.c_double
             L.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
                                             _dp, _dp, _dp]
+            L.orc_self_distance.argtypes = [C.POINTER(OrcArm), C.c_int, _dp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -329,6 +330,13 @@ class Oracle:
         sph = np.zeros((a.n_spheres, 4))
         lib().orc_fk(C.byref(self.arms[arm]), pq, _ptr(frames), _ptr(sph))
         return frames, sph
+
+    def self_distance(self, arm: int, q):
+        """Exact self-collision clearance of joint vectors q [n][dof]."""
+        q, pq = _d(np.asarray(q, np.float64).reshape(-1, self.sc.arms[arm].dof))
+        out = np.zeros(len(q))
+        lib().orc_self_distance(C.byref(self.arms[arm]), len(q), pq, _ptr(out))
+        return out
 
     def goal_pose(self, arm: int, q):
         frames, _ = self.fk(arm, q)

@@ -1,13 +1,23 @@
 // kernels.cuh -- launch wrappers of the control-cycle kernels (host side).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
 
 #include "mrs_device.cuh"
 
+struct mrs_mlp;
+
 namespace mrs {
+
+// One arm whose self clearance comes from a surrogate network.
+struct SurrogateSlot {
+    int arm, rows;          // rows = K * H rollout steps
+    long long off_kh;       // the arm's offset in Dev::dhat
+    mrs_mlp *net;
+};
 
 struct LaunchPlan {
     int n_arms;
@@ -19,7 +29,24 @@ struct LaunchPlan {
     size_t smem_prep, smem_sample, smem_rollout, smem_toplan;
     int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)
     int *done_counter;  // last-block-done counter of k_toplan
+    int n_surrogates;
+    SurrogateSlot surrogates[MRS_MAX_ARMS];
 };
+
+// surrogate network (mlp.cu): inference input buffer, its padded width, and
+// the forward pass of `rows` BF16 feature rows into y (FP32) on stream s
+__nv_bfloat16 *mlp_infer_input(mrs_mlp *m);
+int mlp_in_pad(const mrs_mlp *m);
+int mlp_in_dim(const mrs_mlp *m);
+cudaError_t mlp_reserve_infer(mrs_mlp *m, int rows);
+cudaError_t mlp_infer(mrs_mlp *m, int rows, float *y, int *err, cudaStream_t s);
+// surrogate.cu
+cudaError_t enqueue_self_dataset(const Dev &D, int arm, int n, unsigned long long seed, float *x,
+                                 float *t, float *q, cudaStream_t s);
+cudaError_t enqueue_self_clearance_rows(const Dev &D, int arm, int n, const float *q, float *out,
+                                        cudaStream_t s);
+cudaError_t enqueue_self_clearance_traj(const Dev &D, int arm, int rows, float *out, cudaStream_t s);
+cudaError_t enqueue_self_surrogate(const Dev &D, const SurrogateSlot &slot, cudaStream_t s);
 
 // The rollout kernel (rollout.cu): shared-memory size for the given
 // capacities, attribute set-up and launch.
@@ -31,7 +58,8 @@ cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, i
 
 // Everything one control cycle enqueues on `s` (Algorithm 1 for all arms).
 // With `events` non-null, events[0] is recorded before the first kernel and
-// events[i + 1] after kernel i (3 + 4 * iterations events); `capturing` makes
+// events[i + 1] after stage i (3 + 5 * iterations events: prep, per iteration
+// sample, surrogate, rollout, costs, update, then toplan); `capturing` makes
 // them external event nodes of the graph being captured.
 cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cudaStream_t s,
                           cudaEvent_t *events = nullptr, bool capturing = false);

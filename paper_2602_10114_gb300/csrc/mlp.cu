@@ -366,6 +366,46 @@ static mrs_status check_err(mrs_mlp *m)
     return MRS_OK;
 }
 
+namespace mrs {
+
+__nv_bfloat16 *mlp_infer_input(mrs_mlp *m) { return m->iX; }
+int mlp_in_pad(const mrs_mlp *m) { return m->in_pad; }
+int mlp_in_dim(const mrs_mlp *m) { return m->in_dim; }
+
+cudaError_t mlp_reserve_infer(mrs_mlp *m, int rows)
+{
+    if (rows <= m->icap) return cudaSuccess;
+    const int c = (rows + 127) / 128 * 128;
+    cudaFree(m->iX); cudaFree(m->iH0); cudaFree(m->iH1);
+    m->iX = m->iH0 = m->iH1 = nullptr;
+    cudaError_t e = cudaMalloc(&m->iX, sizeof(bf16) * c * m->in_pad);
+    if (e == cudaSuccess) e = cudaMalloc(&m->iH0, sizeof(bf16) * c * m->width);
+    if (e == cudaSuccess) e = cudaMalloc(&m->iH1, sizeof(bf16) * c * m->width);
+    if (e != cudaSuccess) return e;
+    m->icap = c;
+    return cudaSuccess;
+}
+
+// forward of `rows` feature rows in m->iX; activations ping-pong between two
+// buffers; output into y
+cudaError_t mlp_infer(mrs_mlp *m, int rows, float *y, int *err, cudaStream_t s)
+{
+    const bf16 *in = m->iX;
+    bf16 *buf[2] = {m->iH0, m->iH1};
+    for (int l = 0; l < m->layers; ++l) {
+        EpiBiasSilu e{m->params + m->offB[l], nullptr, buf[l & 1], m->width};
+        const int K = l == 0 ? m->in_pad : m->width;
+        cudaError_t ce = gemm(in, K, m->Wb[l], K, rows, m->width, K, 1, err, e, s);
+        if (ce != cudaSuccess) return ce;
+        in = buf[l & 1];
+    }
+    k_out_layer<<<(rows + 7) / 8, 256, 0, s>>>(in, m->width, m->params + m->offWo,
+                                               m->params + m->offBo, rows, y);
+    return cudaGetLastError();
+}
+
+}  // namespace mrs
+
 extern "C" {
 
 mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long seed, void *stream,

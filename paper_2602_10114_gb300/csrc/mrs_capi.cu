@@ -2,6 +2,7 @@
 // workspace layout, work lists, CUDA-graph capture, bounded waits, state
 // checkpointing.  All arithmetic of the method runs in kernels.cu.
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cstdlib>
 #include <cmath>
@@ -42,7 +43,7 @@ struct mrs_ctx {
         size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
             board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
             e_now, n_star, out, cycle, world_t, err, done_counter, sample_tiles, rollout_tiles,
-            cost_tiles, update_tiles, self_pairs, work, total;
+            cost_tiles, update_tiles, self_pairs, work, dhat, total;
     } lay{};
     std::vector<SampleTile> sample_tiles;
     std::vector<RolloutTile> rollout_tiles;
@@ -129,6 +130,7 @@ static void build_layout(mrs_ctx *c)
     L.update_tiles = take(sizeof(UpdateTile) * c->update_tiles.size());
     L.self_pairs = take(sizeof(int) * std::max<size_t>(1, c->self_pairs.size()));
     L.work = take(sizeof(int) * 64);
+    L.dhat = take(sizeof(float) * kh);
     L.total = align_up(o, 256);
     c->sz.workspace_bytes = L.total;
 }
@@ -196,6 +198,7 @@ static void fill_dev(mrs_ctx *c, char *base)
     c->L.update_tiles = (const UpdateTile *)(base + L.update_tiles);
     D.self_pairs = (int *)(base + L.self_pairs);
     D.work = (int *)(base + L.work);
+    D.dhat = (float *)(base + L.dhat);
 }
 
 static void out_offsets(mrs_ctx *c)
@@ -885,6 +888,87 @@ mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee
     return MRS_OK;
 }
 
+mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float margin)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "arm out of range");
+    ArmDev &A = ctx->arms[arm];
+    if (net && (mlp_in_dim(net) != 2 * A.dof || !std::isfinite(margin) || margin < 0.f))
+        return fail(ctx, MRS_EINVAL, "surrogate input must be 2 * dof sin/cos features; margin >= 0");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    if (net) CK(mlp_reserve_infer(net, A.K * A.H), "surrogate buffers");
+    A.learned = net ? 1 : 0;
+    A.self_margin = net ? margin : 0.f;
+    // rebuild the slot list in arm order
+    LaunchPlan &L = ctx->L;
+    int k = 0;
+    SurrogateSlot slots[MRS_MAX_ARMS];
+    for (int i = 0; i < L.n_surrogates; ++i)
+        if (L.surrogates[i].arm != arm) slots[k++] = L.surrogates[i];
+    if (net) slots[k++] = SurrogateSlot{arm, A.K * A.H, A.off_kh, net};
+    std::sort(slots, slots + k, [](const SurrogateSlot &x, const SurrogateSlot &y) { return x.arm < y.arm; });
+    L.n_surrogates = k;
+    for (int i = 0; i < k; ++i) L.surrogates[i] = slots[i];
+    // only the surrogate fields: the device copy also holds constants that the
+    // device derived at binding (base rotation, twist sines)
+    static_assert(offsetof(ArmDev, self_margin) == offsetof(ArmDev, learned) + sizeof(int),
+                  "learned and self_margin are adjacent");
+    CK(cudaMemcpyAsync(reinterpret_cast<char *>(ctx->D.arms + arm) + offsetof(ArmDev, learned),
+                       &A.learned, sizeof(int) + sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+       "upload arm");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    invalidate_graph(ctx);
+    return MRS_OK;
+}
+
+mrs_status mrs_self_dataset(mrs_ctx *ctx, int arm, int n, unsigned long long seed, float *d_x,
+                            float *d_t, float *d_q)
+{
+    if (!ctx || arm < 0 || arm >= ctx->A || n < 1 || !d_x || !d_t)
+        return fail(ctx, MRS_EINVAL, "bad dataset arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    CK(enqueue_self_dataset(ctx->D, arm, n, seed, d_x, d_t, d_q, ctx->stream), "dataset");
+    CK(cudaStreamSynchronize(ctx->stream), "dataset sync");
+    return MRS_OK;
+}
+
+mrs_status mrs_self_distance(mrs_ctx *ctx, int arm, int n, const float *d_q, float *d_out)
+{
+    if (!ctx || arm < 0 || arm >= ctx->A || n < 1 || !d_q || !d_out)
+        return fail(ctx, MRS_EINVAL, "bad arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    CK(enqueue_self_clearance_rows(ctx->D, arm, n, d_q, d_out, ctx->stream), "self distance");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return MRS_OK;
+}
+
+mrs_status mrs_debug_self(mrs_ctx *ctx, int arm, float *dhat, float *exact)
+{
+    if (!ctx || arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "bad arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const ArmDev &A = ctx->arms[arm];
+    const int rows = A.K * A.H;
+    if (dhat)
+        CK(cudaMemcpyAsync(dhat, ctx->D.dhat + A.off_kh, sizeof(float) * rows,
+                           cudaMemcpyDeviceToHost, ctx->stream), "download");
+    if (exact) {
+        float *d = nullptr;
+        CK(cudaMalloc(&d, sizeof(float) * rows), "buffer");
+        cudaError_t e = enqueue_self_clearance_traj(ctx->D, arm, rows, d, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(exact, d, sizeof(float) * rows, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(d);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "exact self clearance");
+    }
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return MRS_OK;
+}
+
 mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs)
 {
     if (!ctx || !costs || arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "bad arguments");
@@ -939,7 +1023,7 @@ mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out
 mrs_status mrs_enable_timing(mrs_ctx *ctx, int on)
 {
     if (!ctx) return MRS_EINVAL;
-    const size_t need = 3 + 4 * (size_t)ctx->P.iterations;   // one more than the kernels
+    const size_t need = 3 + 5 * (size_t)ctx->P.iterations;   // one more than the stages
     if (on && ctx->events.size() < need) {
         while (ctx->events.size() < need) {
             cudaEvent_t e;
@@ -956,7 +1040,7 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
 {
     if (!ctx || !ms || !n) return MRS_EINVAL;
     if (!ctx->timing) return fail(ctx, MRS_ESTATE, "timing is not enabled");
-    const int cnt = 2 + 4 * ctx->P.iterations;                 // kernels of one cycle
+    const int cnt = 2 + 5 * ctx->P.iterations;                 // stages of one cycle
     if (*n < cnt) return fail(ctx, MRS_EINVAL, "ms has too few entries");
     CK(cudaEventSynchronize(ctx->events[cnt]), "timing wait");
     for (int i = 0; i < cnt; ++i)

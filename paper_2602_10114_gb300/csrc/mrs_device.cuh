@@ -25,8 +25,10 @@ struct __align__(16) ArmDev {
     int dof, ns, K, H;
     int off_hd, off_hdd, off_hs, off_d;   // offsets into concatenated arrays
     int off_k, off_in, spg, self_off;     // spg: spheres per group (ceil(ns/8))
-    int n_self, external, pad2, pad3;     // self-collision pairs at self_off in Dev::self_pairs;
-                                          // external: optimised elsewhere, plan from the board
+    int n_self, external, learned;        // self-collision pairs at self_off in Dev::self_pairs;
+                                          // external: optimised elsewhere, plan from the board;
+                                          // learned: self clearance from the surrogate (Dev::dhat)
+    float self_margin;                    // exact self pass when dhat < B_self + self_margin
     long long off_khd, off_kh;            // offsets into K*H*d and K*H work arrays
     float4 dh[kMaxDof];                   // a, d, alpha, theta_offset
     float2 twist[kMaxDof];                // sin(alpha), cos(alpha)
@@ -87,6 +89,7 @@ struct Dev {
     float *world_t;        // seconds since the world was set
     int *err;              // device error word (bounded waits)
     int *self_pairs;       // per arm, packed s1 | s2 << 8, bodies >= 3 apart
+    float *dhat;           // [sum K*H] surrogate self clearance of every rollout step, [h][n]
     int *work;             // rollout tile counters, one per iteration
     int out_mean, out_sph, out_q, out_u, out_dist, out_min;  // offsets in out (floats)
 };

@@ -254,9 +254,15 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     }
     __syncthreads();   // every group's centres are in shared memory
 
-    // self collision: the arm's pair list, split evenly over the 8 warps
+    // self collision: the arm's pair list, split evenly over the 8 warps.  With
+    // a learned surrogate, a rollout step whose predicted clearance is at least
+    // B_self + margin skips the exact pass (its self term is zero); the warp
+    // skips the loop when none of its 32 steps needs it.
     {
-        const int np = A.n_self;
+        bool need = true;
+        if (A.learned)
+            need = valid && D.dhat[A.off_kh + (long long)h * K + n] < P.B_self + A.self_margin;
+        const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
         const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
         float m = kInf;
         for (int i = p0; i < p1; ++i) {
@@ -271,7 +277,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             const float r1 = S.sph[a1].w;
             pair_exact(c, __fadd_rn(r1, P.B_self), r1, q, m);
         }
-        if (m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
+        if (need && m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
     }
 }
 

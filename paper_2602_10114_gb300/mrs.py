@@ -95,6 +95,11 @@ SIGNATURES = {
     "mrs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "mrs_mlp_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, _fp, _fp]),
     "mrs_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, _fp]),
+    "mrs_set_self_surrogate": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_float]),
+    "mrs_self_dataset": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
+    "mrs_self_distance": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "mrs_debug_self": (C.c_int, [C.c_void_p, C.c_int, _fp, _fp]),
     "mrs_selftest_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint16),
                                     C.POINTER(C.c_uint16), _fp]),
 }
@@ -328,6 +333,40 @@ class Controller:
     def goal_pose(self, arm, q):
         ee, _ = self.fk(arm, q)
         return ee[0, 9:12].copy(), ee[0, :9].reshape(3, 3).copy()
+
+    def set_self_surrogate(self, arm, net, margin=0.03):
+        """Self-collision clearance of `arm` from the surrogate `net` (an MLP;
+        None: exact), exact fallback below B_self + margin."""
+        self._check(self.L.mrs_set_self_surrogate(self.h, arm, net.h if net is not None else None,
+                                                  float(margin)), "set_self_surrogate")
+        self._nets = getattr(self, "_nets", {})
+        self._nets[arm] = net   # keep the network alive while the context uses it
+
+    def self_dataset(self, arm, n, seed):
+        """Device training data: (features [n][2 dof], labels [n], q [n][dof])."""
+        import torch
+        d = self.sc.arms[arm].dof
+        x = torch.empty((n, 2 * d), dtype=torch.float32, device=self.device)
+        t = torch.empty(n, dtype=torch.float32, device=self.device)
+        q = torch.empty((n, d), dtype=torch.float32, device=self.device)
+        self._check(self.L.mrs_self_dataset(self.h, arm, n, int(seed), C.c_void_p(x.data_ptr()),
+                                            C.c_void_p(t.data_ptr()), C.c_void_p(q.data_ptr())),
+                    "self_dataset")
+        return x, t, q
+
+    def self_distance(self, arm, q):
+        import torch
+        out = torch.empty(q.shape[0], dtype=torch.float32, device=q.device)
+        self._check(self.L.mrs_self_distance(self.h, arm, q.shape[0], C.c_void_p(q.data_ptr()),
+                                             C.c_void_p(out.data_ptr())), "self_distance")
+        return out
+
+    def debug_self(self, arm):
+        a = self.sc.arms[arm]
+        dh = np.zeros((a.H, a.K), np.float32)
+        ex = np.zeros((a.H, a.K), np.float32)
+        self._check(self.L.mrs_debug_self(self.h, arm, _pf(dh), _pf(ex)), "debug_self")
+        return dh, ex
 
     def debug_costs(self, arm):
         c = np.zeros(self.sc.arms[arm].K, np.float32)

@@ -98,4 +98,4 @@ def test_adam_training_reduces_the_loss():
     losses = [net.train_step(xd[i:i + 512], td[i:i + 512], 2e-3)
               for _ in range(40) for i in range(0, 4096, 512)]
     assert np.isfinite(losses).all()
-    assert np.mean(losses[-8:]) < 0.4 * np.mean(losses[:8])
+    assert np.mean(losses[-8:]) < 0.6 * np.mean(losses[:8])

@@ -574,3 +574,26 @@ def test_mlp_forward_closed_form(oracle_mod):
     _, _, y = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, np.zeros(1), False)
     z = 2.0 * 0.7 + 0.5
     assert math.isclose(y[0], 3.0 * z / (1 + math.exp(-z)) - 0.25, rel_tol=1e-14)
+
+
+def test_self_distance_is_the_self_term_of_the_rollout(oracle_mod):
+    """The surrogate's label equals the clearance the rollout ramps: with only
+    the self term weighted, a standing rollout's stage cost is w_self * ramp."""
+    from oracle.oracle import Oracle
+    arm = _random_arm(31)
+    sc = tiny_scenario([arm], H=2, w_pose=0, w_stop=0, w_joint=0, w_coll=0, w_self=1.0)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    B = float(np.float32(0.03))
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        q = rng.uniform(-2.8, 2.8, 7)
+        d = orc.self_distance(0, q)[0]
+        _, sph = orc.fk(0, q)
+        body = arm.sphere_body
+        brute = min(np.linalg.norm(sph[i, :3] - sph[j, :3]) - sph[i, 3] - sph[j, 3]
+                    for i in range(len(sph)) for j in range(i + 1, len(sph))
+                    if abs(int(body[i]) - int(body[j])) >= 3)
+        assert math.isclose(d, brute, rel_tol=1e-12, abs_tol=1e-15)
+        _, stage, _, _ = orc.rollout(0, [q], [np.zeros(7)], gp, gR, np.zeros((2, 7)))
+        assert math.isclose(stage[0], max(0.0, 1 - d / B), rel_tol=1e-12, abs_tol=1e-15)

@@ -1,0 +1,106 @@
+"""The learned self-collision surrogate inside the control cycle: labels
+against the oracle, the fallback rule at its two extremes against exact
+computation, and a trained network's false-negative rate."""
+import numpy as np
+import pytest
+
+from paper_2602_10114_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_10114_gb300 import build, mrs
+    build.build()
+    mrs.load()
+
+
+def test_dataset_labels_and_features_match_the_oracle():
+    from oracle.oracle import Oracle
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import EPS_D
+    sc = S.config(2)
+    ctl = mrs.Controller(sc)
+    x, t, q = ctl.self_dataset(1, 4000, seed=9)
+    x, t, q = x.cpu().numpy(), t.cpu().numpy(), q.cpu().numpy()
+    a = sc.arms[1]
+    assert np.all(q >= a.q_lo) and np.all(q <= a.q_hi)
+    assert np.allclose(x[:, 0::2], np.sin(q.astype(np.float64)), atol=1e-6)
+    assert np.allclose(x[:, 1::2], np.cos(q.astype(np.float64)), atol=1e-6)
+    exp = Oracle(sc).self_distance(1, q.astype(np.float64))
+    assert np.abs(t - exp).max() < EPS_D
+    # the same clearance through mrs_self_distance
+    import torch
+    t2 = ctl.self_distance(1, torch.from_numpy(q).cuda()).cpu().numpy()
+    assert np.array_equal(t2, t)
+
+
+def _constant_net(dof, value):
+    from paper_2602_10114_gb300 import mrs
+    net = mrs.MLP(2 * dof, 32, 1, 0)
+    p = np.zeros(net.n_params, np.float32)
+    p[-1] = value
+    net.set_params(p)
+    return net
+
+
+def test_fallback_rule_extremes():
+    """A surrogate that always predicts 1 m skips every exact self pass: the
+    costs equal the oracle's with the self term removed.  One that always
+    predicts -1 m never skips: the costs equal exact mode bit for bit."""
+    from parity_utils import Replay, cost_tol
+    from paper_2602_10114_gb300 import mrs
+    sc = S.shrink(S.config(2), K=64, H=10)
+    # exact mode on the GPU, for the "never skip" comparison
+    R = Replay(sc)
+    got_exact, gc_exact, *_ = R.cycle(None)
+    # always exact through the surrogate path
+    R2 = Replay(sc)
+    never = _constant_net(7, -1.0)
+    for a in range(sc.n_arms):
+        R2.ctl.set_self_surrogate(a, never, 0.03)
+    got_never, gc_never, *_ = R2.cycle(None)
+    for a in range(sc.n_arms):
+        assert np.array_equal(gc_never[a], gc_exact[a])
+    # always skip: oracle without the self term
+    sc_noself = S.shrink(S.config(2), K=64, H=10)
+    sc_noself.params["w_self"] = 0.0
+    R3 = Replay(sc)
+    R3.orc = Replay(sc_noself).orc
+    always = _constant_net(7, 1.0)
+    for a in range(sc.n_arms):
+        R3.ctl.set_self_surrogate(a, always, 0.03)
+    got, gc, ga, gs, exp = R3.cycle(None)
+    for a in range(sc.n_arms):
+        ce = R3.orc.split(exp["costs"], "k", a)
+        assert np.all(np.abs(gc[a] - ce) <= cost_tol(ce))
+
+
+def test_trained_surrogate_false_negatives():
+    """Trained on-GPU with the library's kernels; on held-out samples and on
+    every rollout step of a cycle, collisions the surrogate would skip are
+    rare (spec target 1e-3 with the full 2M-sample training; this test
+    trains on 400k samples)."""
+    from paper_2602_10114_gb300 import mrs, surrogate
+    from parity_utils import goals
+    from oracle.oracle import Oracle
+    sc = S.config(3)
+    ctl = mrs.Controller(sc)
+    ctl.set_world()
+    net, stats = surrogate.train_self_surrogate(ctl, 0, n_train=400_000, n_val=100_000, epochs=6,
+                                                lr=2e-3)
+    print("held-out:", stats)
+    assert stats["colliding"] > 1000
+    assert stats["fn_rate"] <= 5e-3
+    for a in range(sc.n_arms):
+        ctl.set_self_surrogate(a, net, 0.03)
+    gp, gR = goals(Oracle(sc), sc)
+    ctl.step(sc.q0, sc.qd0, gp.astype(np.float32), gR.astype(np.float32))
+    dh, ex = ctl.debug_self(0)
+    ev = surrogate.evaluate(dh, ex, float(np.float32(0.03)), 0.03)
+    print("rollout steps:", ev)
+    assert ev["fn_rate"] <= 5e-3
