@@ -195,6 +195,205 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_device(ctl, d_in, steps, warmup, flush, ws, local=0, sample_clocks=False):
+    """Per-cycle CUDA-event times (ms) of device-resident cycles, L2 flushed
+    before each; also the per-stage times of every cycle."""
+    import torch
+    s = ctl.stream
+    ctl.enable_timing(True)
+    for _ in range(max(warmup, 3)):
+        ctl.step_device(d_in)
+    ctl.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ktimes = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    for i in range(steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+            starts[i].record(s)
+        ctl.step_device(d_in)
+        with torch.cuda.stream(s):
+            ends[i].record(s)
+        ktimes.append(ctl.kernel_times())
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    barrier(ws)
+    ctl.enable_timing(False)
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], np.asarray(ktimes), clk
+
+
+def time_e2e(ctls, sc, gp, gR, cycles, warmup, flush, ws, episode=50):
+    """Wall-clock latency of mrs_step with host buffers, closed loop (the host
+    plant integrates U_*, goals drift), in episodes of `episode` cycles that
+    restart from the initial state.  `ctls` is one Controller holding every
+    arm, or one Controller per arm (the others external, their plans passed
+    through mrs_share_plans after each arm's call: one arm at a time)."""
+    import torch
+    from paper_2602_10114_gb300 import exchange
+    ctls = ctls if isinstance(ctls, list) else [ctls]
+    blobs = [c.save_state() for c in ctls]
+    dt = np.float32(sc.params["dt"])
+
+    def one_cycle(q, qd, gpl, k):
+        outs = {}
+        for c in ctls:
+            out = c.step(q, qd, gpl, gR)
+            if len(ctls) > 1:
+                ents = exchange.local_entries(c, out, k)
+                for o in ctls:
+                    if o is not c:
+                        exchange.share_remote(o, ents)
+            for a in range(sc.n_arms):
+                if a not in c.external:
+                    outs[a] = c.split(out["u_star"], "d", a)
+        return outs
+
+    def episode_state():
+        return ([x.astype(np.float32).copy() for x in sc.q0],
+                [x.astype(np.float32).copy() for x in sc.qd0], [g.copy() for g in gp])
+
+    q, qd, gpl = episode_state()
+    for k in range(max(warmup, 3)):
+        one_cycle(q, qd, gpl, k)
+    lat = []
+    barrier(ws)
+    k = 0
+    while len(lat) < cycles:
+        if k % episode == 0:
+            for c, b in zip(ctls, blobs):
+                c.load_state(b)
+            q, qd, gpl = episode_state()
+        with torch.cuda.stream(ctls[0].stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        u = one_cycle(q, qd, gpl, k)
+        lat.append(time.perf_counter() - t)
+        for a in range(sc.n_arms):
+            qd[a] = (qd[a] + u[a] * dt).astype(np.float32)
+            q[a] = (q[a] + qd[a] * dt).astype(np.float32)
+            gpl[a] = (gpl[a] + sc.goal_vel[a] * dt).astype(np.float32)
+        k += 1
+    barrier(ws)
+    for c, b in zip(ctls, blobs):
+        c.load_state(b)
+    return lat
+
+
+def plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, dev):
+    """The same kernels in exact mode, one arm at a time: one context per arm
+    (the other arms external, their plans shared), all on one stream, each
+    cycle launched kernel by kernel without a CUDA graph."""
+    import torch
+    from paper_2602_10114_gb300 import exchange, mrs
+    A = sc.n_arms
+    ctls = [mrs.Controller(sc, device=dev, stream=ctl.stream,
+                           external=[b for b in range(A) if b != a]) for a in range(A)]
+    # every context sees the other arms' plans from one batched cycle
+    out = ctl.step(sc.q0, sc.qd0, gp, gR)
+    ents = exchange.local_entries(ctl, out, 0)
+    for c in ctls:
+        c.set_world()
+        c.use_graph(False)
+        exchange.share_remote(c, ents)
+    s = ctl.stream
+    for _ in range(max(args.warmup, 3)):
+        for c in ctls:
+            c.step_device(d_in)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    for i in range(args.steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+            starts[i].record(s)
+        for c in ctls:
+            c.step_device(d_in)
+        with torch.cuda.stream(s):
+            ends[i].record(s)
+    torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = max_over_ranks(float(np.mean(step_ms)), ws)
+    lat = time_e2e(ctls, sc, gp, gR, args.latency_cycles, args.warmup, flush, ws)
+    e2e_s = max_over_ranks(float(np.mean(lat)), ws)
+    for c in ctls:
+        c.close()
+    return {"value": units * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "device_p50": float(np.percentile(step_ms, 50)),
+            "device_p99": float(np.percentile(step_ms, 99)),
+            "e2e": {"value": units * ws / e2e_s, "cycles": len(lat),
+                    "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                    "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))},
+            "gpu_launches_per_step": int(A * (2 + 4 * sc.params["iterations"]))}
+
+
+def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
+    """The same cycle with the self-collision surrogate (trained here, on the
+    device, by the library's kernels): throughput, latency, false negatives,
+    skip fraction and cost deviation against exact mode."""
+    from paper_2602_10114_gb300 import surrogate
+    groups = {}
+    for a, arm in enumerate(sc.arms):
+        groups.setdefault((arm.dof, arm.dh.tobytes(), arm.sphere_xyzr.tobytes()), []).append(a)
+    nets, stats = [], []
+    for arms in groups.values():
+        net, st = surrogate.train_self_surrogate(ctl, arms[0], n_train=args.surrogate_samples,
+                                                 n_val=200_000, epochs=8, lr=2e-3)
+        nets.append(net)
+        stats.append(st)
+        for a in arms:
+            ctl.set_self_surrogate(a, net, 0.03)
+    # cost deviation on one cycle from the same state
+    blob = ctl.save_state()
+    for a in range(sc.n_arms):
+        ctl.set_self_surrogate(a, None)
+    ctl.step_device(d_in)
+    ctl.sync()
+    c_exact = np.concatenate([ctl.debug_costs(a) for a in range(sc.n_arms)])
+    for arms, net in zip(groups.values(), nets):
+        for a in arms:
+            ctl.set_self_surrogate(a, net, 0.03)
+    ctl.load_state(blob)
+    ctl.step_device(d_in)
+    ctl.sync()
+    c_learned = np.concatenate([ctl.debug_costs(a) for a in range(sc.n_arms)])
+    roll = [ctl.debug_self(a) for a in range(sc.n_arms)]
+    ev = surrogate.evaluate(np.concatenate([r[0].ravel() for r in roll]),
+                            np.concatenate([r[1].ravel() for r in roll]),
+                            float(np.float32(sc.params["B_self"])), 0.03)
+    step_ms, kt, _ = time_device(ctl, d_in, args.steps, args.warmup, flush, ws)
+    ms = max_over_ranks(float(np.mean(step_ms)), ws)
+    lat = time_e2e(ctl, sc, gp, gR, args.latency_cycles, args.warmup, flush, ws)
+    e2e_s = max_over_ranks(float(np.mean(lat)), ws)
+    for a in range(sc.n_arms):
+        ctl.set_self_surrogate(a, None)
+    dev = np.abs(c_learned - c_exact)
+    return {
+        "value": units * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+        "speedup_vs_exact": exact_ms / ms,
+        "e2e": {"value": units * ws / e2e_s, "cycles": len(lat), "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))},
+        "surrogate_ms": float(kt[:, 2].mean()), "rollout_ms": float(kt[:, 3].mean()),
+        "held_out": {k: stats[0][k] for k in ("fn_rate", "fn_rate_active", "skip_fraction", "mae",
+                                              "colliding", "samples")},
+        "rollout_steps": {k: ev[k] for k in ("fn_rate", "skip_fraction", "mae", "colliding",
+                                             "samples")},
+        "cost_deviation": {"mean_rel": float(dev.mean() / np.abs(c_exact).mean()),
+                           "max_abs": float(dev.max())},
+        "train": {"samples": args.surrogate_samples, "epochs": 8,
+                  "seconds": float(sum(st["train_seconds"] for st in stats)),
+                  "networks": len(nets), "architecture": "2d sin/cos -> 3 x 256 SiLU -> 1, BF16"},
+    }
+
+
 def run(args):
     import torch
 
@@ -213,71 +412,36 @@ def run(args):
         gp.append(p)
         gR.append(R)
     units_per_step = sc.rollout_steps() * sc.params["iterations"]
-    s = ctl.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    # ---- device-resident cycles -------------------------------------------
     d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
-    ctl.enable_timing(True)
-    for _ in range(max(args.warmup, 3)):
-        ctl.step_device(d_in)
-    ctl.sync()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ktimes = []
-    barrier(ws)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            with torch.cuda.stream(s):
-                flush.zero_()
-                starts[i].record(s)
-            ctl.step_device(d_in)
-            with torch.cuda.stream(s):
-                ends[i].record(s)
-            ktimes.append(ctl.kernel_times())
-        torch.cuda.synchronize()
-    barrier(ws)
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+    # ---- device-resident cycles (exact costs) ------------------------------
+    step_ms, kt, clk = time_device(ctl, d_in, args.steps, args.warmup, flush, ws, local, True)
     ms = float(np.mean(step_ms))
     ms_max = max_over_ranks(ms, ws)
     value = units_per_step * ws / (ms_max / 1e3)
-    kt = np.asarray(ktimes)            # [steps][kernels]
     names = ["prep"] + ["sample", "surrogate", "rollout", "costs", "update"] * sc.params["iterations"] + ["toplan"]
-    k_mean = {n: float(kt[:, i].mean()) for i, n in enumerate(names[:kt.shape[1]])}
+    k_mean = {n: float(kt[:, i].mean()) for i, n in enumerate(names[:kt.shape[1]]) if n != "surrogate"}
     roll_ms = float(np.mean([kt[:, i] for i, n in enumerate(names) if n == "rollout"]))
     flops = rollout_flops(sc) / sc.params["iterations"]
     achieved = flops / (roll_ms / 1e3) / 1e12
-    ctl.enable_timing(False)
 
     # ---- end to end through mrs_step with host buffers ---------------------
-    q = [x.astype(np.float32).copy() for x in sc.q0]
-    qd = [x.astype(np.float32).copy() for x in sc.qd0]
-    gpl = [g.copy() for g in gp]
-    dt = np.float32(sc.params["dt"])
-    for _ in range(max(args.warmup, 3)):
-        ctl.step(q, qd, gpl, gR)
-    lat = []
-    barrier(ws)
-    for i in range(args.steps):
-        with torch.cuda.stream(s):
-            flush.zero_()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        out = ctl.step(q, qd, gpl, gR)
-        lat.append(time.perf_counter() - t)
-        for a in range(sc.n_arms):     # host plant: Execute(U_*), goals drift
-            u = ctl.split(out["u_star"], "d", a)
-            qd[a] = (qd[a] + u * dt).astype(np.float32)
-            q[a] = (q[a] + qd[a] * dt).astype(np.float32)
-            gpl[a] = (gpl[a] + sc.goal_vel[a] * dt).astype(np.float32)
-    barrier(ws)
+    lat = time_e2e(ctl, sc, gp, gR, args.latency_cycles, args.warmup, flush, ws)
     e2e_s = max_over_ranks(float(np.mean(lat)), ws)
     e2e = {"value": units_per_step * ws / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(4 * ctl.sizes.input_floats),
            "d2h_bytes_per_step": int(4 * ctl.sizes.output_floats + 4),
+           "cycles": len(lat), "episode": 50,
            "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
            "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+
+    plain = None
+    if not args.no_plain:
+        plain = plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, dev)
+    learned = None
+    if not args.no_learned:
+        learned = learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, ms_max)
 
     if rank != 0:
         return
@@ -306,7 +470,9 @@ def run(args):
                      "flops_per_launch": flops},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),   # no surrogate
+        "plain": plain,
+        "learned": learned,
+        "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -321,6 +487,13 @@ def main():
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-surrogate comparison")
+    ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the one-arm-at-a-time, graph-free comparison")
+    ap.add_argument("--latency-cycles", type=int, default=1000,
+                    help="closed-loop mrs_step calls for the latency percentiles")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -631,8 +631,8 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
         const int last = (it == P.iterations - 1);
         k_sample<<<L.n_sample_tiles, 512, L.smem_sample, s>>>(P, D, L.sample_tiles, it);
         mark();
-        for (int i = 0; i < L.n_surrogates; ++i)   // learned self clearance of every step
-            if ((rec = enqueue_self_surrogate(D, L.surrogates[i], s)) != cudaSuccess) return rec;
+        for (int i = 0; i < L.n_groups; ++i)   // learned self clearance of every step
+            if ((rec = enqueue_self_surrogate(D, L.groups[i], s)) != cudaSuccess) return rec;
         mark();
         if ((rec = launch_rollout(P, D, L, it, s)) != cudaSuccess) return rec;
         mark();

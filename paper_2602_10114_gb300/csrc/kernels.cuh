@@ -6,6 +6,7 @@
 
 #include <string>
 
+#include "mlp_fused.cuh"
 #include "mrs_device.cuh"
 
 struct mrs_mlp;
@@ -15,8 +16,16 @@ namespace mrs {
 // One arm whose self clearance comes from a surrogate network.
 struct SurrogateSlot {
     int arm, rows;          // rows = K * H rollout steps
+    int K, dof;
     long long off_kh;       // the arm's offset in Dev::dhat
+    long long off_khd;      // the arm's offset in Dev::traj
     mrs_mlp *net;
+};
+
+// arms that share one surrogate network: one fused inference launch
+struct SurrogateGroup {
+    mrs_mlp *net;
+    fused::TrajSegs segs;
 };
 
 struct LaunchPlan {
@@ -31,22 +40,23 @@ struct LaunchPlan {
     int *done_counter;  // last-block-done counter of k_toplan
     int n_surrogates;
     SurrogateSlot surrogates[MRS_MAX_ARMS];
+    int n_groups;
+    SurrogateGroup groups[MRS_MAX_ARMS];
 };
 
-// surrogate network (mlp.cu): inference input buffer, its padded width, and
-// the forward pass of `rows` BF16 feature rows into y (FP32) on stream s
-__nv_bfloat16 *mlp_infer_input(mrs_mlp *m);
-int mlp_in_pad(const mrs_mlp *m);
+// surrogate network (mlp.cu): input width, and the fused forward pass over
+// the sin/cos features of every rollout step of a set of arms into their
+// slices of dhat, on stream s
 int mlp_in_dim(const mrs_mlp *m);
-cudaError_t mlp_reserve_infer(mrs_mlp *m, int rows);
-cudaError_t mlp_infer(mrs_mlp *m, int rows, float *y, int *err, cudaStream_t s);
+cudaError_t mlp_infer_trajs(mrs_mlp *m, const float *traj, const fused::TrajSegs &segs,
+                            float *dhat, int *err, cudaStream_t s);
 // surrogate.cu
 cudaError_t enqueue_self_dataset(const Dev &D, int arm, int n, unsigned long long seed, float *x,
                                  float *t, float *q, cudaStream_t s);
 cudaError_t enqueue_self_clearance_rows(const Dev &D, int arm, int n, const float *q, float *out,
                                         cudaStream_t s);
 cudaError_t enqueue_self_clearance_traj(const Dev &D, int arm, int rows, float *out, cudaStream_t s);
-cudaError_t enqueue_self_surrogate(const Dev &D, const SurrogateSlot &slot, cudaStream_t s);
+cudaError_t enqueue_self_surrogate(const Dev &D, const SurrogateGroup &g, cudaStream_t s);
 
 // The rollout kernel (rollout.cu): shared-memory size for the given
 // capacities, attribute set-up and launch.

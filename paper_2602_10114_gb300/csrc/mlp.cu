@@ -11,6 +11,7 @@
 
 #include "kernels.cuh"
 #include "mrs.h"
+#include "mlp_fused.cuh"
 #include "tc_gemm.cuh"
 
 namespace mrs {
@@ -208,6 +209,19 @@ __global__ void k_weights_bf16(const float *W, int rows, int cols, bf16 *Wb, bf1
     WbT[(size_t)c * rows + r] = b;
 }
 
+// W [rows][cols] (cols a multiple of 16) into 16-column chunks in the
+// canonical K-major layout of a tcgen05 B operand: within a chunk, element
+// (n, k) at byte (n / 8) * 256 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2.
+__global__ void k_pack_chunks(const float *W, int rows, int cols, unsigned char *dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const int n = i / cols, k = i % cols, c = k >> 4, kk = k & 15;
+    const size_t off = (size_t)c * rows * 32 + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 +
+                       (kk & 7) * 2;
+    *reinterpret_cast<bf16 *>(dst + off) = __float2bfloat16_rn(W[i]);
+}
+
 // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from Philox, zero biases
 __global__ void k_init_param(float *p, size_t n, float scale, unsigned long long seed,
                              unsigned tensor)
@@ -240,9 +254,11 @@ struct mrs_mlp {
     std::vector<bf16 *> Hs;
     float *y = nullptr, *dy = nullptr, *dH = nullptr, *loss = nullptr;
     bf16 *dZ = nullptr, *dZT = nullptr, *HT = nullptr;
-    // inference buffers
-    int icap = 0;
-    bf16 *iX = nullptr, *iH0 = nullptr, *iH1 = nullptr;
+    // fused inference: packed BF16 weight chunks and the kernel's set-up
+    unsigned char *wpack = nullptr;
+    fused::Net fnet{};
+    int per_sm_rows = 0, per_sm_traj = 0, num_sms = 0;
+    size_t fnet_smem = 0;
     int *err = nullptr;
     std::string msg;
 };
@@ -264,12 +280,60 @@ static mrs_status mlp_fail(mrs_mlp *m, mrs_status s, const std::string &why)
 
 static int in_of(const mrs_mlp *m, int l) { return l == 0 ? m->in_pad : m->width; }
 
+// index of the first 16-column weight chunk of layer l
+static int chunk_index(const mrs_mlp *m, int l)
+{
+    int c = 0;
+    for (int i = 0; i < l; ++i) c += in_of(m, i) / 16;
+    return c;
+}
+
+// Shared memory, ring depth and occupancy of the fused inference kernel.
+// Two CTAs per SM when the width allows (about 110 KB each); the ring takes
+// what the layer input leaves.  More CTAs per SM than the tensor memory
+// holds (512 columns) would wait in tcgen05.alloc, so the shared memory is
+// padded until they cannot be resident.
+template <class In>
+static cudaError_t configure_fused(mrs_mlp *m, int *per_sm)
+{
+    fused::Net &n = m->fnet;
+    const size_t smem = fused::smem_bytes(n);
+    const int max_ctas = 512 / (int)n.tmem_cols;
+    size_t need = smem;
+    const size_t sm_bytes = 228 * 1024, reserve = 1024;
+    if ((size_t)(max_ctas + 1) * (smem + reserve) <= sm_bytes)
+        need = sm_bytes / (size_t)(max_ctas + 1) - reserve + 16;
+    need = (need + 15) / 16 * 16;
+    cudaError_t e = cudaFuncSetAttribute(fused::k_mlp_fused<In>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fused::k_mlp_fused<In>, fused::kThreads,
+                                                      need);
+    if (e != cudaSuccess) return e;
+    if (*per_sm < 1 || *per_sm > max_ctas) return cudaErrorInvalidConfiguration;
+    m->fnet_smem = need;
+    return cudaSuccess;
+}
+
+template <class In>
+static cudaError_t launch_fused(mrs_mlp *m, const In &in, int rows, float *y, int *err, int per_sm,
+                                cudaStream_t s)
+{
+    const int tiles = (rows + 127) / 128;
+    const int grid = std::min(tiles, per_sm * m->num_sms);
+    fused::k_mlp_fused<In><<<grid, fused::kThreads, m->fnet_smem, s>>>(m->fnet, in, rows, y, err);
+    return cudaGetLastError();
+}
+
 static mrs_status mlp_refresh_bf16(mrs_mlp *m)
 {
     for (int l = 0; l < m->layers; ++l) {
         const int rows = m->width, cols = in_of(m, l);
         k_weights_bf16<<<(rows * cols + 255) / 256, 256, 0, m->stream>>>(
             m->params + m->offW[l], rows, cols, m->Wb[l], m->WbT[l]);
+        k_pack_chunks<<<(rows * cols + 255) / 256, 256, 0, m->stream>>>(
+            m->params + m->offW[l], rows, cols,
+            m->wpack + (size_t)m->fnet.chunk_bytes * chunk_index(m, l));
     }
     MCK(cudaGetLastError(), "bf16 weights");
     return MRS_OK;
@@ -368,40 +432,15 @@ static mrs_status check_err(mrs_mlp *m)
 
 namespace mrs {
 
-__nv_bfloat16 *mlp_infer_input(mrs_mlp *m) { return m->iX; }
-int mlp_in_pad(const mrs_mlp *m) { return m->in_pad; }
 int mlp_in_dim(const mrs_mlp *m) { return m->in_dim; }
 
-cudaError_t mlp_reserve_infer(mrs_mlp *m, int rows)
+// surrogate inference over every rollout step of a set of arms (segments of
+// the trajectory array) into their slices of dhat, in one fused launch
+cudaError_t mlp_infer_trajs(mrs_mlp *m, const float *traj, const fused::TrajSegs &segs,
+                            float *dhat, int *err, cudaStream_t s)
 {
-    if (rows <= m->icap) return cudaSuccess;
-    const int c = (rows + 127) / 128 * 128;
-    cudaFree(m->iX); cudaFree(m->iH0); cudaFree(m->iH1);
-    m->iX = m->iH0 = m->iH1 = nullptr;
-    cudaError_t e = cudaMalloc(&m->iX, sizeof(bf16) * c * m->in_pad);
-    if (e == cudaSuccess) e = cudaMalloc(&m->iH0, sizeof(bf16) * c * m->width);
-    if (e == cudaSuccess) e = cudaMalloc(&m->iH1, sizeof(bf16) * c * m->width);
-    if (e != cudaSuccess) return e;
-    m->icap = c;
-    return cudaSuccess;
-}
-
-// forward of `rows` feature rows in m->iX; activations ping-pong between two
-// buffers; output into y
-cudaError_t mlp_infer(mrs_mlp *m, int rows, float *y, int *err, cudaStream_t s)
-{
-    const bf16 *in = m->iX;
-    bf16 *buf[2] = {m->iH0, m->iH1};
-    for (int l = 0; l < m->layers; ++l) {
-        EpiBiasSilu e{m->params + m->offB[l], nullptr, buf[l & 1], m->width};
-        const int K = l == 0 ? m->in_pad : m->width;
-        cudaError_t ce = gemm(in, K, m->Wb[l], K, rows, m->width, K, 1, err, e, s);
-        if (ce != cudaSuccess) return ce;
-        in = buf[l & 1];
-    }
-    k_out_layer<<<(rows + 7) / 8, 256, 0, s>>>(in, m->width, m->params + m->offWo,
-                                               m->params + m->offBo, rows, y);
-    return cudaGetLastError();
+    return launch_fused(m, fused::InTrajSet{traj, segs}, segs.row_start[segs.n], dhat, err,
+                        m->per_sm_traj, s);
 }
 
 }  // namespace mrs
@@ -453,9 +492,42 @@ mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long 
     for (int l = 0; okk && l < layers; ++l)
         okk = cudaMalloc(&m->Wb[l], sizeof(bf16) * width * in_of(m, l)) == cudaSuccess &&
               cudaMalloc(&m->WbT[l], sizeof(bf16) * width * in_of(m, l)) == cudaSuccess;
+    const int n_chunks = chunk_index(m, layers);
+    if (okk) okk = cudaMalloc(&m->wpack, (size_t)n_chunks * width * 32) == cudaSuccess;
     if (!okk) {
         mrs_mlp_destroy(m);
         return MRS_ENOMEM;
+    }
+    // fused inference set-up
+    {
+        fused::Net &n = m->fnet;
+        n.wpack = m->wpack;
+        n.params = m->params;
+        n.offB0 = (int)m->offB[0];
+        for (int l = 1; l < layers; ++l)
+            if (m->offB[l] != m->offB[0] + (size_t)l * (width * width + width)) {
+                mrs_mlp_destroy(m);
+                return MRS_EINVAL;
+            }
+        n.offWo = (int)m->offWo;
+        n.offBo = (int)m->offBo;
+        n.in_pad = m->in_pad;
+        n.width = width;
+        n.layers = layers;
+        n.chunk_bytes = (unsigned)width * 32u;
+        n.a_bytes = 128u * 2u * (unsigned)std::max(m->in_pad, width);
+        n.tmem_cols = 32;
+        while ((int)n.tmem_cols < width) n.tmem_cols *= 2;
+        const long budget = 110 * 1024 - (long)n.a_bytes - (long)sizeof(fused::Ctl);
+        n.slots = (int)std::max(2L, std::min((long)fused::kMaxSlots, budget / (long)n.chunk_bytes));
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            configure_fused<fused::InRows>(m, &m->per_sm_rows) != cudaSuccess ||
+            configure_fused<fused::InTrajSet>(m, &m->per_sm_traj) != cudaSuccess) {
+            mrs_mlp_destroy(m);
+            return MRS_ECUDA;
+        }
     }
     cudaMemsetAsync(m->params, 0, sizeof(float) * o, m->stream);
     cudaMemsetAsync(m->am, 0, sizeof(float) * o, m->stream);
@@ -488,7 +560,7 @@ void mrs_mlp_destroy(mrs_mlp *m)
     for (auto p : m->Z) cudaFree(p);
     for (auto p : m->Hs) cudaFree(p);
     cudaFree(m->y); cudaFree(m->dy); cudaFree(m->dH); cudaFree(m->dZ); cudaFree(m->dZT); cudaFree(m->HT);
-    cudaFree(m->iX); cudaFree(m->iH0); cudaFree(m->iH1);
+    cudaFree(m->wpack);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -527,11 +599,8 @@ mrs_status mrs_mlp_set_params(mrs_mlp *m, const float *host, size_t n)
 mrs_status mrs_mlp_forward(mrs_mlp *m, const float *d_x, int n, float *d_y)
 {
     if (!m || !d_x || !d_y || n < 1) return MRS_EINVAL;
-    mrs_status st = mlp_reserve(m, n);
-    if (st != MRS_OK) return st;
-    if ((st = load_x(m, d_x, n)) != MRS_OK) return st;
-    if ((st = mlp_forward_train(m, n)) != MRS_OK) return st;
-    MCK(cudaMemcpyAsync(d_y, m->y, sizeof(float) * n, cudaMemcpyDeviceToDevice, m->stream), "copy");
+    MCK(launch_fused(m, fused::InRows{d_x, m->in_dim}, n, d_y, m->err, m->per_sm_rows, m->stream),
+        "fused forward");
     return check_err(m);
 }
 

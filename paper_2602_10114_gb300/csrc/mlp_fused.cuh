@@ -1,0 +1,379 @@
+// mlp_fused.cuh -- fused inference of the clearance surrogate: input
+// features, every hidden layer and the output layer of 128 rows in one CTA,
+// activations never leaving the SM.
+//
+// Per 128-row tile the CTA keeps the layer input A [128][K] (BF16, canonical
+// K-major layout without swizzle) in shared memory and the layer's
+// accumulator [128][width] (FP32) in tensor memory.  The weights stream
+// through a ring of shared-memory slots, one 16-wide K chunk of one layer per
+// slot, pre-packed in global memory in the same canonical layout so that
+// one cp.async.bulk moves a chunk.  Warp roles (320 threads):
+//   warps 0-7  features of the tile into A; after each layer, bias + SiLU
+//              of the accumulator back into A (hidden layers) or the dot
+//              product with the output weights (last layer).  Warp w reads
+//              TMEM lanes 32 (w % 4) .. + 31 (one row per thread) and every
+//              other 16-column chunk, starting at chunk w / 4.
+//   warp 8     producer: the chunk sequence (tile, layer, chunk) into the
+//              ring, an mbarrier pair (full / empty) per slot.
+//   warp 9     owns the TMEM allocation; one lane issues tcgen05.mma
+//              (M = 128, N = width, K = 16) per chunk, commits each to the
+//              slot's empty barrier and each layer to acc_full.
+// The weight sequence does not depend on the data, so the producer runs
+// ahead across layer and tile boundaries, bounded only by the ring depth.
+// Every wait is bounded; a timeout sets the error word and the shared abort
+// flag, which every role polls, then the producer waits for its copies in
+// flight, the issuer for its MMAs, and the CTA frees its TMEM and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "tc_gemm.cuh"
+
+namespace mrs {
+namespace fused {
+
+constexpr int kEpiWarps = 8;
+constexpr int kProducerWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kThreads = 320;
+constexpr int kMaxLayers = 8;
+constexpr int kMaxSlots = 16;
+
+struct Net {
+    const unsigned char *wpack;   // chunks of all layers in order, chunk_bytes each
+    const float *params;          // FP32 master parameters (biases, output layer)
+    int offB0;                    // bias of layer 0; layer l's at offB0 + l (width^2 + width)
+    int offWo, offBo;
+    int in_pad, width, layers;
+    int slots;                    // ring depth
+    unsigned chunk_bytes;         // width * 16 * 2
+    unsigned a_bytes;             // 128 * max(in_pad, width) * 2
+    unsigned tmem_cols;           // power of two >= max(32, width)
+};
+
+struct Ctl {                      // follows the A buffer and the ring
+    uint64_t full[kMaxSlots], empty[kMaxSlots];
+    uint64_t acc_full, a_ready, part_full, drain;
+    float part[128];
+    uint32_t tmem;
+    int abort;
+};
+
+__host__ __device__ inline size_t smem_bytes(const Net &n)
+{
+    return (size_t)n.a_bytes + (size_t)n.slots * n.chunk_bytes + sizeof(Ctl);
+}
+
+__device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(tc::smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    for (unsigned it = 0; it < tc::kWaitLimit; ++it) {
+        if (try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(tc::smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(tc::smem_u32(dst_smem)), "l"(__cvta_generic_to_global(src_gmem)), "r"(bytes),
+                   "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fail(Ctl &C, int *err)
+{
+    C.abort = 1;
+    atomicExch(err, 1);
+}
+
+// z sigmoid(z) with the fast exponential and division (relative error near
+// 1e-6, far below the BF16 rounding of the result); exp(-z) is capped at
+// e^80 so that the denominator stays finite
+__device__ __forceinline__ float silu(float z)
+{
+    return __fdividef(z, 1.f + __expf(fminf(-z, 80.f)));
+}
+
+// two floats as BF16 (round to nearest even), a in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ int in_of(const Net &n, int l) { return l == 0 ? n.in_pad : n.width; }
+
+// Features of plain FP32 rows x [rows][in_dim].
+struct InRows {
+    const float *x;
+    int in_dim;
+    __device__ __forceinline__ void operator()(int row, int g, float (&v)[8]) const
+    {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * g + i;
+            v[i] = k < in_dim ? x[(size_t)row * in_dim + k] : 0.f;
+        }
+    }
+    __device__ __forceinline__ size_t out(int row) const { return (size_t)row; }
+};
+
+// sin, cos of each joint of every rollout step of a set of arms that share
+// one network: segment s covers rows [row_start[s], row_start[s+1]) of arm
+// trajectories traj + off_khd[s] ([H][dof][K], local row = h K + n), its
+// outputs go to off_kh[s] + local row; feature 2j = sin q_j, 2j+1 = cos q_j.
+constexpr int kMaxSegs = 32;
+struct TrajSegs {
+    int n;
+    int row_start[kMaxSegs + 1];
+    int K[kMaxSegs], dof[kMaxSegs];
+    long long off_khd[kMaxSegs], off_kh[kMaxSegs];
+};
+
+struct InTrajSet {
+    const float *traj;
+    TrajSegs seg;
+    __device__ __forceinline__ int find(int row) const
+    {
+        int s = 0;
+        while (s + 1 < seg.n && row >= seg.row_start[s + 1]) ++s;
+        return s;
+    }
+    __device__ __forceinline__ void operator()(int row, int g, float (&v)[8]) const
+    {
+        const int s = find(row), K = seg.K[s], dof = seg.dof[s];
+        const int r = row - seg.row_start[s], h = r / K, n = r - h * K;
+        const float *qh = traj + seg.off_khd[s] + (size_t)h * dof * K + n;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int j = 4 * g + p;
+            float sn = 0.f, cs = 0.f;
+            if (j < dof) sincosf(qh[(size_t)j * K], &sn, &cs);
+            v[2 * p] = sn;
+            v[2 * p + 1] = cs;
+        }
+    }
+    __device__ __forceinline__ size_t out(int row) const
+    {
+        const int s = find(row);
+        return (size_t)(seg.off_kh[s] + (row - seg.row_start[s]));
+    }
+};
+
+// Input functor interface: in(row, g, v) fills the 8 features 8g .. 8g+7 of
+// a valid row (row < rows), features at or beyond the input width 0; the
+// row's output goes to y[in.out(row)].
+template <class In>
+__global__ void __launch_bounds__(kThreads, 2)
+k_mlp_fused(Net net, In in, int rows, float *y, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;
+    unsigned char *ring = smem + net.a_bytes;
+    Ctl &C = *reinterpret_cast<Ctl *>(ring + (size_t)net.slots * net.chunk_bytes);
+    volatile int *abort = &C.abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (rows + 127) / 128;
+    const int S = net.slots;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&C.full[s], 1);
+            tc::mbar_init(&C.empty[s], 1);
+        }
+        tc::mbar_init(&C.acc_full, 1);
+        tc::mbar_init(&C.a_ready, kEpiWarps * 32);
+        tc::mbar_init(&C.part_full, 4 * 32);
+        tc::mbar_init(&C.drain, 1);
+        C.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) tc::tmem_alloc(&C.tmem, net.tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = C.tmem;
+
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
+                const unsigned char *src = net.wpack;
+                for (int l = 0; ok && l < net.layers; ++l) {
+                    const int nch = in_of(net, l) / 16;
+                    for (int c = 0; c < nch; ++c, ++cnt, src += net.chunk_bytes) {
+                        const int s = (int)(cnt % S);
+                        if (!wait_or_abort(&C.empty[s], ((cnt / S) & 1u) ^ 1u, abort)) {
+                            fail(C, err);
+                            ok = false;
+                            break;
+                        }
+                        arrive_expect_tx(&C.full[s], net.chunk_bytes);
+                        bulk_copy(ring + (size_t)s * net.chunk_bytes, src, net.chunk_bytes, &C.full[s]);
+                    }
+                }
+            }
+            // no copy may still be landing in shared memory when the CTA exits
+            const uint32_t first = cnt > (uint32_t)S ? cnt - S : 0u;
+            for (uint32_t k = first; k < cnt; ++k)
+                if (!tc::mbar_wait(&C.full[k % S], (k / S) & 1u)) atomicExch(err, 1);
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            uint32_t cnt = 0, v = 0;
+            bool ok = true;
+            const uint32_t idesc = tc::idesc_bf16_f32(128, net.width);
+            const uint32_t a0 = tc::smem_u32(Abuf), r0 = tc::smem_u32(ring);
+            for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
+                for (int l = 0; ok && l < net.layers; ++l) {
+                    if (!wait_or_abort(&C.a_ready, (v++) & 1u, abort)) {
+                        fail(C, err);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const int K = in_of(net, l), nch = K / 16;
+                    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+                    for (int c = 0; c < nch; ++c, ++cnt) {
+                        const int s = (int)(cnt % S);
+                        if (!wait_or_abort(&C.full[s], (cnt / S) & 1u, abort)) {
+                            fail(C, err);
+                            ok = false;
+                            break;
+                        }
+                        const uint64_t ad = tc::smem_desc(a0 + (uint32_t)c * 256u, 128u, sbo);
+                        const uint64_t bd = tc::smem_desc(r0 + (uint32_t)s * net.chunk_bytes, 128u, 256u);
+                        tc::mma_bf16(tmem, ad, bd, idesc, c > 0 ? 1u : 0u);
+                        tc::mma_commit(&C.empty[s]);
+                    }
+                    if (ok) tc::mma_commit(&C.acc_full);
+                }
+            }
+            // every MMA issued has completed before the TMEM is freed
+            tc::mma_commit(&C.drain);
+            if (!tc::mbar_wait(&C.drain, 0)) atomicExch(err, 1);
+        }
+    } else {
+        // epilogue warps
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = quarter * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int W = net.width;
+        const float *w_out = net.params + net.offWo;
+        const float b_out = net.params[net.offBo];
+        uint32_t u = 0, pp = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
+            const int row = t * 128 + m;
+            const bool valid = row < rows;
+            // features of this row into A (layout of K = in_pad)
+            {
+                const uint32_t sbo = (uint32_t)(net.in_pad / 8) * 128u;
+                for (int g = half; g < net.in_pad / 8; g += 2) {
+                    float v[8];
+                    if (valid) {
+                        in(row, g, v);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[i] = 0.f;
+                    }
+                    *reinterpret_cast<uint4 *>(Abuf + (m >> 3) * sbo + g * 128 + (m & 7) * 16) =
+                        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                                   pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+                }
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            arrive(&C.a_ready);
+            float part = 0.f;
+            for (int l = 0; l < net.layers; ++l) {
+                const bool got = wait_or_abort(&C.acc_full, (u++) & 1u, abort);
+                if (!__all_sync(0xffffffffu, got)) {
+                    fail(C, err);
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const bool last = l == net.layers - 1;
+                const float *bias = net.params + net.offB0 + (size_t)l * (W * W + W);
+                const uint32_t sbo = (uint32_t)(W / 8) * 128u;
+                for (int cc = half; cc < W / 16; cc += 2) {
+                    float v[16];
+                    tc::tmem_ld16(lane_base + (uint32_t)(cc * 16), v);
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        pk[i] = pack_bf16(silu(v[2 * i] + bias[cc * 16 + 2 * i]),
+                                          silu(v[2 * i + 1] + bias[cc * 16 + 2 * i + 1]));
+                    if (!last) {
+                        unsigned char *dst = Abuf + (m >> 3) * sbo + (2 * cc) * 128 + (m & 7) * 16;
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *reinterpret_cast<uint4 *>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            part = fmaf(__uint_as_float(pk[i] << 16), w_out[cc * 16 + 2 * i], part);
+                            part = fmaf(__uint_as_float(pk[i] & 0xffff0000u), w_out[cc * 16 + 2 * i + 1],
+                                        part);
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                if (!last) {
+                    tc::fence_async_smem();
+                    arrive(&C.a_ready);
+                }
+            }
+            if (!ok) break;
+            // output: the two column halves of a row meet in shared memory
+            if (half == 1) {
+                C.part[m] = part;
+                arrive(&C.part_full);
+            } else {
+                const bool got = wait_or_abort(&C.part_full, (pp++) & 1u, abort);
+                if (!got) {
+                    fail(C, err);
+                    ok = false;
+                } else if (valid) {
+                    y[in.out(row)] = part + C.part[m] + b_out;
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, net.tmem_cols);
+    }
+}
+
+}  // namespace fused
+}  // namespace mrs

@@ -897,7 +897,6 @@ mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float mar
         return fail(ctx, MRS_EINVAL, "surrogate input must be 2 * dof sin/cos features; margin >= 0");
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
-    if (net) CK(mlp_reserve_infer(net, A.K * A.H), "surrogate buffers");
     A.learned = net ? 1 : 0;
     A.self_margin = net ? margin : 0.f;
     // rebuild the slot list in arm order
@@ -906,10 +905,29 @@ mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float mar
     SurrogateSlot slots[MRS_MAX_ARMS];
     for (int i = 0; i < L.n_surrogates; ++i)
         if (L.surrogates[i].arm != arm) slots[k++] = L.surrogates[i];
-    if (net) slots[k++] = SurrogateSlot{arm, A.K * A.H, A.off_kh, net};
+    if (net) slots[k++] = SurrogateSlot{arm, A.K * A.H, A.K, A.dof, A.off_kh, A.off_khd, net};
     std::sort(slots, slots + k, [](const SurrogateSlot &x, const SurrogateSlot &y) { return x.arm < y.arm; });
     L.n_surrogates = k;
     for (int i = 0; i < k; ++i) L.surrogates[i] = slots[i];
+    // one inference launch per distinct network, over all of its arms
+    L.n_groups = 0;
+    for (int i = 0; i < k; ++i) {
+        const SurrogateSlot &sl = slots[i];
+        int gi = 0;
+        while (gi < L.n_groups && L.groups[gi].net != sl.net) ++gi;
+        if (gi == L.n_groups) {
+            L.groups[gi] = SurrogateGroup{};
+            L.groups[gi].net = sl.net;
+            L.n_groups += 1;
+        }
+        fused::TrajSegs &g = L.groups[gi].segs;
+        g.K[g.n] = sl.K;
+        g.dof[g.n] = sl.dof;
+        g.off_khd[g.n] = sl.off_khd;
+        g.off_kh[g.n] = sl.off_kh;
+        g.row_start[g.n + 1] = g.row_start[g.n] + sl.rows;
+        g.n += 1;
+    }
     // only the surrogate fields: the device copy also holds constants that the
     // device derived at binding (base rotation, twist sines)
     static_assert(offsetof(ArmDev, self_margin) == offsetof(ArmDev, learned) + sizeof(int),

@@ -5,18 +5,14 @@
 //                     (Philox), sin/cos features and the exact clearance label;
 //  * k_self_clearance exact self-collision clearance of given joint vectors,
 //                     or of every rollout step of the last cycle (evaluation);
-//  * k_self_features  BF16 sin/cos features of every rollout step of an arm,
-//                     the surrogate's input inside the cycle.
+// The surrogate's own inference (features, layers, output) is one fused
+// kernel of mlp_fused.cuh.
 // The clearance is the minimum over the arm's sphere pairs on bodies at least
 // three apart of sqrt(d2) - r1 - r2, with the rollout's kinematics and pair
 // arithmetic (same functions, same operation order).
-#include <cuda_bf16.h>
-
 #include "kernels.cuh"
 
 namespace mrs {
-
-using bf16 = __nv_bfloat16;
 
 __device__ float self_clearance(const Dev &D, const ArmDev &A, const float *q, int q_stride)
 {
@@ -90,22 +86,6 @@ __global__ void k_self_clearance_traj(Dev D, int arm, float *out)
     out[r] = self_clearance(D, A, D.traj + A.off_khd + (size_t)h * A.dof * A.K + n, A.K);
 }
 
-// BF16 features [H*K][in_pad] of every rollout step: sin, cos of each joint
-__global__ void k_self_features(Dev D, int arm, int in_pad, bf16 *X)
-{
-    const ArmDev &A = D.arms[arm];
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.H * A.K) return;
-    const int h = r / A.K, n = r % A.K, d = A.dof;
-    const float *qh = D.traj + A.off_khd + (size_t)h * d * A.K + n;
-    for (int j = 0; j < in_pad / 2; ++j) {
-        float s = 0.f, c = 0.f;
-        if (j < d) sincosf(qh[(size_t)j * A.K], &s, &c);
-        X[(size_t)r * in_pad + 2 * j] = __float2bfloat16_rn(s);
-        X[(size_t)r * in_pad + 2 * j + 1] = __float2bfloat16_rn(j < d ? c : 0.f);
-    }
-}
-
 cudaError_t enqueue_self_dataset(const Dev &D, int arm, int n, unsigned long long seed, float *x,
                                  float *t, float *q, cudaStream_t s)
 {
@@ -126,15 +106,12 @@ cudaError_t enqueue_self_clearance_traj(const Dev &D, int arm, int rows, float *
     return cudaGetLastError();
 }
 
-// Surrogate inference for one arm inside the cycle: features of every rollout
-// step, then the network, into dhat[off_kh ...] ([H][K] order).
-cudaError_t enqueue_self_surrogate(const Dev &D, const SurrogateSlot &slot, cudaStream_t s)
+// Surrogate inference inside the cycle for the arms sharing one network:
+// features, hidden layers and output of every rollout step in one fused
+// launch, into each arm's slice of dhat ([H][K] order).
+cudaError_t enqueue_self_surrogate(const Dev &D, const SurrogateGroup &g, cudaStream_t s)
 {
-    bf16 *X = mlp_infer_input(slot.net);
-    k_self_features<<<(slot.rows + 127) / 128, 128, 0, s>>>(D, slot.arm, mlp_in_pad(slot.net), X);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return mlp_infer(slot.net, slot.rows, D.dhat + slot.off_kh, D.err, s);
+    return mlp_infer_trajs(g.net, D.traj, g.segs, D.dhat, D.err, s);
 }
 
 }  // namespace mrs

@@ -77,15 +77,43 @@ def test_gradients_match_the_fp64_oracle():
         assert np.dot(a, b) / (np.linalg.norm(a) * nb) > 0.999
 
 
-def test_forward_matches_the_fp64_oracle():
+@pytest.mark.parametrize("in_dim,width,layers,rows", [
+    (14, 256, 3, 300),      # the self-collision surrogate's shape, a ragged tile
+    (14, 256, 3, 5000),     # 40 tiles over the persistent grid
+    (20, 48, 2, 257),       # two layer-0 chunks; an odd number of 16-column chunks
+    (7, 16, 1, 129),        # one hidden layer of one chunk
+    (100, 128, 4, 1000),    # seven layer-0 chunks, four layers
+])
+def test_forward_matches_the_fp64_oracle(in_dim, width, layers, rows):
+    """The fused inference kernel (features, every layer and the output of
+    128 rows per CTA) against the FP64 forward with the same BF16 weights and
+    inputs; BF16 activations bound the error to about 1e-2 relative."""
     import torch
     from oracle import oracle as O
-    rng = np.random.default_rng(6)
-    net, p = _net()
-    x = bf16_bits(rng.normal(size=(300, 14)))[1]
+    rng = np.random.default_rng(6 + rows)
+    net, p = _net(in_dim, width, layers)
+    x = bf16_bits(rng.normal(size=(rows, in_dim)))[1]
     y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
-    _, _, y_o = O.mlp_loss_grad(14, 256, 3, p.astype(np.float64), x, np.zeros(300), False)
+    _, _, y_o = O.mlp_loss_grad(in_dim, width, layers, p.astype(np.float64), x, np.zeros(rows),
+                                False)
     assert np.abs(y - y_o).max() <= 2e-2 * max(1.0, np.abs(y_o).max())
+
+
+def test_fused_forward_agrees_with_the_training_forward():
+    """The training step's layer-by-layer forward and the fused inference
+    kernel compute the same network: the loss from the former equals the loss
+    of the latter's outputs up to summation order and the fused kernel's fast
+    exponential (rare BF16 rounding flips of the activations)."""
+    import torch
+    rng = np.random.default_rng(8)
+    net, _ = _net()
+    x = rng.uniform(-1, 1, (1000, 14)).astype(np.float32)
+    t = rng.uniform(-0.05, 0.25, 1000).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    _, loss = net.grads(xd, td)
+    y = net.forward(xd).cpu().numpy().astype(np.float64)
+    ref = np.mean((y - np.clip(t, -0.1, 0.3)) ** 2)
+    assert abs(loss - ref) <= 1e-3 * ref
 
 
 def test_adam_training_reduces_the_loss():

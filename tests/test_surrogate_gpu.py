@@ -39,6 +39,32 @@ def test_dataset_labels_and_features_match_the_oracle():
     assert np.array_equal(t2, t)
 
 
+def test_in_cycle_inference_matches_the_oracle_forward():
+    """Inside the cycle the surrogate sees the sin/cos features of every
+    rollout step: its predictions equal the FP64 network on the oracle's own
+    rollout of the same samples (BF16 tolerance)."""
+    from oracle import oracle as O
+    from parity_utils import Replay
+    from test_mlp_gpu import _net, bf16_bits
+    sc = S.shrink(S.config(3), K=64, H=10)
+    R = Replay(sc)
+    net, p = _net(14, 256, 3, seed=5)
+    for a in range(sc.n_arms):
+        R.ctl.set_self_surrogate(a, net, 0.03)
+    q0, qd0 = [q.copy() for q in R.q], [q.copy() for q in R.qd]
+    got, gc, ga, gs, exp = R.cycle(None)
+    for a in (0, 3):
+        dh, _ = R.ctl.debug_self(a)                       # [H][K]
+        U = R.orc.split(exp["U"], "U", a)                 # [K][H][d]
+        for n in (0, 1, 31, 32, 63):
+            _, _, _, qo = R.orc.rollout(a, q0, qd0, R.gp, R.gR, U[n])
+            x = np.empty((sc.arms[a].H, 14))
+            x[:, 0::2], x[:, 1::2] = np.sin(qo), np.cos(qo)
+            x = bf16_bits(x.astype(np.float32))[1]
+            _, _, y = O.mlp_loss_grad(14, 256, 3, p.astype(np.float64), x, np.zeros(len(x)), False)
+            assert np.abs(dh[:, n] - y).max() <= 2e-2 * max(1.0, np.abs(y).max()), (a, n)
+
+
 def _constant_net(dof, value):
     from paper_2602_10114_gb300 import mrs
     net = mrs.MLP(2 * dof, 32, 1, 0)
