@@ -295,6 +295,13 @@ mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long 
 void mrs_mlp_destroy(mrs_mlp *m);
 const char *mrs_mlp_last_error(const mrs_mlp *m);
 mrs_status mrs_mlp_param_count(const mrs_mlp *m, size_t *n);
+/* Launch shape of the fused inference kernel (features, every layer and the
+ * output of 128 rows per CTA; weights streamed through a ring of shared
+ * memory slots): info[0] resident CTAs per SM for plain rows
+ * (mrs_mlp_forward), info[1] for rollout trajectories (inside the control
+ * cycle), info[2] ring slots, info[3] dynamic shared memory bytes per CTA,
+ * info[4] SMs.  `n` >= 5 entries, host memory. */
+mrs_status mrs_mlp_launch_info(const mrs_mlp *m, int *info, int n);
 mrs_status mrs_mlp_get_params(mrs_mlp *m, float *host, size_t n);
 mrs_status mrs_mlp_set_params(mrs_mlp *m, const float *host, size_t n);
 /* y [n] = network(x [n][in_dim]), device pointers. */

@@ -306,11 +306,26 @@ static cudaError_t configure_fused(mrs_mlp *m, int *per_sm)
     need = (need + 15) / 16 * 16;
     cudaError_t e = cudaFuncSetAttribute(fused::k_mlp_fused<In>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fused::k_mlp_fused<In>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fused::k_mlp_fused<In>, fused::kThreads,
-                                                      need);
+    // resident CTAs per SM from the kernel's own limits (shared memory with
+    // the 1 KB the driver reserves per CTA, registers allocated per warp in
+    // units of 256, threads, tensor-memory columns); the occupancy query
+    // answered 1 where two fit
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, fused::k_mlp_fused<In>);
     if (e != cudaSuccess) return e;
-    if (*per_sm < 1 || *per_sm > max_ctas) return cudaErrorInvalidConfiguration;
+    const int warps = fused::kThreads / 32;
+    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int fit = (int)(sm_bytes / (need + reserve));
+    fit = std::min(fit, 65536 / (regs_per_warp * warps));
+    fit = std::min(fit, 2048 / fused::kThreads);
+    fit = std::min(fit, max_ctas);
+    *per_sm = fit;
+    if (*per_sm < 1) return cudaErrorInvalidConfiguration;
     m->fnet_smem = need;
     return cudaSuccess;
 }
@@ -518,7 +533,9 @@ mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long 
         n.a_bytes = 128u * 2u * (unsigned)std::max(m->in_pad, width);
         n.tmem_cols = 32;
         while ((int)n.tmem_cols < width) n.tmem_cols *= 2;
-        const long budget = 110 * 1024 - (long)n.a_bytes - (long)sizeof(fused::Ctl);
+        n.p_floats = (unsigned)(layers * width + width + 1);
+        const long budget = 110 * 1024 - (long)n.a_bytes - (long)sizeof(fused::Ctl) -
+                            (long)n.p_floats * 4 - 16;
         n.slots = (int)std::max(2L, std::min((long)fused::kMaxSlots, budget / (long)n.chunk_bytes));
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -571,6 +588,17 @@ mrs_status mrs_mlp_param_count(const mrs_mlp *m, size_t *n)
 {
     if (!m || !n) return MRS_EINVAL;
     *n = m->n_params;
+    return MRS_OK;
+}
+
+mrs_status mrs_mlp_launch_info(const mrs_mlp *m, int *info, int n)
+{
+    if (!m || !info || n < 5) return MRS_EINVAL;
+    info[0] = m->per_sm_rows;
+    info[1] = m->per_sm_traj;
+    info[2] = m->fnet.slots;
+    info[3] = (int)m->fnet_smem;
+    info[4] = m->num_sms;
     return MRS_OK;
 }
 

@@ -50,6 +50,7 @@ struct Net {
     unsigned chunk_bytes;         // width * 16 * 2
     unsigned a_bytes;             // 128 * max(in_pad, width) * 2
     unsigned tmem_cols;           // power of two >= max(32, width)
+    unsigned p_floats;            // biases, output weights and bias: layers * width + width + 1
 };
 
 struct Ctl {                      // follows the A buffer and the ring
@@ -60,9 +61,11 @@ struct Ctl {                      // follows the A buffer and the ring
     int abort;
 };
 
+// A buffer, weight ring, control block, then the FP32 biases and output layer
 __host__ __device__ inline size_t smem_bytes(const Net &n)
 {
-    return (size_t)n.a_bytes + (size_t)n.slots * n.chunk_bytes + sizeof(Ctl);
+    return (size_t)n.a_bytes + (size_t)n.slots * n.chunk_bytes + sizeof(Ctl) +
+           ((size_t)n.p_floats * 4 + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity)
@@ -197,6 +200,7 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
     unsigned char *Abuf = smem;
     unsigned char *ring = smem + net.a_bytes;
     Ctl &C = *reinterpret_cast<Ctl *>(ring + (size_t)net.slots * net.chunk_bytes);
+    float *Ps = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(&C) + sizeof(Ctl));
     volatile int *abort = &C.abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (rows + 127) / 128;
@@ -215,6 +219,20 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) tc::tmem_alloc(&C.tmem, net.tmem_cols);
+    {
+        // biases of every layer, output weights and bias, read by the epilogue
+        const int W = net.width, LW = net.layers * W;
+        for (int i = threadIdx.x; i < (int)net.p_floats; i += kThreads) {
+            float v;
+            if (i < LW)
+                v = net.params[net.offB0 + (size_t)(i / W) * (W * W + W) + i % W];
+            else if (i < LW + W)
+                v = net.params[net.offWo + i - LW];
+            else
+                v = net.params[net.offBo];
+            Ps[i] = v;
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -286,8 +304,8 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
         const int m = quarter * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const int W = net.width;
-        const float *w_out = net.params + net.offWo;
-        const float b_out = net.params[net.offBo];
+        const float *w_out = Ps + net.layers * W;
+        const float b_out = Ps[net.layers * W + W];
         uint32_t u = 0, pp = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
@@ -322,16 +340,16 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
                 }
                 tc::fence_after_sync();
                 const bool last = l == net.layers - 1;
-                const float *bias = net.params + net.offB0 + (size_t)l * (W * W + W);
+                const float *bias = Ps + l * W;
                 const uint32_t sbo = (uint32_t)(W / 8) * 128u;
-                for (int cc = half; cc < W / 16; cc += 2) {
-                    float v[16];
-                    tc::tmem_ld16(lane_base + (uint32_t)(cc * 16), v);
+                // this thread's 16-column chunks cc = half, half + 2, ..., two
+                // loads in flight per wait
+                auto finish = [&](int cc, const uint32_t (&r)[16]) {
                     uint32_t pk[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        pk[i] = pack_bf16(silu(v[2 * i] + bias[cc * 16 + 2 * i]),
-                                          silu(v[2 * i + 1] + bias[cc * 16 + 2 * i + 1]));
+                        pk[i] = pack_bf16(silu(__uint_as_float(r[2 * i]) + bias[cc * 16 + 2 * i]),
+                                          silu(__uint_as_float(r[2 * i + 1]) + bias[cc * 16 + 2 * i + 1]));
                     if (!last) {
                         unsigned char *dst = Abuf + (m >> 3) * sbo + (2 * cc) * 128 + (m & 7) * 16;
                         *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -344,6 +362,16 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
                                         part);
                         }
                     }
+                };
+                const int nc = W / 16;
+                for (int cc = half; cc < nc; cc += 4) {
+                    uint32_t r0[16], r1[16];
+                    const bool two = cc + 2 < nc;      // uniform over the warp
+                    tc::tmem_ld16_async(lane_base + (uint32_t)(cc * 16), r0);
+                    if (two) tc::tmem_ld16_async(lane_base + (uint32_t)((cc + 2) * 16), r1);
+                    tc::tmem_wait_ld();
+                    finish(cc, r0);
+                    if (two) finish(cc + 2, r1);
                 }
                 tc::fence_before_sync();
                 if (!last) {

@@ -90,6 +90,7 @@ SIGNATURES = {
     "mrs_mlp_destroy": (None, [C.c_void_p]),
     "mrs_mlp_last_error": (C.c_char_p, [C.c_void_p]),
     "mrs_mlp_param_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "mrs_mlp_launch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
     "mrs_mlp_get_params": (C.c_int, [C.c_void_p, _fp, C.c_size_t]),
     "mrs_mlp_set_params": (C.c_int, [C.c_void_p, _fp, C.c_size_t]),
     "mrs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -461,6 +462,14 @@ class MLP:
     def _check(self, st, what):
         if st != 0:
             raise MrsError(st, f"{what}: {self.L.mrs_mlp_last_error(self.h).decode()}")
+
+    def launch_info(self):
+        """Fused inference launch shape: CTAs per SM (plain rows, rollout
+        trajectories), ring slots, shared memory per CTA, SMs."""
+        info = (C.c_int * 5)()
+        self._check(self.L.mrs_mlp_launch_info(self.h, info, 5), "launch_info")
+        return dict(per_sm_rows=info[0], per_sm_traj=info[1], slots=info[2], smem=info[3],
+                    sms=info[4])
 
     def close(self):
         if getattr(self, "h", None):
