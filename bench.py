@@ -414,6 +414,15 @@ def run(args):
     units_per_step = sc.rollout_steps() * sc.params["iterations"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
+    ctl.step_device(d_in)
+    ctl.sync()
+    tune = None
+    if not args.no_autotune:
+        best, table = ctl.autotune(reps=5)
+        tune = {"chosen": best, "tried": len(table),
+                "default_ms": next(t["rollout_ms"] for t in table
+                                   if (t["tile_samples"], t["order"]) == (32, 0)
+                                   and t["blocks_per_sm"] == max(x["blocks_per_sm"] for x in table))}
 
     # ---- device-resident cycles (exact costs) ------------------------------
     step_ms, kt, clk = time_device(ctl, d_in, args.steps, args.warmup, flush, ws, local, True)
@@ -458,7 +467,8 @@ def run(args):
                    "spheres": sc.arms[0].n_spheres, "world_spheres": int(len(sc.world)),
                    "boxes": int(len(sc.aabb)), "mode": "exact",
                    "l2": "flushed (256 MiB write) before every timed cycle",
-                   "parallelism": f"replicas x{ws}", "graph": True},
+                   "parallelism": f"replicas x{ws}", "graph": True,
+                   "rollout_shape": tune},
         "latency_ms": {"device_p50": float(np.percentile(step_ms, 50)),
                        "device_p99": float(np.percentile(step_ms, 99))},
         "kernel_ms": k_mean,
@@ -490,6 +500,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-surrogate comparison")
     ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default rollout shape")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-arm-at-a-time, graph-free comparison")
     ap.add_argument("--latency-cycles", type=int, default=1000,

@@ -273,6 +273,39 @@ mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise);
 mrs_status mrs_enable_timing(mrs_ctx *ctx, int on);
 mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
 
+/* Launch shape of the rollout (the kernel that runs FK, the collision passes
+ * and the stage cost of every sampled step; the paper fixes no GPU mapping):
+ *   tile_samples   samples per work unit, a multiple of 32 in [32, 256]: the
+ *                  unit's inputs (world at the step's time, neighbour plans
+ *                  at the step) are staged once, the samples pass through
+ *                  in groups of 32;
+ *   blocks_per_sm  resident blocks of the persistent grid per SM, 1 ..
+ *                  max_blocks_per_sm (0 = the maximum);
+ *   order          0 step-major work list (all arms' units of step h, then
+ *                  h + 1: concurrent blocks share the step's plans), 1
+ *                  arm-major.
+ * Results do not depend on the shape (each sample's cost is reduced by its
+ * own lane in every shape); only the time does.  mrs_set_rollout_shape
+ * returns MRS_EINVAL for a shape out of range. */
+typedef struct {
+    int tile_samples, blocks_per_sm, order;
+    float rollout_ms;          /* mrs_autotune: median rollout time of the shape */
+} mrs_rollout_shape;
+mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
+mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
+
+/* Autotuner: times every shape of the grid {32, 64, 128} samples x 1 ..
+ * max resident blocks per SM x {step-major, arm-major} over `reps` control
+ * cycles each (rollout stage, CUDA events, median) on the context's current
+ * inputs, and keeps the fastest.  The controller state is saved before and
+ * restored after the trials, so the next cycle is unaffected.  Needs one
+ * earlier mrs_step / mrs_step_device (the inputs the trials use);
+ * otherwise MRS_ESTATE.  `table` (host, capacity `cap`, may be null)
+ * receives every shape tried with its time, *n_tried their count; `best`
+ * (may be null) the one kept. */
+mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int cap, int *n_tried,
+                        mrs_rollout_shape *best);
+
 /* Philox4x32-10 self-test (Salmon et al., SC'11): out[n][4] = Philox of
  * ctr[n][4] under key[2], computed by the device generator the sampling
  * uses.  Host arrays; allocates a temporary device buffer. */

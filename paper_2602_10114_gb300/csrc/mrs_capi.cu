@@ -51,6 +51,9 @@ struct mrs_ctx {
     std::vector<UpdateTile> update_tiles;
     std::vector<int> self_pairs;
     int num_sms = 0;
+    // rollout launch shape (mrs_set_rollout_shape / mrs_autotune)
+    int tile_samples = 32, blocks_per_sm = 0, tile_order = 0, max_blocks_per_sm = 1;
+    bool has_input = false;
 };
 
 static const char *g_noctx = "null context";
@@ -135,6 +138,30 @@ static void build_layout(mrs_ctx *c)
     c->sz.workspace_bytes = L.total;
 }
 
+// rollout work units of tile_samples samples; step-major order lets the
+// concurrently resident blocks share the step's plan slices in L2
+static void build_rollout_tiles(mrs_ctx *c)
+{
+    c->rollout_tiles.clear();
+    const int nsub = c->tile_samples / 32;
+    int Hmax = 0;
+    for (auto &A : c->arms) Hmax = std::max(Hmax, A.H);
+    auto push = [&](int a, int h) {
+        const ArmDev &A = c->arms[a];
+        for (int n0 = 0; n0 < A.K; n0 += 32 * nsub)
+            c->rollout_tiles.push_back({a, h, n0, std::min(nsub, (A.K - n0 + 31) / 32)});
+    };
+    if (c->tile_order == 0) {
+        for (int h = 0; h < Hmax; ++h)
+            for (int a = 0; a < c->A; ++a)
+                if (h < c->arms[a].H && !c->arms[a].external) push(a, h);
+    } else {
+        for (int a = 0; a < c->A; ++a)
+            if (!c->arms[a].external)
+                for (int h = 0; h < c->arms[a].H; ++h) push(a, h);
+    }
+}
+
 static void build_work_lists(mrs_ctx *c)
 {
     c->sample_tiles.clear();
@@ -148,15 +175,7 @@ static void build_work_lists(mrs_ctx *c)
         for (int n0 = 0; n0 < A.K; n0 += 256) c->cost_tiles.push_back({a, n0});
         for (int h = 0; h < A.H; ++h) c->update_tiles.push_back({a, h});
     }
-    // rollout tiles step-major so that concurrently resident blocks share steps
-    int Hmax = 0;
-    for (auto &A : c->arms) Hmax = std::max(Hmax, A.H);
-    for (int h = 0; h < Hmax; ++h)
-        for (int a = 0; a < c->A; ++a) {
-            const ArmDev &A = c->arms[a];
-            if (h >= A.H || A.external) continue;
-            for (int n0 = 0; n0 < A.K; n0 += kTileSamples) c->rollout_tiles.push_back({a, h, n0, 0});
-        }
+    build_rollout_tiles(c);
 }
 
 static void fill_dev(mrs_ctx *c, char *base)
@@ -415,7 +434,8 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         mrs_destroy(ctx);
         return MRS_ECUDA;
     }
-    L.rollout_grid = rollout_blocks_per_sm(L.smem_rollout) * ctx->num_sms;
+    ctx->max_blocks_per_sm = rollout_blocks_per_sm(L.smem_rollout);
+    L.rollout_grid = ctx->max_blocks_per_sm * ctx->num_sms;
     *out = ctx;
     return MRS_OK;
 }
@@ -536,7 +556,10 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
         ctx->P.aabb_cap = std::min(ctx->P.aabb_cap, MRS_MAX_AABBS);
         ctx->L.smem_rollout = rollout_smem_bytes(ctx->P, ctx->A);
         CK(configure_rollout(ctx->L), "rollout shared memory");
-        ctx->L.rollout_grid = rollout_blocks_per_sm(ctx->L.smem_rollout) * ctx->num_sms;
+        ctx->max_blocks_per_sm = rollout_blocks_per_sm(ctx->L.smem_rollout);
+        const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, ctx->max_blocks_per_sm)
+                                               : ctx->max_blocks_per_sm;
+        ctx->L.rollout_grid = bps * ctx->num_sms;
         invalidate_graph(ctx);
     }
     std::vector<float4> w(n_spheres), v(n_spheres), b(2 * n_aabbs);
@@ -642,6 +665,7 @@ mrs_status mrs_step_device(mrs_ctx *ctx, const float *d_input)
     if (st != MRS_OK) return st;
     CK(cudaMemcpyAsync(ctx->D.input, d_input, sizeof(float) * ctx->sz.input_floats,
                        cudaMemcpyDeviceToDevice, ctx->stream), "input copy");
+    ctx->has_input = true;
     return launch_cycle(ctx);
 }
 
@@ -666,6 +690,7 @@ mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out
     if (st != MRS_OK) return st;
     CK(cudaMemcpyAsync(ctx->D.input, ctx->pin_in, sizeof(float) * ctx->sz.input_floats,
                        cudaMemcpyHostToDevice, ctx->stream), "input upload");
+    ctx->has_input = true;
     st = launch_cycle(ctx);
     if (st != MRS_OK) return st;
     CK(cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
@@ -1064,6 +1089,103 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
     for (int i = 0; i < cnt; ++i)
         CK(cudaEventElapsedTime(&ms[i], ctx->events[i], ctx->events[i + 1]), "elapsed time");
     *n = cnt;
+    return MRS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rollout launch shape and its autotuner
+
+static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm, int order)
+{
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    ctx->tile_samples = tile_samples;
+    ctx->blocks_per_sm = blocks_per_sm;
+    ctx->tile_order = order;
+    build_rollout_tiles(ctx);
+    LaunchPlan &L = ctx->L;
+    L.n_rollout_tiles = (int)ctx->rollout_tiles.size();
+    const int bps = blocks_per_sm > 0 ? blocks_per_sm : ctx->max_blocks_per_sm;
+    L.rollout_grid = bps * ctx->num_sms;
+    // the list is never longer than the 32-sample list the workspace holds
+    CK(cudaMemcpyAsync(const_cast<RolloutTile *>(L.rollout_tiles), ctx->rollout_tiles.data(),
+                       sizeof(RolloutTile) * ctx->rollout_tiles.size(), cudaMemcpyHostToDevice,
+                       ctx->stream), "upload rollout tiles");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    invalidate_graph(ctx);
+    return MRS_OK;
+}
+
+mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
+{
+    if (!ctx || !shape) return MRS_EINVAL;
+    if (shape->tile_samples < 32 || shape->tile_samples > 256 || shape->tile_samples % 32 ||
+        shape->blocks_per_sm < 0 || shape->blocks_per_sm > ctx->max_blocks_per_sm ||
+        (shape->order != 0 && shape->order != 1))
+        return fail(ctx, MRS_EINVAL, "rollout shape out of range");
+    return apply_shape(ctx, shape->tile_samples, shape->blocks_per_sm, shape->order);
+}
+
+mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (shape) {
+        shape->tile_samples = ctx->tile_samples;
+        shape->blocks_per_sm = ctx->blocks_per_sm;
+        shape->order = ctx->tile_order;
+        shape->rollout_ms = 0.f;
+    }
+    if (max_blocks_per_sm) *max_blocks_per_sm = ctx->max_blocks_per_sm;
+    return MRS_OK;
+}
+
+mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int cap, int *n_tried,
+                        mrs_rollout_shape *best)
+{
+    if (!ctx || reps < 1 || reps > 1000 || cap < 0) return fail(ctx, MRS_EINVAL, "bad arguments");
+    if (!ctx->has_input) return fail(ctx, MRS_ESTATE, "autotune needs the inputs of an earlier step");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    std::vector<char> blob(ctx->sz.state_bytes);
+    if ((st = mrs_save_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;
+    const bool timing = ctx->timing;
+    if ((st = mrs_enable_timing(ctx, 1)) != MRS_OK) return st;
+    const int stages = 2 + 5 * ctx->P.iterations;
+    std::vector<mrs_rollout_shape> tried;
+    mrs_rollout_shape keep{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
+    float best_ms = INFINITY;
+    for (int ts : {32, 64, 128}) {
+        for (int bps = 1; bps <= ctx->max_blocks_per_sm; ++bps) {
+            for (int order = 0; order < 2; ++order) {
+                if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) return st;
+                std::vector<float> t;
+                for (int r = 0; r <= reps; ++r) {   // the first cycle warms up
+                    if ((st = launch_cycle(ctx)) != MRS_OK) return st;
+                    float ms[64];
+                    int n = 64;
+                    if ((st = mrs_kernel_times(ctx, ms, &n)) != MRS_OK) return st;
+                    float roll = 0.f;
+                    for (int it = 0; it < ctx->P.iterations; ++it) roll += ms[1 + 5 * it + 2];
+                    if (r > 0) t.push_back(roll);
+                }
+                (void)stages;
+                std::sort(t.begin(), t.end());
+                const float med = t[t.size() / 2];
+                tried.push_back(mrs_rollout_shape{ts, bps, order, med});
+                if (med < best_ms) {
+                    best_ms = med;
+                    keep = tried.back();
+                }
+            }
+        }
+    }
+    if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order)) != MRS_OK) return st;
+    if ((st = mrs_enable_timing(ctx, timing ? 1 : 0)) != MRS_OK) return st;
+    if ((st = mrs_load_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;
+    if (n_tried) *n_tried = (int)tried.size();
+    if (table)
+        for (int i = 0; i < (int)tried.size() && i < cap; ++i) table[i] = tried[i];
+    if (best) *best = keep;
     return MRS_OK;
 }
 

@@ -96,7 +96,7 @@ struct Dev {
 
 // Work items of the launch-grid work lists.
 struct SampleTile { int arm, n0; };
-struct RolloutTile { int arm, h, n0, pad; };
+struct RolloutTile { int arm, h, n0, nsub; };   // samples n0 .. n0 + 32 nsub - 1 at step h
 struct CostTile { int arm, n0; };
 struct UpdateTile { int arm, h; };
 

@@ -2,10 +2,14 @@
 // the collision spheres at each sampled state and the stage cost of Eq. 5
 // with the prioritised coordination term of Eq. 9 (Sec. IV-A/B).
 //
-// Work unit (tile): (arm, step h, 32 samples).  A persistent grid of 256-thread
-// blocks takes tiles from an atomic counter.  Warp g of a block owns sphere
-// group g (spheres [g*spg, (g+1)*spg), spg = ceil(N_S / 8)) of the tile's 32
-// rollout steps, one sample per lane; its centres stay in registers.
+// Work unit (tile): (arm, step h, 32 nsub samples).  A persistent grid of
+// 256-thread blocks takes tiles from an atomic counter and stages the tile's
+// inputs (world at the step's time, the neighbours' plan spheres at step h,
+// the arm's constants) once; the samples then pass through in sub-batches of
+// 32.  Warp g of a block owns sphere group g (spheres [g*spg, (g+1)*spg),
+// spg = ceil(N_S / 8)) of the sub-batch's 32 rollout steps, one sample per
+// lane; its centres stay in registers.  The samples per tile, the tile order
+// and the resident blocks per SM are chosen at run time (mrs_autotune).
 //
 // Pair test.  A pair (own sphere c, radius r; other sphere p, radius r_p) can
 // change a ramp cost max(0, 1 - dist/B) only if |c - p| < r + r_p + B.  With
@@ -18,6 +22,8 @@
 // workspace) gets an exact pass: direct squared distance, and the square root
 // only for pairs inside the ramp.  Since the cost is zero outside the ramp,
 // the result equals the brute-force minimum of Eq. 6 restricted to the ramp.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 // tuning knobs of the rollout kernel (set at build time)
@@ -379,40 +385,46 @@ __global__ void __launch_bounds__(kRolloutThreads, MRS_ROLLOUT_MIN_BLOCKS) k_rol
         __syncthreads();
         const int n_nb = s_nnb;
 
-        const int n = T.n0 + lane;
-        const bool valid = n < A.K;
-        float pose = 0.f;
-        switch (A.spg) {
-            case 1: rollout_group<1>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            case 2: rollout_group<2>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            case 3: rollout_group<3>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            case 4: rollout_group<4>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            case 5: rollout_group<5>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            case 6: rollout_group<6>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            case 7: rollout_group<7>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            default: rollout_group<8>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-        }
-        if (g == kGroups - 1) s_pose[lane] = pose;
-        __syncthreads();
-
-        // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
-        if (g == 0 && valid) {
-            const long long idx = A.off_kh + (long long)h * A.K + n;
-            const float dw = ordered_to_float(S.red[0 * 32 + lane]);
-            const float dsf = ordered_to_float(S.red[1 * 32 + lane]);
-            float dyn = 0.f;
-            for (int nb = 0; nb < n_nb; ++nb) {
-                const float rho = fmaxf(ordered_to_float(S.red[(2 + nb) * 32 + lane]), 0.f);
-                dyn = __fmaf_rn(S.nb_alpha[nb], ramp(rho, P.B), dyn);
+        for (int sb = 0; sb < T.nsub; ++sb) {
+            const int n = T.n0 + sb * 32 + lane;
+            const bool valid = n < A.K;
+            float pose = 0.f;
+            switch (A.spg) {
+                case 1: rollout_group<1>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 2: rollout_group<2>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 3: rollout_group<3>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 4: rollout_group<4>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 5: rollout_group<5>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 6: rollout_group<6>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 7: rollout_group<7>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                default: rollout_group<8>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
             }
-            float c = __fmul_rn(P.w_pose, s_pose[lane]);
-            c = __fadd_rn(c, D.stage_lim[idx]);
-            c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
-            c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
-            c = __fmaf_rn(P.w_dyn, dyn, c);
-            D.stage[idx] = c;
+            if (g == kGroups - 1) s_pose[lane] = pose;
+            __syncthreads();
+
+            // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
+            if (g == 0) {
+                if (valid) {
+                    const long long idx = A.off_kh + (long long)h * A.K + n;
+                    const float dw = ordered_to_float(S.red[0 * 32 + lane]);
+                    const float dsf = ordered_to_float(S.red[1 * 32 + lane]);
+                    float dyn = 0.f;
+                    for (int nb = 0; nb < n_nb; ++nb) {
+                        const float rho = fmaxf(ordered_to_float(S.red[(2 + nb) * 32 + lane]), 0.f);
+                        dyn = __fmaf_rn(S.nb_alpha[nb], ramp(rho, P.B), dyn);
+                    }
+                    float c = __fmul_rn(P.w_pose, s_pose[lane]);
+                    c = __fadd_rn(c, D.stage_lim[idx]);
+                    c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
+                    c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
+                    c = __fmaf_rn(P.w_dyn, dyn, c);
+                    D.stage[idx] = c;
+                }
+                // this lane's minima are read: reset them for the next sub-batch
+                for (int k = lane; k < (2 + n_nb) * 32; k += 32) S.red[k] = float_to_ordered(kInf);
+            }
+            __syncthreads();   // shared memory is reused by the next sub-batch or tile
         }
-        __syncthreads();   // shared memory is reused by the next tile
     }
 }
 
@@ -434,14 +446,23 @@ cudaError_t configure_rollout(const LaunchPlan &L)
                                 (int)L.smem_rollout);
 }
 
+// Resident rollout blocks per SM from the kernel's own limits: shared memory
+// (with the 1 KB the driver reserves per block), registers (allocated per
+// warp in units of 256), threads.
 int rollout_blocks_per_sm(size_t smem)
 {
-    int nb = 0;
+    cudaFuncAttributes fa{};
     if (cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rollout, kRolloutThreads, smem) !=
-            cudaSuccess)
+        cudaFuncSetAttribute(k_rollout, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_rollout) != cudaSuccess)
         return 1;
+    const int warps = kRolloutThreads / 32;
+    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int nb = (int)((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024));
+    nb = std::min(nb, 65536 / std::max(1, regs_per_warp * warps));
+    nb = std::min(nb, 2048 / kRolloutThreads);
     return nb > 0 ? nb : 1;
 }
 

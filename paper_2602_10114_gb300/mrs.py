@@ -51,6 +51,11 @@ class MrsStepOut(C.Structure):
                 ("dist_to_goal", _fp), ("min_cost", _fp)]
 
 
+class MrsRolloutShape(C.Structure):
+    _fields_ = [("tile_samples", C.c_int), ("blocks_per_sm", C.c_int), ("order", C.c_int),
+                ("rollout_ms", C.c_float)]
+
+
 class MrsSizes(C.Structure):
     _fields_ = [("n_arms", C.c_size_t), ("hd", C.c_size_t), ("hs", C.c_size_t),
                 ("d", C.c_size_t), ("k", C.c_size_t), ("hdd", C.c_size_t),
@@ -83,6 +88,10 @@ SIGNATURES = {
     "mrs_set_zero_noise": (C.c_int, [C.c_void_p, C.c_int]),
     "mrs_enable_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "mrs_kernel_times": (C.c_int, [C.c_void_p, _fp, C.POINTER(C.c_int)]),
+    "mrs_set_rollout_shape": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mrs_get_rollout_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "mrs_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                               C.c_void_p]),
     "mrs_philox": (C.c_int, [C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                              C.POINTER(C.c_uint32)]),
     "mrs_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
@@ -302,6 +311,29 @@ class Controller:
         ms = np.zeros(64, np.float32)
         self._check(self.L.mrs_kernel_times(self.h, _pf(ms), C.byref(n)), "kernel_times")
         return ms[:n.value].copy()
+
+    def set_rollout_shape(self, tile_samples=32, blocks_per_sm=0, order=0):
+        sh = MrsRolloutShape(tile_samples, blocks_per_sm, order, 0.0)
+        self._check(self.L.mrs_set_rollout_shape(self.h, C.byref(sh)), "set_rollout_shape")
+
+    def rollout_shape(self):
+        """(tile_samples, blocks_per_sm, order) and the maximum blocks per SM."""
+        sh = MrsRolloutShape()
+        mx = C.c_int()
+        self._check(self.L.mrs_get_rollout_shape(self.h, C.byref(sh), C.byref(mx)), "get_rollout_shape")
+        return (sh.tile_samples, sh.blocks_per_sm, sh.order), mx.value
+
+    def autotune(self, reps=5):
+        """Time every rollout shape, keep the fastest; returns (best, table)
+        as dicts with tile_samples, blocks_per_sm, order, rollout_ms."""
+        tab = (MrsRolloutShape * 64)()
+        n = C.c_int()
+        best = MrsRolloutShape()
+        self._check(self.L.mrs_autotune(self.h, int(reps), tab, 64, C.byref(n), C.byref(best)),
+                    "autotune")
+        conv = lambda x: dict(tile_samples=x.tile_samples, blocks_per_sm=x.blocks_per_sm,
+                              order=x.order, rollout_ms=float(x.rollout_ms))
+        return conv(best), [conv(tab[i]) for i in range(min(n.value, 64))]
 
     def save_state(self) -> bytes:
         buf = (C.c_char * int(self.sizes.state_bytes))()
