@@ -37,6 +37,23 @@ UNIT = "trajectory-steps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
+def measured_peaks():
+    """The machine's measured HBM and BF16 peaks, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def mlp_flops(rows, in_pad, width, layers):
+    """Dense BF16 work of one surrogate launch: 2 x rows x (in_pad x width +
+    (layers - 1) x width^2 + width)."""
+    return 2.0 * rows * (in_pad * width + (layers - 1) * width * width + width)
+
+
 def workload(idx):
     from paper_2602_10114_gb300 import scenarios as S
     return S.config(idx)
@@ -376,12 +393,19 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     for a in range(sc.n_arms):
         ctl.set_self_surrogate(a, None)
     dev = np.abs(c_learned - c_exact)
+    sur_ms = float(kt[:, 2].mean())
+    fl = mlp_flops(sc.rollout_steps(), 16, 256, 3)
+    pk = measured_peaks()
     return {
         "value": units * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
         "speedup_vs_exact": exact_ms / ms,
         "e2e": {"value": units * ws / e2e_s, "cycles": len(lat), "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                 "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))},
-        "surrogate_ms": float(kt[:, 2].mean()), "rollout_ms": float(kt[:, 3].mean()),
+        "surrogate_ms": sur_ms, "rollout_ms": float(kt[:, 3].mean()),
+        "roofline": {"kernel": "k_mlp_fused", "bound": "tensor",
+                     "achieved": fl / (sur_ms / 1e3) / 1e12, "peak": pk["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": fl / (sur_ms / 1e3) / 1e12 / pk["bf16_tflops"],
+                     "peak_source": pk["source"] + " BF16 burst", "flops_per_launch": fl},
         "held_out": {k: stats[0][k] for k in ("fn_rate", "fn_rate_active", "skip_fraction", "mae",
                                               "colliding", "samples")},
         "rollout_steps": {k: ev[k] for k in ("fn_rate", "skip_fraction", "mae", "colliding",
@@ -425,7 +449,9 @@ def run(args):
                                    and t["blocks_per_sm"] == max(x["blocks_per_sm"] for x in table))}
 
     # ---- device-resident cycles (exact costs) ------------------------------
-    step_ms, kt, clk = time_device(ctl, d_in, args.steps, args.warmup, flush, ws, local, True)
+    clk = ClockSampler(local)
+    clk.__enter__()
+    step_ms, kt, _ = time_device(ctl, d_in, args.steps, args.warmup, flush, ws)
     ms = float(np.mean(step_ms))
     ms_max = max_over_ranks(ms, ws)
     value = units_per_step * ws / (ms_max / 1e3)
@@ -452,6 +478,7 @@ def run(args):
     if not args.no_learned:
         learned = learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, ms_max)
 
+    clk.__exit__()
     if rank != 0:
         return
     cpu = None
