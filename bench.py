@@ -418,6 +418,36 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     }
 
 
+def other_workload(idx, args, flush, ws, dev):
+    """Device-timed cycles of another workload (exact costs, autotuned shape):
+    throughput, cycle time, rollout time and its FP32 roofline fraction."""
+    import torch
+    from paper_2602_10114_gb300 import mrs
+    sc = workload(idx)
+    ctl = mrs.Controller(sc, device=dev)
+    ctl.set_world()
+    gp, gR = [], []
+    for a in range(sc.n_arms):
+        p, R = ctl.goal_pose(a, sc.goal_q[a])
+        gp.append(p)
+        gR.append(R)
+    d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
+    ctl.step_device(d_in)
+    ctl.sync()
+    best, table = ctl.autotune(reps=3)
+    steps = max(5, args.steps // 5)
+    step_ms, kt, _ = time_device(ctl, d_in, steps, 3, flush, ws)
+    ms = max_over_ranks(float(np.mean(step_ms)), ws)
+    roll = float(kt[:, 3].mean())
+    fl = rollout_flops(sc)
+    ctl.close()
+    units = sc.rollout_steps() * sc.params["iterations"]
+    return {"workload": sc.name, "value": units * ws / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "rollout_ms": roll,
+            "rollout_shape": best, "roofline_frac": fl / (roll / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+            "flops_per_launch": fl}
+
+
 def run(args):
     import torch
 
@@ -478,6 +508,9 @@ def run(args):
     if not args.no_learned:
         learned = learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, ms_max)
 
+    others = {}
+    for idx in args.other_workloads:
+        others[f"cfg{idx}"] = other_workload(idx, args, flush, ws, dev)
     clk.__exit__()
     if rank != 0:
         return
@@ -509,6 +542,7 @@ def run(args):
         "e2e": e2e,
         "plain": plain,
         "learned": learned,
+        "other_workloads": others,
         "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),
         "clocks": clk.summary(),
     }
@@ -527,6 +561,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-surrogate comparison")
     ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
+    ap.add_argument("--other-workloads", type=int, nargs="*", default=[4, 5],
+                    help="also time these workloads (device-resident, exact, autotuned)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rollout shape")
     ap.add_argument("--no-plain", action="store_true",

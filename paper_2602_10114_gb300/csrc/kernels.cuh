@@ -37,6 +37,7 @@ struct LaunchPlan {
     const UpdateTile *update_tiles;
     size_t smem_prep, smem_sample, smem_rollout, smem_toplan;
     int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)
+    int rollout_variant;   // register budget of the rollout kernel: 2 or 3 blocks per SM
     int *done_counter;  // last-block-done counter of k_toplan
     int n_surrogates;
     SurrogateSlot surrogates[MRS_MAX_ARMS];

@@ -162,6 +162,17 @@ static void build_rollout_tiles(mrs_ctx *c)
     }
 }
 
+// persistent rollout grid and kernel variant for the shape's blocks per SM
+// (0 = the maximum): up to two blocks the variant with the larger register
+// budget, three the other
+static void set_rollout_grid(mrs_ctx *c)
+{
+    const int bps = c->blocks_per_sm > 0 ? std::min(c->blocks_per_sm, c->max_blocks_per_sm)
+                                         : c->max_blocks_per_sm;
+    c->L.rollout_grid = bps * c->num_sms;
+    c->L.rollout_variant = bps >= 3 ? 3 : 2;
+}
+
 static void build_work_lists(mrs_ctx *c)
 {
     c->sample_tiles.clear();
@@ -435,7 +446,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         return MRS_ECUDA;
     }
     ctx->max_blocks_per_sm = rollout_blocks_per_sm(L.smem_rollout);
-    L.rollout_grid = ctx->max_blocks_per_sm * ctx->num_sms;
+    set_rollout_grid(ctx);
     *out = ctx;
     return MRS_OK;
 }
@@ -557,9 +568,7 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
         ctx->L.smem_rollout = rollout_smem_bytes(ctx->P, ctx->A);
         CK(configure_rollout(ctx->L), "rollout shared memory");
         ctx->max_blocks_per_sm = rollout_blocks_per_sm(ctx->L.smem_rollout);
-        const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, ctx->max_blocks_per_sm)
-                                               : ctx->max_blocks_per_sm;
-        ctx->L.rollout_grid = bps * ctx->num_sms;
+        set_rollout_grid(ctx);
         invalidate_graph(ctx);
     }
     std::vector<float4> w(n_spheres), v(n_spheres), b(2 * n_aabbs);
@@ -1105,8 +1114,7 @@ static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm,
     build_rollout_tiles(ctx);
     LaunchPlan &L = ctx->L;
     L.n_rollout_tiles = (int)ctx->rollout_tiles.size();
-    const int bps = blocks_per_sm > 0 ? blocks_per_sm : ctx->max_blocks_per_sm;
-    L.rollout_grid = bps * ctx->num_sms;
+    set_rollout_grid(ctx);
     // the list is never longer than the 32-sample list the workspace holds
     CK(cudaMemcpyAsync(const_cast<RolloutTile *>(L.rollout_tiles), ctx->rollout_tiles.data(),
                        sizeof(RolloutTile) * ctx->rollout_tiles.size(), cudaMemcpyHostToDevice,

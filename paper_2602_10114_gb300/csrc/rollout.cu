@@ -1,478 +1,43 @@
-// rollout.cu -- the Rollout step of Algorithm 1 for every arm: kinematics of
-// the collision spheres at each sampled state and the stage cost of Eq. 5
-// with the prioritised coordination term of Eq. 9 (Sec. IV-A/B).
-//
-// Work unit (tile): (arm, step h, 32 nsub samples).  A persistent grid of
-// 256-thread blocks takes tiles from an atomic counter and stages the tile's
-// inputs (world at the step's time, the neighbours' plan spheres at step h,
-// the arm's constants) once; the samples then pass through in sub-batches of
-// 32.  Warp g of a block owns sphere group g (spheres [g*spg, (g+1)*spg),
-// spg = ceil(N_S / 8)) of the sub-batch's 32 rollout steps, one sample per
-// lane; its centres stay in registers.  The samples per tile, the tile order
-// and the resident blocks per SM are chosen at run time (mrs_autotune).
-//
-// Pair test.  A pair (own sphere c, radius r; other sphere p, radius r_p) can
-// change a ramp cost max(0, 1 - dist/B) only if |c - p| < r + r_p + B.  With
-//   g = |c - p|^2 - (r + B + r_p)^2
-//     = [|p|^2 - r_p^2] - 2 c.p - 2 (r + B) r_p + [|c|^2 - (r + B)^2]
-// the bracketed per-sphere terms are precomputed, so the inner loop is four
-// FMAs and a min per pair, without branches, issued as packed f32x2
-// instructions on two own spheres at a time.  An own sphere whose minimum g
-// falls below eps_g (the FP32 cancellation margin of this expansion over the
-// workspace) gets an exact pass: direct squared distance, and the square root
-// only for pairs inside the ramp.  Since the cost is zero outside the ramp,
-// the result equals the brute-force minimum of Eq. 6 restricted to the ramp.
-#include <algorithm>
-
-#include "kernels.cuh"
-
-// tuning knobs of the rollout kernel (set at build time)
-#ifndef MRS_ROLLOUT_MIN_BLOCKS
-#define MRS_ROLLOUT_MIN_BLOCKS 3
-#endif
-#ifndef MRS_PRETEST_UNROLL
-#define MRS_PRETEST_UNROLL 2
-#endif
+// rollout.cu -- host side of the rollout kernel (rollout_kernel.cuh):
+// shared-memory size, attributes, resident blocks, launch; instantiates the
+// three-blocks-per-SM variant.
+#include "rollout_kernel.cuh"
 
 namespace mrs {
-
-constexpr int kPretestUnroll = MRS_PRETEST_UNROLL;
-
-struct RolloutSmem {
-    float4 *other;     // world spheres at the step's time, then neighbours' plan spheres
-    float *other_w;    // |p|^2 - r_p^2 of each
-    ulonglong2 *pa;    // packed pairs for the f32x2 pre-test: (x, x), (y, y)
-    ulonglong2 *pb;    //                                      (z, z), (r, r)
-    unsigned long long *pc;   //                               (w, w)
-    float4 *aabb;      // [2 * n_aabb] centre, half extents
-    float4 *sph;       // [ns] local centre + radius
-    int *frame;        // [ns]
-    int *pairs;        // [n_self] s1 | s2 << 8
-    float *own;        // [ns][3][32] own sphere centres of the tile
-    int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
-    int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
-    float *nb_alpha;   // [n_nb]
-};
-
-__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-// packed binary32 pairs (Blackwell f32x2 FMA: two lanes, each rounded exactly
-// like the scalar instruction)
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pack2(float a, float b)
-{
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void unpack2(f32x2 v, float &a, float &b)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
-{
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// store one other sphere (and its |p|^2 - r^2) in every layout the passes read
-__device__ __forceinline__ void put_other(const RolloutSmem &S, int k, float4 w)
-{
-    const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
-                                -__fmul_rn(w.w, w.w))));
-    S.other[k] = w;
-    S.other_w[k] = pw;
-    S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
-    S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
-    S.pc[k] = pack2(pw, pw);
-}
-
-// exact distance of a candidate pair, as in the oracle: sqrt(d2) - r - r_p
-__device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p, float &m)
-{
-    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
-    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float t = __fadd_rn(rB, p.w);
-    if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
-}
-
-// Minimum signed distance, inside the ramp of buffer B, between the warp's
-// own spheres and other[k0, k1).  Returns +inf when no pair is in the ramp.
-// Own sphere centres arrive packed in pairs as -2c (NP = ceil(SPG / 2)); the
-// pre-test runs on both spheres of a pair with one f32x2 FMA chain.
-template <int NP>
-__device__ __forceinline__ float clearance_pass(const RolloutSmem &S, int k0, int k1, float B,
-                                                float eps_g, int s0, int cnt, int lane,
-                                                const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
-                                                const f32x2 (&MZ)[NP])
-{
-    f32x2 MR[NP];
-    float gmin[2 * NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const int a = 2 * q, b = 2 * q + 1;
-        const float ra = (a < cnt) ? -2.f * __fadd_rn(S.sph[s0 + a].w, B) : 0.f;
-        const float rb = (b < cnt) ? -2.f * __fadd_rn(S.sph[s0 + b].w, B) : 0.f;
-        MR[q] = pack2(ra, rb);
-        gmin[a] = gmin[b] = kInf;
-    }
-#pragma unroll kPretestUnroll
-    for (int k = k0; k < k1; ++k) {
-        const ulonglong2 A = S.pa[k], Bv = S.pb[k];
-        const f32x2 W = S.pc[k];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            float g0, g1;
-            unpack2(fma2(MX[q], A.x, fma2(MY[q], A.y, fma2(MZ[q], Bv.x, fma2(MR[q], Bv.y, W)))),
-                    g0, g1);
-            gmin[2 * q] = fminf(gmin[2 * q], g0);
-            gmin[2 * q + 1] = fminf(gmin[2 * q + 1], g1);
-        }
-    }
-    // own spheres whose pre-test minimum is within the margin of the ramp
-    unsigned flagged = 0u;
-#pragma unroll
-    for (int s = 0; s < 2 * NP; ++s) {
-        if (s < cnt) {
-            // g = gmin + |c|^2 - (r + B)^2 with c = -m/2
-            float x0, x1, y0, y1, z0, z1;
-            unpack2(MX[s / 2], x0, x1);
-            unpack2(MY[s / 2], y0, y1);
-            unpack2(MZ[s / 2], z0, z1);
-            const float cx = -0.5f * ((s & 1) ? x1 : x0), cy = -0.5f * ((s & 1) ? y1 : y0),
-                        cz = -0.5f * ((s & 1) ? z1 : z0);
-            const float rB = __fadd_rn(S.sph[s0 + s].w, B);
-            const float ac = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmaf_rn(cx, cx, -__fmul_rn(rB, rB))));
-            if (__fadd_rn(gmin[s], ac) < eps_g) flagged |= 1u << s;
-        }
-    }
-    // exact pass (rare): one loop for all flagged spheres, centres read back
-    // from the warp's shared-memory copy
-    float m = kInf;
-    unsigned any = __ballot_sync(0xffffffffu, flagged != 0u);
-    while (any) {
-        unsigned bits = flagged;
-        flagged = 0u;
-        if (bits) {
-            const int s = __ffs(bits) - 1;
-            flagged = bits & (bits - 1u);
-            const float3 c = make_float3(S.own[((s0 + s) * 3 + 0) * 32 + lane],
-                                         S.own[((s0 + s) * 3 + 1) * 32 + lane],
-                                         S.own[((s0 + s) * 3 + 2) * 32 + lane]);
-            const float r = S.sph[s0 + s].w;
-            const float rB = __fadd_rn(r, B);
-            for (int k = k0; k < k1; ++k) pair_exact(c, rB, r, S.other[k], m);
-        }
-        any = __ballot_sync(0xffffffffu, flagged != 0u);
-    }
-    return m;
-}
-
-// centre of own sphere s from the packed -2c registers
-template <int NP>
-__device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
-                                             const f32x2 (&MZ)[NP], int s)
-{
-    float x0, x1, y0, y1, z0, z1;
-    unpack2(MX[s / 2], x0, x1);
-    unpack2(MY[s / 2], y0, y1);
-    unpack2(MZ[s / 2], z0, z1);
-    return make_float3(-0.5f * ((s & 1) ? x1 : x0), -0.5f * ((s & 1) ? y1 : y0),
-                       -0.5f * ((s & 1) ? z1 : z0));
-}
-
-template <int SPG>
-__device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmDev &A,
-                                              const RolloutSmem &S, int h, int n, bool valid,
-                                              int g, int lane, int n_world, int n_aabb, int n_nb,
-                                              float *pose_out)
-{
-    const int d = A.dof, K = A.K;
-    const int s0 = g * SPG;
-    const int cnt = max(0, min(SPG, A.ns - s0));
-    const float *qh = D.traj + A.off_khd + (long long)h * d * K + (valid ? n : 0);
-
-    // DH chain up to the last frame this group needs; the last warp always
-    // runs to the end effector for the pose cost.  Own centres are kept as
-    // packed pairs of -2c (padding far away, never tested).
-    constexpr int NP = (SPG + 1) / 2;
-    f32x2 MX[NP], MY[NP], MZ[NP];
-    Frame F;
-    frame_base(A, F);
-    int f = 0;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        float cx[2], cy[2], cz[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int s = 2 * q + u;
-            if (s < cnt) {
-                const int fs = S.frame[s0 + s];
-                while (f < fs) {
-                    frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
-                    ++f;
-                }
-                const float3 c = sphere_centre(F, S.sph[s0 + s]);
-                cx[u] = -2.f * c.x; cy[u] = -2.f * c.y; cz[u] = -2.f * c.z;
-                S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
-                S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
-                S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
-            } else {
-                cx[u] = cy[u] = cz[u] = -2e15f;
-            }
-        }
-        MX[q] = pack2(cx[0], cx[1]);
-        MY[q] = pack2(cy[0], cy[1]);
-        MZ[q] = pack2(cz[0], cz[1]);
-    }
-    if (g == kGroups - 1) {
-        while (f < d) {
-            frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
-            ++f;
-        }
-        const float *in = D.input + A.off_in;
-        *pose_out = pose_cost(F, in + 2 * d, in + 2 * d + 3, P.w_rot);
-    }
-
-    if (cnt > 0) {
-        // world boxes (exact), then one pre-tested pass per sphere set: the
-        // world spheres (slot 0, buffer B_world) and each published neighbour
-        // plan at this step (slot 2 + nb, buffer B)
-        float mbox = kInf;
-        for (int b = 0; b < n_aabb; ++b) {
-            const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
-#pragma unroll
-            for (int s = 0; s < SPG; ++s)
-                if (s < cnt)
-                    mbox = fminf(mbox, sphere_aabb(own_centre<NP>(MX, MY, MZ, s), S.sph[s0 + s].w,
-                                                   bc, bh));
-        }
-        for (int ps = 0; ps <= n_nb; ++ps) {
-            const bool world = ps == 0;
-            const int k0 = world ? 0 : S.nb_start[ps - 1];
-            const int k1 = world ? n_world : S.nb_start[ps];
-            const float Bp = world ? P.B_world : P.B;
-            float m = clearance_pass<NP>(S, k0, k1, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ);
-            if (world) m = fminf(m, mbox);
-            if (m < Bp) atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
-        }
-    }
-    __syncthreads();   // every group's centres are in shared memory
-
-    // self collision: the arm's pair list, split evenly over the 8 warps.  With
-    // a learned surrogate, a rollout step whose predicted clearance is at least
-    // B_self + margin skips the exact pass (its self term is zero); the warp
-    // skips the loop when none of its 32 steps needs it.
-    {
-        bool need = true;
-        if (A.learned)
-            need = valid && D.dhat[A.off_kh + (long long)h * K + n] < P.B_self + A.self_margin;
-        const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
-        const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
-        float m = kInf;
-        for (int i = p0; i < p1; ++i) {
-            const int pr = S.pairs[i];
-            const int a1 = pr & 0xff, a2 = pr >> 8;
-            const float3 c = make_float3(S.own[(a1 * 3 + 0) * 32 + lane],
-                                         S.own[(a1 * 3 + 1) * 32 + lane],
-                                         S.own[(a1 * 3 + 2) * 32 + lane]);
-            const float4 q = make_float4(S.own[(a2 * 3 + 0) * 32 + lane],
-                                         S.own[(a2 * 3 + 1) * 32 + lane],
-                                         S.own[(a2 * 3 + 2) * 32 + lane], S.sph[a2].w);
-            const float r1 = S.sph[a1].w;
-            pair_exact(c, __fadd_rn(r1, P.B_self), r1, q, m);
-        }
-        if (need && m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
-    }
-}
-
-__global__ void __launch_bounds__(kRolloutThreads, MRS_ROLLOUT_MIN_BLOCKS) k_rollout(Params P, Dev D,
-                                                             const RolloutTile *tiles, int n_tiles,
-                                                             int iter)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int NA = P.n_arms;
-    RolloutSmem S;
-    {
-        unsigned char *p = smraw;
-        const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * NA;
-        S.other = (float4 *)p;     p += align16(sizeof(float4) * n_other);
-        S.aabb = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.aabb_cap);
-        S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
-        S.own = (float *)p;        p += align16(sizeof(float) * P.max_ns * 3 * 32);
-        S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
-        S.pa = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
-        S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
-        S.pc = (unsigned long long *)p; p += align16(sizeof(unsigned long long) * n_other);
-        S.frame = (int *)p;        p += align16(sizeof(int) * P.max_ns);
-        S.pairs = (int *)p;        p += align16(sizeof(int) * P.max_pairs);
-        S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
-        S.nb_alpha = (float *)p;   p += align16(sizeof(float) * MRS_MAX_ARMS);
-        S.red = (int *)p;
-    }
-    __shared__ int s_nb_arm[MRS_MAX_ARMS];
-    __shared__ int s_nnb, s_tile;
-    __shared__ float s_pose[32];
-    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_world = D.world_n[0], n_aabb = D.world_n[1];
-    const long long cycle = *D.cycle;
-
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&D.work[iter], 1);
-        __syncthreads();
-        const int ti = s_tile;
-        if (ti >= n_tiles) break;
-        const RolloutTile T = tiles[ti];
-        const ArmDev &A = D.arms[T.arm];
-        const int h = T.h;
-
-        // stage the tile's inputs: neighbour list (published plans whose
-        // horizon reaches step h), world at the step's time, arm constants
-        if (g == 0) {
-            // lane i decides whether arm i's published plan reaches step h
-            const int i = lane;
-            bool ok = false;
-            int ns_i = 0;
-            float al = 0.f;
-            if (i < NA && i != T.arm && h < D.arms[i].H &&   // min(H_j, H_i)
-                plan_usable(P, D.board_valid[i], D.board_stamp[i], cycle)) {
-                ok = true;
-                ns_i = D.arms[i].ns;
-                al = D.alpha[T.arm * NA + i];
-            }
-            const unsigned mask = __ballot_sync(0xffffffffu, ok);
-            int incl = ns_i;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int pos = __popc(mask & ((1u << lane) - 1u));
-            if (ok) {
-                s_nb_arm[pos] = i;
-                S.nb_start[pos] = n_world + incl - ns_i;
-                S.nb_alpha[pos] = al;
-            }
-            if (lane == 31) {
-                s_nnb = __popc(mask);
-                S.nb_start[__popc(mask)] = n_world + incl;
-            }
-            __syncwarp();
-            // the same warp stages the neighbours' plan spheres at step h
-            const int nnb = __popc(mask);
-            for (int nb = 0; nb < nnb; ++nb) {
-                const ArmDev &Ai = D.arms[s_nb_arm[nb]];
-                const float4 *src = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
-                const int o = S.nb_start[nb];
-                for (int k = lane; k < Ai.ns; k += 32) put_other(S, o + k, src[k]);
-            }
-            for (int k = lane; k < (2 + nnb) * 32; k += 32) S.red[k] = float_to_ordered(kInf);
-        }
-        const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
-        for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
-            const float4 o = D.world[k], v = D.world_vel[k];
-            put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
-                                        __fmaf_rn(v.z, t_h, o.z), o.w));
-        }
-        for (int k = threadIdx.x; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
-        for (int k = threadIdx.x; k < A.ns; k += blockDim.x) {
-            S.sph[k] = A.sph[k];
-            S.frame[k] = A.frame[k];
-        }
-        for (int k = threadIdx.x; k < A.n_self; k += blockDim.x)
-            S.pairs[k] = D.self_pairs[A.self_off + k];
-        __syncthreads();
-        const int n_nb = s_nnb;
-
-        for (int sb = 0; sb < T.nsub; ++sb) {
-            const int n = T.n0 + sb * 32 + lane;
-            const bool valid = n < A.K;
-            float pose = 0.f;
-            switch (A.spg) {
-                case 1: rollout_group<1>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 2: rollout_group<2>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 3: rollout_group<3>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 4: rollout_group<4>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 5: rollout_group<5>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 6: rollout_group<6>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 7: rollout_group<7>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                default: rollout_group<8>(P, D, A, S, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-            }
-            if (g == kGroups - 1) s_pose[lane] = pose;
-            __syncthreads();
-
-            // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
-            if (g == 0) {
-                if (valid) {
-                    const long long idx = A.off_kh + (long long)h * A.K + n;
-                    const float dw = ordered_to_float(S.red[0 * 32 + lane]);
-                    const float dsf = ordered_to_float(S.red[1 * 32 + lane]);
-                    float dyn = 0.f;
-                    for (int nb = 0; nb < n_nb; ++nb) {
-                        const float rho = fmaxf(ordered_to_float(S.red[(2 + nb) * 32 + lane]), 0.f);
-                        dyn = __fmaf_rn(S.nb_alpha[nb], ramp(rho, P.B), dyn);
-                    }
-                    float c = __fmul_rn(P.w_pose, s_pose[lane]);
-                    c = __fadd_rn(c, D.stage_lim[idx]);
-                    c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
-                    c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
-                    c = __fmaf_rn(P.w_dyn, dyn, c);
-                    D.stage[idx] = c;
-                }
-                // this lane's minima are read: reset them for the next sub-batch
-                for (int k = lane; k < (2 + n_nb) * 32; k += 32) S.red[k] = float_to_ordered(kInf);
-            }
-            __syncthreads();   // shared memory is reused by the next sub-batch or tile
-        }
-    }
-}
 
 size_t rollout_smem_bytes(const Params &P, int n_arms)
 {
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * n_arms;
     return a16(sizeof(float4) * n_other) + a16(sizeof(float4) * 2 * P.aabb_cap) +
-           a16(sizeof(float4) * P.max_ns) + a16(sizeof(float) * P.max_ns * 3 * 32) +
+           a16(sizeof(float4) * P.max_ns) + a16(sizeof(float) * 2 * P.max_ns * 3 * 32) +
            a16(sizeof(float) * n_other) + 2 * a16(sizeof(ulonglong2) * n_other) +
            a16(sizeof(unsigned long long) * n_other) + a16(sizeof(int) * P.max_ns) +
            a16(sizeof(int) * P.max_pairs) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +
-           a16(sizeof(float) * MRS_MAX_ARMS) + sizeof(int) * (2 + MRS_MAX_ARMS) * 32;
+           a16(sizeof(float) * 2 * MRS_MAX_ARMS) +
+           a16(sizeof(float) * kGroups * 8) +
+           a16(sizeof(unsigned short) * kGroups * ((n_other + 7) & ~size_t(7))) +
+           sizeof(int) * 2 * (2 + MRS_MAX_ARMS) * 32;
 }
 
 cudaError_t configure_rollout(const LaunchPlan &L)
 {
-    return cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)L.smem_rollout);
+    const cudaError_t e = rollout_configure_t<3>(L.smem_rollout);
+    return e != cudaSuccess ? e : rollout_configure_mb2(L.smem_rollout);
 }
 
-// Resident rollout blocks per SM from the kernel's own limits: shared memory
-// (with the 1 KB the driver reserves per block), registers (allocated per
-// warp in units of 256), threads.
+// Resident blocks per SM: the larger of the two variants' (the three-block
+// variant's, unless its shared memory does not fit)
 int rollout_blocks_per_sm(size_t smem)
 {
-    cudaFuncAttributes fa{};
-    if (cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_rollout, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_rollout) != cudaSuccess)
-        return 1;
-    const int warps = kRolloutThreads / 32;
-    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-    int nb = (int)((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024));
-    nb = std::min(nb, 65536 / std::max(1, regs_per_warp * warps));
-    nb = std::min(nb, 2048 / kRolloutThreads);
-    return nb > 0 ? nb : 1;
+    return std::max(rollout_occupancy_t<3>(smem), rollout_occupancy_mb2(smem));
 }
 
 cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                            cudaStream_t s)
 {
-    const int grid = L.n_rollout_tiles < L.rollout_grid ? L.n_rollout_tiles : L.rollout_grid;
-    k_rollout<<<grid, kRolloutThreads, L.smem_rollout, s>>>(P, D, L.rollout_tiles,
-                                                            L.n_rollout_tiles, iter);
-    return cudaGetLastError();
+    if (L.rollout_variant == 2) return rollout_launch_mb2(P, D, L, iter, s);
+    return rollout_launch_t<3>(P, D, L, iter, s);
 }
 
 }  // namespace mrs

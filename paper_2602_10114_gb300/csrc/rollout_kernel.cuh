@@ -1,0 +1,586 @@
+// rollout_kernel.cuh -- the Rollout step of Algorithm 1 for every arm: kinematics of
+// the collision spheres at each sampled state and the stage cost of Eq. 5
+// with the prioritised coordination term of Eq. 9 (Sec. IV-A/B).
+//
+// Work unit (tile): (arm, step h, 32 nsub samples).  A persistent grid of
+// 256-thread blocks takes tiles from an atomic counter and stages the tile's
+// inputs (world at the step's time, the neighbours' plan spheres at step h,
+// the arm's constants) once; the samples then pass through in sub-batches of
+// 32.  Warp g of a block owns sphere group g (spheres [g*spg, (g+1)*spg),
+// spg = ceil(N_S / 8)) of the sub-batch's 32 rollout steps, one sample per
+// lane; its centres stay in registers.  The samples per tile, the tile order
+// and the resident blocks per SM are chosen at run time (mrs_autotune).
+//
+// Pair test.  A pair (own sphere c, radius r; other sphere p, radius r_p) can
+// change a ramp cost max(0, 1 - dist/B) only if |c - p| < r + r_p + B.  With
+//   g = |c - p|^2 - (r + B + r_p)^2
+//     = [|p|^2 - r_p^2] - 2 c.p - 2 (r + B) r_p + [|c|^2 - (r + B)^2]
+// the bracketed per-sphere terms are precomputed, so the inner loop is four
+// FMAs and a min per pair, without branches, issued as packed f32x2
+// instructions on two own spheres at a time.  An own sphere whose minimum g
+// falls below eps_g (the FP32 cancellation margin of this expansion over the
+// workspace) gets an exact pass: direct squared distance, and the square root
+// only for pairs inside the ramp.  Since the cost is zero outside the ramp,
+// the result equals the brute-force minimum of Eq. 6 restricted to the ramp.
+#pragma once
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+// build-time knob of the pre-test loop
+#ifndef MRS_PRETEST_UNROLL
+#define MRS_PRETEST_UNROLL 1
+#endif
+
+namespace mrs {
+
+constexpr int kPretestUnroll = MRS_PRETEST_UNROLL;
+
+struct RolloutSmem {
+    float4 *other;     // world spheres at the step's time, then neighbours' plan spheres
+    float *other_w;    // |p|^2 - r_p^2 of each
+    ulonglong2 *pa;    // packed pairs for the f32x2 pre-test: (x, x), (y, y)
+    ulonglong2 *pb;    //                                      (z, z), (r, r)
+    unsigned long long *pc;   //                               (w, w)
+    float4 *aabb;      // [2 * n_aabb] centre, half extents
+    float4 *sph;       // [ns] local centre + radius
+    int *frame;        // [ns]
+    int *pairs;        // [n_self] s1 | s2 << 8
+    float *own;        // [ns][3][32] own sphere centres of the tile
+    int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
+    int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
+    float *nb_alpha;   // [n_nb]
+    unsigned short *cand;   // [kGroups][cand_cap] per-warp candidate lists
+    int cand_cap;
+    float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
+};
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// packed binary32 pairs (Blackwell f32x2 FMA: two lanes, each rounded exactly
+// like the scalar instruction)
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// minimum of three (sm_100+ three-input min; exact, like fminf twice)
+__device__ __forceinline__ float min3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// store one other sphere (and its |p|^2 - r^2) in every layout the passes read
+__device__ __forceinline__ void put_other(const RolloutSmem &S, int k, float4 w)
+{
+    const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
+                                -__fmul_rn(w.w, w.w))));
+    S.other[k] = w;
+    S.other_w[k] = pw;
+    S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
+    S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
+    S.pc[k] = pack2(pw, pw);
+}
+
+// exact distance of a candidate pair, as in the oracle: sqrt(d2) - r - r_p
+__device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p, float &m)
+{
+    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const float t = __fadd_rn(rB, p.w);
+    if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
+}
+
+// Candidates of one pass: the other spheres in [k0, k1) that come within
+// r_p + B + margin of the box bounding the warp's own spheres (each centre
+// +- its radius, over the 32 lanes).  A sphere outside is farther than
+// r + r_p + B + margin from every own sphere, so its pairs are outside the
+// ramp and, with margin >= eps_g / B, also fail the pre-test: dropping them
+// changes no result.  Warp-cooperative; returns the count (warp-uniform).
+__device__ __forceinline__ int cull(const RolloutSmem &S, int k0, int k1, float B, float margin,
+                                    const float *box, int lane, unsigned short *list)
+{
+    const float3 lo = make_float3(box[0], box[1], box[2]), hi = make_float3(box[3], box[4], box[5]);
+    int nc = 0;
+    for (int base = k0; base < k1; base += 32) {
+        const int k = base + lane;
+        bool keep = false;
+        if (k < k1) {
+            const float4 p = S.other[k];
+            const float dx = fmaxf(fmaxf(lo.x - p.x, p.x - hi.x), 0.f);
+            const float dy = fmaxf(fmaxf(lo.y - p.y, p.y - hi.y), 0.f);
+            const float dz = fmaxf(fmaxf(lo.z - p.z, p.z - hi.z), 0.f);
+            const float t = p.w + B + margin;
+            keep = dx * dx + dy * dy + dz * dz < t * t;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) list[nc + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
+        nc += __popc(m);
+    }
+    __syncwarp();
+    return nc;
+}
+
+// Minimum signed distance, inside the ramp of buffer B, between the warp's
+// own spheres and the candidates other[list[0 .. nc)).  Returns +inf when no
+// pair is in the ramp.
+// Own sphere centres arrive packed in pairs as -2c (NP = ceil(SPG / 2)); the
+// pre-test runs on both spheres of a pair with one f32x2 FMA chain.
+template <int NP>
+__device__ __forceinline__ float clearance_pass(const RolloutSmem &S, const unsigned short *list,
+                                                int nc, float B, float eps_g, int s0, int cnt,
+                                                int lane, const f32x2 (&MX)[NP],
+                                                const f32x2 (&MY)[NP], const f32x2 (&MZ)[NP])
+{
+    f32x2 MR[NP];
+    float gmin[2 * NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int a = 2 * q, b = 2 * q + 1;
+        const float ra = (a < cnt) ? -2.f * __fadd_rn(S.sph[s0 + a].w, B) : 0.f;
+        const float rb = (b < cnt) ? -2.f * __fadd_rn(S.sph[s0 + b].w, B) : 0.f;
+        MR[q] = pack2(ra, rb);
+        gmin[a] = gmin[b] = kInf;
+    }
+    // two candidates per step: their values meet the running minimum in one
+    // three-input min
+    int i = 0;
+#pragma unroll kPretestUnroll
+    for (; i + 1 < nc; i += 2) {
+        const int k = list[i], k1 = list[i + 1];
+        const ulonglong2 A0 = S.pa[k], B0 = S.pb[k], A1 = S.pa[k1], B1 = S.pb[k1];
+        const f32x2 W0 = S.pc[k], W1 = S.pc[k1];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float g0, g1, h0, h1;
+            unpack2(fma2(MX[q], A0.x, fma2(MY[q], A0.y, fma2(MZ[q], B0.x, fma2(MR[q], B0.y, W0)))),
+                    g0, g1);
+            unpack2(fma2(MX[q], A1.x, fma2(MY[q], A1.y, fma2(MZ[q], B1.x, fma2(MR[q], B1.y, W1)))),
+                    h0, h1);
+            gmin[2 * q] = min3(gmin[2 * q], g0, h0);
+            gmin[2 * q + 1] = min3(gmin[2 * q + 1], g1, h1);
+        }
+    }
+    if (i < nc) {
+        const int k = list[i];
+        const ulonglong2 A = S.pa[k], Bv = S.pb[k];
+        const f32x2 W = S.pc[k];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float g0, g1;
+            unpack2(fma2(MX[q], A.x, fma2(MY[q], A.y, fma2(MZ[q], Bv.x, fma2(MR[q], Bv.y, W)))),
+                    g0, g1);
+            gmin[2 * q] = fminf(gmin[2 * q], g0);
+            gmin[2 * q + 1] = fminf(gmin[2 * q + 1], g1);
+        }
+    }
+    // own spheres whose pre-test minimum is within the margin of the ramp
+    unsigned flagged = 0u;
+#pragma unroll
+    for (int s = 0; s < 2 * NP; ++s) {
+        if (s < cnt) {
+            // g = gmin + |c|^2 - (r + B)^2 with c = -m/2
+            float x0, x1, y0, y1, z0, z1;
+            unpack2(MX[s / 2], x0, x1);
+            unpack2(MY[s / 2], y0, y1);
+            unpack2(MZ[s / 2], z0, z1);
+            const float cx = -0.5f * ((s & 1) ? x1 : x0), cy = -0.5f * ((s & 1) ? y1 : y0),
+                        cz = -0.5f * ((s & 1) ? z1 : z0);
+            const float rB = __fadd_rn(S.sph[s0 + s].w, B);
+            const float ac = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmaf_rn(cx, cx, -__fmul_rn(rB, rB))));
+            if (__fadd_rn(gmin[s], ac) < eps_g) flagged |= 1u << s;
+        }
+    }
+    // exact pass (rare): one loop for all flagged spheres, centres read back
+    // from the warp's shared-memory copy
+    float m = kInf;
+    unsigned any = __ballot_sync(0xffffffffu, flagged != 0u);
+    while (any) {
+        unsigned bits = flagged;
+        flagged = 0u;
+        if (bits) {
+            const int s = __ffs(bits) - 1;
+            flagged = bits & (bits - 1u);
+            const float3 c = make_float3(S.own[((s0 + s) * 3 + 0) * 32 + lane],
+                                         S.own[((s0 + s) * 3 + 1) * 32 + lane],
+                                         S.own[((s0 + s) * 3 + 2) * 32 + lane]);
+            const float r = S.sph[s0 + s].w;
+            const float rB = __fadd_rn(r, B);
+            for (int j = 0; j < nc; ++j) pair_exact(c, rB, r, S.other[list[j]], m);
+        }
+        any = __ballot_sync(0xffffffffu, flagged != 0u);
+    }
+    return m;
+}
+
+// centre of own sphere s from the packed -2c registers
+template <int NP>
+__device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
+                                             const f32x2 (&MZ)[NP], int s)
+{
+    float x0, x1, y0, y1, z0, z1;
+    unpack2(MX[s / 2], x0, x1);
+    unpack2(MY[s / 2], y0, y1);
+    unpack2(MZ[s / 2], z0, z1);
+    return make_float3(-0.5f * ((s & 1) ? x1 : x0), -0.5f * ((s & 1) ? y1 : y0),
+                       -0.5f * ((s & 1) ? z1 : z0));
+}
+
+template <int SPG>
+__device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmDev &A,
+                                              const RolloutSmem &S, int h, int n, bool valid,
+                                              int g, int lane, int n_world, int n_aabb, int n_nb,
+                                              float *pose_out)
+{
+    const int d = A.dof, K = A.K;
+    const int s0 = g * SPG;
+    const int cnt = max(0, min(SPG, A.ns - s0));
+    const float *qh = D.traj + A.off_khd + (long long)h * d * K + (valid ? n : 0);
+
+    // DH chain up to the last frame this group needs; the last warp always
+    // runs to the end effector for the pose cost.  Own centres are kept as
+    // packed pairs of -2c (padding far away, never tested).
+    constexpr int NP = (SPG + 1) / 2;
+    f32x2 MX[NP], MY[NP], MZ[NP];
+    Frame F;
+    frame_base(A, F);
+    int f = 0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        float cx[2], cy[2], cz[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = 2 * q + u;
+            if (s < cnt) {
+                const int fs = S.frame[s0 + s];
+                while (f < fs) {
+                    frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+                    ++f;
+                }
+                const float3 c = sphere_centre(F, S.sph[s0 + s]);
+                cx[u] = -2.f * c.x; cy[u] = -2.f * c.y; cz[u] = -2.f * c.z;
+                S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
+                S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
+                S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
+            } else {
+                cx[u] = cy[u] = cz[u] = -2e15f;
+            }
+        }
+        MX[q] = pack2(cx[0], cx[1]);
+        MY[q] = pack2(cy[0], cy[1]);
+        MZ[q] = pack2(cz[0], cz[1]);
+    }
+    if (g == kGroups - 1) {
+        while (f < d) {
+            frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+            ++f;
+        }
+        const float *in = D.input + A.off_in;
+        *pose_out = pose_cost(F, in + 2 * d, in + 2 * d + 3, P.w_rot);
+    }
+
+    if (cnt > 0) {
+        // box bounding the warp's own spheres over its 32 samples
+        float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
+#pragma unroll
+        for (int s = 0; s < SPG; ++s)
+            if (s < cnt) {
+                const float3 c = own_centre<NP>(MX, MY, MZ, s);
+                const float r = S.sph[s0 + s].w;
+                lo.x = fminf(lo.x, c.x - r); lo.y = fminf(lo.y, c.y - r); lo.z = fminf(lo.z, c.z - r);
+                hi.x = fmaxf(hi.x, c.x + r); hi.y = fmaxf(hi.y, c.y + r); hi.z = fmaxf(hi.z, c.z + r);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+            lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+            lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+            hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+            hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+            hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+        }
+        unsigned short *list = S.cand + g * S.cand_cap;
+        float *box = S.box + g * 8;
+        if (lane == 0) {
+            box[0] = lo.x; box[1] = lo.y; box[2] = lo.z;
+            box[3] = hi.x; box[4] = hi.y; box[5] = hi.z;
+        }
+        __syncwarp();
+
+        // world boxes (exact), then one pre-tested pass per sphere set over its
+        // candidates: the world spheres (slot 0, buffer B_world) and each
+        // published neighbour plan at this step (slot 2 + nb, buffer B)
+        float mbox = kInf;
+        for (int b = 0; b < n_aabb; ++b) {
+            const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
+#pragma unroll
+            for (int s = 0; s < SPG; ++s)
+                if (s < cnt)
+                    mbox = fminf(mbox, sphere_aabb(own_centre<NP>(MX, MY, MZ, s), S.sph[s0 + s].w,
+                                                   bc, bh));
+        }
+        for (int ps = 0; ps <= n_nb; ++ps) {
+            const bool world = ps == 0;
+            const int k0 = world ? 0 : S.nb_start[ps - 1];
+            const int k1 = world ? n_world : S.nb_start[ps];
+            const float Bp = world ? P.B_world : P.B;
+            const int nc = cull(S, k0, k1, Bp, 1e-3f + P.eps_g / Bp, box, lane, list);
+            float m = clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ);
+            if (world) m = fminf(m, mbox);
+            if (m < Bp) atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
+        }
+    }
+    __syncthreads();   // every group's centres are in shared memory
+
+    // self collision: the arm's pair list, split evenly over the 8 warps.  With
+    // a learned surrogate, a rollout step whose predicted clearance is at least
+    // B_self + margin skips the exact pass (its self term is zero); the warp
+    // skips the loop when none of its 32 steps needs it.
+    {
+        bool need = true;
+        if (A.learned)
+            need = valid && D.dhat[A.off_kh + (long long)h * K + n] < P.B_self + A.self_margin;
+        const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
+        const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
+        float m = kInf;
+        for (int i = p0; i < p1; ++i) {
+            const int pr = S.pairs[i];
+            const int a1 = pr & 0xff, a2 = pr >> 8;
+            const float3 c = make_float3(S.own[(a1 * 3 + 0) * 32 + lane],
+                                         S.own[(a1 * 3 + 1) * 32 + lane],
+                                         S.own[(a1 * 3 + 2) * 32 + lane]);
+            const float4 q = make_float4(S.own[(a2 * 3 + 0) * 32 + lane],
+                                         S.own[(a2 * 3 + 1) * 32 + lane],
+                                         S.own[(a2 * 3 + 2) * 32 + lane], S.sph[a2].w);
+            const float r1 = S.sph[a1].w;
+            pair_exact(c, __fadd_rn(r1, P.B_self), r1, q, m);
+        }
+        if (need && m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
+    }
+}
+
+// Per-block shared state that changes with the sub-batch (own centres, the
+// per-lane minima, the end-effector pose cost) is double-buffered by
+// sub-batch parity, and the neighbour weights by work-unit parity, so that
+// warp 0's per-sample cost of one sub-batch overlaps the other warps' next
+// sub-batch (or the staging of the next unit) without a barrier between
+// them: three block barriers per sub-batch of 32 samples (inputs staged,
+// own centres written, minima complete).  The next work unit's index is
+// fetched one unit ahead.
+//
+// The kernel is built for two register budgets: MB resident blocks per SM
+// (MB = 3: 80 registers per thread; MB = 2: up to 128, no spills), compiled
+// in separate translation units; the launch shape picks one.
+template <int MB>
+__global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D,
+                                                                const RolloutTile *tiles,
+                                                                int n_tiles, int iter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int NA = P.n_arms;
+    RolloutSmem S;
+    const int own_stride = P.max_ns * 3 * 32;
+    constexpr int kRedStride = (2 + MRS_MAX_ARMS) * 32;
+    {
+        unsigned char *p = smraw;
+        const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * NA;
+        S.other = (float4 *)p;     p += align16(sizeof(float4) * n_other);
+        S.aabb = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.aabb_cap);
+        S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
+        S.own = (float *)p;        p += align16(sizeof(float) * 2 * own_stride);
+        S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
+        S.pa = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
+        S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
+        S.pc = (unsigned long long *)p; p += align16(sizeof(unsigned long long) * n_other);
+        S.frame = (int *)p;        p += align16(sizeof(int) * P.max_ns);
+        S.pairs = (int *)p;        p += align16(sizeof(int) * P.max_pairs);
+        S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
+        S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
+        S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
+        S.cand = (unsigned short *)p;
+        S.cand_cap = (int)((n_other + 7) & ~size_t(7));
+        p += align16(sizeof(unsigned short) * kGroups * S.cand_cap);
+        S.red = (int *)p;
+    }
+    __shared__ int s_tile[2];
+    __shared__ float s_pose[2][32];
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_world = D.world_n[0], n_aabb = D.world_n[1];
+    const long long cycle = *D.cycle;
+
+    // both minima buffers start at +inf; every sub-batch's cost stage resets
+    // the entries it used, so they are +inf again when reused
+    for (int k = threadIdx.x; k < 2 * kRedStride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
+    if (threadIdx.x == 0) s_tile[0] = atomicAdd(&D.work[iter], 1);
+    __syncthreads();
+
+    int buf = 0;   // sub-batch parity
+    for (int it = 0;; ++it) {
+        const int tp = it & 1;   // work-unit parity
+        const int ti = s_tile[tp];
+        if (ti >= n_tiles) break;
+        if (threadIdx.x == 0) s_tile[tp ^ 1] = atomicAdd(&D.work[iter], 1);
+        const RolloutTile T = tiles[ti];
+        const ArmDev &A = D.arms[T.arm];
+        const int h = T.h;
+
+        // neighbour list (published plans whose horizon reaches step h), in
+        // every warp: lane i decides for arm i
+        bool ok = false;
+        int ns_i = 0;
+        float al = 0.f;
+        {
+            const int i = lane;
+            if (i < NA && i != T.arm && h < D.arms[i].H &&   // min(H_j, H_i)
+                plan_usable(P, D.board_valid[i], D.board_stamp[i], cycle)) {
+                ok = true;
+                ns_i = D.arms[i].ns;
+                al = D.alpha[T.arm * NA + i];
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        const int nnb = __popc(mask);
+        int incl = ns_i;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (g == 0) {
+            const int pos = __popc(mask & ((1u << lane) - 1u));
+            if (ok) {
+                S.nb_start[pos] = n_world + incl - ns_i;
+                S.nb_alpha[tp * MRS_MAX_ARMS + pos] = al;
+            }
+            if (lane == 31) S.nb_start[nnb] = n_world + incl;
+        }
+        // warp w stages the plan spheres at step h of neighbours w, w + 8, ...
+        for (int nb = g; nb < nnb; nb += kGroups) {
+            const int src = __fns(mask, 0, nb + 1);          // lane (= arm) of neighbour nb
+            const int start = n_world + __shfl_sync(0xffffffffu, incl - ns_i, src);
+            const ArmDev &Ai = D.arms[src];
+            const float4 *sp = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
+            for (int k = lane; k < Ai.ns; k += 32) put_other(S, start + k, sp[k]);
+        }
+        const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
+        for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
+            const float4 o = D.world[k], v = D.world_vel[k];
+            put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
+                                        __fmaf_rn(v.z, t_h, o.z), o.w));
+        }
+        for (int k = threadIdx.x; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
+        for (int k = threadIdx.x; k < A.ns; k += blockDim.x) {
+            S.sph[k] = A.sph[k];
+            S.frame[k] = A.frame[k];
+        }
+        for (int k = threadIdx.x; k < A.n_self; k += blockDim.x)
+            S.pairs[k] = D.self_pairs[A.self_off + k];
+        __syncthreads();   // the unit's inputs are staged
+        const int n_nb = nnb;
+
+        for (int sb = 0; sb < T.nsub; ++sb, buf ^= 1) {
+            RolloutSmem Sb = S;
+            Sb.own = S.own + buf * own_stride;
+            Sb.red = S.red + buf * kRedStride;
+            const int n = T.n0 + sb * 32 + lane;
+            const bool valid = n < A.K;
+            float pose = 0.f;
+            switch (A.spg) {
+                case 1: rollout_group<1>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 2: rollout_group<2>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 3: rollout_group<3>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 4: rollout_group<4>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 5: rollout_group<5>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 6: rollout_group<6>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 7: rollout_group<7>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                default: rollout_group<8>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            }
+            if (g == kGroups - 1) s_pose[buf][lane] = pose;
+            __syncthreads();   // every warp's minima and the pose cost are in
+
+            // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
+            if (g == 0) {
+                if (valid) {
+                    const long long idx = A.off_kh + (long long)h * A.K + n;
+                    const float dw = ordered_to_float(Sb.red[0 * 32 + lane]);
+                    const float dsf = ordered_to_float(Sb.red[1 * 32 + lane]);
+                    float dyn = 0.f;
+                    for (int nb = 0; nb < n_nb; ++nb) {
+                        const float rho = fmaxf(ordered_to_float(Sb.red[(2 + nb) * 32 + lane]), 0.f);
+                        dyn = __fmaf_rn(S.nb_alpha[tp * MRS_MAX_ARMS + nb], ramp(rho, P.B), dyn);
+                    }
+                    float c = __fmul_rn(P.w_pose, s_pose[buf][lane]);
+                    c = __fadd_rn(c, D.stage_lim[idx]);
+                    c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
+                    c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
+                    c = __fmaf_rn(P.w_dyn, dyn, c);
+                    D.stage[idx] = c;
+                }
+                // this lane's minima are read: +inf again for their next use
+                for (int k = lane; k < (2 + n_nb) * 32; k += 32) Sb.red[k] = float_to_ordered(kInf);
+            }
+        }
+    }
+}
+
+// Resident blocks per SM of variant MB from the kernel's own limits: shared
+// memory (with the 1 KB the driver reserves per block), registers (allocated
+// per warp in units of 256), threads.
+template <int MB>
+int rollout_occupancy_t(size_t smem)
+{
+    cudaFuncAttributes fa{};
+    if (cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_rollout<MB>) != cudaSuccess)
+        return 1;
+    const int warps = kRolloutThreads / 32;
+    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int nb = (int)((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024));
+    nb = std::min(nb, 65536 / std::max(1, regs_per_warp * warps));
+    nb = std::min(nb, 2048 / kRolloutThreads);
+    return nb > 0 ? nb : 1;
+}
+
+template <int MB>
+cudaError_t rollout_configure_t(size_t smem)
+{
+    return cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+template <int MB>
+cudaError_t rollout_launch_t(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
+                             cudaStream_t s)
+{
+    const int grid = L.n_rollout_tiles < L.rollout_grid ? L.n_rollout_tiles : L.rollout_grid;
+    k_rollout<MB><<<grid, kRolloutThreads, L.smem_rollout, s>>>(P, D, L.rollout_tiles,
+                                                                L.n_rollout_tiles, iter);
+    return cudaGetLastError();
+}
+
+// the two-blocks-per-SM variant (rollout_mb2.cu)
+int rollout_occupancy_mb2(size_t smem);
+cudaError_t rollout_configure_mb2(size_t smem);
+cudaError_t rollout_launch_mb2(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
+                               cudaStream_t s);
+
+}  // namespace mrs
