@@ -10,7 +10,7 @@ size_t rollout_smem_bytes(const Params &P, int n_arms)
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * n_arms;
     return a16(sizeof(float4) * n_other) + a16(sizeof(float4) * 2 * P.aabb_cap) +
-           a16(sizeof(float4) * P.max_ns) + a16(sizeof(float) * 2 * P.max_ns * 3 * 32) +
+           a16(sizeof(float4) * P.max_ns) + a16(sizeof(float4) * 2 * P.max_ns * 32) +
            a16(sizeof(float) * n_other) + 2 * a16(sizeof(ulonglong2) * n_other) +
            a16(sizeof(unsigned long long) * n_other) + a16(sizeof(int) * P.max_ns) +
            a16(sizeof(int) * P.max_pairs) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +

@@ -47,7 +47,7 @@ struct RolloutSmem {
     float4 *sph;       // [ns] local centre + radius
     int *frame;        // [ns]
     int *pairs;        // [n_self] s1 | s2 << 8
-    float *own;        // [ns][3][32] own sphere centres of the tile
+    float4 *own;       // [ns][32] own sphere centre and radius of each sample
     int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
     int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
     float *nb_alpha;   // [n_nb]
@@ -217,9 +217,8 @@ __device__ __forceinline__ float clearance_pass(const RolloutSmem &S, const unsi
         if (bits) {
             const int s = __ffs(bits) - 1;
             flagged = bits & (bits - 1u);
-            const float3 c = make_float3(S.own[((s0 + s) * 3 + 0) * 32 + lane],
-                                         S.own[((s0 + s) * 3 + 1) * 32 + lane],
-                                         S.own[((s0 + s) * 3 + 2) * 32 + lane]);
+            const float4 o = S.own[(s0 + s) * 32 + lane];
+            const float3 c = make_float3(o.x, o.y, o.z);
             const float r = S.sph[s0 + s].w;
             const float rB = __fadd_rn(r, B);
             for (int j = 0; j < nc; ++j) pair_exact(c, rB, r, S.other[list[j]], m);
@@ -275,9 +274,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 }
                 const float3 c = sphere_centre(F, S.sph[s0 + s]);
                 cx[u] = -2.f * c.x; cy[u] = -2.f * c.y; cz[u] = -2.f * c.z;
-                S.own[((s0 + s) * 3 + 0) * 32 + lane] = c.x;
-                S.own[((s0 + s) * 3 + 1) * 32 + lane] = c.y;
-                S.own[((s0 + s) * 3 + 2) * 32 + lane] = c.z;
+                S.own[(s0 + s) * 32 + lane] = make_float4(c.x, c.y, c.z, S.sph[s0 + s].w);
             } else {
                 cx[u] = cy[u] = cz[u] = -2e15f;
             }
@@ -359,17 +356,11 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
         const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
         float m = kInf;
+#pragma unroll 4
         for (int i = p0; i < p1; ++i) {
             const int pr = S.pairs[i];
-            const int a1 = pr & 0xff, a2 = pr >> 8;
-            const float3 c = make_float3(S.own[(a1 * 3 + 0) * 32 + lane],
-                                         S.own[(a1 * 3 + 1) * 32 + lane],
-                                         S.own[(a1 * 3 + 2) * 32 + lane]);
-            const float4 q = make_float4(S.own[(a2 * 3 + 0) * 32 + lane],
-                                         S.own[(a2 * 3 + 1) * 32 + lane],
-                                         S.own[(a2 * 3 + 2) * 32 + lane], S.sph[a2].w);
-            const float r1 = S.sph[a1].w;
-            pair_exact(c, __fadd_rn(r1, P.B_self), r1, q, m);
+            const float4 c1 = S.own[(pr & 0xff) * 32 + lane], c2 = S.own[(pr >> 8) * 32 + lane];
+            pair_exact(make_float3(c1.x, c1.y, c1.z), __fadd_rn(c1.w, P.B_self), c1.w, c2, m);
         }
         if (need && m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
     }
@@ -395,7 +386,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NA = P.n_arms;
     RolloutSmem S;
-    const int own_stride = P.max_ns * 3 * 32;
+    const int own_stride = P.max_ns * 32;
     constexpr int kRedStride = (2 + MRS_MAX_ARMS) * 32;
     {
         unsigned char *p = smraw;
@@ -403,7 +394,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.other = (float4 *)p;     p += align16(sizeof(float4) * n_other);
         S.aabb = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.aabb_cap);
         S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
-        S.own = (float *)p;        p += align16(sizeof(float) * 2 * own_stride);
+        S.own = (float4 *)p;       p += align16(sizeof(float4) * 2 * own_stride);
         S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
         S.pa = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
         S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
