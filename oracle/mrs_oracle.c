@@ -818,6 +818,23 @@ double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const do
  * minus both radii (the quantity the self-collision term ramps, Eq. 5);
  * +infinity when the arm has no such pair.  The training label of the
  * learned surrogate. */
+void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *qa,
+                       const double *qb, double *out)
+{
+    double Sa[ORC_MAX_SPHERES * 4], Sb[ORC_MAX_SPHERES * 4];
+    for (int r = 0; r < n; ++r) {
+        orc_fk(a, qa + (size_t)r * a->dof, NULL, Sa);
+        orc_fk(b, qb + (size_t)r * b->dof, NULL, Sb);
+        double m = INFINITY;
+        for (int s1 = 0; s1 < a->n_spheres; ++s1)
+            for (int s2 = 0; s2 < b->n_spheres; ++s2) {
+                double d = orc_sphere_sphere(Sa + 4 * s1, Sb + 4 * s2);
+                if (d < m) m = d;
+            }
+        out[r] = m;
+    }
+}
+
 void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out)
 {
     double S[ORC_MAX_SPHERES * 4];

@@ -161,6 +161,14 @@ double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const do
 /* Exact self-collision clearance of joint vectors q [n][dof] (+inf if the
  * arm has no sphere pair on bodies at least three apart). */
 void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out);
+
+/* Arm-to-arm clearance (the set distance of Eq. 6 without the clamp at 0):
+ * for each of n rows, the minimum over all sphere pairs of arm a (at joints
+ * qa [n][a->dof]) and arm b (at qb [n][b->dof]) of centre distance minus
+ * radii, each arm at its own base pose.  The learned arm-pair surrogate's
+ * label; negative when the arms overlap. */
+void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *qa,
+                       const double *qb, double *out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

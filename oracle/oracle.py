@@ -118,6 +118,8 @@ def lib():
             L.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
                                             _dp, _dp, _dp]
             L.orc_self_distance.argtypes = [C.POINTER(OrcArm), C.c_int, _dp, _dp]
+            L.orc_pair_distance.argtypes = [C.POINTER(OrcArm), C.POINTER(OrcArm), C.c_int, _dp,
+                                            _dp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -336,6 +338,22 @@ class Oracle:
         q, pq = _d(np.asarray(q, np.float64).reshape(-1, self.sc.arms[arm].dof))
         out = np.zeros(len(q))
         lib().orc_self_distance(C.byref(self.arms[arm]), len(q), pq, _ptr(out))
+        return out
+
+    def pair_distance(self, a: int, b: int, qa, qb, base_b=None):
+        """Exact clearance between arm a at joints qa [n][d_a] and arm b at qb
+        [n][d_b], each at its base pose (arm b's replaced by `base_b`, xyz +
+        quaternion w x y z, when given)."""
+        qa, pqa = _d(np.asarray(qa, np.float64).reshape(-1, self.sc.arms[a].dof))
+        qb, pqb = _d(np.asarray(qb, np.float64).reshape(-1, self.sc.arms[b].dof))
+        assert len(qa) == len(qb)
+        arm_b = self.arms[b]
+        if base_b is not None:
+            arm_b = OrcArm.from_buffer_copy(self.arms[b])
+            for k in range(7):
+                arm_b.base_pose[k] = float(base_b[k])
+        out = np.zeros(len(qa))
+        lib().orc_pair_distance(C.byref(self.arms[a]), C.byref(arm_b), len(qa), pqa, pqb, _ptr(out))
         return out
 
     def goal_pose(self, arm: int, q):

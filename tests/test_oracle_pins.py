@@ -597,3 +597,66 @@ def test_self_distance_is_the_self_term_of_the_rollout(oracle_mod):
         assert math.isclose(d, brute, rel_tol=1e-12, abs_tol=1e-15)
         _, stage, _, _ = orc.rollout(0, [q], [np.zeros(7)], gp, gR, np.zeros((2, 7)))
         assert math.isclose(stage[0], max(0.0, 1 - d / B), rel_tol=1e-12, abs_tol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# arm-to-arm clearance (the label of the learned arm-pair surrogate)
+
+def _planar_tip_arm(a1, a2, r, base_xyz, yaw):
+    """Planar two-link arm (alpha = d = 0) with one sphere of radius r at the
+    frame-2 origin (the tip), base rotated by yaw about z."""
+    return S.Arm(dof=2, n_spheres=1, K=8, H=4,
+                 dh=np.array([[a1, 0, 0, 0], [a2, 0, 0, 0]], np.float32),
+                 q_lo=np.full(2, -2.8, np.float32), q_hi=np.full(2, 2.8, np.float32),
+                 qd_max=np.full(2, 2.0, np.float32), sphere_body=np.array([2], np.int32),
+                 sphere_xyzr=np.array([[0, 0, 0, r]], np.float32),
+                 base_pose=np.array([*base_xyz, math.cos(yaw / 2), 0, 0, math.sin(yaw / 2)],
+                                    np.float32))
+
+
+def test_pair_distance_planar_closed_form(oracle_mod):
+    """Two planar two-link arms facing each other: the clearance of their tip
+    spheres is |tip_a - tip_b| - r_a - r_b with tip = base + R_yaw (a1 c1 +
+    a2 c12, a1 s1 + a2 s12, 0)."""
+    from oracle.oracle import Oracle
+    A = _planar_tip_arm(0.5, 0.25, 0.05, (0.0, 0.0, 0.0), 0.0)
+    Bm = _planar_tip_arm(0.375, 0.5, 0.0625, (1.5, 0.25, 0.125), math.pi)
+    orc = Oracle(tiny_scenario([A, Bm]))
+    rng = np.random.default_rng(9)
+    qa, qb = rng.uniform(-2.8, 2.8, (50, 2)), rng.uniform(-2.8, 2.8, (50, 2))
+    got = orc.pair_distance(0, 1, qa, qb)
+
+    def tip(arm, q):
+        a1, a2 = float(arm.dh[0, 0]), float(arm.dh[1, 0])
+        w, z = float(arm.base_pose[3]), float(arm.base_pose[6])
+        yaw = 2 * math.atan2(z, w)
+        x = a1 * math.cos(q[0]) + a2 * math.cos(q[0] + q[1])
+        y = a1 * math.sin(q[0]) + a2 * math.sin(q[0] + q[1])
+        c, s = math.cos(yaw), math.sin(yaw)
+        b = arm.base_pose.astype(np.float64)
+        return np.array([b[0] + c * x - s * y, b[1] + s * x + c * y, b[2]])
+    for k in range(50):
+        ref = (np.linalg.norm(tip(A, qa[k]) - tip(Bm, qb[k])) - float(np.float32(0.05)) - 0.0625)
+        assert math.isclose(got[k], ref, rel_tol=1e-12, abs_tol=1e-13)
+
+
+def test_pair_distance_symmetry_and_base_override(oracle_mod):
+    """Swapping the two arms leaves the clearance unchanged; moving arm b's
+    base far away along x raises it by the distance moved once the arms
+    cannot reach each other; overriding b's base with its own pose is a
+    no-op."""
+    from oracle.oracle import Oracle
+    a, b = _random_arm(41), _random_arm(42)
+    b.base_pose = np.array([1.0, 0.2, 0.0, 0, 0, 0, 1], np.float32)
+    orc = Oracle(tiny_scenario([a, b]))
+    rng = np.random.default_rng(4)
+    qa, qb = rng.uniform(-2.8, 2.8, (20, 7)), rng.uniform(-2.8, 2.8, (20, 7))
+    d_ab = orc.pair_distance(0, 1, qa, qb)
+    d_ba = orc.pair_distance(1, 0, qb, qa)
+    assert np.allclose(d_ab, d_ba, rtol=0, atol=1e-13)
+    assert np.array_equal(orc.pair_distance(0, 1, qa, qb, base_b=b.base_pose), d_ab)
+    far1 = orc.pair_distance(0, 1, qa, qb, base_b=[20.0, 0.2, 0.0, 0, 0, 0, 1])
+    far2 = orc.pair_distance(0, 1, qa, qb, base_b=[23.0, 0.2, 0.0, 0, 0, 0, 1])
+    assert np.all(far1 > 10)
+    assert np.allclose(far2 - far1, 3.0, atol=1e-2)   # nearly parallel to x at this range
+    assert np.all(far2 - far1 <= 3.0 + 1e-12)          # triangle inequality
