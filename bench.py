@@ -418,6 +418,78 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     }
 
 
+def learned_pair_mode(args, flush, ws, dev):
+    """Workload 5 with both learned clearances: the self-collision network and
+    the arm-pair network (asymmetric loss, fallback margin calibrated on
+    held-out pairs to a 1e-3 false-negative rate), trained on the device;
+    throughput against exact mode, false negatives on held-out samples and on
+    every rollout step of a cycle, skip fractions, cost deviation."""
+    import torch
+    from paper_2602_10114_gb300 import mrs, surrogate
+    sc = workload(5)
+    ctl = mrs.Controller(sc, device=dev)
+    ctl.set_world()
+    gp, gR = [], []
+    for a in range(sc.n_arms):
+        p, R = ctl.goal_pose(a, sc.goal_q[a])
+        gp.append(p)
+        gR.append(R)
+    d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
+    ctl.step_device(d_in)
+    ctl.sync()
+    best, _ = ctl.autotune(reps=3)
+    steps = max(5, args.steps // 5)
+    ex_ms, _, _ = time_device(ctl, d_in, steps, 3, flush, ws)
+    t0 = time.perf_counter()
+    snet, sst = surrogate.train_self_surrogate(ctl, 0, n_train=args.surrogate_samples, n_val=200_000,
+                                               epochs=8, lr=2e-3)
+    pnet, pst = surrogate.train_pair_surrogate(ctl, 0, n_train=args.pair_samples, n_val=400_000,
+                                               epochs=12, lr=1e-3, over_weight=32.0,
+                                               target_fn=1e-3)
+    train_s = time.perf_counter() - t0
+    blob = ctl.save_state()
+    ctl.step_device(d_in)
+    ctl.sync()
+    c_exact = np.concatenate([ctl.debug_costs(a) for a in range(sc.n_arms)])
+    for a in range(sc.n_arms):
+        ctl.set_self_surrogate(a, snet, 0.03)
+        ctl.set_pair_surrogate(a, -1, pnet, pst["margin"])
+    ctl.load_state(blob)
+    ctl.step_device(d_in)
+    ctl.sync()
+    c_learned = np.concatenate([ctl.debug_costs(a) for a in range(sc.n_arms)])
+    B = float(np.float32(sc.params["B"]))
+    pr = [ctl.debug_pair(0, b) for b in range(1, sc.n_arms)]
+    ev_pair = surrogate.evaluate(np.concatenate([r[0].ravel() for r in pr]),
+                                 np.concatenate([r[1].ravel() for r in pr]), B, pst["margin"])
+    sr = [ctl.debug_self(a) for a in range(sc.n_arms)]
+    ev_self = surrogate.evaluate(np.concatenate([r[0].ravel() for r in sr]),
+                                 np.concatenate([r[1].ravel() for r in sr]),
+                                 float(np.float32(sc.params["B_self"])), 0.03)
+    ln_ms, kt, _ = time_device(ctl, d_in, steps, 3, flush, ws)
+    ctl.close()
+    ex = max_over_ranks(float(np.mean(ex_ms)), ws)
+    ln = max_over_ranks(float(np.mean(ln_ms)), ws)
+    units = sc.rollout_steps() * sc.params["iterations"]
+    dev_ = np.abs(c_learned - c_exact)
+    keep = ("fn_rate", "fn_rate_active", "skip_fraction", "mae", "colliding", "samples")
+    return {"workload": sc.name + ", learned self + arm-pair clearance",
+            "value": units * ws / (ln / 1e3), "unit": UNIT, "ms_per_step": ln,
+            "exact_ms_per_step": ex, "speedup_vs_exact": ex / ln, "steps": steps,
+            "surrogate_ms": float(kt[:, 2].mean()), "rollout_ms": float(kt[:, 3].mean()),
+            "pair_margin": pst["margin"],
+            "held_out": {"self": {k: sst[k] for k in keep}, "pair": {k: pst[k] for k in keep}},
+            "rollout_steps": {"self": {k: ev_self[k] for k in keep},
+                              "pair": {k: ev_pair[k] for k in keep}},
+            "cost_deviation": {"mean_rel": float(dev_.mean() / np.abs(c_exact).mean()),
+                               "max_abs": float(dev_.max())},
+            "train": {"self_samples": args.surrogate_samples, "pair_samples": args.pair_samples,
+                      "seconds": train_s,
+                      "architecture": "self 14 -> 3 x 256 SiLU -> 1; pair 35 -> 4 x 256 SiLU "
+                                      "-> 1, BF16"},
+            "rollout_shape": best}
+
+
 def other_workload(idx, args, flush, ws, dev):
     """Device-timed cycles of another workload (exact costs, autotuned shape):
     throughput, cycle time, rollout time and its FP32 roofline fraction."""
@@ -511,6 +583,9 @@ def run(args):
     others = {}
     for idx in args.other_workloads:
         others[f"cfg{idx}"] = other_workload(idx, args, flush, ws, dev)
+    learned_pair = None
+    if not args.no_learned and not args.no_learned_pair:
+        learned_pair = learned_pair_mode(args, flush, ws, dev)
     clk.__exit__()
     if rank != 0:
         return
@@ -542,6 +617,7 @@ def run(args):
         "e2e": e2e,
         "plain": plain,
         "learned": learned,
+        "learned_pair": learned_pair,
         "other_workloads": others,
         "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),
         "clocks": clk.summary(),
@@ -561,6 +637,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-surrogate comparison")
     ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
+    ap.add_argument("--pair-samples", type=int, default=5_000_000)
+    ap.add_argument("--no-learned-pair", action="store_true",
+                    help="skip the eight-arm learned self + arm-pair leg")
     ap.add_argument("--other-workloads", type=int, nargs="*", default=[4, 5],
                     help="also time these workloads (device-resident, exact, autotuned)")
     ap.add_argument("--no-autotune", action="store_true",

@@ -180,7 +180,8 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
 /* Publish (Alg. 1, Publish; Sec. IV-A plan communication): overwrite arm
  * `arm`'s entry of the plan board that the next mrs_step reads, with an
  * anticipated plan received from elsewhere.  plan_spheres [H_arm][NS][4]
- * time-major, plan_q [H_arm][dof] (may be NULL), dist_to_goal >= 0 its
+ * time-major, plan_q [H_arm][dof] (may be NULL: then the entry carries no
+ * joints and an arm-pair surrogate takes the exact pass for it), dist_to_goal >= 0 its
  * published distance-to-goal, `cycle` its publication stamp.  A negative
  * dist_to_goal withdraws the entry (the arm is then ignored, Sec. IV-C). */
 mrs_status mrs_share_plans(mrs_ctx *ctx, int arm, const float *plan_spheres, const float *plan_q,
@@ -330,6 +331,11 @@ mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long 
 void mrs_mlp_destroy(mrs_mlp *m);
 const char *mrs_mlp_last_error(const mrs_mlp *m);
 mrs_status mrs_mlp_param_count(const mrs_mlp *m, size_t *n);
+/* Training loss: squared error against targets clipped to [-0.1, 0.3] m, an
+ * over-prediction (output above the clipped target: a clearance claimed
+ * larger than it is, the error that can skip a colliding step) weighted by
+ * over_weight >= 1 (1, the default: plain MSE). */
+mrs_status mrs_mlp_set_loss(mrs_mlp *m, float over_weight);
 /* Launch shape of the fused inference kernel (features, every layer and the
  * output of 128 rows per CTA; weights streamed through a ring of shared
  * memory slots): info[0] resident CTAs per SM for plain rows
@@ -367,6 +373,41 @@ mrs_status mrs_self_distance(mrs_ctx *ctx, int arm, int n, const float *d_q, flo
 /* Of the last cycle, every rollout step [H][K] of an arm: the surrogate's
  * predicted clearance and (recomputed) the exact one; either may be NULL. */
 mrs_status mrs_debug_self(mrs_ctx *ctx, int arm, float *dhat, float *exact);
+
+/* Learned arm-to-arm clearance (not in the paper): a network (mrs_mlp with
+ * input 2 d_a + 2 d_b + 7: sin, cos of arm a's joints at the sampled step,
+ * sin, cos of arm b's published plan joints at the same step, arm b's base
+ * pose in arm a's base frame as xyz + quaternion w x y z) that predicts the
+ * clearance between arm a's spheres and arm b's plan spheres (the set
+ * distance of Eq. 6, unclamped).  With a network set for (a, b) (b = -1:
+ * every other arm), every rollout step of arm a is predicted before the
+ * rollout, and a step whose prediction is at least B + margin skips the exact
+ * pass against b's plan (its coordination term with b is zero); the others,
+ * and plans published without joints, take the exact pass.  net = NULL
+ * removes it.  The first call allocates the prediction buffer (sum_a K_a H_a
+ * x n_arms floats, owned by the context).  The network must outlive its use
+ * by the context. */
+mrs_status mrs_set_pair_surrogate(mrs_ctx *ctx, int a, int b, mrs_mlp *net, float margin);
+/* Arm b's base pose in arm a's base frame, pose[7] = xyz, quaternion w x y z
+ * (host): the pose inputs of the arm-pair network. */
+mrs_status mrs_relative_pose(mrs_ctx *ctx, int a, int b, float *pose);
+/* Arm-pair training data, on the device: n rows of joint vectors of arms a
+ * and b uniform within their limits (Philox, `seed`) and a relative pose, one
+ * of poses [n_pose][7] (host; NULL: b's actual pose in a's frame) drawn
+ * uniformly and jittered by +-jit_t per axis and +-jit_yaw (radians) about
+ * its z axis; features d_x [n][2 d_a + 2 d_b + 7], exact clearance d_t [n]
+ * (arm a at its base frame, arm b at the pose: minimum over all sphere pairs
+ * of centre distance minus radii); d_qa [n][d_a], d_qb [n][d_b] and d_pose
+ * [n][7] receive the joints and poses (each may be NULL). */
+mrs_status mrs_pair_dataset(mrs_ctx *ctx, int a, int b, int n, unsigned long long seed,
+                            const float *poses, int n_pose, float jit_t, float jit_yaw, float *d_x,
+                            float *d_t, float *d_qa, float *d_qb, float *d_pose);
+/* Of the last cycle, every rollout step [H_a][K_a] of arm a: the arm-pair
+ * surrogate's predicted clearance to arm b's plan and (recomputed) the exact
+ * one against b's plan spheres at step min(h, H_b - 1) as that cycle read
+ * them (with an arm-pair surrogate set, the cycle keeps a copy: the board
+ * holds the new plans after it); either may be NULL (host). */
+mrs_status mrs_debug_pair(mrs_ctx *ctx, int a, int b, float *rhohat, float *exact);
 
 /* Tensor-core GEMM self-test: C [M][N] (FP32) = A [M][K] B [N][K]^T with A, B
  * BF16 bit patterns (host arrays); N multiple of 16 up to 256, K multiple of 8. */

@@ -749,6 +749,13 @@ static double dsilu(double z)
 double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const double *params, int n,
                          const double *x, const double *t, double *grad, double *y_out)
 {
+    return orc_mlp_loss_grad_w(in_dim, in_pad, width, layers, params, n, x, t, 1.0, grad, y_out);
+}
+
+double orc_mlp_loss_grad_w(int in_dim, int in_pad, int width, int layers, const double *params,
+                           int n, const double *x, const double *t, double over_weight,
+                           double *grad, double *y_out)
+{
     const int L = layers;
     double *h = (double *)malloc(sizeof(double) * (size_t)(L + 1) * (in_pad > width ? in_pad : width));
     double *z = (double *)malloc(sizeof(double) * (size_t)L * width);
@@ -782,10 +789,11 @@ double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const do
         if (y_out) y_out[r] = y;
         double tc = t[r] < -0.1 ? -0.1 : (t[r] > 0.3 ? 0.3 : t[r]);
         double e = y - tc;
-        loss += e * e / n;
+        const double we = e > 0 ? over_weight : 1.0;
+        loss += we * e * e / n;
         if (!grad) continue;
         /* backward */
-        double dy = 2.0 * e / n;
+        double dy = 2.0 * we * e / n;
         for (int j = 0; j < width; ++j) {
             grad[o + j] += dy * h[L * stride + j];
             dh[j] = dy * wo[j];

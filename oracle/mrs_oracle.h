@@ -158,6 +158,12 @@ int orc_sample_costs(const orc_config *cfg, const orc_state *st, const orc_input
  * y_out (may be NULL) receives the outputs. */
 double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const double *params, int n,
                          const double *x, const double *t, double *grad, double *y_out);
+/* The same with an asymmetric squared error: an over-prediction (output above
+ * the clipped target: a clearance claimed larger than it is) weighs
+ * over_weight, an under-prediction 1; over_weight = 1 is the plain MSE. */
+double orc_mlp_loss_grad_w(int in_dim, int in_pad, int width, int layers, const double *params,
+                           int n, const double *x, const double *t, double over_weight,
+                           double *grad, double *y_out);
 /* Exact self-collision clearance of joint vectors q [n][dof] (+inf if the
  * arm has no sphere pair on bodies at least three apart). */
 void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out);

@@ -115,6 +115,9 @@ def lib():
             L.orc_sample_costs.argtypes = [C.POINTER(OrcConfig), C.POINTER(OrcState),
                                            C.POINTER(OrcInputs), C.c_int, C.c_int, _ip, _dp, _dp]
             L.orc_mlp_loss_grad.restype = C.c_double
+            L.orc_mlp_loss_grad_w.restype = C.c_double
+            L.orc_mlp_loss_grad_w.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
+                                              _dp, C.c_double, _dp, _dp]
             L.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
                                             _dp, _dp, _dp]
             L.orc_self_distance.argtypes = [C.POINTER(OrcArm), C.c_int, _dp, _dp]
@@ -212,16 +215,17 @@ def weights(Cn, lam):
     return w
 
 
-def mlp_loss_grad(in_dim, width, layers, params, x, t, want_grad=True):
-    """FP64 loss, gradient and outputs of the surrogate MLP."""
+def mlp_loss_grad(in_dim, width, layers, params, x, t, want_grad=True, over_weight=1.0):
+    """FP64 loss, gradient and outputs of the surrogate MLP (over-predictions
+    weighted by over_weight)."""
     in_pad = (in_dim + 15) // 16 * 16
     p, pp = _d(params)
     x, px = _d(x)
     t, pt = _d(t)
     g = np.zeros(len(p)) if want_grad else None
     y = np.zeros(len(t))
-    loss = lib().orc_mlp_loss_grad(in_dim, in_pad, width, layers, pp, len(t), px, pt,
-                                   _ptr(g), _ptr(y))
+    loss = lib().orc_mlp_loss_grad_w(in_dim, in_pad, width, layers, pp, len(t), px, pt,
+                                     float(over_weight), _ptr(g), _ptr(y))
     return loss, g, y
 
 
@@ -340,20 +344,23 @@ class Oracle:
         lib().orc_self_distance(C.byref(self.arms[arm]), len(q), pq, _ptr(out))
         return out
 
-    def pair_distance(self, a: int, b: int, qa, qb, base_b=None):
+    def pair_distance(self, a: int, b: int, qa, qb, base_b=None, base_a=None):
         """Exact clearance between arm a at joints qa [n][d_a] and arm b at qb
-        [n][d_b], each at its base pose (arm b's replaced by `base_b`, xyz +
+        [n][d_b], each at its base pose (replaced by `base_a` / `base_b`, xyz +
         quaternion w x y z, when given)."""
         qa, pqa = _d(np.asarray(qa, np.float64).reshape(-1, self.sc.arms[a].dof))
         qb, pqb = _d(np.asarray(qb, np.float64).reshape(-1, self.sc.arms[b].dof))
         assert len(qa) == len(qb)
-        arm_b = self.arms[b]
-        if base_b is not None:
-            arm_b = OrcArm.from_buffer_copy(self.arms[b])
-            for k in range(7):
-                arm_b.base_pose[k] = float(base_b[k])
+        def with_base(i, base):
+            arm = self.arms[i]
+            if base is not None:
+                arm = OrcArm.from_buffer_copy(self.arms[i])
+                for k in range(7):
+                    arm.base_pose[k] = float(base[k])
+            return arm
+        arm_a, arm_b = with_base(a, base_a), with_base(b, base_b)
         out = np.zeros(len(qa))
-        lib().orc_pair_distance(C.byref(self.arms[a]), C.byref(arm_b), len(qa), pqa, pqb, _ptr(out))
+        lib().orc_pair_distance(C.byref(arm_a), C.byref(arm_b), len(qa), pqa, pqb, _ptr(out))
         return out
 
     def goal_pose(self, arm: int, q):

@@ -31,18 +31,7 @@ __global__ void k_init_arms(ArmDev *arms)
     ArmDev &A = arms[blockIdx.x];
     const int t = threadIdx.x;
     if (t == 0) {
-        float w = A.base_pose[3], x = A.base_pose[4], y = A.base_pose[5], z = A.base_pose[6];
-        const float n = sqrtf(w * w + x * x + y * y + z * z);
-        w /= n; x /= n; y /= n; z /= n;
-        A.base_R[0] = 1.f - 2.f * (y * y + z * z);
-        A.base_R[1] = 2.f * (x * y - w * z);
-        A.base_R[2] = 2.f * (x * z + w * y);
-        A.base_R[3] = 2.f * (x * y + w * z);
-        A.base_R[4] = 1.f - 2.f * (x * x + z * z);
-        A.base_R[5] = 2.f * (y * z - w * x);
-        A.base_R[6] = 2.f * (x * z - w * y);
-        A.base_R[7] = 2.f * (y * z + w * x);
-        A.base_R[8] = 1.f - 2.f * (x * x + y * y);
+        quat_to_R(A.base_pose[3], A.base_pose[4], A.base_pose[5], A.base_pose[6], A.base_R);
         A.base_t[0] = A.base_pose[0];
         A.base_t[1] = A.base_pose[1];
         A.base_t[2] = A.base_pose[2];
@@ -633,6 +622,12 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
         mark();
         for (int i = 0; i < L.n_groups; ++i)   // learned self clearance of every step
             if ((rec = enqueue_self_surrogate(D, L.groups[i], s)) != cudaSuccess) return rec;
+        if (L.n_pair_groups > 0 && it == 0 && D.pair_board &&
+            (rec = cudaMemcpyAsync(D.pair_board, D.board_sph, L.board_bytes,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return rec;
+        for (int i = 0; i < L.n_pair_groups; ++i)   // learned clearance to the neighbours' plans
+            if ((rec = enqueue_pair_surrogate(D, L.pair_groups[i], s)) != cudaSuccess) return rec;
         mark();
         if ((rec = launch_rollout(P, D, L, it, s)) != cudaSuccess) return rec;
         mark();

@@ -28,6 +28,12 @@ struct SurrogateGroup {
     fused::TrajSegs segs;
 };
 
+// (arm, neighbour) pairs that share one arm-pair network: one launch
+struct PairGroup {
+    mrs_mlp *net;
+    fused::PairSegs segs;
+};
+
 struct LaunchPlan {
     int n_arms;
     int n_sample_tiles, n_rollout_tiles, n_cost_tiles, n_update_tiles;
@@ -43,6 +49,9 @@ struct LaunchPlan {
     SurrogateSlot surrogates[MRS_MAX_ARMS];
     int n_groups;
     SurrogateGroup groups[MRS_MAX_ARMS];
+    int n_pair_groups;
+    PairGroup *pair_groups;   // host array owned by the context
+    size_t board_bytes;       // plan spheres of the board (copied for evaluation)
 };
 
 // surrogate network (mlp.cu): input width, and the fused forward pass over
@@ -51,6 +60,8 @@ struct LaunchPlan {
 int mlp_in_dim(const mrs_mlp *m);
 cudaError_t mlp_infer_trajs(mrs_mlp *m, const float *traj, const fused::TrajSegs &segs,
                             float *dhat, int *err, cudaStream_t s);
+cudaError_t mlp_infer_pairs(mrs_mlp *m, const float *traj, const float *plan,
+                            const fused::PairSegs &segs, float *rhohat, int *err, cudaStream_t s);
 // surrogate.cu
 cudaError_t enqueue_self_dataset(const Dev &D, int arm, int n, unsigned long long seed, float *x,
                                  float *t, float *q, cudaStream_t s);
@@ -58,6 +69,20 @@ cudaError_t enqueue_self_clearance_rows(const Dev &D, int arm, int n, const floa
                                         cudaStream_t s);
 cudaError_t enqueue_self_clearance_traj(const Dev &D, int arm, int rows, float *out, cudaStream_t s);
 cudaError_t enqueue_self_surrogate(const Dev &D, const SurrogateGroup &g, cudaStream_t s);
+cudaError_t enqueue_pair_surrogate(const Dev &D, const PairGroup &g, cudaStream_t s);
+// arm-pair training data: rows of (q_a, q_b, pose) with q uniform within the
+// limits and the pose one of poses[n_pose][7] (arm b's base in arm a's frame)
+// jittered by +-jit_t per axis and +-jit_yaw about z; features x [n][2 d_a +
+// 2 d_b + 7], exact clearance t [n], joints qa [n][d_a], qb [n][d_b] and the
+// jittered poses [n][7] (the last three may be null)
+cudaError_t enqueue_pair_dataset(const Dev &D, int a, int b, int n, unsigned long long seed,
+                                 const float *poses, int n_pose, float jit_t, float jit_yaw,
+                                 float *x, float *t, float *qa, float *qb, float *pose_out,
+                                 cudaStream_t s);
+// exact clearance of every rollout step of arm a to arm b's published plan at
+// the same step: out [H_a][K_a]
+cudaError_t enqueue_pair_clearance_traj(const Dev &D, int a, int b, int rows, float *out,
+                                        cudaStream_t s);
 
 // The rollout kernel (rollout.cu): shared-memory size for the given
 // capacities, attribute set-up and launch.

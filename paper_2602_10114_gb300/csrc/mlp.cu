@@ -116,18 +116,20 @@ __global__ void k_out_layer(const bf16 *H, int width, const float *w, const floa
     if (lane == 0) y[r] = s + b[0];
 }
 
-// MSE loss on clipped targets: dy = 2 (y - t) / n, loss += (y - t)^2 / n
-__global__ void k_loss(const float *y, const float *t, int n, float lo, float hi, float *dy,
-                       float *loss)
+// squared error on clipped targets, an over-prediction (y above the target)
+// weighted by over_w: dy = 2 w (y - t) / n, loss += w (y - t)^2 / n
+__global__ void k_loss(const float *y, const float *t, int n, float lo, float hi, float over_w,
+                       float *dy, float *loss)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    float e = 0.f;
+    float e = 0.f, w = 1.f;
     if (r < n) {
         const float tc = fminf(fmaxf(t[r], lo), hi);
         e = y[r] - tc;
-        dy[r] = 2.f * e / (float)n;
+        w = e > 0.f ? over_w : 1.f;
+        dy[r] = 2.f * w * e / (float)n;
     }
-    float s = e * e / (float)n;
+    float s = w * e * e / (float)n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
@@ -246,6 +248,7 @@ struct mrs_mlp {
     size_t offWo = 0, offBo = 0, n_params = 0;
     float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
     long long step = 0;
+    float over_weight = 1.f;   // loss weight of over-predictions
     std::vector<bf16 *> Wb, WbT;
     // training buffers (capacity `cap` rows)
     int cap = 0;
@@ -257,7 +260,7 @@ struct mrs_mlp {
     // fused inference: packed BF16 weight chunks and the kernel's set-up
     unsigned char *wpack = nullptr;
     fused::Net fnet{};
-    int per_sm_rows = 0, per_sm_traj = 0, num_sms = 0;
+    int per_sm_rows = 0, per_sm_traj = 0, per_sm_pair = 0, num_sms = 0;
     size_t fnet_smem = 0;
     int *err = nullptr;
     std::string msg;
@@ -400,7 +403,8 @@ static mrs_status mlp_backward(mrs_mlp *m, const float *t, int n)
     const int W = m->width;
     MCK(cudaMemsetAsync(m->grads, 0, sizeof(float) * m->n_params, m->stream), "memset");
     MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream), "memset");
-    k_loss<<<(n + 255) / 256, 256, 0, m->stream>>>(m->y, t, n, -0.1f, 0.3f, m->dy, m->loss);
+    k_loss<<<(n + 255) / 256, 256, 0, m->stream>>>(m->y, t, n, -0.1f, 0.3f, m->over_weight, m->dy,
+                                                   m->loss);
     k_out_back<<<(n + 31) / 32, W, 0, m->stream>>>(m->Hs[m->layers - 1], W, m->params + m->offWo,
                                                    m->dy, n, m->dH, m->grads + m->offWo,
                                                    m->grads + m->offBo);
@@ -456,6 +460,14 @@ cudaError_t mlp_infer_trajs(mrs_mlp *m, const float *traj, const fused::TrajSegs
 {
     return launch_fused(m, fused::InTrajSet{traj, segs}, segs.row_start[segs.n], dhat, err,
                         m->per_sm_traj, s);
+}
+
+// arm-pair surrogate over every rollout step of a set of (a, b) segments
+cudaError_t mlp_infer_pairs(mrs_mlp *m, const float *traj, const float *plan,
+                            const fused::PairSegs &segs, float *rhohat, int *err, cudaStream_t s)
+{
+    return launch_fused(m, fused::InPairSet{traj, plan, segs}, segs.row_start[segs.n], rhohat,
+                        err, m->per_sm_pair, s);
 }
 
 }  // namespace mrs
@@ -541,7 +553,8 @@ mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long 
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             configure_fused<fused::InRows>(m, &m->per_sm_rows) != cudaSuccess ||
-            configure_fused<fused::InTrajSet>(m, &m->per_sm_traj) != cudaSuccess) {
+            configure_fused<fused::InTrajSet>(m, &m->per_sm_traj) != cudaSuccess ||
+            configure_fused<fused::InPairSet>(m, &m->per_sm_pair) != cudaSuccess) {
             mrs_mlp_destroy(m);
             return MRS_ECUDA;
         }
@@ -588,6 +601,13 @@ mrs_status mrs_mlp_param_count(const mrs_mlp *m, size_t *n)
 {
     if (!m || !n) return MRS_EINVAL;
     *n = m->n_params;
+    return MRS_OK;
+}
+
+mrs_status mrs_mlp_set_loss(mrs_mlp *m, float over_weight)
+{
+    if (!m || !std::isfinite(over_weight) || over_weight < 1.f) return MRS_EINVAL;
+    m->over_weight = over_weight;
     return MRS_OK;
 }
 

@@ -189,6 +189,61 @@ struct InTrajSet {
     }
 };
 
+// Features of the arm-pair surrogate for every rollout step of arm a against
+// the published plan of arm b, for a set of (a, b) segments sharing one
+// network: row = h K_a + n of segment s; features 2j, 2j+1 = sin, cos of
+// arm a's joint j at the sampled step (trajectory traj + off_khd[s],
+// [H][d_a][K_a]), then sin, cos of arm b's plan joints at step min(h,
+// H_b - 1) (plan + off_hd[s], [H_b][d_b]), then the 7 numbers of arm b's
+// base pose in arm a's base frame (xyz, quaternion w x y z); outputs to
+// off_out[s] + row within the segment.
+struct PairSegs {
+    int n;
+    int row_start[kMaxSegs + 1];
+    int K[kMaxSegs], Hb[kMaxSegs], da[kMaxSegs], db[kMaxSegs];
+    long long off_khd[kMaxSegs], off_hd[kMaxSegs], off_out[kMaxSegs];
+    float pose[kMaxSegs][7];
+};
+
+struct InPairSet {
+    const float *traj, *plan;
+    PairSegs seg;
+    __device__ __forceinline__ int find(int row) const
+    {
+        int s = 0;
+        while (s + 1 < seg.n && row >= seg.row_start[s + 1]) ++s;
+        return s;
+    }
+    __device__ __forceinline__ void operator()(int row, int g, float (&v)[8]) const
+    {
+        const int s = find(row), K = seg.K[s], da = seg.da[s], db = seg.db[s];
+        const int r = row - seg.row_start[s], h = r / K, n = r - h * K;
+        const float *qa = traj + seg.off_khd[s] + (size_t)h * da * K + n;
+        const float *qb = plan + seg.off_hd[s] + (size_t)min(h, seg.Hb[s] - 1) * db;
+#pragma unroll
+        for (int p = 0; p < 8; p += 2) {
+            const int f = 8 * g + p;                 // even: (sin, cos) pairs stay together
+            float a = 0.f, b = 0.f;
+            if (f < 2 * da) {
+                sincosf(qa[(size_t)(f >> 1) * K], &a, &b);
+            } else if (f < 2 * da + 2 * db) {
+                sincosf(qb[(f - 2 * da) >> 1], &a, &b);
+            } else {
+                const int k = f - 2 * da - 2 * db;
+                a = k < 7 ? seg.pose[s][k] : 0.f;
+                b = k + 1 < 7 ? seg.pose[s][k + 1] : 0.f;
+            }
+            v[p] = a;
+            v[p + 1] = b;
+        }
+    }
+    __device__ __forceinline__ size_t out(int row) const
+    {
+        const int s = find(row);
+        return (size_t)(seg.off_out[s] + (row - seg.row_start[s]));
+    }
+};
+
 // Input functor interface: in(row, g, v) fills the 8 features 8g .. 8g+7 of
 // a valid row (row < rows), features at or beyond the input width 0; the
 // row's output goes to y[in.out(row)].

@@ -54,6 +54,13 @@ struct mrs_ctx {
     // rollout launch shape (mrs_set_rollout_shape / mrs_autotune)
     int tile_samples = 32, blocks_per_sm = 0, tile_order = 0, max_blocks_per_sm = 1;
     bool has_input = false;
+    // arm-pair surrogate: (arm, neighbour, network) slots, their launch groups
+    // and the prediction buffer ([sum K*H][A] floats, allocated on first use)
+    struct PairSlot { int a, b; mrs_mlp *net; };
+    std::vector<PairSlot> pair_slots;
+    std::vector<PairGroup> pair_groups;
+    float *rhohat = nullptr;
+    float4 *pair_board = nullptr;
 };
 
 static const char *g_noctx = "null context";
@@ -455,6 +462,8 @@ void mrs_destroy(mrs_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->rhohat) cudaFree(ctx->rhohat);
+    if (ctx->pair_board) cudaFree(ctx->pair_board);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
@@ -609,7 +618,9 @@ mrs_status mrs_share_plans(mrs_ctx *ctx, int arm, const float *plan_spheres, con
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
     const ArmDev &A = ctx->arms[arm];
-    int valid = dist_to_goal >= 0.f ? 1 : 0;
+    // 1: plan with joints, 2: spheres only (the arm-pair surrogate, which
+    // reads the joints, then falls back to the exact pass for it)
+    int valid = dist_to_goal >= 0.f ? (plan_q ? 1 : 2) : 0;
     if (valid) {
         if (!plan_spheres) return fail(ctx, MRS_EINVAL, "null plan");
         const size_t nsph = (size_t)A.H * A.ns * 4;
@@ -1016,6 +1027,187 @@ mrs_status mrs_debug_self(mrs_ctx *ctx, int arm, float *dhat, float *exact)
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         cudaFree(d);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "exact self clearance");
+    }
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return MRS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned arm-pair clearance
+
+// pose of arm b's base in arm a's base frame: translation R_a^T (t_b - t_a),
+// rotation conj(q_a) q_b, computed in double from the float inputs
+static void relative_pose(const ArmDev &A, const ArmDev &B, float out[7])
+{
+    double qa[4], qb[4];
+    for (int k = 0; k < 4; ++k) {
+        qa[k] = A.base_pose[3 + k];
+        qb[k] = B.base_pose[3 + k];
+    }
+    auto norm = [](double *q) {
+        const double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int k = 0; k < 4; ++k) q[k] /= n;
+    };
+    norm(qa);
+    norm(qb);
+    const double w = qa[0], x = qa[1], y = qa[2], z = qa[3];
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                         2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    const double d[3] = {(double)B.base_pose[0] - A.base_pose[0],
+                         (double)B.base_pose[1] - A.base_pose[1],
+                         (double)B.base_pose[2] - A.base_pose[2]};
+    for (int r = 0; r < 3; ++r) out[r] = (float)(R[r] * d[0] + R[3 + r] * d[1] + R[6 + r] * d[2]);
+    // conj(qa) * qb
+    const double cw = w, cx = -x, cy = -y, cz = -z;
+    const double rw = cw * qb[0] - cx * qb[1] - cy * qb[2] - cz * qb[3];
+    const double rx = cw * qb[1] + cx * qb[0] + cy * qb[3] - cz * qb[2];
+    const double ry = cw * qb[2] - cx * qb[3] + cy * qb[0] + cz * qb[1];
+    const double rz = cw * qb[3] + cx * qb[2] - cy * qb[1] + cz * qb[0];
+    out[3] = (float)rw; out[4] = (float)rx; out[5] = (float)ry; out[6] = (float)rz;
+}
+
+mrs_status mrs_relative_pose(mrs_ctx *ctx, int a, int b, float *pose)
+{
+    if (!ctx || !pose || a < 0 || a >= ctx->A || b < 0 || b >= ctx->A)
+        return fail(ctx, MRS_EINVAL, "bad arguments");
+    relative_pose(ctx->arms[a], ctx->arms[b], pose);
+    return MRS_OK;
+}
+
+static void rebuild_pair_groups(mrs_ctx *ctx)
+{
+    ctx->pair_groups.clear();
+    for (const auto &sl : ctx->pair_slots) {
+        PairGroup *g = nullptr;
+        for (auto &x : ctx->pair_groups)
+            if (x.net == sl.net && x.segs.n < fused::kMaxSegs) g = &x;
+        if (!g) {
+            ctx->pair_groups.push_back(PairGroup{});
+            g = &ctx->pair_groups.back();
+            g->net = sl.net;
+        }
+        const ArmDev &A = ctx->arms[sl.a], &B = ctx->arms[sl.b];
+        fused::PairSegs &q = g->segs;
+        const int k = q.n;
+        q.K[k] = A.K;
+        q.Hb[k] = B.H;
+        q.da[k] = A.dof;
+        q.db[k] = B.dof;
+        q.off_khd[k] = A.off_khd;
+        q.off_hd[k] = B.off_hd;
+        q.off_out[k] = A.off_kh * ctx->A + (long long)sl.b * A.K * A.H;
+        relative_pose(A, B, q.pose[k]);
+        q.row_start[k + 1] = q.row_start[k] + A.K * A.H;
+        q.n = k + 1;
+    }
+    ctx->L.n_pair_groups = (int)ctx->pair_groups.size();
+    ctx->L.pair_groups = ctx->pair_groups.data();
+}
+
+mrs_status mrs_set_pair_surrogate(mrs_ctx *ctx, int a, int b, mrs_mlp *net, float margin)
+{
+    if (!ctx) return MRS_EINVAL;
+    if (a < 0 || a >= ctx->A || b < -1 || b >= ctx->A || b == a)
+        return fail(ctx, MRS_EINVAL, "arm out of range");
+    if (net && (!std::isfinite(margin) || margin < 0.f)) return fail(ctx, MRS_EINVAL, "margin >= 0");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    ArmDev &A = ctx->arms[a];
+    for (int i = 0; i < ctx->A; ++i) {
+        if (i == a || (b >= 0 && i != b)) continue;
+        const ArmDev &B = ctx->arms[i];
+        if (net && mlp_in_dim(net) != 2 * A.dof + 2 * B.dof + 7)
+            return fail(ctx, MRS_EINVAL, "arm-pair surrogate input must be 2 d_a + 2 d_b + 7");
+    }
+    if (net && !ctx->rhohat) {
+        size_t rows = 0;
+        for (const auto &x : ctx->arms) rows += (size_t)x.K * x.H;
+        CK(cudaMalloc(&ctx->rhohat, sizeof(float) * rows * ctx->A), "arm-pair prediction buffer");
+        ctx->D.rhohat = ctx->rhohat;
+        ctx->L.board_bytes = sizeof(float) * ctx->sz.hs;
+        CK(cudaMalloc(&ctx->pair_board, ctx->L.board_bytes), "plan snapshot buffer");
+        ctx->D.pair_board = ctx->pair_board;
+    }
+    // replace the slots of (a, b) or (a, every other arm)
+    std::vector<mrs_ctx::PairSlot> keep;
+    for (const auto &sl : ctx->pair_slots)
+        if (!(sl.a == a && (b < 0 || sl.b == b))) keep.push_back(sl);
+    if (net)
+        for (int i = 0; i < ctx->A; ++i)
+            if (i != a && (b < 0 || i == b)) keep.push_back({a, i, net});
+    std::sort(keep.begin(), keep.end(), [](const mrs_ctx::PairSlot &x, const mrs_ctx::PairSlot &y) {
+        return x.a != y.a ? x.a < y.a : x.b < y.b;
+    });
+    ctx->pair_slots = keep;
+    A.pair_mask = 0u;
+    for (const auto &sl : ctx->pair_slots)
+        if (sl.a == a) A.pair_mask |= 1u << sl.b;
+    if (net) A.pair_margin = margin;
+    rebuild_pair_groups(ctx);
+    static_assert(offsetof(ArmDev, pair_margin) == offsetof(ArmDev, pair_mask) + sizeof(unsigned),
+                  "pair_mask and pair_margin are adjacent");
+    CK(cudaMemcpyAsync(reinterpret_cast<char *>(ctx->D.arms + a) + offsetof(ArmDev, pair_mask),
+                       &A.pair_mask, sizeof(unsigned) + sizeof(float), cudaMemcpyHostToDevice,
+                       ctx->stream), "upload arm");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    invalidate_graph(ctx);
+    return MRS_OK;
+}
+
+mrs_status mrs_pair_dataset(mrs_ctx *ctx, int a, int b, int n, unsigned long long seed,
+                            const float *poses, int n_pose, float jit_t, float jit_yaw, float *d_x,
+                            float *d_t, float *d_qa, float *d_qb, float *d_pose)
+{
+    if (!ctx || a < 0 || a >= ctx->A || b < 0 || b >= ctx->A || n < 1 || !d_x || !d_t ||
+        (poses && n_pose < 1) || !(jit_t >= 0.f) || !(jit_yaw >= 0.f))
+        return fail(ctx, MRS_EINVAL, "bad dataset arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    std::vector<float> p;
+    if (poses) {
+        if (!finite_arr(poses, 7 * (size_t)n_pose)) return fail(ctx, MRS_EINVAL, "non-finite pose");
+        p.assign(poses, poses + 7 * (size_t)n_pose);
+    } else {
+        p.resize(7);
+        relative_pose(ctx->arms[a], ctx->arms[b], p.data());
+        n_pose = 1;
+    }
+    float *dp = nullptr;
+    CK(cudaMalloc(&dp, sizeof(float) * p.size()), "pose buffer");
+    cudaError_t e = cudaMemcpyAsync(dp, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = enqueue_pair_dataset(ctx->D, a, b, n, seed, dp, n_pose, jit_t, jit_yaw, d_x, d_t, d_qa,
+                                 d_qb, d_pose, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pair dataset");
+    return MRS_OK;
+}
+
+mrs_status mrs_debug_pair(mrs_ctx *ctx, int a, int b, float *rhohat, float *exact)
+{
+    if (!ctx || a < 0 || a >= ctx->A || b < 0 || b >= ctx->A || a == b)
+        return fail(ctx, MRS_EINVAL, "bad arguments");
+    mrs_status st = ensure_bound(ctx);
+    if (st != MRS_OK) return st;
+    const ArmDev &A = ctx->arms[a];
+    const int rows = A.K * A.H;
+    if (rhohat) {
+        if (!ctx->rhohat) return fail(ctx, MRS_ESTATE, "no arm-pair surrogate was set");
+        CK(cudaMemcpyAsync(rhohat, ctx->rhohat + A.off_kh * ctx->A + (long long)b * rows,
+                           sizeof(float) * rows, cudaMemcpyDeviceToHost, ctx->stream), "download");
+    }
+    if (exact) {
+        float *d = nullptr;
+        CK(cudaMalloc(&d, sizeof(float) * rows), "buffer");
+        cudaError_t e = enqueue_pair_clearance_traj(ctx->D, a, b, rows, d, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(exact, d, sizeof(float) * rows, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(d);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "exact pair clearance");
     }
     CK(cudaStreamSynchronize(ctx->stream), "sync");
     return MRS_OK;

@@ -29,6 +29,9 @@ struct __align__(16) ArmDev {
                                           // external: optimised elsewhere, plan from the board;
                                           // learned: self clearance from the surrogate (Dev::dhat)
     float self_margin;                    // exact self pass when dhat < B_self + self_margin
+    unsigned pair_mask;                   // bit i: the clearance to arm i's plan comes from
+                                          // the arm-pair surrogate (Dev::rhohat)
+    float pair_margin;                    // exact pass when rhohat < B + pair_margin
     long long off_khd, off_kh;            // offsets into K*H*d and K*H work arrays
     float4 dh[kMaxDof];                   // a, d, alpha, theta_offset
     float2 twist[kMaxDof];                // sin(alpha), cos(alpha)
@@ -90,6 +93,11 @@ struct Dev {
     int *err;              // device error word (bounded waits)
     int *self_pairs;       // per arm, packed s1 | s2 << 8, bodies >= 3 apart
     float *dhat;           // [sum K*H] surrogate self clearance of every rollout step, [h][n]
+    float *rhohat;         // [sum K*H][A] surrogate clearance of every rollout step to each
+                           // neighbour's plan: arm j's block at off_kh * A, [i][h][n]
+                           // (null without an arm-pair surrogate)
+    float4 *pair_board;    // with an arm-pair surrogate: copy of the plan spheres the
+                           // cycle read (the board itself holds the new plans afterwards)
     int *work;             // rollout tile counters, one per iteration
     int out_mean, out_sph, out_q, out_u, out_dist, out_min;  // offsets in out (floats)
 };
@@ -158,6 +166,22 @@ struct Frame {
     float R[9];
     float t[3];
 };
+
+// rotation of a quaternion (w, x, y, z), normalised first
+__device__ __forceinline__ void quat_to_R(float w, float x, float y, float z, float *R)
+{
+    const float n = sqrtf(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    R[0] = 1.f - 2.f * (y * y + z * z);
+    R[1] = 2.f * (x * y - w * z);
+    R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);
+    R[4] = 1.f - 2.f * (x * x + z * z);
+    R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);
+    R[7] = 2.f * (y * z + w * x);
+    R[8] = 1.f - 2.f * (x * x + y * y);
+}
 
 __device__ __forceinline__ void frame_base(const ArmDev &A, Frame &F)
 {

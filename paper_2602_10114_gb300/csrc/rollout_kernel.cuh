@@ -51,6 +51,7 @@ struct RolloutSmem {
     int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
     int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
     float *nb_alpha;   // [n_nb]
+    int *nb_arm;       // [n_nb] arm index of each neighbour
     unsigned short *cand;   // [kGroups][cand_cap] per-warp candidate lists
     int cand_cap;
     float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
@@ -337,10 +338,24 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             const int k0 = world ? 0 : S.nb_start[ps - 1];
             const int k1 = world ? n_world : S.nb_start[ps];
             const float Bp = world ? P.B_world : P.B;
+            // with an arm-pair surrogate, a step whose predicted clearance to
+            // this neighbour's plan is at least B + margin skips the exact
+            // pass (its coordination term is zero); a plan published without
+            // joints always takes the exact pass
+            bool need = true;
+            if (!world) {
+                const int ai = S.nb_arm[ps - 1];
+                if ((A.pair_mask >> ai) & 1u)
+                    need = valid && (D.board_valid[ai] != 1 ||
+                                     D.rhohat[A.off_kh * P.n_arms + (long long)ai * A.H * K +
+                                              (long long)h * K + n] < P.B + A.pair_margin);
+                if (!__any_sync(0xffffffffu, need)) continue;
+            }
             const int nc = cull(S, k0, k1, Bp, 1e-3f + P.eps_g / Bp, box, lane, list);
             float m = clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ);
             if (world) m = fminf(m, mbox);
-            if (m < Bp) atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
+            if (need && m < Bp)
+                atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
         }
     }
     __syncthreads();   // every group's centres are in shared memory
@@ -403,6 +418,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.pairs = (int *)p;        p += align16(sizeof(int) * P.max_pairs);
         S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
         S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
+        S.nb_arm = (int *)p;       p += align16(sizeof(int) * MRS_MAX_ARMS);
         S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
         S.cand = (unsigned short *)p;
         S.cand_cap = (int)((n_other + 7) & ~size_t(7));
@@ -457,6 +473,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             const int pos = __popc(mask & ((1u << lane) - 1u));
             if (ok) {
                 S.nb_start[pos] = n_world + incl - ns_i;
+                S.nb_arm[pos] = lane;
                 S.nb_alpha[tp * MRS_MAX_ARMS + pos] = al;
             }
             if (lane == 31) S.nb_start[nnb] = n_world + incl;

@@ -100,6 +100,13 @@ SIGNATURES = {
     "mrs_mlp_last_error": (C.c_char_p, [C.c_void_p]),
     "mrs_mlp_param_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "mrs_mlp_launch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
+    "mrs_mlp_set_loss": (C.c_int, [C.c_void_p, C.c_float]),
+    "mrs_set_pair_surrogate": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_float]),
+    "mrs_relative_pose": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp]),
+    "mrs_pair_dataset": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_ulonglong, _fp,
+                                   C.c_int, C.c_float, C.c_float, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrs_debug_pair": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp, _fp]),
     "mrs_mlp_get_params": (C.c_int, [C.c_void_p, _fp, C.c_size_t]),
     "mrs_mlp_set_params": (C.c_int, [C.c_void_p, _fp, C.c_size_t]),
     "mrs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -401,6 +408,48 @@ class Controller:
         self._check(self.L.mrs_debug_self(self.h, arm, _pf(dh), _pf(ex)), "debug_self")
         return dh, ex
 
+    def set_pair_surrogate(self, a, b, net, margin=0.03):
+        """Arm-to-arm clearance of arm a to arm b's plan (b = -1: every other
+        arm) from the network `net` (None: exact), exact below B + margin."""
+        self._check(self.L.mrs_set_pair_surrogate(self.h, a, b, net.h if net is not None else None,
+                                                  float(margin)), "set_pair_surrogate")
+        self._nets = getattr(self, "_nets", {})
+        self._nets[("pair", a, b)] = net
+
+    def relative_pose(self, a, b):
+        out = np.zeros(7, np.float32)
+        self._check(self.L.mrs_relative_pose(self.h, a, b, _pf(out)), "relative_pose")
+        return out
+
+    def pair_dataset(self, a, b, n, seed, poses=None, jit_t=0.02, jit_yaw=0.05):
+        """Device training data of the arm-pair network: (features [n][2 d_a +
+        2 d_b + 7], exact clearance [n], q_a [n][d_a], q_b [n][d_b], pose [n][7])."""
+        import torch
+        da, db = self.sc.arms[a].dof, self.sc.arms[b].dof
+        dev = self.device
+        x = torch.empty((n, 2 * da + 2 * db + 7), dtype=torch.float32, device=dev)
+        t = torch.empty(n, dtype=torch.float32, device=dev)
+        qa = torch.empty((n, da), dtype=torch.float32, device=dev)
+        qb = torch.empty((n, db), dtype=torch.float32, device=dev)
+        po = torch.empty((n, 7), dtype=torch.float32, device=dev)
+        p = None if poses is None else _f32(poses).reshape(-1, 7)
+        self._check(self.L.mrs_pair_dataset(
+            self.h, a, b, n, seed, _pf(p) if p is not None else None,
+            0 if p is None else len(p), float(jit_t), float(jit_yaw),
+            C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), C.c_void_p(qa.data_ptr()),
+            C.c_void_p(qb.data_ptr()), C.c_void_p(po.data_ptr())), "pair_dataset")
+        return x, t, qa, qb, po
+
+    def debug_pair(self, a, b, predicted=True):
+        """(predicted, exact) clearance [H_a][K_a] of arm a's rollout steps to
+        arm b's plan in the last cycle; predicted is None when not asked."""
+        A = self.sc.arms[a]
+        rh = np.zeros((A.H, A.K), np.float32) if predicted else None
+        ex = np.zeros((A.H, A.K), np.float32)
+        self._check(self.L.mrs_debug_pair(self.h, a, b, _pf(rh) if predicted else None, _pf(ex)),
+                    "debug_pair")
+        return rh, ex
+
     def debug_costs(self, arm):
         c = np.zeros(self.sc.arms[arm].K, np.float32)
         self._check(self.L.mrs_debug_costs(self.h, arm, _pf(c)), "debug_costs")
@@ -494,6 +543,10 @@ class MLP:
     def _check(self, st, what):
         if st != 0:
             raise MrsError(st, f"{what}: {self.L.mrs_mlp_last_error(self.h).decode()}")
+
+    def set_loss(self, over_weight=1.0):
+        """Weight of over-predictions in the training loss (1: plain MSE)."""
+        self._check(self.L.mrs_mlp_set_loss(self.h, float(over_weight)), "set_loss")
 
     def launch_info(self):
         """Fused inference launch shape: CTAs per SM (plain rows, rollout

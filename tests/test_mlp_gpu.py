@@ -49,19 +49,22 @@ def _net(in_dim=14, width=256, layers=3, seed=3):
     return net, p
 
 
-def test_gradients_match_the_fp64_oracle():
+@pytest.mark.parametrize("over_weight", [1.0, 4.0])
+def test_gradients_match_the_fp64_oracle(over_weight):
     """GPU gradients (BF16 GEMMs and activations, FP32 accumulation) against
     the FP64 backward with the same BF16 weights and inputs: 3e-2 relative
-    per parameter tensor, cosine > 0.999."""
+    per parameter tensor, cosine > 0.999; plain and asymmetric loss."""
     import torch
     from oracle import oracle as O
     rng = np.random.default_rng(5)
     net, p = _net()
+    net.set_loss(over_weight)
     n = 64
     x = bf16_bits(rng.normal(size=(n, 14)))[1]
     t = rng.uniform(-0.15, 0.35, n).astype(np.float32)
     g, loss = net.grads(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
-    loss_o, g_o, _ = O.mlp_loss_grad(14, 256, 3, p.astype(np.float64), x, t)
+    loss_o, g_o, _ = O.mlp_loss_grad(14, 256, 3, p.astype(np.float64), x, t,
+                                     over_weight=over_weight)
     assert abs(loss - loss_o) <= 2e-2 * loss_o
     (Ws, (wo, bo)) = net.unpack(g)
     (Wo, (woo, boo)) = net.unpack(g_o)

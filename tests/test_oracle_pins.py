@@ -539,7 +539,8 @@ def test_sample_costs_agree_with_the_cycle(oracle_mod):
 # ---------------------------------------------------------------------------
 # learned surrogate (not in the paper): FP64 MLP gradient
 
-def test_mlp_gradient_matches_central_differences(oracle_mod):
+@pytest.mark.parametrize("over_weight", [1.0, 6.0])
+def test_mlp_gradient_matches_central_differences(oracle_mod, over_weight):
     rng = np.random.default_rng(21)
     in_dim, width, layers = 14, 16, 3
     in_pad = 16
@@ -547,7 +548,7 @@ def test_mlp_gradient_matches_central_differences(oracle_mod):
     p = rng.normal(scale=0.4, size=n_par)
     x = rng.normal(size=(9, in_dim))
     t = rng.uniform(-0.2, 0.4, 9)          # some targets beyond the clip range
-    loss, g, _ = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, t)
+    loss, g, _ = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, t, over_weight=over_weight)
     idx = rng.choice(n_par, 60, replace=False)
     h = 1e-6
     for i in idx:
@@ -557,9 +558,31 @@ def test_mlp_gradient_matches_central_differences(oracle_mod):
         pp, pm = p.copy(), p.copy()
         pp[i] += h
         pm[i] -= h
-        fd = (oracle_mod.mlp_loss_grad(in_dim, width, layers, pp, x, t, False)[0]
-              - oracle_mod.mlp_loss_grad(in_dim, width, layers, pm, x, t, False)[0]) / (2 * h)
+        fd = (oracle_mod.mlp_loss_grad(in_dim, width, layers, pp, x, t, False, over_weight)[0]
+              - oracle_mod.mlp_loss_grad(in_dim, width, layers, pm, x, t, False, over_weight)[0]
+              ) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_asymmetric_loss_weights_over_predictions(oracle_mod):
+    """With every output above its (clipped) target the weighted loss is
+    over_weight times the plain one; with every output below, the same."""
+    rng = np.random.default_rng(22)
+    in_dim, width, layers = 3, 16, 1
+    p = rng.normal(scale=0.05, size=16 * 16 + 16 + 16 + 1)
+    x = rng.normal(size=(12, in_dim))
+    _, _, y = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, np.zeros(12), False)
+    p[-1] += 0.1 - y.mean()                    # outputs near 0.1
+    _, _, y = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, np.zeros(12), False)
+    below, above = y - 0.05, y + 0.05          # targets inside the clip range
+    assert np.all(below > -0.1) and np.all(above < 0.3)
+    plain_b = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, below, False)[0]
+    plain_a = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, above, False)[0]
+    assert math.isclose(plain_b, 0.05 ** 2, rel_tol=1e-12)
+    w_b = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, below, False, 7.0)[0]
+    w_a = oracle_mod.mlp_loss_grad(in_dim, width, layers, p, x, above, False, 7.0)[0]
+    assert math.isclose(w_b, 7.0 * plain_b, rel_tol=1e-12)
+    assert math.isclose(w_a, plain_a, rel_tol=1e-12)
 
 
 def test_mlp_forward_closed_form(oracle_mod):
@@ -660,3 +683,4 @@ def test_pair_distance_symmetry_and_base_override(oracle_mod):
     assert np.all(far1 > 10)
     assert np.allclose(far2 - far1, 3.0, atol=1e-2)   # nearly parallel to x at this range
     assert np.all(far2 - far1 <= 3.0 + 1e-12)          # triangle inequality
+

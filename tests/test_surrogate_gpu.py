@@ -65,9 +65,9 @@ def test_in_cycle_inference_matches_the_oracle_forward():
             assert np.abs(dh[:, n] - y).max() <= 2e-2 * max(1.0, np.abs(y).max()), (a, n)
 
 
-def _constant_net(dof, value):
+def _constant_net(dof, value, in_dim=None):
     from paper_2602_10114_gb300 import mrs
-    net = mrs.MLP(2 * dof, 32, 1, 0)
+    net = mrs.MLP(2 * dof if in_dim is None else in_dim, 32, 1, 0)
     p = np.zeros(net.n_params, np.float32)
     p[-1] = value
     net.set_params(p)
@@ -128,5 +128,146 @@ def test_trained_surrogate_false_negatives():
     ctl.step(sc.q0, sc.qd0, gp.astype(np.float32), gR.astype(np.float32))
     dh, ex = ctl.debug_self(0)
     ev = surrogate.evaluate(dh, ex, float(np.float32(0.03)), 0.03)
+    print("rollout steps:", ev)
+    assert ev["fn_rate"] <= 5e-3
+
+
+# ---------------------------------------------------------------------------
+# learned arm-to-arm clearance (eight-arm workload shape)
+
+def _pair_scenario(K=32, H=8):
+    return S.shrink(S.config(5), K=K, H=H, n_world=32)
+
+
+def test_pair_dataset_labels_match_the_oracle():
+    """Labels of the arm-pair data against the oracle's clearance with arm a
+    at the identity and arm b at the drawn pose; without jitter the pose is b's
+    pose in a's frame, and the labels then also equal the oracle's clearance of
+    the two arms at their actual bases (which checks the relative pose)."""
+    from oracle.oracle import Oracle
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import EPS_D
+    sc = _pair_scenario()
+    ctl = mrs.Controller(sc)
+    orc = Oracle(sc)
+    ident = [0, 0, 0, 1, 0, 0, 0]
+    x, t, qa, qb, po = [v.cpu().numpy() for v in ctl.pair_dataset(0, 3, 3000, 5, jit_t=0.05,
+                                                                   jit_yaw=0.2)]
+    a = sc.arms[0]
+    assert np.all(qa >= a.q_lo) and np.all(qa <= a.q_hi)
+    assert np.allclose(x[:, 0:14:2], np.sin(qa.astype(np.float64)), atol=1e-6)
+    assert np.allclose(x[:, 15:28:2], np.cos(qb.astype(np.float64)), atol=1e-6)
+    assert np.array_equal(x[:, 28:35], po)
+    exp = np.array([orc.pair_distance(0, 3, qa[i], qb[i], base_b=po[i], base_a=ident)[0]
+                    for i in range(len(qa))])
+    assert np.abs(t - exp).max() < 2 * EPS_D
+    # no jitter: the pose is the relative pose, and the arms' own bases agree
+    x, t, qa, qb, po = [v.cpu().numpy() for v in ctl.pair_dataset(2, 5, 500, 6, jit_t=0.0,
+                                                                   jit_yaw=0.0)]
+    assert np.allclose(po, ctl.relative_pose(2, 5)[None], atol=0)
+    exp = orc.pair_distance(2, 5, qa, qb)
+    assert np.abs(t - exp).max() < 2 * EPS_D
+
+
+def test_pair_in_cycle_inference_matches_the_oracle_forward():
+    """Inside the cycle the arm-pair network sees arm a's sampled joints, arm
+    b's published plan joints at the same step and the relative pose: its
+    predictions equal the FP64 network on the oracle's rollout of the same
+    samples and the oracle's plan (BF16 tolerance); the exact clearance the
+    library recomputes equals the oracle's."""
+    from oracle import oracle as O
+    from parity_utils import Replay, EPS_D
+    from test_mlp_gpu import _net, bf16_bits
+    sc = _pair_scenario()
+    R = Replay(sc)
+    net, p = _net(35, 256, 4, seed=7)
+    R.ctl.set_pair_surrogate(0, -1, net, 0.03)
+    R.ctl.set_pair_surrogate(5, 2, net, 0.03)
+    exp = R.cycle(None)[-1]
+    R.advance(exp)                       # the second cycle reads published plans
+    q0, qd0 = [q.copy() for q in R.q], [q.copy() for q in R.qd]
+    plan_q = R.orc.state["plan_q"].copy()
+    exp = R.cycle(None)[-1]
+    for a, b in ((0, 3), (0, 7), (5, 2)):
+        rh, ex = R.ctl.debug_pair(a, b)                    # [H][K]
+        U = R.orc.split(exp["U"], "U", a)
+        pb = R.orc.split(plan_q, "hd", b)                  # [H_b][d]
+        pose = R.ctl.relative_pose(a, b).astype(np.float64)
+        for n in (0, 13, 31):
+            _, _, sph, qo = R.orc.rollout(a, q0, qd0, R.gp, R.gR, U[n])
+            xf = np.zeros((sc.arms[a].H, 35))
+            xf[:, 0:14:2], xf[:, 1:14:2] = np.sin(qo), np.cos(qo)
+            xf[:, 14:28:2], xf[:, 15:28:2] = np.sin(pb), np.cos(pb)
+            xf[:, 28:35] = pose
+            xf = bf16_bits(xf.astype(np.float32))[1]
+            _, _, y = O.mlp_loss_grad(35, 256, 4, p.astype(np.float64), xf, np.zeros(len(xf)), False)
+            assert np.abs(rh[:, n] - y).max() <= 2e-2 * max(1.0, np.abs(y).max()), (a, b, n)
+            ref = R.orc.pair_distance(a, b, qo, pb)
+            assert np.abs(ex[:, n] - ref).max() < 2 * EPS_D, (a, b, n)
+
+
+def test_pair_fallback_rule_extremes():
+    """A network that always predicts -1 m never skips: every output equals
+    exact mode bit for bit.  One that predicts +1 m skips every exact pass
+    against the neighbours' plans: the costs equal the oracle's without the
+    coordination term."""
+    from parity_utils import Replay, cost_tol
+    sc = _pair_scenario(K=32, H=6)
+    R0 = Replay(sc)
+    e0 = R0.cycle(None)[-1]
+    R0.advance(e0)
+    got0, gc0, *_ = R0.cycle(None)
+    never = _constant_net(0, -1.0, in_dim=35)
+    R1 = Replay(sc)
+    for a in range(sc.n_arms):
+        R1.ctl.set_pair_surrogate(a, -1, never, 0.03)
+    e1 = R1.cycle(None)[-1]
+    R1.advance(e1)
+    got1, gc1, *_ = R1.cycle(None)
+    for a in range(sc.n_arms):
+        assert np.array_equal(gc1[a], gc0[a])
+    for k in got0:
+        assert np.array_equal(got1[k], got0[k])
+    # always skip: the oracle without the coordination term (w_dyn = 0)
+    from oracle.oracle import Oracle
+    sc_nodyn = _pair_scenario(K=32, H=6)
+    sc_nodyn.params["w_dyn"] = 0.0
+    always = _constant_net(0, 1.0, in_dim=35)
+    R2 = Replay(sc)
+    R2.orc = Oracle(sc_nodyn, threads=8)
+    for a in range(sc.n_arms):
+        R2.ctl.set_pair_surrogate(a, -1, always, 0.03)
+    for c in range(2):
+        got, gc, ga, gs, exp = R2.cycle(None)
+        for a in range(sc.n_arms):
+            ce = R2.orc.split(exp["costs"], "k", a)
+            assert np.all(np.abs(gc[a] - ce) <= cost_tol(ce)), (c, a)
+        R2.advance(exp)
+
+
+def test_trained_pair_surrogate_false_negatives():
+    """Trained on the device over the layout's relative poses with the
+    asymmetric loss, the fallback margin calibrated on held-out samples to a
+    1e-3 false-negative rate: on the other held-out samples and on every
+    rollout step of a cycle, colliding arm pairs the surrogate would skip stay
+    rare (this test trains on 400k samples)."""
+    from paper_2602_10114_gb300 import mrs, surrogate
+    from parity_utils import goals
+    from oracle.oracle import Oracle
+    sc = _pair_scenario(K=64, H=16)
+    ctl = mrs.Controller(sc)
+    ctl.set_world()
+    net, stats = surrogate.train_pair_surrogate(ctl, 0, n_train=400_000, n_val=100_000, epochs=3,
+                                                lr=2e-3, over_weight=32.0, target_fn=1e-3)
+    print("held-out:", stats)
+    assert stats["colliding"] > 1000
+    assert stats["fn_rate"] <= 5e-3
+    for a in range(sc.n_arms):
+        ctl.set_pair_surrogate(a, -1, net, stats["margin"])
+    gp, gR = goals(Oracle(sc), sc)
+    for _ in range(2):
+        ctl.step(sc.q0, sc.qd0, gp.astype(np.float32), gR.astype(np.float32))
+    rh, ex = ctl.debug_pair(0, 1)
+    ev = surrogate.evaluate(rh, ex, float(np.float32(0.03)), stats["margin"])
     print("rollout steps:", ev)
     assert ev["fn_rate"] <= 5e-3
