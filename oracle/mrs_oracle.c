@@ -256,6 +256,81 @@ double orc_joint_cost(int d, const double *q, const double *lo, const double *hi
     return c;
 }
 
+void orc_jacobian(const orc_arm *arm, const double *frames, double *J)
+{
+    const int d = arm->dof;
+    const double *E = frames + 16 * d;
+    for (int i = 0; i < d; ++i) {
+        const double *T = frames + 16 * i;          /* frame i-1 of joint i+1 (0-based i) */
+        const double z[3] = {T[2], T[6], T[10]};
+        const double r[3] = {E[3] - T[3], E[7] - T[7], E[11] - T[11]};
+        J[0 * d + i] = z[1] * r[2] - z[2] * r[1];
+        J[1 * d + i] = z[2] * r[0] - z[0] * r[2];
+        J[2 * d + i] = z[0] * r[1] - z[1] * r[0];
+        J[3 * d + i] = z[0];
+        J[4 * d + i] = z[1];
+        J[5 * d + i] = z[2];
+    }
+}
+
+/* determinant of an n x n matrix (row-major, overwritten) by Gaussian
+ * elimination with partial pivoting */
+static double det_inplace(int n, double *M)
+{
+    double det = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r * n + c]) > fabs(M[p * n + c])) p = r;
+        if (M[p * n + c] == 0.0) return 0.0;
+        if (p != c) {
+            for (int k = 0; k < n; ++k) {
+                double t = M[c * n + k];
+                M[c * n + k] = M[p * n + k];
+                M[p * n + k] = t;
+            }
+            det = -det;
+        }
+        det *= M[c * n + c];
+        for (int r = c + 1; r < n; ++r) {
+            double f = M[r * n + c] / M[c * n + c];
+            for (int k = c; k < n; ++k) M[r * n + k] -= f * M[c * n + k];
+        }
+    }
+    return det;
+}
+
+double orc_manipulability(int dof, const double *J)
+{
+    double G[ORC_MAX_DOF * ORC_MAX_DOF];
+    int n;
+    if (dof >= 6) {              /* G = J J^T, 6 x 6 */
+        n = 6;
+        for (int a = 0; a < 6; ++a)
+            for (int b = 0; b < 6; ++b) {
+                double s = 0.0;
+                for (int k = 0; k < dof; ++k) s += J[a * dof + k] * J[b * dof + k];
+                G[a * 6 + b] = s;
+            }
+    } else {                     /* G = J^T J, dof x dof */
+        n = dof;
+        for (int a = 0; a < dof; ++a)
+            for (int b = 0; b < dof; ++b) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += J[k * dof + a] * J[k * dof + b];
+                G[a * dof + b] = s;
+            }
+    }
+    double det = det_inplace(n, G);
+    return det > 0.0 ? sqrt(det) : 0.0;
+}
+
+double orc_manip_cost(double w, double w0)
+{
+    double c = 1.0 - w / w0;
+    return c > 0.0 ? c : 0.0;
+}
+
 /* C = max(0, 1 - dist/B): 0 at dist >= B, 1 at contact, linear between. */
 double orc_ramp(double dist, double B)
 {
@@ -388,6 +463,12 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
         double c_pose = orc_pose_cost(F + 16 * d, g_p, g_R, cfg->w_rot);
         double c_stop = orc_stop_cost(d, qd, A->qd_max);
         double c_joint = orc_joint_cost(d, q, A->q_lo, A->q_hi, cfg->q_margin);
+        double c_manip = 0.0;
+        if (cfg->w_manip > 0.0) {
+            double J[6 * ORC_MAX_DOF];
+            orc_jacobian(A, F, J);
+            c_manip = orc_manip_cost(orc_manipulability(d, J), cfg->manip_w0);
+        }
 
         /* world clearance: spheres and boxes; moving spheres are predicted at
          * constant velocity to the time of step h (h+1 steps ahead). */
@@ -445,7 +526,8 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
         }
 
         double c = cfg->w_pose * c_pose + cfg->w_stop * c_stop + cfg->w_joint * c_joint +
-                   cfg->w_coll * c_coll + cfg->w_self * c_self + cfg->w_dyn * c_dyn;
+                   cfg->w_manip * c_manip + cfg->w_coll * c_coll + cfg->w_self * c_self +
+                   cfg->w_dyn * c_dyn;
         if (stage) stage[h] = c;
         total += pow(cfg->gamma, (double)h) * c;
         double slope = cfg->w_pose + cfg->w_dyn * slope_dyn;

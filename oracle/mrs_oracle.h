@@ -49,6 +49,8 @@ typedef struct {
     uint64_t seed;            /* Philox key */
     int max_plan_age;         /* plans older than this many cycles are ignored (0: no limit) */
     const int *active;        /* [A] arms this controller optimises (NULL: all) */
+    double w_manip;           /* weight of C_manip in Eq. 5 (0: term off) */
+    double manip_w0;          /* manipulability below which C_manip is positive */
 } orc_config;
 
 /* Controller state carried from cycle to cycle.  Per-arm blocks are
@@ -167,6 +169,18 @@ double orc_mlp_loss_grad_w(int in_dim, int in_pad, int width, int layers, const 
 /* Exact self-collision clearance of joint vectors q [n][dof] (+inf if the
  * arm has no sphere pair on bodies at least three apart). */
 void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out);
+
+/* Geometric Jacobian of the end-effector (the origin of frame d) in the world
+ * frame, J [6][dof] row-major: for revolute joint i (axis z_{i-1} through
+ * o_{i-1}, frames of orc_fk), column i = (z_{i-1} x (o_d - o_{i-1}), z_{i-1}). */
+void orc_jacobian(const orc_arm *arm, const double *frames, double *J);
+/* Yoshikawa manipulability, the volume of the Jacobian's velocity ellipsoid:
+ * sqrt(det(J J^T)) for dof >= 6, sqrt(det(J^T J)) for dof < 6 (the product
+ * of J's singular values). */
+double orc_manipulability(int dof, const double *J);
+/* C_manip of Eq. 5 (singularity avoidance, Sec. III-B), reading: the ramp
+ * max(0, 1 - w / w0) of the manipulability w. */
+double orc_manip_cost(double w, double w0);
 
 /* Arm-to-arm clearance (the set distance of Eq. 6 without the clamp at 0):
  * for each of n rows, the minimum over all sphere pairs of arm a (at joints

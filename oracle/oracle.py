@@ -38,7 +38,8 @@ class OrcConfig(C.Structure):
                 ("w_self", C.c_double), ("w_dyn", C.c_double), ("B", C.c_double),
                 ("B_world", C.c_double), ("B_self", C.c_double), ("tau", C.c_double),
                 ("q_margin", C.c_double), ("iterations", C.c_int), ("seed", C.c_uint64),
-                ("max_plan_age", C.c_int), ("active", _ip)]
+                ("max_plan_age", C.c_int), ("active", _ip), ("w_manip", C.c_double),
+                ("manip_w0", C.c_double)]
 
 
 class OrcState(C.Structure):
@@ -121,6 +122,11 @@ def lib():
             L.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
                                             _dp, _dp, _dp]
             L.orc_self_distance.argtypes = [C.POINTER(OrcArm), C.c_int, _dp, _dp]
+            L.orc_jacobian.argtypes = [C.POINTER(OrcArm), _dp, _dp]
+            L.orc_manipulability.restype = C.c_double
+            L.orc_manipulability.argtypes = [C.c_int, _dp]
+            L.orc_manip_cost.restype = C.c_double
+            L.orc_manip_cost.argtypes = [C.c_double, C.c_double]
             L.orc_pair_distance.argtypes = [C.POINTER(OrcArm), C.POINTER(OrcArm), C.c_int, _dp,
                                             _dp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
@@ -215,6 +221,10 @@ def weights(Cn, lam):
     return w
 
 
+def manip_cost(w, w0):
+    return float(lib().orc_manip_cost(float(w), float(w0)))
+
+
 def mlp_loss_grad(in_dim, width, layers, params, x, t, want_grad=True, over_weight=1.0):
     """FP64 loss, gradient and outputs of the surrogate MLP (over-predictions
     weighted by over_weight)."""
@@ -266,7 +276,7 @@ class Oracle:
                              p["w_stop"], p["w_joint"], p["w_coll"], p["w_self"], p["w_dyn"],
                              p["B"], p["B_world"], p["B_self"], p["tau"], p["q_margin"],
                              int(p["iterations"]), int(p["seed"]), int(p.get("max_plan_age", 0)),
-                             None)
+                             None, p.get("w_manip", 0.0), p.get("manip_w0", 0.02))
         if active is not None:          # arms this controller optimises
             self._active = np.ascontiguousarray(active, dtype=np.int32)
             self.cfg.active = self._active.ctypes.data_as(_ip)
@@ -362,6 +372,20 @@ class Oracle:
         out = np.zeros(len(qa))
         lib().orc_pair_distance(C.byref(arm_a), C.byref(arm_b), len(qa), pqa, pqb, _ptr(out))
         return out
+
+    def jacobian(self, arm: int, q):
+        """End-effector geometric Jacobian [6][dof] at joints q."""
+        frames, _ = self.fk(arm, q)
+        d = self.sc.arms[arm].dof
+        f, pf = _d(frames)
+        J = np.zeros((6, d))
+        lib().orc_jacobian(C.byref(self.arms[arm]), pf, _ptr(J))
+        return J
+
+    def manipulability(self, arm: int, q):
+        J = self.jacobian(arm, q)
+        j, pj = _d(J)
+        return float(lib().orc_manipulability(self.sc.arms[arm].dof, pj))
 
     def goal_pose(self, arm: int, q):
         frames, _ = self.fk(arm, q)

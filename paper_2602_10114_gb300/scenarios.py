@@ -38,7 +38,7 @@ DEFAULT_PARAMS = dict(
     dt=0.02, lam=10.0, gamma=1.0, alpha_mu=0.9, alpha_sigma=0.5, sigma_init=0.3,
     w_pose=10.0, w_rot=0.5, w_stop=10.0, w_joint=100.0, w_coll=1000.0, w_self=1000.0,
     w_dyn=5000.0, B=0.03, B_world=0.03, B_self=0.03, tau=3.0, q_margin=0.1,
-    iterations=1, seed=0, max_plan_age=0,
+    iterations=1, seed=0, max_plan_age=0, w_manip=0.0, manip_w0=0.02,
 )
 
 

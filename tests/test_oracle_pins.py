@@ -684,3 +684,87 @@ def test_pair_distance_symmetry_and_base_override(oracle_mod):
     assert np.allclose(far2 - far1, 3.0, atol=1e-2)   # nearly parallel to x at this range
     assert np.all(far2 - far1 <= 3.0 + 1e-12)          # triangle inequality
 
+
+
+# ---------------------------------------------------------------------------
+# manipulability (Eq. 5, C_manip: singularity avoidance)
+
+def _rot_vee(M):
+    return np.array([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]]) / 2
+
+
+def test_jacobian_matches_finite_differences_of_fk(oracle_mod):
+    """Linear columns = d p_ee / d q_i, angular columns = the rotation rate of
+    the end-effector frame, both by central differences of the FK."""
+    from oracle.oracle import Oracle
+    arm = _random_arm(51)
+    orc = Oracle(tiny_scenario([arm]))
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for _ in range(5):
+        q = rng.uniform(-2.8, 2.8, 7)
+        J = orc.jacobian(0, q)
+        for i in range(7):
+            qp, qm = q.copy(), q.copy()
+            qp[i] += h
+            qm[i] -= h
+            Fp, Fm = orc.fk(0, qp)[0][-1], orc.fk(0, qm)[0][-1]
+            dp = (Fp[:3, 3] - Fm[:3, 3]) / (2 * h)
+            w = _rot_vee((Fp[:3, :3] - Fm[:3, :3]) / (2 * h) @ orc.fk(0, q)[0][-1][:3, :3].T)
+            assert np.allclose(J[:3, i], dp, atol=1e-8)
+            assert np.allclose(J[3:, i], w, atol=1e-8)
+
+
+def test_manipulability_is_the_product_of_singular_values(oracle_mod):
+    from oracle.oracle import Oracle
+    for dof, seed in ((7, 52), (6, 53), (9, 54)):
+        arm = _random_arm(seed, dof=dof)
+        orc = Oracle(tiny_scenario([arm]))
+        rng = np.random.default_rng(seed)
+        for _ in range(5):
+            q = rng.uniform(-2.8, 2.8, dof)
+            sv = np.linalg.svd(orc.jacobian(0, q), compute_uv=False)
+            assert math.isclose(orc.manipulability(0, q), float(np.prod(sv[:min(6, dof)])),
+                                rel_tol=1e-9)
+
+
+def test_manipulability_planar_two_link_closed_form(oracle_mod):
+    """Planar two-link arm: J has the linear rows (-a1 s1 - a2 s12, -a2 s12;
+    a1 c1 + a2 c12, a2 c12; 0, 0) and the angular rows (0, 0; 0, 0; 1, 1);
+    the manipulability is sqrt(det(J^T J))."""
+    from oracle.oracle import Oracle
+    a1, a2 = 0.5, 0.25
+    orc = Oracle(tiny_scenario([dh_arm([[a1, 0, 0, 0], [a2, 0, 0, 0]])]))
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        q = rng.uniform(-2.8, 2.8, 2)
+        s1, c1 = math.sin(q[0]), math.cos(q[0])
+        s12, c12 = math.sin(q[0] + q[1]), math.cos(q[0] + q[1])
+        J = np.array([[-a1 * s1 - a2 * s12, -a2 * s12], [a1 * c1 + a2 * c12, a2 * c12],
+                      [0, 0], [0, 0], [0, 0], [1, 1]])
+        assert np.allclose(orc.jacobian(0, q), J, atol=1e-14)
+        assert math.isclose(orc.manipulability(0, q), math.sqrt(np.linalg.det(J.T @ J)),
+                            rel_tol=1e-9, abs_tol=1e-12)
+
+
+def test_manip_cost_ramp(oracle_mod):
+    assert oracle_mod.manip_cost(0.0, 0.02) == 1.0
+    assert oracle_mod.manip_cost(0.01, 0.02) == 0.5
+    assert oracle_mod.manip_cost(0.02, 0.02) == 0.0
+    assert oracle_mod.manip_cost(0.5, 0.02) == 0.0
+
+
+def test_manip_term_enters_the_stage_cost(oracle_mod):
+    """With only w_manip weighted, a standing rollout's stage cost is
+    w_manip * max(0, 1 - w(q_h) / w0) at every step."""
+    from oracle.oracle import Oracle
+    arm = _random_arm(55)
+    sc = tiny_scenario([arm], H=3, w_pose=0, w_stop=0, w_joint=0, w_coll=0, w_self=0,
+                       w_manip=2.0, manip_w0=0.5)
+    orc = Oracle(sc)
+    gp, gR = goals_of(orc, sc)
+    q = np.random.default_rng(1).uniform(-2.8, 2.8, 7)
+    _, stage, _, _ = orc.rollout(0, [q], [np.zeros(7)], gp, gR, np.zeros((3, 7)))
+    w = orc.manipulability(0, q)
+    assert w < 0.5
+    assert np.allclose(stage, 2.0 * (1 - w / 0.5), rtol=1e-12)
