@@ -55,8 +55,15 @@ def mlp_flops(rows, in_pad, width, layers):
 
 
 def workload(idx):
+    """Workload 1..5, or "M": workload 2 in the paper's M setting (5
+    optimisation iterations per cycle, Sec. V-A) with the manipulability term
+    on (w_manip = 10)."""
     from paper_2602_10114_gb300 import scenarios as S
-    return S.config(idx)
+    if str(idx) == "M":
+        sc = S.config(2, iterations=5, w_manip=10.0)
+        sc.name = "cfg2 in the M setting: 4 arms x 7 DoF, K=512, H=30, 5 iterations, C_manip"
+        return sc
+    return S.config(int(idx))
 
 
 def rollout_flops(sc):
@@ -510,8 +517,9 @@ def other_workload(idx, args, flush, ws, dev):
     steps = max(5, args.steps // 5)
     step_ms, kt, _ = time_device(ctl, d_in, steps, 3, flush, ws)
     ms = max_over_ranks(float(np.mean(step_ms)), ws)
-    roll = float(kt[:, 3].mean())
-    fl = rollout_flops(sc)
+    it = sc.params["iterations"]
+    roll = float(np.mean([kt[:, 3 + 5 * i] for i in range(it)]))     # one rollout launch
+    fl = rollout_flops(sc) / it
     ctl.close()
     units = sc.rollout_steps() * sc.params["iterations"]
     return {"workload": sc.name, "value": units * ws / (ms / 1e3), "unit": UNIT,
@@ -631,7 +639,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--workload", default="2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-learned", action="store_true",
@@ -640,7 +648,7 @@ def main():
     ap.add_argument("--pair-samples", type=int, default=5_000_000)
     ap.add_argument("--no-learned-pair", action="store_true",
                     help="skip the eight-arm learned self + arm-pair leg")
-    ap.add_argument("--other-workloads", type=int, nargs="*", default=[4, 5],
+    ap.add_argument("--other-workloads", nargs="*", default=["4", "5", "M"],
                     help="also time these workloads (device-resident, exact, autotuned)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rollout shape")

@@ -99,7 +99,13 @@ typedef struct {
  *  seed         Philox key of the sampling.
  *  mode         0 = exact costs (the only mode of this build).
  *  max_plan_age a board entry older than this many cycles counts as not
- *               published and is ignored (Sec. IV-C); 0 = no limit.     */
+ *               published and is ignored (Sec. IV-C); 0 = no limit.
+ *  w_manip      weight of C_manip of Eq. 5 (singularity avoidance, Sec.
+ *               III-B): max(0, 1 - w / manip_w0) of the end-effector
+ *               Jacobian's manipulability w = sqrt(det(J J^T)) (J^T J below
+ *               6 DoF); 0 = term off.
+ *  manip_w0     manipulability below which C_manip is positive (> 0 when
+ *               w_manip > 0; ignored otherwise).                         */
 typedef struct {
     int n_arms;
     const mrs_arm_desc *arms;
@@ -110,6 +116,7 @@ typedef struct {
     unsigned long long seed;
     int mode;
     int max_plan_age;
+    float w_manip, manip_w0;
 } mrs_config;
 
 /* Sensed state of one arm for one cycle (Alg. 1, Sense): host pointers.

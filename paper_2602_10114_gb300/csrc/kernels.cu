@@ -582,6 +582,75 @@ __global__ void k_philox(int n, const uint4 *ctr, uint2 key, uint4 *out)
 // ---------------------------------------------------------------------------
 // host wrappers
 
+// C_manip of Eq. 5 for every rollout step (w_manip > 0 only): FK frames of
+// the sampled joints, the end-effector geometric Jacobian (joint i: axis z
+// and origin o of the frame before it; column (z x (o_ee - o), z)), its
+// Gram matrix (J J^T for d >= 6, J^T J below), the determinant by Cholesky
+// (a non-positive pivot: singular), w = sqrt(det) and max(0, 1 - w / w0),
+// added with weight w_manip to the stop + joint-limit term of the step.
+__global__ void k_manip(Params P, Dev D, int total_kh)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= total_kh) return;
+    int a = 0;
+    while (a + 1 < P.n_arms && r >= D.arms[a + 1].off_kh) ++a;
+    const ArmDev &A = D.arms[a];
+    if (A.external) return;
+    const int d = A.dof, K = A.K;
+    const int loc = r - (int)A.off_kh, h = loc / K, n = loc - h * K;
+    const float *qh = D.traj + A.off_khd + (long long)h * d * K + n;
+    float z[kMaxDof][3], o[kMaxDof][3];
+    Frame F;
+    frame_base(A, F);
+    for (int j = 0; j < d; ++j) {
+        z[j][0] = F.R[2]; z[j][1] = F.R[5]; z[j][2] = F.R[8];
+        o[j][0] = F.t[0]; o[j][1] = F.t[1]; o[j][2] = F.t[2];
+        frame_step(F, qh[(long long)j * K], A.dh[j], A.twist[j]);
+    }
+    float J[6][kMaxDof];
+    for (int j = 0; j < d; ++j) {
+        const float rx = F.t[0] - o[j][0], ry = F.t[1] - o[j][1], rz = F.t[2] - o[j][2];
+        J[0][j] = z[j][1] * rz - z[j][2] * ry;
+        J[1][j] = z[j][2] * rx - z[j][0] * rz;
+        J[2][j] = z[j][0] * ry - z[j][1] * rx;
+        J[3][j] = z[j][0];
+        J[4][j] = z[j][1];
+        J[5][j] = z[j][2];
+    }
+    const int m = d >= 6 ? 6 : d;
+    float G[6][6];
+    for (int u = 0; u < m; ++u)
+        for (int v = 0; v <= u; ++v) {
+            float s = 0.f;
+            if (d >= 6)
+                for (int k = 0; k < d; ++k) s = fmaf(J[u][k], J[v][k], s);
+            else
+                for (int k = 0; k < 6; ++k) s = fmaf(J[k][u], J[k][v], s);
+            G[u][v] = s;
+        }
+    // Cholesky in place (lower triangle); det = prod L_kk^2
+    float det = 1.f;
+    for (int k = 0; k < m && det > 0.f; ++k) {
+        float p = G[k][k];
+        for (int t = 0; t < k; ++t) p -= G[k][t] * G[k][t];
+        if (!(p > 0.f)) {
+            det = 0.f;
+            break;
+        }
+        const float l = sqrtf(p);
+        G[k][k] = l;
+        det *= p;
+        for (int i = k + 1; i < m; ++i) {
+            float s = G[i][k];
+            for (int t = 0; t < k; ++t) s -= G[i][t] * G[k][t];
+            G[i][k] = s / l;
+        }
+    }
+    const float w = sqrtf(det);
+    const float c = fmaxf(0.f, 1.f - w / P.manip_w0);
+    D.stage_lim[A.off_kh + (long long)h * K + n] += P.w_manip * c;
+}
+
 cudaError_t configure_kernels(const LaunchPlan &L)
 {
     cudaError_t e;
@@ -619,6 +688,8 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
     for (int it = 0; it < P.iterations; ++it) {
         const int last = (it == P.iterations - 1);
         k_sample<<<L.n_sample_tiles, 512, L.smem_sample, s>>>(P, D, L.sample_tiles, it);
+        if (P.w_manip > 0.f)
+            k_manip<<<(L.total_kh + 127) / 128, 128, 0, s>>>(P, D, L.total_kh);
         mark();
         for (int i = 0; i < L.n_groups; ++i)   // learned self clearance of every step
             if ((rec = enqueue_self_surrogate(D, L.groups[i], s)) != cudaSuccess) return rec;

@@ -52,6 +52,7 @@ struct LaunchPlan {
     int n_pair_groups;
     PairGroup *pair_groups;   // host array owned by the context
     size_t board_bytes;       // plan spheres of the board (copied for evaluation)
+    int total_kh;             // rollout steps of all arms, sum K * H
 };
 
 // surrogate network (mlp.cu): input width, and the fused forward pass over

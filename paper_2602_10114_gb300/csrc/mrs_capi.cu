@@ -276,6 +276,9 @@ static mrs_status validate(const mrs_config *cfg, std::string &why)
         return why = "cost weights and tau must be >= 0", MRS_EINVAL;
     if (cfg->iterations < 1 || cfg->iterations > 64) return why = "iterations out of range", MRS_EINVAL;
     if (cfg->max_plan_age < 0) return why = "max_plan_age must be >= 0", MRS_EINVAL;
+    if (!(cfg->w_manip >= 0.f) || !std::isfinite(cfg->w_manip) ||
+        (cfg->w_manip > 0.f && !(cfg->manip_w0 > 0.f && std::isfinite(cfg->manip_w0))))
+        return why = "w_manip must be >= 0, and manip_w0 > 0 when w_manip > 0", MRS_EINVAL;
     if (cfg->mode != 0) return why = "only exact mode (0) is built", MRS_EUNSUPPORTED;
     for (int a = 0; a < cfg->n_arms; ++a) {
         const mrs_arm_desc &d = cfg->arms[a];
@@ -336,6 +339,8 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     P.B = cfg->B; P.B_world = cfg->B_world; P.B_self = cfg->B_self; P.tau = cfg->tau;
     P.q_margin = cfg->q_margin; P.seed = cfg->seed;
     P.max_plan_age = cfg->max_plan_age;
+    P.w_manip = cfg->w_manip;
+    P.manip_w0 = cfg->manip_w0;
 
     size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
     long long khd = 0, kh = 0;
@@ -415,6 +420,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     L.n_rollout_tiles = (int)ctx->rollout_tiles.size();
     L.n_cost_tiles = (int)ctx->cost_tiles.size();
     L.n_update_tiles = (int)ctx->update_tiles.size();
+    L.total_kh = (int)kh;
     size_t sp = 0, ss = 0, st2 = 0;
     for (auto &A : ctx->arms) {
         sp = std::max(sp, sizeof(float) * (size_t)A.H * (2 * A.dof * A.dof + A.dof));

@@ -53,6 +53,7 @@ struct Params {
     int world_cap, aabb_cap;      // shared-memory capacity of the rollout for the world
     float eps_g;                  // cancellation margin of the expanded pair pre-test (m^2)
     int max_plan_age;             // board entries older than this are ignored (0: no limit)
+    float w_manip, manip_w0;      // C_manip weight (0: off) and manipulability threshold
 };
 
 // A neighbour's board entry is used when it is published and, with a

@@ -39,7 +39,7 @@ class MrsConfig(C.Structure):
                 ("w_dyn", C.c_float), ("B", C.c_float), ("B_world", C.c_float),
                 ("B_self", C.c_float), ("tau", C.c_float), ("q_margin", C.c_float),
                 ("iterations", C.c_int), ("seed", C.c_ulonglong), ("mode", C.c_int),
-                ("max_plan_age", C.c_int)]
+                ("max_plan_age", C.c_int), ("w_manip", C.c_float), ("manip_w0", C.c_float)]
 
 
 class MrsArmState(C.Structure):
@@ -205,7 +205,8 @@ class Controller:
                              p["w_stop"], p["w_joint"], p["w_coll"], p["w_self"], p["w_dyn"],
                              p["B"], p["B_world"], p["B_self"], p["tau"], p["q_margin"],
                              int(p["iterations"]), int(p["seed"]), 0,
-                             int(p.get("max_plan_age", 0)))
+                             int(p.get("max_plan_age", 0)), p.get("w_manip", 0.0),
+                             p.get("manip_w0", 0.02))
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         h = C.c_void_p()

@@ -310,3 +310,42 @@ def test_full_size_sampled_rollouts(idx):
         for i, (n, h) in enumerate([(n, h) for n in range(len(ns)) for h in hs]):
             e = np.abs(gs[i, :ns_a] - sph[n, h]).max()
             assert e < 1e-5 and e < EPS_D / 4
+
+
+def test_manipulability_term_replay():
+    """C_manip of Eq. 5 on (w_manip = 10, w0 = 0.02): every output of two
+    replayed cycles of the one-arm workload and of the four-arm workload
+    (K = 64, H = 10) within the usual tolerances."""
+    from parity_utils import Replay
+    for sc in (S.config(1, w_manip=10.0), S.shrink(S.config(2, w_manip=10.0), K=64, H=10)):
+        R = Replay(sc)
+        for c in range(2):
+            d = _dump(sc)
+            got, gc, ga, gs, exp = R.cycle(d)
+            _check_cycle(R, got, gc, ga, gs, exp, d)
+            R.advance(exp)
+
+
+def test_several_iterations_per_cycle_replay():
+    """Three optimisation iterations per cycle (Algorithm 1's K^(i); the
+    paper's M setting uses 5), with C_manip on: the iteration index enters the
+    Philox counter, mean and covariance carry from iteration to iteration, U_*
+    and the costs are the last iteration's.  A large lambda (1e4: near-uniform
+    weights) keeps the FP32 / FP64 difference of one iteration's mean from
+    being amplified by the next iteration's softmax, so the single-iteration
+    tolerances apply to the end of the cycle."""
+    from parity_utils import Replay
+    sc = S.shrink(S.config(2, iterations=3, w_manip=10.0, lam=1e4), K=64, H=10)
+    R = Replay(sc)
+    for c in range(2):
+        d = _dump(sc)
+        got, gc, ga, gs, exp = R.cycle(d)
+        _check_cycle(R, got, gc, ga, gs, exp, d)
+        R.advance(exp)
+    # the iterations do work: one iteration from the same state gives another mean
+    sc1 = S.shrink(S.config(2, iterations=1, w_manip=10.0, lam=1e4), K=64, H=10)
+    R1 = Replay(sc1)
+    got1 = R1.cycle(None)[0]
+    R3 = Replay(sc)
+    got3 = R3.cycle(None)[0]
+    assert np.abs(got1["mean_plan"] - got3["mean_plan"]).max() > 1e-3
