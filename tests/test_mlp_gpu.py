@@ -105,8 +105,9 @@ def test_forward_matches_the_fp64_oracle(in_dim, width, layers, rows):
 def test_fused_forward_agrees_with_the_training_forward():
     """The training step's layer-by-layer forward and the fused inference
     kernel compute the same network: the loss from the former equals the loss
-    of the latter's outputs up to summation order and the fused kernel's fast
-    exponential (rare BF16 rounding flips of the activations)."""
+    of the latter's outputs up to summation order and the fused kernel's
+    hardware tanh in SiLU (activation errors of the order of their BF16
+    rounding)."""
     import torch
     rng = np.random.default_rng(8)
     net, _ = _net()
@@ -116,7 +117,7 @@ def test_fused_forward_agrees_with_the_training_forward():
     _, loss = net.grads(xd, td)
     y = net.forward(xd).cpu().numpy().astype(np.float64)
     ref = np.mean((y - np.clip(t, -0.1, 0.3)) ** 2)
-    assert abs(loss - ref) <= 1e-3 * ref
+    assert abs(loss - ref) <= 1e-2 * ref
 
 
 def test_adam_training_reduces_the_loss():
