@@ -4,9 +4,10 @@
 //
 // Work unit (tile): (arm, step h, 32 nsub samples).  A persistent grid of
 // 256-thread blocks takes tiles from an atomic counter and stages the tile's
-// inputs (world at the step's time, the neighbours' plan spheres at step h,
-// the arm's constants) once; the samples then pass through in sub-batches of
-// 32.  Warp g of a block owns sphere group g (spheres [g*spg, (g+1)*spg),
+// inputs (world at the step's time, the neighbours' plan spheres at step h --
+// copied from the plan board by the bulk-copy engine, cp.async.bulk on an
+// mbarrier -- and the arm's constants) once; the samples then pass through in
+// sub-batches of 32.  Warp g of a block owns sphere group g (spheres [g*spg, (g+1)*spg),
 // spg = ceil(N_S / 8)) of the sub-batch's 32 rollout steps, one sample per
 // lane; its centres stay in registers.  The samples per tile, the tile order
 // and the resident blocks per SM are chosen at run time (mrs_autotune).
@@ -27,6 +28,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 
 // build-time knob of the pre-test loop
 #ifndef MRS_PRETEST_UNROLL
@@ -85,6 +87,25 @@ __device__ __forceinline__ float min3(float a, float b, float c)
     float d;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
+}
+
+// mbarrier arrive with an expected transaction count (the bytes of the bulk
+// copies that complete the phase)
+__device__ __forceinline__ void fused_bar_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(tc::smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> shared (16-byte aligned addresses, size a multiple of
+// 16) completing on mbarrier bar
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(tc::smem_u32(dst_smem)), "l"(__cvta_generic_to_global(src_gmem)), "r"(bytes),
+                   "r"(tc::smem_u32(bar))
+                 : "memory");
 }
 
 // store one other sphere (and its |p|^2 - r^2) in every layout the passes read
@@ -434,7 +455,13 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     // both minima buffers start at +inf; every sub-batch's cost stage resets
     // the entries it used, so they are +inf again when reused
     for (int k = threadIdx.x; k < 2 * kRedStride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
-    if (threadIdx.x == 0) s_tile[0] = atomicAdd(&D.work[iter], 1);
+    __shared__ __align__(8) uint64_t s_bar;   // completion of the plan-slice copies
+    uint32_t bar_phase = 0;
+    if (threadIdx.x == 0) {
+        s_tile[0] = atomicAdd(&D.work[iter], 1);
+        tc::mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
 
     int buf = 0;   // sub-batch parity
@@ -478,13 +505,25 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             }
             if (lane == 31) S.nb_start[nnb] = n_world + incl;
         }
-        // warp w stages the plan spheres at step h of neighbours w, w + 8, ...
-        for (int nb = g; nb < nnb; nb += kGroups) {
-            const int src = __fns(mask, 0, nb + 1);          // lane (= arm) of neighbour nb
-            const int start = n_world + __shfl_sync(0xffffffffu, incl - ns_i, src);
-            const ArmDev &Ai = D.arms[src];
-            const float4 *sp = D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns;
-            for (int k = lane; k < Ai.ns; k += 32) put_other(S, start + k, sp[k]);
+        // the neighbours' plan spheres at step h (one contiguous 16 N_S-byte
+        // run per neighbour on the board, time-major) are copied into their
+        // slots of S.other by the bulk-copy engine, issued by one thread
+        // against one mbarrier; meanwhile the block stages the world
+        const int n_plan = __shfl_sync(0xffffffffu, incl, 31);   // plan spheres of all neighbours
+        if (g == 0 && n_plan > 0) {
+            if (lane == 0) {
+                tc::fence_async_smem();   // the previous unit's generic reads come first
+                fused_bar_expect(&s_bar, (uint32_t)n_plan * 16u);
+            }
+            for (int nb = 0; nb < nnb; ++nb) {
+                const int src = __fns(mask, 0, nb + 1);          // lane (= arm) of neighbour nb
+                const int start = n_world + __shfl_sync(0xffffffffu, incl - ns_i, src);
+                if (lane == 0) {
+                    const ArmDev &Ai = D.arms[src];
+                    bulk_load(&S.other[start], D.board_sph + (Ai.off_hs >> 2) + (size_t)h * Ai.ns,
+                              (uint32_t)Ai.ns * 16u, &s_bar);
+                }
+            }
         }
         const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
         for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
@@ -499,6 +538,20 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         for (int k = threadIdx.x; k < A.n_self; k += blockDim.x)
             S.pairs[k] = D.self_pairs[A.self_off + k];
+        if (n_plan > 0) {
+            // bounded wait for the plan copies, then the derived layouts; if
+            // a copy did not land in time the block records the error, waits
+            // (bounded) for the copies still in flight and stops
+            const bool landed = tc::mbar_wait(&s_bar, bar_phase);
+            if (__syncthreads_or(!landed)) {
+                if (threadIdx.x == 0) atomicExch(D.err, 1);
+                tc::mbar_wait(&s_bar, bar_phase);
+                return;
+            }
+            bar_phase ^= 1u;
+            for (int k = threadIdx.x; k < n_plan; k += blockDim.x)
+                put_other(S, n_world + k, S.other[n_world + k]);
+        }
         __syncthreads();   // the unit's inputs are staged
         const int n_nb = nnb;
 
