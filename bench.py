@@ -221,35 +221,46 @@ def run_reference(args):
 
 def time_device(ctl, d_in, steps, warmup, flush, ws, local=0, sample_clocks=False):
     """Per-cycle CUDA-event times (ms) of device-resident cycles, L2 flushed
-    before each; also the per-stage times of every cycle."""
+    before each, with the cycle's graph as a user runs it (no timing nodes);
+    then the per-stage times from a second run of the same cycles with event
+    nodes between the stages."""
     import torch
     s = ctl.stream
-    ctl.enable_timing(True)
-    for _ in range(max(warmup, 3)):
-        ctl.step_device(d_in)
-    ctl.sync()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ktimes = []
-    barrier(ws)
-    torch.cuda.synchronize()
+
+    def loop(n, stages):
+        ctl.enable_timing(stages)
+        for _ in range(max(warmup, 3)):
+            ctl.step_device(d_in)
+        ctl.sync()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        kt = []
+        barrier(ws)
+        torch.cuda.synchronize()
+        for i in range(n):
+            with torch.cuda.stream(s):
+                flush.zero_()          # 256 MiB write: also covers the host's launch latency
+                starts[i].record(s)
+            ctl.step_device(d_in)
+            with torch.cuda.stream(s):
+                ends[i].record(s)
+            if stages:
+                kt.append(ctl.kernel_times())
+            else:
+                ends[i].synchronize()
+        torch.cuda.synchronize()
+        barrier(ws)
+        return [x.elapsed_time(y) for x, y in zip(starts, ends)], kt
+
     clk = ClockSampler(local) if sample_clocks else None
     if clk:
         clk.__enter__()
-    for i in range(steps):
-        with torch.cuda.stream(s):
-            flush.zero_()
-            starts[i].record(s)
-        ctl.step_device(d_in)
-        with torch.cuda.stream(s):
-            ends[i].record(s)
-        ktimes.append(ctl.kernel_times())
-    torch.cuda.synchronize()
+    step_ms, _ = loop(steps, False)
+    _, kt = loop(min(steps, 20), True)
     if clk:
         clk.__exit__()
-    barrier(ws)
     ctl.enable_timing(False)
-    return [a.elapsed_time(b) for a, b in zip(starts, ends)], np.asarray(ktimes), clk
+    return step_ms, np.asarray(kt), clk
 
 
 def time_e2e(ctls, sc, gp, gR, cycles, warmup, flush, ws, episode=50):
