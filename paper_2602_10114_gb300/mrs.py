@@ -273,23 +273,35 @@ class Controller:
                       _f32(goal_R[a]).ravel()]
         return np.concatenate(parts).astype(np.float32)
 
-    def step(self, q, qd, goal_p, goal_R):
-        """One control cycle with host inputs; returns a dict of host arrays."""
+    def _step_buffers(self):
+        """Input staging arrays, the arm-state array pointing at them, the
+        output arrays and the output struct: built once per controller."""
         A = len(self.sc.arms)
-        keep = []
+        sz = self.sizes
+        ins = [(np.zeros(a.dof, np.float32), np.zeros(a.dof, np.float32),
+                np.zeros(3, np.float32), np.zeros(9, np.float32)) for a in self.sc.arms]
         states = (MrsArmState * A)()
         for a in range(A):
-            arrs = [_f32(q[a]), _f32(qd[a]), _f32(goal_p[a]).ravel(), _f32(goal_R[a]).ravel()]
-            keep += arrs
-            states[a] = MrsArmState(*[_pf(x) for x in arrs])
-        sz = self.sizes
+            states[a] = MrsArmState(*[_pf(x) for x in ins[a]])
         out = dict(mean_plan=np.zeros(sz.hd, np.float32), plan_spheres=np.zeros(sz.hs, np.float32),
                    plan_q=np.zeros(sz.hd, np.float32), u_star=np.zeros(sz.d, np.float32),
                    dist_to_goal=np.zeros(A, np.float32), min_cost=np.zeros(A, np.float32))
         o = MrsStepOut(*[_pf(out[k]) for k in ("mean_plan", "plan_spheres", "plan_q", "u_star",
                                                "dist_to_goal", "min_cost")])
+        self._sbuf = (ins, states, out, o)
+        return self._sbuf
+
+    def step(self, q, qd, goal_p, goal_R):
+        """One control cycle with host inputs; returns a dict of host arrays
+        (fresh copies)."""
+        ins, states, out, o = getattr(self, "_sbuf", None) or self._step_buffers()
+        for a, (iq, iqd, ip, iR) in enumerate(ins):
+            iq[...] = q[a]
+            iqd[...] = qd[a]
+            ip[...] = np.reshape(goal_p[a], 3)
+            iR[...] = np.reshape(goal_R[a], 9)
         self._check(self.L.mrs_step(self.h, states, C.byref(o)), "step")
-        return out
+        return {k: v.copy() for k, v in out.items()}
 
     def step_device(self, d_input):
         """Enqueue one cycle with a device-resident packed input (torch float32
