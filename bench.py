@@ -438,8 +438,9 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
 
 def learned_pair_mode(args, flush, ws, dev):
     """Workload 5 with both learned clearances: the self-collision network and
-    the arm-pair network (asymmetric loss, fallback margin calibrated on
-    held-out pairs to a 1e-3 false-negative rate), trained on the device;
+    the arm-pair network (asymmetric loss, fallback margin calibrated on half
+    of the held-out pairs to a 7e-4 false-negative rate, so that the other
+    half stays within the 1e-3 target), trained on the device;
     throughput against exact mode, false negatives on held-out samples and on
     every rollout step of a cycle, skip fractions, cost deviation."""
     import torch
@@ -463,7 +464,7 @@ def learned_pair_mode(args, flush, ws, dev):
                                                epochs=8, lr=2e-3)
     pnet, pst = surrogate.train_pair_surrogate(ctl, 0, n_train=args.pair_samples, n_val=400_000,
                                                epochs=12, lr=1e-3, over_weight=32.0,
-                                               target_fn=1e-3)
+                                               target_fn=7e-4)
     train_s = time.perf_counter() - t0
     blob = ctl.save_state()
     ctl.step_device(d_in)
