@@ -162,8 +162,11 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out);
 /* Release everything the context allocated (not a bound workspace). */
 void mrs_destroy(mrs_ctx *ctx);
 
-/* One-line reason of the last failure on ctx ("" if none; a static string
- * if ctx is NULL). */
+/* One-line reason of the last failure on ctx ("" if none); with ctx NULL,
+ * the reason of the last failed mrs_create on this thread.  mrs_create
+ * returns MRS_EUNSUPPORTED when the rollout's shared-memory staging (world
+ * spheres + n_arms x the largest sphere count) exceeds the device's per-block
+ * limit, and mrs_set_world when a larger world would. */
 const char *mrs_last_error(const mrs_ctx *ctx);
 
 mrs_status mrs_query_sizes(const mrs_ctx *ctx, mrs_sizes *out);

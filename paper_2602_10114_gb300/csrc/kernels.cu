@@ -205,17 +205,18 @@ __global__ void k_prep(Params P, Dev D)
 // ---------------------------------------------------------------------------
 // SampleControls + integration (one block per (arm, 32 samples))
 
-__global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTile *tiles, int iter)
+__global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTile *tiles, int iter,
+                                                int smem_floats)
 {
     extern __shared__ float sm[];
     const SampleTile T = tiles[blockIdx.x];
     const ArmDev &A = D.arms[T.arm];
     const int d = A.dof, H = A.H, K = A.K, dd = d * d;
-    float *sL = sm;                 // [H][d][d]
-    float *sU = sL + H * dd;        // [H][d][32]: U, then the joint-limit terms
-    float *sS = sU + H * d * 32;    // [H][d][32]: stop terms
-    for (int i = threadIdx.x; i < H * dd; i += blockDim.x) sL[i] = D.L[A.off_hdd + i];
-    __syncthreads();
+    // the horizon in chunks of Hc steps that fit the block's shared memory
+    const int Hc = max(1, min(H, smem_floats / (dd + 2 * d * 32)));
+    float *sL = sm;                 // [Hc][d][d]
+    float *sU = sL + Hc * dd;       // [Hc][d][32]: U, then the joint-limit terms
+    float *sS = sU + Hc * d * 32;   // [Hc][d][32]: stop terms
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = T.n0 + lane;
@@ -223,53 +224,71 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
     const long long cycle = *D.cycle;
     const float *mu = D.mu + A.off_hd;
     float *eps_out = D.eps + A.off_khd;
-
-    for (int h = warp; h < H; h += blockDim.x >> 5) {
-        float z[kMaxDof];
-        normals(P.seed, T.arm, cycle, iter, n, h, d, z);
-        const float *Lh = sL + h * dd;
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) {
-            if (j < d) {
-                float e = 0.f;
-#pragma unroll
-                for (int c = 0; c <= j; ++c) e = __fmaf_rn(Lh[j * d + c], z[c], e);
-                if (P.zero_noise) e = 0.f;
-                sU[(h * d + j) * 32 + lane] = __fadd_rn(mu[h * d + j], e);
-                if (valid) eps_out[(long long)(h * d + j) * K + n] = e;
-            }
-        }
-    }
-    __syncthreads();
-
-    // Integration, one thread per (sample, joint), sequential over the horizon.
     const float *in = D.input + A.off_in;
     float *traj = D.traj + A.off_khd;
-    for (int t = threadIdx.x; t < 32 * d; t += blockDim.x) {
-        const int l = t & 31, j = t >> 5;
-        const int nn = T.n0 + l;
-        float q = in[j], qd = in[d + j];
-        const float hi = __fsub_rn(A.q_hi[j], P.q_margin), lo = __fadd_rn(A.q_lo[j], P.q_margin);
-        for (int h = 0; h < H; ++h) {
-            const int idx = (h * d + j) * 32 + l;
-            integrate(q, qd, sU[idx], P.dt);
-            if (nn < K) traj[(long long)(h * d + j) * K + nn] = q;
-            sS[idx] = hinge2(__fsub_rn(fabsf(qd), A.qd_max[j]));
-            sU[idx] = __fadd_rn(hinge2(__fsub_rn(q, hi)), hinge2(__fsub_rn(lo, q)));
-        }
-    }
-    __syncthreads();
     float *lim = D.stage_lim + A.off_kh;
-    for (int t = threadIdx.x; t < 32 * H; t += blockDim.x) {
-        const int l = t & 31, h = t >> 5;
-        const int nn = T.n0 + l;
-        if (nn >= K) continue;
-        float s = 0.f, jc = 0.f;
-        for (int j = 0; j < d; ++j) {
-            s = __fadd_rn(s, sS[(h * d + j) * 32 + l]);
-            jc = __fadd_rn(jc, sU[(h * d + j) * 32 + l]);
+
+    // integration state of this thread's (sample, joint), carried across chunks
+    const int ti = threadIdx.x, il = ti & 31, ij = ti >> 5;
+    const bool integrates = ti < 32 * d;
+    float q = 0.f, qd = 0.f, hi = 0.f, lo = 0.f;
+    if (integrates) {
+        q = in[ij];
+        qd = in[d + ij];
+        hi = __fsub_rn(A.q_hi[ij], P.q_margin);
+        lo = __fadd_rn(A.q_lo[ij], P.q_margin);
+    }
+
+    for (int h0 = 0; h0 < H; h0 += Hc) {
+        const int nh = min(Hc, H - h0);
+        for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
+            sL[i] = D.L[A.off_hdd + (long long)h0 * dd + i];
+        __syncthreads();
+
+        for (int hl = warp; hl < nh; hl += blockDim.x >> 5) {
+            const int h = h0 + hl;
+            float z[kMaxDof];
+            normals(P.seed, T.arm, cycle, iter, n, h, d, z);
+            const float *Lh = sL + hl * dd;
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j) {
+                if (j < d) {
+                    float e = 0.f;
+#pragma unroll
+                    for (int c = 0; c <= j; ++c) e = __fmaf_rn(Lh[j * d + c], z[c], e);
+                    if (P.zero_noise) e = 0.f;
+                    sU[(hl * d + j) * 32 + lane] = __fadd_rn(mu[h * d + j], e);
+                    if (valid) eps_out[(long long)(h * d + j) * K + n] = e;
+                }
+            }
         }
-        lim[(long long)h * K + nn] = __fmaf_rn(P.w_joint, jc, __fmul_rn(P.w_stop, s));
+        __syncthreads();
+
+        // Integration, one thread per (sample, joint), sequential over the horizon.
+        if (integrates) {
+            const int nn = T.n0 + il;
+            for (int hl = 0; hl < nh; ++hl) {
+                const int h = h0 + hl;
+                const int idx = (hl * d + ij) * 32 + il;
+                integrate(q, qd, sU[idx], P.dt);
+                if (nn < K) traj[(long long)(h * d + ij) * K + nn] = q;
+                sS[idx] = hinge2(__fsub_rn(fabsf(qd), A.qd_max[ij]));
+                sU[idx] = __fadd_rn(hinge2(__fsub_rn(q, hi)), hinge2(__fsub_rn(lo, q)));
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 32 * nh; t += blockDim.x) {
+            const int l = t & 31, hl = t >> 5;
+            const int nn = T.n0 + l;
+            if (nn >= K) continue;
+            float s = 0.f, jc = 0.f;
+            for (int j = 0; j < d; ++j) {
+                s = __fadd_rn(s, sS[(hl * d + j) * 32 + l]);
+                jc = __fadd_rn(jc, sU[(hl * d + j) * 32 + l]);
+            }
+            lim[(long long)(h0 + hl) * K + nn] = __fmaf_rn(P.w_joint, jc, __fmul_rn(P.w_stop, s));
+        }
+        __syncthreads();   // the chunk's shared memory is reused by the next
     }
 }
 
@@ -687,7 +706,8 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
     mark();
     for (int it = 0; it < P.iterations; ++it) {
         const int last = (it == P.iterations - 1);
-        k_sample<<<L.n_sample_tiles, 512, L.smem_sample, s>>>(P, D, L.sample_tiles, it);
+        k_sample<<<L.n_sample_tiles, 512, L.smem_sample, s>>>(P, D, L.sample_tiles, it,
+                                                              (int)(L.smem_sample / sizeof(float)));
         if (P.w_manip > 0.f)
             k_manip<<<(L.total_kh + 127) / 128, 128, 0, s>>>(P, D, L.total_kh);
         mark();

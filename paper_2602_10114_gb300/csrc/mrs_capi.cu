@@ -54,6 +54,7 @@ struct mrs_ctx {
     // rollout launch shape (mrs_set_rollout_shape / mrs_autotune)
     int tile_samples = 32, blocks_per_sm = 0, tile_order = 0, max_blocks_per_sm = 1;
     bool has_input = false;
+    int smem_optin = 0;
     // arm-pair surrogate: (arm, neighbour, network) slots, their launch groups
     // and the prediction buffer ([sum K*H][A] floats, allocated on first use)
     struct PairSlot { int a, b; mrs_mlp *net; };
@@ -64,6 +65,8 @@ struct mrs_ctx {
 };
 
 static const char *g_noctx = "null context";
+// reason of the last failed mrs_create on this thread (mrs_last_error(NULL))
+static thread_local std::string g_create_err;
 
 static mrs_status fail(mrs_ctx *c, mrs_status s, const std::string &m)
 {
@@ -322,8 +325,12 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     if (!out) return MRS_EINVAL;
     *out = nullptr;
     std::string why;
+    g_create_err.clear();
     mrs_status st = validate(cfg, why);
-    if (st != MRS_OK) return st;
+    if (st != MRS_OK) {
+        g_create_err = why;
+        return st;
+    }
     mrs_ctx *ctx = new (std::nothrow) mrs_ctx();
     if (!ctx) return MRS_ENOMEM;
     ctx->A = cfg->n_arms;
@@ -424,7 +431,9 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     size_t sp = 0, ss = 0, st2 = 0;
     for (auto &A : ctx->arms) {
         sp = std::max(sp, sizeof(float) * (size_t)A.H * (2 * A.dof * A.dof + A.dof));
-        ss = std::max(ss, sizeof(float) * (size_t)A.H * (A.dof * A.dof + 2 * A.dof * 32));
+        // k_sample: the whole horizon, or chunks of it within 96 KB
+        const size_t per_h = sizeof(float) * (size_t)(A.dof * A.dof + 2 * A.dof * 32);
+        ss = std::max(ss, std::min((size_t)A.H * per_h, std::max(per_h, (size_t)96 * 1024)));
         st2 = std::max(st2, sizeof(float) * (size_t)A.H * 2 * A.dof);
     }
     L.smem_prep = sp;
@@ -451,13 +460,31 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         mrs_destroy(ctx);
         return MRS_ENOMEM;
     }
-    int dev = 0;
+    int dev = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        configure_kernels(L) != cudaSuccess) {
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
         mrs_destroy(ctx);
+        g_create_err = "no CUDA device";
         return MRS_ECUDA;
     }
+    // the rollout stages the world and every neighbour's plan slice of a step
+    // in shared memory: (world spheres + n_arms x the largest sphere count)
+    // must fit one block
+    if (L.smem_rollout > (size_t)smem_optin) {
+        mrs_destroy(ctx);
+        g_create_err = "the rollout's shared memory (" + std::to_string(L.smem_rollout) +
+                       " bytes for n_arms x the largest sphere count) exceeds the device's " +
+                       std::to_string(smem_optin) + " bytes per block";
+        return MRS_EUNSUPPORTED;
+    }
+    if (configure_kernels(L) != cudaSuccess) {
+        mrs_destroy(ctx);
+        g_create_err = "kernel configuration failed";
+        return MRS_ECUDA;
+    }
+    ctx->smem_optin = smem_optin;
     ctx->max_blocks_per_sm = rollout_blocks_per_sm(L.smem_rollout);
     set_rollout_grid(ctx);
     *out = ctx;
@@ -482,7 +509,11 @@ void mrs_destroy(mrs_ctx *ctx)
     delete ctx;
 }
 
-const char *mrs_last_error(const mrs_ctx *ctx) { return ctx ? ctx->err.c_str() : g_noctx; }
+const char *mrs_last_error(const mrs_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_create_err.empty() ? g_noctx : g_create_err.c_str();
+}
 
 mrs_status mrs_query_sizes(const mrs_ctx *ctx, mrs_sizes *out)
 {
@@ -576,11 +607,19 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
     if (st != MRS_OK) return st;
     if (n_spheres > ctx->P.world_cap || n_aabbs > ctx->P.aabb_cap) {
         // grow the rollout's shared-memory world capacity (powers of two)
-        while (ctx->P.world_cap < n_spheres) ctx->P.world_cap *= 2;
-        while (ctx->P.aabb_cap < n_aabbs) ctx->P.aabb_cap *= 2;
-        ctx->P.world_cap = std::min(ctx->P.world_cap, MRS_MAX_WORLD_SPHERES);
-        ctx->P.aabb_cap = std::min(ctx->P.aabb_cap, MRS_MAX_AABBS);
-        ctx->L.smem_rollout = rollout_smem_bytes(ctx->P, ctx->A);
+        Params grown = ctx->P;
+        while (grown.world_cap < n_spheres) grown.world_cap *= 2;
+        while (grown.aabb_cap < n_aabbs) grown.aabb_cap *= 2;
+        grown.world_cap = std::min(grown.world_cap, MRS_MAX_WORLD_SPHERES);
+        grown.aabb_cap = std::min(grown.aabb_cap, MRS_MAX_AABBS);
+        const size_t need = rollout_smem_bytes(grown, ctx->A);
+        if (need > (size_t)ctx->smem_optin)
+            return fail(ctx, MRS_EUNSUPPORTED,
+                        "the world does not fit the rollout's shared memory with this many arms "
+                        "and spheres");
+        ctx->P.world_cap = grown.world_cap;
+        ctx->P.aabb_cap = grown.aabb_cap;
+        ctx->L.smem_rollout = need;
         CK(configure_rollout(ctx->L), "rollout shared memory");
         ctx->max_blocks_per_sm = rollout_blocks_per_sm(ctx->L.smem_rollout);
         set_rollout_grid(ctx);

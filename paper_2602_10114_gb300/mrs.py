@@ -212,7 +212,7 @@ class Controller:
         h = C.c_void_p()
         st = self.L.mrs_create(C.byref(self.cfg), C.c_void_p(self.stream.cuda_stream), C.byref(h))
         if st != 0:
-            raise MrsError(st, "mrs_create")
+            raise MrsError(st, "mrs_create: " + self.L.mrs_last_error(None).decode())
         self.h = h
         self.sizes = MrsSizes()
         self._check(self.L.mrs_query_sizes(self.h, C.byref(self.sizes)), "query_sizes")
