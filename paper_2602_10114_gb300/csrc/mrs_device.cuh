@@ -212,6 +212,21 @@ __device__ __forceinline__ void frame_step(Frame &F, float q, float4 dh, float2 
     }
 }
 
+// the same step from the sine and cosine of q + theta computed beforehand
+__device__ __forceinline__ void frame_step_sc(Frame &F, float s, float c, float4 dh, float2 tw)
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float r0 = F.R[3 * r], r1 = F.R[3 * r + 1], r2 = F.R[3 * r + 2];
+        const float u = __fmaf_rn(r1, s, __fmul_rn(r0, c));
+        const float v = __fmaf_rn(r1, c, -__fmul_rn(r0, s));
+        F.R[3 * r] = u;
+        F.R[3 * r + 1] = __fmaf_rn(r2, tw.x, __fmul_rn(v, tw.y));
+        F.R[3 * r + 2] = __fmaf_rn(r2, tw.y, -__fmul_rn(v, tw.x));
+        F.t[r] = __fmaf_rn(dh.y, r2, __fmaf_rn(dh.x, u, F.t[r]));
+    }
+}
+
 __device__ __forceinline__ float3 sphere_centre(const Frame &F, float4 p)
 {
     float3 c;

@@ -57,6 +57,7 @@ struct RolloutSmem {
     unsigned short *cand;   // [kGroups][cand_cap] per-warp candidate lists
     int cand_cap;
     float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
+    float2 *sc;             // [dof][32] sin, cos of q_j + theta_j of the sub-batch's samples
 };
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -272,7 +273,6 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     const int d = A.dof, K = A.K;
     const int s0 = g * SPG;
     const int cnt = max(0, min(SPG, A.ns - s0));
-    const float *qh = D.traj + A.off_khd + (long long)h * d * K + (valid ? n : 0);
 
     // DH chain up to the last frame this group needs; the last warp always
     // runs to the end effector for the pose cost.  Own centres are kept as
@@ -291,7 +291,8 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             if (s < cnt) {
                 const int fs = S.frame[s0 + s];
                 while (f < fs) {
-                    frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+                    const float2 sc = S.sc[f * 32 + lane];
+                    frame_step_sc(F, sc.x, sc.y, A.dh[f], A.twist[f]);
                     ++f;
                 }
                 const float3 c = sphere_centre(F, S.sph[s0 + s]);
@@ -307,7 +308,8 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     }
     if (g == kGroups - 1) {
         while (f < d) {
-            frame_step(F, qh[(long long)f * K], A.dh[f], A.twist[f]);
+            const float2 sc = S.sc[f * 32 + lane];
+            frame_step_sc(F, sc.x, sc.y, A.dh[f], A.twist[f]);
             ++f;
         }
         const float *in = D.input + A.off_in;
@@ -441,6 +443,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
         S.nb_arm = (int *)p;       p += align16(sizeof(int) * MRS_MAX_ARMS);
         S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
+        S.sc = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof * 32);
         S.cand = (unsigned short *)p;
         S.cand_cap = (int)((n_other + 7) & ~size_t(7));
         p += align16(sizeof(unsigned short) * kGroups * S.cand_cap);
@@ -561,6 +564,16 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             Sb.red = S.red + buf * kRedStride;
             const int n = T.n0 + sb * 32 + lane;
             const bool valid = n < A.K;
+            // sine and cosine of every joint angle of the sub-batch, once
+            // (warp j takes joint j): the sphere groups' kinematic chains
+            // share them
+            for (int j = g; j < A.dof; j += kGroups) {
+                float sn, cs;
+                const float qj = D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
+                sincosf(__fadd_rn(qj, A.dh[j].w), &sn, &cs);
+                S.sc[j * 32 + lane] = make_float2(sn, cs);
+            }
+            __syncthreads();
             float pose = 0.f;
             switch (A.spg) {
                 case 1: rollout_group<1>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
