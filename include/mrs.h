@@ -307,7 +307,8 @@ typedef struct {
 mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
 
-/* Autotuner: times every shape of the grid {32, 64, 128} samples x 1 ..
+/* Autotuner: times every shape of the grid {32, 64, 96, 128, 192, 256}
+ * samples x 1 ..
  * max resident blocks per SM x {step-major, arm-major} over `reps` control
  * cycles each (rollout stage, CUDA events, median) on the context's current
  * inputs, and keeps the fastest.  The controller state is saved before and

@@ -1399,7 +1399,7 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     std::vector<mrs_rollout_shape> tried;
     mrs_rollout_shape keep{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
     float best_ms = INFINITY;
-    for (int ts : {32, 64, 128}) {
+    for (int ts : {32, 64, 96, 128, 192, 256}) {
         for (int bps = 1; bps <= ctx->max_blocks_per_sm; ++bps) {
             for (int order = 0; order < 2; ++order) {
                 if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) return st;
