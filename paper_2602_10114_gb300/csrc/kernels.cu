@@ -152,10 +152,12 @@ __global__ void k_prep(Params P, Dev D)
     // kinematic constants and the board's published distances
     const bool shift = cycle > 0;
     const float s2 = P.sigma_init * P.sigma_init;
+#pragma unroll 4
     for (int i = threadIdx.x; i < H * dd; i += blockDim.x) {
         const int h = i / dd, k = i % dd;
         sS[i] = !shift ? Sig[i] : (h + 1 < H ? Sig[i + dd] : ((k % (d + 1) == 0) ? s2 : 0.f));
     }
+#pragma unroll 4
     for (int i = threadIdx.x; i < H * d; i += blockDim.x) {
         const int h = i / d;
         sM[i] = (shift && h + 1 < H) ? mu[i + d] : mu[i];
@@ -303,13 +305,13 @@ __global__ void __launch_bounds__(256) k_costs(Params P, Dev D, const CostTile *
     if (n >= A.K) return;
     const float *st = D.stage + A.off_kh;
     float s = 0.f, c = 0.f;
-    for (int h0 = 0; h0 < A.H; h0 += 8) {
-        float v[8];
+    for (int h0 = 0; h0 < A.H; h0 += 32) {
+        float v[32];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)       // loads first, then the ordered sum
+        for (int u = 0; u < 32; ++u)      // loads first (one round trip), then the ordered sum
             v[u] = (h0 + u < A.H) ? st[(long long)(h0 + u) * A.K + n] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 32; ++u) {
             if (h0 + u >= A.H) break;
             const float gh = (P.gamma == 1.f) ? 1.f : powf(P.gamma, (float)(h0 + u));
             const float y = __fsub_rn(__fmul_rn(gh, v[u]), c);
@@ -356,6 +358,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTil
     // minimum cost and its lowest index
     float bv = kInf;
     int bi = 0x7fffffff;
+#pragma unroll 4
     for (int n = threadIdx.x; n < K; n += NT) {
         const float v = C[n];
         if (v < bv || (v == bv && n < bi)) { bv = v; bi = n; }
@@ -389,6 +392,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTil
 #pragma unroll
     for (int k = 0; k < kM2; ++k) m2[k] = 0.f;
     const float *eps = D.eps + A.off_khd + (long long)h * d * K;
+#pragma unroll 2
     for (int n = threadIdx.x; n < K; n += NT) {
         const float w = expf(-__fmul_rn(__fsub_rn(C[n], beta), inv_lambda));
         z = __fadd_rn(z, w);
@@ -702,7 +706,7 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
                         : cudaEventRecord(events[ev++], s);
     };
     mark();
-    k_prep<<<L.n_arms, 128, L.smem_prep, s>>>(P, D);
+    k_prep<<<L.n_arms, 512, L.smem_prep, s>>>(P, D);
     mark();
     for (int it = 0; it < P.iterations; ++it) {
         const int last = (it == P.iterations - 1);
