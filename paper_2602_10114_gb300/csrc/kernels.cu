@@ -126,18 +126,8 @@ __device__ __forceinline__ void cholesky_unrolled(int d, const float *S, float *
 __global__ void k_prep(Params P, Dev D)
 {
     extern __shared__ float sm[];
-    const int a = blockIdx.x;
+    const int a = blockIdx.x, t = threadIdx.x;
     const ArmDev &A = D.arms[a];
-    if (A.external) {   // optimised elsewhere: only the tile counters
-        if (a == 0)
-            for (int i = threadIdx.x; i < P.iterations; i += blockDim.x) D.work[i] = 0;
-        return;
-    }
-    const int d = A.dof, H = A.H, dd = d * d;
-    const long long cycle = *D.cycle;
-    float *Sig = D.Sigma + A.off_hdd;
-    float *mu = D.mu + A.off_hd;
-    float *sS = sm, *sL = sm + H * dd, *sM = sm + 2 * H * dd;
     __shared__ float s_in[2 * kMaxDof + 12];
     __shared__ float4 s_dh[kMaxDof];
     __shared__ float2 s_tw[kMaxDof];
@@ -146,25 +136,12 @@ __global__ void k_prep(Params P, Dev D)
     __shared__ int s_bvalid[MRS_MAX_ARMS];   // usable: published and fresh enough
     __shared__ float e_self;
 
-    // one parallel wave of loads: the shifted distribution (Shift, Sec. III-A:
-    // phi_h <- phi_{h+1}, the last step keeps its mean and restarts from
-    // sigma_init^2 I; not before the first cycle), the sensed input, the arm's
-    // kinematic constants and the board's published distances
-    const bool shift = cycle > 0;
-    const float s2 = P.sigma_init * P.sigma_init;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < H * dd; i += blockDim.x) {
-        const int h = i / dd, k = i % dd;
-        sS[i] = !shift ? Sig[i] : (h + 1 < H ? Sig[i + dd] : ((k % (d + 1) == 0) ? s2 : 0.f));
-    }
-#pragma unroll 4
-    for (int i = threadIdx.x; i < H * d; i += blockDim.x) {
-        const int h = i / d;
-        sM[i] = (shift && h + 1 < H) ? mu[i + d] : mu[i];
-    }
-    const int t = threadIdx.x;
-    if (t < 2 * d + 12) s_in[t] = D.input[A.off_in + t];
-    if (t < d) {
+    // first wave of loads, none depending on another: the cycle, the arm's
+    // header and kinematic constants, the board's published distances
+    const long long cycle = *D.cycle;
+    const int external = A.external, d = A.dof, H = A.H, dd = d * d;
+    const int off_hdd = A.off_hdd, off_hd = A.off_hd, off_in = A.off_in;
+    if (t < kMaxDof) {
         s_dh[t] = A.dh[t];
         s_tw[t] = A.twist[t];
     }
@@ -176,6 +153,27 @@ __global__ void k_prep(Params P, Dev D)
     }
     if (a == 0)   // rollout tile counters of this cycle's iterations
         for (int i = t; i < P.iterations; i += blockDim.x) D.work[i] = 0;
+    if (external) return;   // optimised elsewhere (uniform over the block)
+    float *Sig = D.Sigma + off_hdd;
+    float *mu = D.mu + off_hd;
+    float *sS = sm, *sL = sm + H * dd, *sM = sm + 2 * H * dd;
+
+    // second wave: the shifted distribution (Shift, Sec. III-A: phi_h <-
+    // phi_{h+1}, the last step keeps its mean and restarts from
+    // sigma_init^2 I; not before the first cycle) and the sensed input
+    const bool shift = cycle > 0;
+    const float s2 = P.sigma_init * P.sigma_init;
+#pragma unroll 4
+    for (int i = t; i < H * dd; i += blockDim.x) {
+        const int h = i / dd, k = i % dd;
+        sS[i] = !shift ? Sig[i] : (h + 1 < H ? Sig[i + dd] : ((k % (d + 1) == 0) ? s2 : 0.f));
+    }
+#pragma unroll 4
+    for (int i = t; i < H * d; i += blockDim.x) {
+        const int h = i / d;
+        sM[i] = (shift && h + 1 < H) ? mu[i + d] : mu[i];
+    }
+    if (t < 2 * d + 12) s_in[t] = D.input[off_in + t];
     __syncthreads();
     if (shift) {
         for (int i = t; i < H * dd; i += blockDim.x) Sig[i] = sS[i];
@@ -196,7 +194,7 @@ __global__ void k_prep(Params P, Dev D)
         D.e_now[a] = e_self;
     }
     __syncthreads();
-    for (int i = t; i < H * dd; i += blockDim.x) D.L[A.off_hdd + i] = sL[i];
+    for (int i = t; i < H * dd; i += blockDim.x) D.L[off_hdd + i] = sL[i];
     // Priority of every neighbour with a published plan (Sec. IV-B), from the
     // own sensed distance and the neighbour's published one.
     for (int i = t; i < P.n_arms; i += blockDim.x)
@@ -212,39 +210,45 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
 {
     extern __shared__ float sm[];
     const SampleTile T = tiles[blockIdx.x];
+    const long long cycle = *D.cycle;
     const ArmDev &A = D.arms[T.arm];
     const int d = A.dof, H = A.H, K = A.K, dd = d * d;
+    const int off_hdd = A.off_hdd, off_hd = A.off_hd;
     // the horizon in chunks of Hc steps that fit the block's shared memory
-    const int Hc = max(1, min(H, smem_floats / (dd + 2 * d * 32)));
+    const int Hc = max(1, min(H, smem_floats / (dd + d + 2 * d * 32)));
     float *sL = sm;                 // [Hc][d][d]
-    float *sU = sL + Hc * dd;       // [Hc][d][32]: U, then the joint-limit terms
+    float *sMu = sL + Hc * dd;      // [Hc][d]
+    float *sU = sMu + Hc * d;       // [Hc][d][32]: U, then the joint-limit terms
     float *sS = sU + Hc * d * 32;   // [Hc][d][32]: stop terms
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = T.n0 + lane;
     const bool valid = n < K;
-    const long long cycle = *D.cycle;
-    const float *mu = D.mu + A.off_hd;
     float *eps_out = D.eps + A.off_khd;
     const float *in = D.input + A.off_in;
     float *traj = D.traj + A.off_khd;
     float *lim = D.stage_lim + A.off_kh;
 
-    // integration state of this thread's (sample, joint), carried across chunks
+    // integration state and constants of this thread's (sample, joint),
+    // carried across chunks; loaded in the same wave as the first chunk
     const int ti = threadIdx.x, il = ti & 31, ij = ti >> 5;
     const bool integrates = ti < 32 * d;
-    float q = 0.f, qd = 0.f, hi = 0.f, lo = 0.f;
+    float q = 0.f, qd = 0.f, hi = 0.f, lo = 0.f, vmax = 0.f;
     if (integrates) {
         q = in[ij];
         qd = in[d + ij];
         hi = __fsub_rn(A.q_hi[ij], P.q_margin);
         lo = __fadd_rn(A.q_lo[ij], P.q_margin);
+        vmax = A.qd_max[ij];
     }
 
     for (int h0 = 0; h0 < H; h0 += Hc) {
         const int nh = min(Hc, H - h0);
+#pragma unroll 4
         for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
-            sL[i] = D.L[A.off_hdd + (long long)h0 * dd + i];
+            sL[i] = D.L[off_hdd + (long long)h0 * dd + i];
+        for (int i = threadIdx.x; i < nh * d; i += blockDim.x)
+            sMu[i] = D.mu[off_hd + h0 * d + i];
         __syncthreads();
 
         for (int hl = warp; hl < nh; hl += blockDim.x >> 5) {
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
 #pragma unroll
                     for (int c = 0; c <= j; ++c) e = __fmaf_rn(Lh[j * d + c], z[c], e);
                     if (P.zero_noise) e = 0.f;
-                    sU[(hl * d + j) * 32 + lane] = __fadd_rn(mu[h * d + j], e);
+                    sU[(hl * d + j) * 32 + lane] = __fadd_rn(sMu[hl * d + j], e);
                     if (valid) eps_out[(long long)(h * d + j) * K + n] = e;
                 }
             }
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
                 const int idx = (hl * d + ij) * 32 + il;
                 integrate(q, qd, sU[idx], P.dt);
                 if (nn < K) traj[(long long)(h * d + ij) * K + nn] = q;
-                sS[idx] = hinge2(__fsub_rn(fabsf(qd), A.qd_max[ij]));
+                sS[idx] = hinge2(__fsub_rn(fabsf(qd), vmax));
                 sU[idx] = __fadd_rn(hinge2(__fsub_rn(q, hi)), hinge2(__fsub_rn(lo, q)));
             }
         }
@@ -472,68 +476,115 @@ __global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTil
 // ToPlan + Publish (one block per arm): integrate the updated mean from the
 // sensed state, kinematics of every sphere at every step, into the board.
 // The last block to finish advances the cycle counter and the world clock.
+//
+// Latency layout: every global read is issued in two waves (the arm's
+// constants with its header, then the mean, the sensed state, the cycle and
+// the sensed distance); the sines and cosines of q_h + theta are taken in
+// parallel, one (step, joint) per thread, so that the kinematics chains run
+// from shared memory only.  frame_step_sc from sincosf(q + theta) is the
+// rollout's frame_step, so a zero-noise rollout still reproduces the plan
+// bit for bit.
 
-__global__ void k_toplan(Params P, Dev D, int *done_counter)
+__global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_counter)
 {
-    extern __shared__ float sq[];   // [H][d] plan joints, then [H][d] mean
-    const int a = blockIdx.x;
+    extern __shared__ float sq[];   // [H][d] plan joints, mean, sin(q + theta), cos(q + theta)
+    __shared__ float4 s_sph[kMaxSpheres];
+    __shared__ int s_frame[kMaxSpheres];
+    __shared__ float4 s_dh[kMaxDof];
+    __shared__ float2 s_tw[kMaxDof];
+    __shared__ float s_base[12];
+    __shared__ float s_in[2 * kMaxDof];
+    __shared__ long long s_cycle;
+    __shared__ float s_e;
+    const int a = blockIdx.x, t = threadIdx.x;
     const ArmDev &A = D.arms[a];
-    const int d = A.dof, H = A.H, ns = A.ns;
+    // wave 1: header and constants (fixed extents, no dependence on the header)
+    const int d = A.dof, H = A.H, ns = A.ns, off_hd = A.off_hd, off_in = A.off_in;
     const bool local = !A.external;   // external arms keep the plan they were given
-    float *smu = sq + H * d;
-    const float *mu = D.mu + A.off_hd;
-    const float *in = D.input + A.off_in;
-    if (local)
-        for (int i = threadIdx.x; i < H * d; i += blockDim.x) smu[i] = mu[i];
-    __syncthreads();
-    for (int j = threadIdx.x; local && j < d; j += blockDim.x) {
-        float q = in[j], qd = in[d + j];
-        for (int h = 0; h < H; ++h) {
-            integrate(q, qd, smu[h * d + j], P.dt);
-            sq[h * d + j] = q;
-        }
+    if (t < kMaxSpheres) {
+        s_sph[t] = A.sph[t];
+        s_frame[t] = A.frame[t];
+    }
+    if (t < kMaxDof) {
+        s_dh[t] = A.dh[t];
+        s_tw[t] = A.twist[t];
+    }
+    if (t < 9) s_base[t] = A.base_R[t];
+    else if (t < 12) s_base[t] = A.base_t[t - 9];
+    const int Hd = H * d;
+    float *smu = sq + Hd, *ssn = sq + 2 * Hd, *scs = sq + 3 * Hd;
+    // wave 2: mean, sensed state, cycle and sensed distance
+    if (local) {
+        const float *mu = D.mu + off_hd;
+#pragma unroll 4
+        for (int i = t; i < Hd; i += blockDim.x) smu[i] = mu[i];
+        if (t < 2 * d) s_in[t] = D.input[off_in + t];
+    }
+    if (t == 0) {
+        s_cycle = *D.cycle;
+        s_e = D.e_now[a];
     }
     __syncthreads();
-    for (int i = threadIdx.x; local && i < H * d; i += blockDim.x) {
-        D.board_q[A.off_hd + i] = sq[i];
-        D.out[D.out_q + A.off_hd + i] = sq[i];
-        D.out[D.out_mean + A.off_hd + i] = smu[i];
-    }
-    // kinematics: one thread per (step, group of 8 spheres), the same chain
-    // and sphere arithmetic as the rollout
-    float4 *board = D.board_sph + (A.off_hs >> 2);
-    float4 *outs = (float4 *)(D.out + D.out_sph) + (A.off_hs >> 2);
-    const int ng = (ns + 7) / 8;
-    for (int t = threadIdx.x; local && t < H * ng; t += blockDim.x) {
-        const int h = t / ng, s0 = (t % ng) * 8, s1 = min(ns, s0 + 8);
-        Frame F;
-        frame_base(A, F);
-        int f = 0;
-        for (int s = s0; s < s1; ++s) {
-            const int fs = A.frame[s];
-            while (f < fs) {
-                frame_step(F, sq[h * d + f], A.dh[f], A.twist[f]);
-                ++f;
+    if (local) {
+        // integration, one thread per joint, sequential over the horizon
+        if (t < d) {
+            float q = s_in[t], qd = s_in[d + t];
+            for (int h = 0; h < H; ++h) {
+                integrate(q, qd, smu[h * d + t], P.dt);
+                sq[h * d + t] = q;
             }
-            const float4 p = A.sph[s];
-            const float3 c = sphere_centre(F, p);
-            const float4 v = make_float4(c.x, c.y, c.z, p.w);
-            board[h * ns + s] = v;
-            outs[h * ns + s] = v;
+        }
+        for (int i = t; i < Hd; i += blockDim.x) D.out[D.out_mean + off_hd + i] = smu[i];
+        __syncthreads();
+        for (int i = t; i < Hd; i += blockDim.x) {
+            const float q = sq[i];
+            float sn, cs;
+            sincosf(__fadd_rn(q, s_dh[i % d].w), &sn, &cs);
+            ssn[i] = sn;
+            scs[i] = cs;
+            D.board_q[off_hd + i] = q;
+            D.out[D.out_q + off_hd + i] = q;
+        }
+        __syncthreads();
+        // kinematics: one thread per (step, group of 8 spheres), the same
+        // chain and sphere arithmetic as the rollout
+        float4 *board = D.board_sph + (A.off_hs >> 2);
+        float4 *outs = (float4 *)(D.out + D.out_sph) + (A.off_hs >> 2);
+        const int ng = (ns + 7) / 8;
+        for (int u = t; u < H * ng; u += blockDim.x) {
+            const int h = u / ng, s0 = (u % ng) * 8, s1 = min(ns, s0 + 8);
+            Frame F;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) F.R[k] = s_base[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) F.t[k] = s_base[9 + k];
+            int f = 0;
+            for (int s = s0; s < s1; ++s) {
+                const int fs = s_frame[s];
+                while (f < fs) {
+                    frame_step_sc(F, ssn[h * d + f], scs[h * d + f], s_dh[f], s_tw[f]);
+                    ++f;
+                }
+                const float4 p = s_sph[s];
+                const float3 c = sphere_centre(F, p);
+                const float4 v = make_float4(c.x, c.y, c.z, p.w);
+                board[h * ns + s] = v;
+                outs[h * ns + s] = v;
+            }
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         if (local) {
             D.board_valid[a] = 1;
-            D.board_stamp[a] = *D.cycle;
-            D.board_dist[a] = D.e_now[a];
-            D.out[D.out_dist + a] = D.e_now[a];
+            D.board_stamp[a] = s_cycle;
+            D.board_dist[a] = s_e;
+            D.out[D.out_dist + a] = s_e;
         }
         __threadfence();
         const int prev = atomicAdd(done_counter, 1);
         if (prev == gridDim.x - 1) {
-            *D.cycle = *D.cycle + 1;
+            *D.cycle = s_cycle + 1;
             *D.world_t = __fadd_rn(*D.world_t, P.dt);
             *done_counter = 0;
         }

@@ -432,9 +432,9 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     for (auto &A : ctx->arms) {
         sp = std::max(sp, sizeof(float) * (size_t)A.H * (2 * A.dof * A.dof + A.dof));
         // k_sample: the whole horizon, or chunks of it within 96 KB
-        const size_t per_h = sizeof(float) * (size_t)(A.dof * A.dof + 2 * A.dof * 32);
+        const size_t per_h = sizeof(float) * (size_t)(A.dof * A.dof + A.dof + 2 * A.dof * 32);
         ss = std::max(ss, std::min((size_t)A.H * per_h, std::max(per_h, (size_t)96 * 1024)));
-        st2 = std::max(st2, sizeof(float) * (size_t)A.H * 2 * A.dof);
+        st2 = std::max(st2, sizeof(float) * (size_t)A.H * 4 * A.dof);
     }
     L.smem_prep = sp;
     L.smem_sample = ss;
