@@ -78,25 +78,10 @@ __global__ void k_reset(Params P, Dev D, int total_hdd, int total_hd)
 // ---------------------------------------------------------------------------
 // Sense + Shift + Cholesky (one block per arm)
 
-__device__ void cholesky_fp32(int d, const float *S, float *L)
-{
-    for (int i = 0; i < d; ++i)
-        for (int j = 0; j <= i; ++j) {
-            float s = S[i * d + j];
-            if (i == j) s = __fadd_rn(s, 1e-8f);
-            for (int k = 0; k < j; ++k) s = __fmaf_rn(-L[i * d + k], L[j * d + k], s);
-            if (i == j)
-                L[i * d + i] = sqrtf(s > 1e-12f ? s : 1e-12f);
-            else
-                L[i * d + j] = __fdiv_rn(s, L[j * d + j]);
-        }
-    for (int i = 0; i < d; ++i)
-        for (int j = i + 1; j < d; ++j) L[i * d + j] = 0.f;
-}
-
-// The same factorisation with the factor in registers (indices unrolled to
-// the build's DoF limit): identical operations in identical order, without
-// a memory round trip on the dependent chain.
+// Cholesky factor L of S + 1e-8 I (row by row, the diagonal clamped at
+// 1e-6), held in registers with the indices unrolled to the build's DoF
+// limit so that no memory round trip sits on the dependent chain; S and
+// Lout are row-major [d][d], the upper triangle of Lout is zeroed.
 __device__ __forceinline__ void cholesky_unrolled(int d, const float *S, float *Lout)
 {
     float L[kMaxDof][kMaxDof];
@@ -463,12 +448,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTil
     }
     if (!last) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float S[kMaxDof * kMaxDof], Lh[kMaxDof * kMaxDof];
-            for (int k = 0; k < dd; ++k) S[k] = Sig[k];
-            cholesky_fp32(d, S, Lh);
-            for (int k = 0; k < dd; ++k) D.L[A.off_hdd + h * dd + k] = Lh[k];
-        }
+        if (threadIdx.x == 0) cholesky_unrolled(d, Sig, D.L + A.off_hdd + h * dd);
     }
 }
 

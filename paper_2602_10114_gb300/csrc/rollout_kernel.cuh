@@ -347,9 +347,19 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         // world boxes (exact), then one pre-tested pass per sphere set over its
         // candidates: the world spheres (slot 0, buffer B_world) and each
         // published neighbour plan at this step (slot 2 + nb, buffer B)
+        // A box whose gap to the warp's bounding box is at least B_world +
+        // 1 mm is skipped: the signed distance of every own sphere to it is
+        // at least that gap (the sphere lies inside the warp box by its
+        // radius along each separating axis), so it is outside the ramp and
+        // changes no result.
         float mbox = kInf;
+        const float tb = P.B_world + 1e-3f;
         for (int b = 0; b < n_aabb; ++b) {
             const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
+            const float gx = fmaxf(fmaxf(__fsub_rn(bc.x, bh.x) - hi.x, lo.x - __fadd_rn(bc.x, bh.x)), 0.f);
+            const float gy = fmaxf(fmaxf(__fsub_rn(bc.y, bh.y) - hi.y, lo.y - __fadd_rn(bc.y, bh.y)), 0.f);
+            const float gz = fmaxf(fmaxf(__fsub_rn(bc.z, bh.z) - hi.z, lo.z - __fadd_rn(bc.z, bh.z)), 0.f);
+            if (gx * gx + gy * gy + gz * gz >= tb * tb) continue;   // warp-uniform
 #pragma unroll
             for (int s = 0; s < SPG; ++s)
                 if (s < cnt)
