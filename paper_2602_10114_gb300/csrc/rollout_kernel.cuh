@@ -385,7 +385,8 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 if (!__any_sync(0xffffffffu, need)) continue;
             }
             const int nc = cull(S, k0, k1, Bp, 1e-3f + P.eps_g / Bp, box, lane, list);
-            float m = clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ);
+            float m = nc > 0 ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
+                             : kInf;   // nc is warp-uniform
             if (world) m = fminf(m, mbox);
             if (need && m < Bp)
                 atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
