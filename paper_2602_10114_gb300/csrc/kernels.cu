@@ -113,6 +113,7 @@ __global__ void k_prep(Params P, Dev D)
     extern __shared__ float sm[];
     const int a = blockIdx.x, t = threadIdx.x;
     const ArmDev &A = D.arms[a];
+    pdl_trigger();   // first kernel of the cycle, launched after the full predecessor
     __shared__ float s_in[2 * kMaxDof + 12];
     __shared__ float4 s_dh[kMaxDof];
     __shared__ float2 s_tw[kMaxDof];
@@ -226,6 +227,8 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
         lo = __fadd_rn(A.q_lo[ij], P.q_margin);
         vmax = A.qd_max[ij];
     }
+    pdl_wait();      // L and mu come from the prep (or the previous update)
+    pdl_trigger();
 
     for (int h0 = 0; h0 < H; h0 += Hc) {
         const int nh = min(Hc, H - h0);
@@ -293,6 +296,8 @@ __global__ void __launch_bounds__(256) k_costs(Params P, Dev D, const CostTile *
     const int n = T.n0 + threadIdx.x;
     if (n >= A.K) return;
     const float *st = D.stage + A.off_kh;
+    pdl_wait();      // the stage costs come from the rollout
+    pdl_trigger();
     float s = 0.f, c = 0.f;
     for (int h0 = 0; h0 < A.H; h0 += 32) {
         float v[32];
@@ -343,6 +348,8 @@ __global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTil
     __shared__ int s_best;
     __shared__ float s_part[kMoments + 1][NT + 1];   // per-thread partial moments and Z
     __shared__ float s_mom[kMoments + 1];
+    pdl_wait();      // the totals come from the costs kernel
+    pdl_trigger();
 
     // minimum cost and its lowest index
     float bv = kInf;
@@ -493,16 +500,19 @@ __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_count
     else if (t < 12) s_base[t] = A.base_t[t - 9];
     const int Hd = H * d;
     float *smu = sq + Hd, *ssn = sq + 2 * Hd, *scs = sq + 3 * Hd;
-    // wave 2: mean, sensed state, cycle and sensed distance
+    // wave 2: sensed state, cycle and sensed distance, then (once the update
+    // has finished) the mean
+    if (local && t < 2 * d) s_in[t] = D.input[off_in + t];
+    if (t == 0) {
+        s_cycle = *D.cycle;
+        s_e = D.e_now[a];
+    }
+    pdl_wait();
+    pdl_trigger();
     if (local) {
         const float *mu = D.mu + off_hd;
 #pragma unroll 4
         for (int i = t; i < Hd; i += blockDim.x) smu[i] = mu[i];
-        if (t < 2 * d) s_in[t] = D.input[off_in + t];
-    }
-    if (t == 0) {
-        s_cycle = *D.cycle;
-        s_e = D.e_now[a];
     }
     __syncthreads();
     if (local) {
@@ -736,16 +746,24 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
         rec = capturing ? cudaEventRecordWithFlags(events[ev++], s, cudaEventRecordExternal)
                         : cudaEventRecord(events[ev++], s);
     };
+    // programmatic dependent launch between consecutive cycle kernels (not
+    // with timing events between them)
+    const bool pdl = events == nullptr;
     mark();
     k_prep<<<L.n_arms, 512, L.smem_prep, s>>>(P, D);
     mark();
     for (int it = 0; it < P.iterations; ++it) {
         const int last = (it == P.iterations - 1);
-        k_sample<<<L.n_sample_tiles, 512, L.smem_sample, s>>>(P, D, L.sample_tiles, it,
-                                                              (int)(L.smem_sample / sizeof(float)));
+        if ((rec = launch_k(k_sample, L.n_sample_tiles, 512, L.smem_sample, s, pdl, P, D,
+                            L.sample_tiles, it, (int)(L.smem_sample / sizeof(float)))) !=
+            cudaSuccess)
+            return rec;
         if (P.w_manip > 0.f)
             k_manip<<<(L.total_kh + 127) / 128, 128, 0, s>>>(P, D, L.total_kh);
         mark();
+        // the rollout follows the sample kernel directly unless a manipulability
+        // or surrogate stage sits between them
+        const bool pdl_roll = pdl && !(P.w_manip > 0.f) && L.n_groups == 0 && L.n_pair_groups == 0;
         for (int i = 0; i < L.n_groups; ++i)   // learned self clearance of every step
             if ((rec = enqueue_self_surrogate(D, L.groups[i], s)) != cudaSuccess) return rec;
         if (L.n_pair_groups > 0 && it == 0 && D.pair_board &&
@@ -755,14 +773,20 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
         for (int i = 0; i < L.n_pair_groups; ++i)   // learned clearance to the neighbours' plans
             if ((rec = enqueue_pair_surrogate(D, L.pair_groups[i], s)) != cudaSuccess) return rec;
         mark();
-        if ((rec = launch_rollout(P, D, L, it, s)) != cudaSuccess) return rec;
+        if ((rec = launch_rollout(P, D, L, it, s, pdl_roll)) != cudaSuccess) return rec;
         mark();
-        k_costs<<<L.n_cost_tiles, 256, 0, s>>>(P, D, L.cost_tiles);
+        if ((rec = launch_k(k_costs, L.n_cost_tiles, 256, 0, s, pdl, P, D, L.cost_tiles)) !=
+            cudaSuccess)
+            return rec;
         mark();
-        k_update<<<L.n_update_tiles, 128, 0, s>>>(P, D, L.update_tiles, last);
+        if ((rec = launch_k(k_update, L.n_update_tiles, 128, 0, s, pdl, P, D, L.update_tiles,
+                            last)) != cudaSuccess)
+            return rec;
         mark();
     }
-    k_toplan<<<L.n_arms, 256, L.smem_toplan, s>>>(P, D, L.done_counter);
+    if ((rec = launch_k(k_toplan, L.n_arms, 256, L.smem_toplan, s, pdl, P, D, L.done_counter)) !=
+        cudaSuccess)
+        return rec;
     mark();
     if (rec != cudaSuccess) return rec;
     return cudaGetLastError();

@@ -85,13 +85,33 @@ cudaError_t enqueue_pair_dataset(const Dev &D, int a, int b, int n, unsigned lon
 cudaError_t enqueue_pair_clearance_traj(const Dev &D, int a, int b, int rows, float *out,
                                         cudaStream_t s);
 
+// Launch of kernel k on stream s, with programmatic stream serialisation
+// when pdl is set (the kernel then calls pdl_wait() before it reads what its
+// predecessor writes).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                     bool pdl, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
+
 // The rollout kernel (rollout.cu): shared-memory size for the given
 // capacities, attribute set-up and launch.
 size_t rollout_smem_bytes(const Params &P, int n_arms);
 cudaError_t configure_rollout(const LaunchPlan &L);
 int rollout_blocks_per_sm(size_t smem);
 cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
-                           cudaStream_t s);
+                           cudaStream_t s, bool pdl = false);
 
 // Everything one control cycle enqueues on `s` (Algorithm 1 for all arms).
 // With `events` non-null, events[0] is recorded before the first kernel and

@@ -103,6 +103,20 @@ struct Dev {
     int out_mean, out_sph, out_q, out_u, out_dist, out_min;  // offsets in out (floats)
 };
 
+// Programmatic dependent launch.  A kernel launched with programmatic
+// stream serialisation may start before its predecessor in the stream has
+// finished; pdl_wait() blocks the calling thread until every prerequisite
+// grid has completed and its memory is visible.  pdl_trigger() lets the
+// next kernel start early; called only after pdl_wait() (or in a kernel
+// launched without the attribute), so that when a kernel starts, every
+// kernel before its predecessor has completed: its code before pdl_wait()
+// may read what those wrote, never what its predecessor writes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Work items of the launch-grid work lists.
 struct SampleTile { int arm, n0; };
 struct RolloutTile { int arm, h, n0, nsub; };   // samples n0 .. n0 + 32 nsub - 1 at step h

@@ -34,10 +34,10 @@ int rollout_blocks_per_sm(size_t smem)
 }
 
 cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
-                           cudaStream_t s)
+                           cudaStream_t s, bool pdl)
 {
-    if (L.rollout_variant == 2) return rollout_launch_mb2(P, D, L, iter, s);
-    return rollout_launch_t<3>(P, D, L, iter, s);
+    if (L.rollout_variant == 2) return rollout_launch_mb2(P, D, L, iter, s, pdl);
+    return rollout_launch_t<3>(P, D, L, iter, s, pdl);
 }
 
 }  // namespace mrs

@@ -568,6 +568,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         __syncthreads();   // the unit's inputs are staged
         const int n_nb = nnb;
+        if (it == 0) {     // the sampled trajectories and limit terms come from the sample kernel
+            pdl_wait();
+            pdl_trigger();
+        }
 
         for (int sb = 0; sb < T.nsub; ++sb, buf ^= 1) {
             RolloutSmem Sb = S;
@@ -654,18 +658,17 @@ cudaError_t rollout_configure_t(size_t smem)
 
 template <int MB>
 cudaError_t rollout_launch_t(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
-                             cudaStream_t s)
+                             cudaStream_t s, bool pdl)
 {
     const int grid = L.n_rollout_tiles < L.rollout_grid ? L.n_rollout_tiles : L.rollout_grid;
-    k_rollout<MB><<<grid, kRolloutThreads, L.smem_rollout, s>>>(P, D, L.rollout_tiles,
-                                                                L.n_rollout_tiles, iter);
-    return cudaGetLastError();
+    return launch_k(k_rollout<MB>, grid, kRolloutThreads, L.smem_rollout, s, pdl, P, D,
+                    L.rollout_tiles, L.n_rollout_tiles, iter);
 }
 
 // the two-blocks-per-SM variant (rollout_mb2.cu)
 int rollout_occupancy_mb2(size_t smem);
 cudaError_t rollout_configure_mb2(size_t smem);
 cudaError_t rollout_launch_mb2(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
-                               cudaStream_t s);
+                               cudaStream_t s, bool pdl);
 
 }  // namespace mrs
