@@ -43,13 +43,14 @@ struct mrs_ctx {
         size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
             board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
             e_now, n_star, out, cycle, world_t, err, done_counter, sample_tiles, rollout_tiles,
-            cost_tiles, update_tiles, self_pairs, work, dhat, total;
+            cost_tiles, update_tiles, self_pairs, self_t2, work, dhat, total;
     } lay{};
     std::vector<SampleTile> sample_tiles;
     std::vector<RolloutTile> rollout_tiles;
     std::vector<CostTile> cost_tiles;
     std::vector<UpdateTile> update_tiles;
     std::vector<int> self_pairs;
+    std::vector<float> self_t2;   // (r1 + B_self + r2)^2 of each self pair
     int num_sms = 0;
     // rollout launch shape (mrs_set_rollout_shape / mrs_autotune)
     int tile_samples = 32, blocks_per_sm = 0, tile_order = 0, max_blocks_per_sm = 1;
@@ -142,6 +143,7 @@ static void build_layout(mrs_ctx *c)
     L.cost_tiles = take(sizeof(CostTile) * c->cost_tiles.size());
     L.update_tiles = take(sizeof(UpdateTile) * c->update_tiles.size());
     L.self_pairs = take(sizeof(int) * std::max<size_t>(1, c->self_pairs.size()));
+    L.self_t2 = take(sizeof(float) * std::max<size_t>(1, c->self_t2.size()));
     L.work = take(sizeof(int) * 64);
     L.dhat = take(sizeof(float) * kh);
     L.total = align_up(o, 256);
@@ -237,6 +239,7 @@ static void fill_dev(mrs_ctx *c, char *base)
     c->L.cost_tiles = (const CostTile *)(base + L.cost_tiles);
     c->L.update_tiles = (const UpdateTile *)(base + L.update_tiles);
     D.self_pairs = (int *)(base + L.self_pairs);
+    D.self_t2 = (float *)(base + L.self_t2);
     D.work = (int *)(base + L.work);
     D.dhat = (float *)(base + L.dhat);
 }
@@ -379,8 +382,12 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         A.self_off = (int)ctx->self_pairs.size();
         for (int s1 = 0; s1 < d.n_spheres; ++s1)
             for (int s2 = s1 + 1; s2 < d.n_spheres; ++s2)
-                if (std::abs(d.sphere_body[s1] - d.sphere_body[s2]) >= 3)
+                if (std::abs(d.sphere_body[s1] - d.sphere_body[s2]) >= 3) {
                     ctx->self_pairs.push_back(s1 | (s2 << 8));
+                    // binary32 sums in the device's order: (r1 + B_self) + r2, squared
+                    const float t = (d.sphere_xyzr[4 * s1 + 3] + cfg->B_self) + d.sphere_xyzr[4 * s2 + 3];
+                    ctx->self_t2.push_back(t * t);
+                }
         A.n_self = (int)ctx->self_pairs.size() - A.self_off;
         max_pairs = std::max(max_pairs, A.n_self);
         // workspace radius for the cancellation margin of the pair pre-test
@@ -554,6 +561,10 @@ static mrs_status bind(mrs_ctx *ctx, void *dev, size_t bytes)
     if (!ctx->self_pairs.empty())
         CK(cudaMemcpyAsync(base + L.self_pairs, ctx->self_pairs.data(),
                            sizeof(int) * ctx->self_pairs.size(), cudaMemcpyHostToDevice,
+                           ctx->stream), "upload self pairs");
+    if (!ctx->self_t2.empty())
+        CK(cudaMemcpyAsync(base + L.self_t2, ctx->self_t2.data(),
+                           sizeof(float) * ctx->self_t2.size(), cudaMemcpyHostToDevice,
                            ctx->stream), "upload self pairs");
     CK(cudaMemsetAsync(base + L.done_counter, 0, sizeof(int), ctx->stream), "memset");
     CK(cudaMemsetAsync(base + L.work, 0, sizeof(int) * 64, ctx->stream), "memset");

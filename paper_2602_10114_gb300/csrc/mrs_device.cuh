@@ -93,6 +93,7 @@ struct Dev {
     float *world_t;        // seconds since the world was set
     int *err;              // device error word (bounded waits)
     int *self_pairs;       // per arm, packed s1 | s2 << 8, bodies >= 3 apart
+    float *self_t2;        // (r1 + B_self + r2)^2 of each self pair, the sums in this order
     float *dhat;           // [sum K*H] surrogate self clearance of every rollout step, [h][n]
     float *rhohat;         // [sum K*H][A] surrogate clearance of every rollout step to each
                            // neighbour's plan: arm j's block at off_kh * A, [i][h][n]

@@ -48,7 +48,8 @@ struct RolloutSmem {
     float4 *aabb;      // [2 * n_aabb] centre, half extents
     float4 *sph;       // [ns] local centre + radius
     int *frame;        // [ns]
-    int *pairs;        // [n_self] s1 | s2 << 8
+    int2 *pairs;       // [n_self] byte offsets of both spheres in own (o1 | o2 << 16),
+                       // and (r1 + B_self + r2)^2 as float bits
     float4 *own;       // [ns][32] own sphere centre and radius of each sample
     int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
     int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
@@ -128,6 +129,15 @@ __device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p
     const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     const float t = __fadd_rn(rB, p.w);
     if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
+}
+
+// The same test for a self pair whose squared ramp bound (r1 + B + r2)^2 was
+// computed beforehand with the same sums: sqrt(d2) - r1 - r2 when inside
+__device__ __forceinline__ void pair_exact_t2(float4 c1, float4 c2, float t2, float &m)
+{
+    const float dx = __fsub_rn(c2.x, c1.x), dy = __fsub_rn(c2.y, c1.y), dz = __fsub_rn(c2.z, c1.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    if (d2 < t2) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), c1.w), c2.w));
 }
 
 // Candidates of one pass: the other spheres in [k0, k1) that come within
@@ -405,11 +415,13 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
         const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
         float m = kInf;
+        const unsigned char *ownb = reinterpret_cast<const unsigned char *>(S.own) + lane * 16;
 #pragma unroll 4
         for (int i = p0; i < p1; ++i) {
-            const int pr = S.pairs[i];
-            const float4 c1 = S.own[(pr & 0xff) * 32 + lane], c2 = S.own[(pr >> 8) * 32 + lane];
-            pair_exact(make_float3(c1.x, c1.y, c1.z), __fadd_rn(c1.w, P.B_self), c1.w, c2, m);
+            const int2 pr = S.pairs[i];
+            const float4 c1 = *reinterpret_cast<const float4 *>(ownb + (pr.x & 0xffff));
+            const float4 c2 = *reinterpret_cast<const float4 *>(ownb + ((unsigned)pr.x >> 16));
+            pair_exact_t2(c1, c2, __int_as_float(pr.y), m);
         }
         if (need && m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
     }
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
         S.pc = (unsigned long long *)p; p += align16(sizeof(unsigned long long) * n_other);
         S.frame = (int *)p;        p += align16(sizeof(int) * P.max_ns);
-        S.pairs = (int *)p;        p += align16(sizeof(int) * P.max_pairs);
+        S.pairs = (int2 *)p;       p += align16(sizeof(int2) * P.max_pairs);
         S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
         S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
         S.nb_arm = (int *)p;       p += align16(sizeof(int) * MRS_MAX_ARMS);
@@ -550,8 +562,13 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             S.sph[k] = A.sph[k];
             S.frame[k] = A.frame[k];
         }
-        for (int k = threadIdx.x; k < A.n_self; k += blockDim.x)
-            S.pairs[k] = D.self_pairs[A.self_off + k];
+        // self pairs as byte offsets of both spheres in the own buffer, with
+        // their squared ramp bound
+        for (int k = threadIdx.x; k < A.n_self; k += blockDim.x) {
+            const int pr = D.self_pairs[A.self_off + k];
+            S.pairs[k] = make_int2(((pr & 0xff) << 9) | ((pr >> 8) << 25),
+                                   __float_as_int(D.self_t2[A.self_off + k]));
+        }
         if (n_plan > 0) {
             // bounded wait for the plan copies, then the derived layouts; if
             // a copy did not land in time the block records the error, waits
