@@ -34,6 +34,10 @@ struct mrs_ctx {
     cudaEvent_t done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // mrs_step's graph: the input upload from pin_in, the cycle, and the
+    // downloads of the outputs and the error word into pin_out / pin_err
+    cudaGraph_t graph_io = nullptr;
+    cudaGraphExec_t gexec_io = nullptr;
     bool use_graph = true;
     bool timing = false;
     std::vector<cudaEvent_t> events;
@@ -317,8 +321,12 @@ static void invalidate_graph(mrs_ctx *ctx)
 {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->gexec_io) cudaGraphExecDestroy(ctx->gexec_io);
+    if (ctx->graph_io) cudaGraphDestroy(ctx->graph_io);
     ctx->gexec = nullptr;
     ctx->graph = nullptr;
+    ctx->gexec_io = nullptr;
+    ctx->graph_io = nullptr;
 }
 
 extern "C" {
@@ -504,8 +512,7 @@ void mrs_destroy(mrs_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->rhohat) cudaFree(ctx->rhohat);
     if (ctx->pair_board) cudaFree(ctx->pair_board);
-    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    invalidate_graph(ctx);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->pin_in) cudaFreeHost(ctx->pin_in);
     if (ctx->pin_out) cudaFreeHost(ctx->pin_out);
@@ -719,6 +726,37 @@ static mrs_status launch_cycle(mrs_ctx *ctx)
     return MRS_OK;
 }
 
+// mrs_step's graph (capture on first use): one launch per control cycle
+static mrs_status launch_cycle_io(mrs_ctx *ctx)
+{
+    if (!ctx->gexec_io) {
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+        cudaError_t e = cudaMemcpyAsync(ctx->D.input, ctx->pin_in,
+                                        sizeof(float) * ctx->sz.input_floats,
+                                        cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = enqueue_cycle(ctx->P, ctx->D, ctx->L, ctx->stream, nullptr, true);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
+                                cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->pin_err, ctx->D.err, sizeof(int), cudaMemcpyDeviceToHost,
+                                ctx->stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(ctx, e != cudaSuccess ? e : e2, "graph capture (step)");
+        }
+        ctx->graph_io = g;
+        CK(cudaGraphInstantiate(&ctx->gexec_io, g, 0), "graph instantiate (step)");
+    }
+    CK(cudaGraphLaunch(ctx->gexec_io, ctx->stream), "graph launch");
+    return MRS_OK;
+}
+
+// Waits for the work enqueued so far, polling: a tight spin for the first
+// 2 ms (a control cycle ends well within it), then yielding the core, and
+// giving up after timeout_s.
 static mrs_status wait_bounded(mrs_ctx *ctx, double timeout_s)
 {
     CK(cudaEventRecord(ctx->done, ctx->stream), "event record");
@@ -729,7 +767,7 @@ static mrs_status wait_bounded(mrs_ctx *ctx, double timeout_s)
         if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream wait");
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) return fail(ctx, MRS_ETIMEOUT, "bounded wait for the cycle gave up");
-        std::this_thread::yield();
+        if (el > 2e-3) std::this_thread::yield();
     }
     return MRS_OK;
 }
@@ -764,15 +802,21 @@ mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out
     }
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
-    CK(cudaMemcpyAsync(ctx->D.input, ctx->pin_in, sizeof(float) * ctx->sz.input_floats,
-                       cudaMemcpyHostToDevice, ctx->stream), "input upload");
+    if (ctx->use_graph && !ctx->timing) {
+        // upload, cycle and downloads in one graph launch
+        st = launch_cycle_io(ctx);
+        if (st != MRS_OK) return st;
+    } else {
+        CK(cudaMemcpyAsync(ctx->D.input, ctx->pin_in, sizeof(float) * ctx->sz.input_floats,
+                           cudaMemcpyHostToDevice, ctx->stream), "input upload");
+        st = launch_cycle(ctx);
+        if (st != MRS_OK) return st;
+        CK(cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
+                           cudaMemcpyDeviceToHost, ctx->stream), "output download");
+        CK(cudaMemcpyAsync(ctx->pin_err, ctx->D.err, sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream), "error word download");
+    }
     ctx->has_input = true;
-    st = launch_cycle(ctx);
-    if (st != MRS_OK) return st;
-    CK(cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
-                       cudaMemcpyDeviceToHost, ctx->stream), "output download");
-    CK(cudaMemcpyAsync(ctx->pin_err, ctx->D.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
-       "error word download");
     st = wait_bounded(ctx, 10.0);
     if (st != MRS_OK) return st;
     if (*ctx->pin_err) return fail(ctx, MRS_ETIMEOUT, "a device-side bounded wait gave up");
