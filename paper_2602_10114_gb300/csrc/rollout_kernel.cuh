@@ -58,6 +58,7 @@ struct RolloutSmem {
     unsigned short *cand;   // [kGroups][cand_cap] per-warp candidate lists
     int cand_cap;
     float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
+    float4 *sbox;           // [ns][2] per-sphere bounding box over the sub-batch: lo, hi
     float2 *sc;             // [dof][32] sin, cos of q_j + theta_j of the sub-batch's samples
 };
 
@@ -129,6 +130,17 @@ __device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p
     const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     const float t = __fadd_rn(rB, p.w);
     if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
+}
+
+// minimum / maximum of a float over the warp (exact: integer min / max of an
+// order-preserving key)
+__device__ __forceinline__ float warp_min(float v)
+{
+    return ordered_to_float(__reduce_min_sync(0xffffffffu, float_to_ordered(v)));
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    return ordered_to_float(__reduce_max_sync(0xffffffffu, float_to_ordered(v)));
 }
 
 // The same test for a self pair whose squared ramp bound (r1 + B + r2)^2 was
@@ -327,25 +339,24 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     }
 
     if (cnt > 0) {
-        // box bounding the warp's own spheres over its 32 samples
+        // box bounding each own sphere (centre +- radius) over the warp's 32
+        // samples (warp-wide integer min / max of order-preserving keys), kept
+        // for the self pass, and their union: the warp's box
         float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
 #pragma unroll
         for (int s = 0; s < SPG; ++s)
             if (s < cnt) {
                 const float3 c = own_centre<NP>(MX, MY, MZ, s);
                 const float r = S.sph[s0 + s].w;
-                lo.x = fminf(lo.x, c.x - r); lo.y = fminf(lo.y, c.y - r); lo.z = fminf(lo.z, c.z - r);
-                hi.x = fmaxf(hi.x, c.x + r); hi.y = fmaxf(hi.y, c.y + r); hi.z = fmaxf(hi.z, c.z + r);
+                const float4 bl = make_float4(warp_min(c.x - r), warp_min(c.y - r), warp_min(c.z - r), 0.f);
+                const float4 bh = make_float4(warp_max(c.x + r), warp_max(c.y + r), warp_max(c.z + r), 0.f);
+                if (lane == 0) {
+                    S.sbox[2 * (s0 + s)] = bl;
+                    S.sbox[2 * (s0 + s) + 1] = bh;
+                }
+                lo.x = fminf(lo.x, bl.x); lo.y = fminf(lo.y, bl.y); lo.z = fminf(lo.z, bl.z);
+                hi.x = fmaxf(hi.x, bh.x); hi.y = fmaxf(hi.y, bh.y); hi.z = fmaxf(hi.z, bh.z);
             }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
-            lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
-            lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
-            hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
-            hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
-            hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
-        }
         unsigned short *list = S.cand + g * S.cand_cap;
         float *box = S.box + g * 8;
         if (lane == 0) {
@@ -414,14 +425,35 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             need = valid && D.dhat[A.off_kh + (long long)h * K + n] < P.B_self + A.self_margin;
         const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
         const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
+        // 32 pairs at a time, one per lane, tested on the two spheres' boxes
+        // over the sub-batch: a pair whose boxes are at least B_self + 1 mm
+        // apart has every sample's spheres that far apart (each ball lies in
+        // its box), outside the ramp, and is skipped (no result changes); the
+        // exact test runs on the others, for every lane
         float m = kInf;
         const unsigned char *ownb = reinterpret_cast<const unsigned char *>(S.own) + lane * 16;
-#pragma unroll 4
-        for (int i = p0; i < p1; ++i) {
-            const int2 pr = S.pairs[i];
-            const float4 c1 = *reinterpret_cast<const float4 *>(ownb + (pr.x & 0xffff));
-            const float4 c2 = *reinterpret_cast<const float4 *>(ownb + ((unsigned)pr.x >> 16));
-            pair_exact_t2(c1, c2, __int_as_float(pr.y), m);
+        const float tb = P.B_self + 1e-3f;
+        for (int base = p0; base < p1; base += 32) {
+            bool near = false;
+            if (base + lane < p1) {
+                const int o = S.pairs[base + lane].x;
+                const int a1 = (o & 0xffff) >> 9, a2 = (int)((unsigned)o >> 25);
+                const float4 l1 = S.sbox[2 * a1], h1 = S.sbox[2 * a1 + 1];
+                const float4 l2 = S.sbox[2 * a2], h2 = S.sbox[2 * a2 + 1];
+                const float gx = fmaxf(fmaxf(l2.x - h1.x, l1.x - h2.x), 0.f);
+                const float gy = fmaxf(fmaxf(l2.y - h1.y, l1.y - h2.y), 0.f);
+                const float gz = fmaxf(fmaxf(l2.z - h1.z, l1.z - h2.z), 0.f);
+                near = gx * gx + gy * gy + gz * gz < tb * tb;
+            }
+            unsigned mk = __ballot_sync(0xffffffffu, near);
+            while (mk) {
+                const int i = base + __ffs(mk) - 1;
+                mk &= mk - 1u;
+                const int2 pr = S.pairs[i];
+                const float4 c1 = *reinterpret_cast<const float4 *>(ownb + (pr.x & 0xffff));
+                const float4 c2 = *reinterpret_cast<const float4 *>(ownb + ((unsigned)pr.x >> 16));
+                pair_exact_t2(c1, c2, __int_as_float(pr.y), m);
+            }
         }
         if (need && m < P.B_self) atomicMin(&S.red[1 * 32 + lane], float_to_ordered(m));
     }
@@ -466,6 +498,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
         S.nb_arm = (int *)p;       p += align16(sizeof(int) * MRS_MAX_ARMS);
         S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
+        S.sbox = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.max_ns);
         S.sc = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof * 32);
         S.cand = (unsigned short *)p;
         S.cand_cap = (int)((n_other + 7) & ~size_t(7));
