@@ -273,35 +273,49 @@ class Controller:
                       _f32(goal_R[a]).ravel()]
         return np.concatenate(parts).astype(np.float32)
 
+    _OUT_KEYS = ("mean_plan", "plan_spheres", "plan_q", "u_star", "dist_to_goal", "min_cost")
+
     def _step_buffers(self):
-        """Input staging arrays, the arm-state array pointing at them, the
-        output arrays and the output struct: built once per controller."""
+        """Built once per controller: one contiguous input array (per arm q,
+        qd, goal_p, goal_R) with the arm-state array pointing into it, one
+        contiguous output array with the output struct pointing into it, and
+        the slices of each output."""
         A = len(self.sc.arms)
         sz = self.sizes
-        ins = [(np.zeros(a.dof, np.float32), np.zeros(a.dof, np.float32),
-                np.zeros(3, np.float32), np.zeros(9, np.float32)) for a in self.sc.arms]
+        xin = np.zeros(sum(2 * a.dof + 12 for a in self.sc.arms), np.float32)
         states = (MrsArmState * A)()
-        for a in range(A):
-            states[a] = MrsArmState(*[_pf(x) for x in ins[a]])
-        out = dict(mean_plan=np.zeros(sz.hd, np.float32), plan_spheres=np.zeros(sz.hs, np.float32),
-                   plan_q=np.zeros(sz.hd, np.float32), u_star=np.zeros(sz.d, np.float32),
-                   dist_to_goal=np.zeros(A, np.float32), min_cost=np.zeros(A, np.float32))
-        o = MrsStepOut(*[_pf(out[k]) for k in ("mean_plan", "plan_spheres", "plan_q", "u_star",
-                                               "dist_to_goal", "min_cost")])
-        self._sbuf = (ins, states, out, o)
+        off = 0
+        for i, a in enumerate(self.sc.arms):
+            d = a.dof
+            parts = (xin[off:off + d], xin[off + d:off + 2 * d], xin[off + 2 * d:off + 2 * d + 3],
+                     xin[off + 2 * d + 3:off + 2 * d + 12])
+            states[i] = MrsArmState(*[_pf(x) for x in parts])
+            off += 2 * d + 12
+        sizes = (sz.hd, sz.hs, sz.hd, sz.d, A, A)
+        bounds = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+        obuf = np.zeros(int(bounds[-1]), np.float32)
+        sl = [slice(int(bounds[i]), int(bounds[i + 1])) for i in range(len(sizes))]
+        o = MrsStepOut(*[_pf(obuf[x]) for x in sl])
+        self._dofs = tuple(a.dof for a in self.sc.arms)
+        self._sbuf = (xin, states, obuf, tuple(zip(self._OUT_KEYS, sl)), C.byref(o), o)
         return self._sbuf
 
     def step(self, q, qd, goal_p, goal_R):
         """One control cycle with host inputs; returns a dict of host arrays
         (fresh copies)."""
-        ins, states, out, o = getattr(self, "_sbuf", None) or self._step_buffers()
-        for a, (iq, iqd, ip, iR) in enumerate(ins):
-            iq[...] = q[a]
-            iqd[...] = qd[a]
-            ip[...] = np.reshape(goal_p[a], 3)
-            iR[...] = np.reshape(goal_R[a], 9)
-        self._check(self.L.mrs_step(self.h, states, C.byref(o)), "step")
-        return {k: v.copy() for k, v in out.items()}
+        xin, states, obuf, keys, oref, _ = getattr(self, "_sbuf", None) or self._step_buffers()
+        parts = []
+        for a, d in enumerate(self._dofs):
+            qa, qda, gpa, gRa = q[a], qd[a], np.ravel(goal_p[a]), np.ravel(goal_R[a])
+            if len(qa) != d or len(qda) != d or gpa.size != 3 or gRa.size != 9:
+                raise ValueError(f"arm {a}: q, qd need {d} values, goal_p 3, goal_R 9")
+            parts += (qa, qda, gpa, gRa)
+        np.concatenate(parts, out=xin)
+        st = self.L.mrs_step(self.h, states, oref)
+        if st != 0:
+            self._check(st, "step")
+        oc = obuf.copy()
+        return {k: oc[s] for k, s in keys}
 
     def step_device(self, d_input):
         """Enqueue one cycle with a device-resident packed input (torch float32
