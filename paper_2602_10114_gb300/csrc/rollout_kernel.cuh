@@ -111,6 +111,18 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
                  : "memory");
 }
 
+// 4-byte asynchronous copy global -> shared (one group per call) and the
+// wait for all of the calling thread's copies
+__device__ __forceinline__ void cp_async4(float *dst_smem, const float *src_gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n cp.async.commit_group;"
+                 ::"r"(tc::smem_u32(dst_smem)), "l"(__cvta_generic_to_global(src_gmem)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // store one other sphere (and its |p|^2 - r^2) in every layout the passes read
 __device__ __forceinline__ void put_other(const RolloutSmem &S, int k, float4 w)
 {
@@ -507,6 +519,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     }
     __shared__ int s_tile[2];
     __shared__ float s_pose[2][32];
+    __shared__ float s_lim[32];   // the sub-batch's joint-limit terms, copied ahead by warp 0
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
     const long long cycle = *D.cycle;
@@ -629,6 +642,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             Sb.red = S.red + buf * kRedStride;
             const int n = T.n0 + sb * 32 + lane;
             const bool valid = n < A.K;
+            // warp 0 uses the sub-batch's stop / joint-limit terms in its cost
+            // stage: copied to shared memory now, behind the kinematics
+            if (g == 0 && valid)
+                cp_async4(&s_lim[lane], D.stage_lim + A.off_kh + (long long)h * A.K + n);
             // sine and cosine of every joint angle of the sub-batch, once
             // (warp j takes joint j): the sphere groups' kinematic chains
             // share them
@@ -655,6 +672,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
 
             // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
             if (g == 0) {
+                cp_async_wait_all();
                 if (valid) {
                     const long long idx = A.off_kh + (long long)h * A.K + n;
                     const float dw = ordered_to_float(Sb.red[0 * 32 + lane]);
@@ -665,7 +683,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                         dyn = __fmaf_rn(S.nb_alpha[tp * MRS_MAX_ARMS + nb], ramp(rho, P.B), dyn);
                     }
                     float c = __fmul_rn(P.w_pose, s_pose[buf][lane]);
-                    c = __fadd_rn(c, D.stage_lim[idx]);
+                    c = __fadd_rn(c, s_lim[lane]);
                     c = __fmaf_rn(P.w_coll, ramp(dw, P.B_world), c);
                     c = __fmaf_rn(P.w_self, ramp(dsf, P.B_self), c);
                     c = __fmaf_rn(P.w_dyn, dyn, c);
