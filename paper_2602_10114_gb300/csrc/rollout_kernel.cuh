@@ -60,6 +60,10 @@ struct RolloutSmem {
     float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
     float4 *sbox;           // [ns][2] per-sphere bounding box over the sub-batch: lo, hi
     float2 *sc;             // [dof][32] sin, cos of q_j + theta_j of the sub-batch's samples
+    float4 *dh;             // [kMaxDof] the arm's DH rows (a, d, alpha, theta)
+    float2 *tw;             // [kMaxDof] sin, cos of the twists
+    float *base;            // [12] base rotation (row-major) and translation
+    float *goal;            // [12] the arm's goal position and rotation (sensed input)
 };
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -314,7 +318,10 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     constexpr int NP = (SPG + 1) / 2;
     f32x2 MX[NP], MY[NP], MZ[NP];
     Frame F;
-    frame_base(A, F);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F.R[k] = S.base[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F.t[k] = S.base[9 + k];
     int f = 0;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -326,7 +333,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 const int fs = S.frame[s0 + s];
                 while (f < fs) {
                     const float2 sc = S.sc[f * 32 + lane];
-                    frame_step_sc(F, sc.x, sc.y, A.dh[f], A.twist[f]);
+                    frame_step_sc(F, sc.x, sc.y, S.dh[f], S.tw[f]);
                     ++f;
                 }
                 const float3 c = sphere_centre(F, S.sph[s0 + s]);
@@ -343,11 +350,10 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     if (g == kGroups - 1) {
         while (f < d) {
             const float2 sc = S.sc[f * 32 + lane];
-            frame_step_sc(F, sc.x, sc.y, A.dh[f], A.twist[f]);
+            frame_step_sc(F, sc.x, sc.y, S.dh[f], S.tw[f]);
             ++f;
         }
-        const float *in = D.input + A.off_in;
-        *pose_out = pose_cost(F, in + 2 * d, in + 2 * d + 3, P.w_rot);
+        *pose_out = pose_cost(F, S.goal, S.goal + 3, P.w_rot);
     }
 
     if (cnt > 0) {
@@ -512,6 +518,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
         S.sbox = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.max_ns);
         S.sc = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof * 32);
+        S.dh = (float4 *)p;        p += align16(sizeof(float4) * kMaxDof);
+        S.tw = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof);
+        S.base = (float *)p;       p += align16(sizeof(float) * 12);
+        S.goal = (float *)p;       p += align16(sizeof(float) * 12);
         S.cand = (unsigned short *)p;
         S.cand_cap = (int)((n_other + 7) & ~size_t(7));
         p += align16(sizeof(unsigned short) * kGroups * S.cand_cap);
@@ -541,7 +551,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         const int tp = it & 1;   // work-unit parity
         const int ti = s_tile[tp];
         if (ti >= n_tiles) break;
-        if (threadIdx.x == 0) s_tile[tp ^ 1] = atomicAdd(&D.work[iter], 1);
+        if (threadIdx.x == kRolloutThreads - 1) s_tile[tp ^ 1] = atomicAdd(&D.work[iter], 1);
         const RolloutTile T = tiles[ti];
         const ArmDev &A = D.arms[T.arm];
         const int h = T.h;
@@ -597,14 +607,26 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 }
             }
         }
+        // the rest of the staging starts on warps 1 to 4 (warp 0 issues the
+        // plan copies, warp 7 claims the next unit)
         const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
-        for (int k = threadIdx.x; k < n_world; k += blockDim.x) {
+        for (int k = (threadIdx.x + 224) & 255; k < n_world; k += blockDim.x) {
             const float4 o = D.world[k], v = D.world_vel[k];
             put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
                                         __fmaf_rn(v.z, t_h, o.z), o.w));
         }
-        for (int k = threadIdx.x; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
-        for (int k = threadIdx.x; k < A.ns; k += blockDim.x) {
+        for (int k = (threadIdx.x + 160) & 255; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
+        {
+            const int k = (threadIdx.x + 128) & 255;
+            if (k < A.dof) {
+                S.dh[k] = A.dh[k];
+                S.tw[k] = A.twist[k];
+            }
+            if (k < 9) S.base[k] = A.base_R[k];
+            else if (k < 12) S.base[k] = A.base_t[k - 9];
+            else if (k < 24) S.goal[k - 12] = D.input[A.off_in + 2 * A.dof + k - 12];
+        }
+        for (int k = (threadIdx.x + 96) & 255; k < A.ns; k += blockDim.x) {
             S.sph[k] = A.sph[k];
             S.frame[k] = A.frame[k];
         }
@@ -652,7 +674,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             for (int j = g; j < A.dof; j += kGroups) {
                 float sn, cs;
                 const float qj = D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
-                sincosf(__fadd_rn(qj, A.dh[j].w), &sn, &cs);
+                sincosf(__fadd_rn(qj, S.dh[j].w), &sn, &cs);
                 S.sc[j * 32 + lane] = make_float2(sn, cs);
             }
             __syncthreads();
