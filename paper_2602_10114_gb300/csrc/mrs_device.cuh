@@ -276,6 +276,10 @@ __device__ __forceinline__ float hinge2(float e) { return e > 0.f ? __fmul_rn(e,
 // max(0, 1 - dist / B)
 __device__ __forceinline__ float ramp(float dist, float B)
 {
+    // at or beyond the buffer (also +inf, no pair inside) the value is 0:
+    // dist / B rounds to at least 1 there, so skipping the division (whose
+    // special-value path +inf would take) changes no result
+    if (!(dist < B)) return 0.f;
     const float c = __fsub_rn(1.0f, __fdiv_rn(dist, B));
     return c > 0.f ? c : 0.f;
 }

@@ -148,15 +148,19 @@ __device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p
     if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
 }
 
-// minimum / maximum of a float over the warp (exact: integer min / max of an
-// order-preserving key)
+// minimum / maximum of a float over the full warp (sm_100+ floating-point
+// warp reduction; exact)
 __device__ __forceinline__ float warp_min(float v)
 {
-    return ordered_to_float(__reduce_min_sync(0xffffffffu, float_to_ordered(v)));
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 __device__ __forceinline__ float warp_max(float v)
 {
-    return ordered_to_float(__reduce_max_sync(0xffffffffu, float_to_ordered(v)));
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 
 // The same test for a self pair whose squared ramp bound (r1 + B + r2)^2 was
@@ -358,7 +362,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
 
     if (cnt > 0) {
         // box bounding each own sphere (centre +- radius) over the warp's 32
-        // samples (warp-wide integer min / max of order-preserving keys), kept
+        // samples (warp-wide floating-point min / max), kept
         // for the self pass, and their union: the warp's box
         float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
 #pragma unroll
