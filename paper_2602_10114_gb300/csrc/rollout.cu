@@ -15,7 +15,9 @@ size_t rollout_smem_bytes(const Params &P, int n_arms)
            a16(sizeof(unsigned long long) * n_other) + a16(sizeof(int) * P.max_ns) +
            a16(sizeof(int2) * P.max_pairs) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +
            a16(sizeof(float) * 2 * MRS_MAX_ARMS) + a16(sizeof(int) * MRS_MAX_ARMS) +
-           a16(sizeof(float) * kGroups * 8) + a16(sizeof(float4) * 2 * P.max_ns) +
+           a16(sizeof(float) * kGroups * 8) + a16(sizeof(float) * 2) +
+           a16(sizeof(float4) * 2 * n_arms) +
+           a16(sizeof(float4) * 2 * P.max_ns) +
            a16(sizeof(float2) * kMaxDof * 32) + a16(sizeof(float4) * kMaxDof) +
            a16(sizeof(float2) * kMaxDof) + 2 * a16(sizeof(float) * 12) +
            a16(sizeof(unsigned short) * kGroups * ((n_other + 7) & ~size_t(7))) +

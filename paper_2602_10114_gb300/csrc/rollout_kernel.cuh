@@ -57,8 +57,10 @@ struct RolloutSmem {
     int *nb_arm;       // [n_nb] arm index of each neighbour
     unsigned short *cand;   // [kGroups][cand_cap] per-warp candidate lists
     int cand_cap;
-    float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
     float4 *sbox;           // [ns][2] per-sphere bounding box over the sub-batch: lo, hi
+    float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
+    float *marg;            // [2] cull margins 1 mm + eps_g / B of the world and plan passes
+    float4 *nbbox;          // [2 * n_arms] box of each neighbour's plan spheres at the unit's step
     float2 *sc;             // [dof][32] sin, cos of q_j + theta_j of the sub-batch's samples
     float4 *dh;             // [kMaxDof] the arm's DH rows (a, d, alpha, theta)
     float2 *tw;             // [kMaxDof] sin, cos of the twists
@@ -133,6 +135,18 @@ __device__ __forceinline__ void put_other(const RolloutSmem &S, int k, float4 w)
     const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
                                 -__fmul_rn(w.w, w.w))));
     S.other[k] = w;
+    S.other_w[k] = pw;
+    S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
+    S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
+    S.pc[k] = pack2(pw, pw);
+}
+
+// the derived layouts of a sphere already in S.other[k] (a plan sphere
+// copied there by the bulk-copy engine)
+__device__ __forceinline__ void put_derived(const RolloutSmem &S, int k, float4 w)
+{
+    const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
+                                -__fmul_rn(w.w, w.w))));
     S.other_w[k] = pw;
     S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
     S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
@@ -395,19 +409,43 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         // at least that gap (the sphere lies inside the warp box by its
         // radius along each separating axis), so it is outside the ramp and
         // changes no result.
+        // the world boxes and the neighbours' plan boxes near enough to
+        // matter, tested one per lane; the others are skipped
         float mbox = kInf;
-        const float tb = P.B_world + 1e-3f;
-        for (int b = 0; b < n_aabb; ++b) {
-            const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
-            const float gx = fmaxf(fmaxf(__fsub_rn(bc.x, bh.x) - hi.x, lo.x - __fadd_rn(bc.x, bh.x)), 0.f);
-            const float gy = fmaxf(fmaxf(__fsub_rn(bc.y, bh.y) - hi.y, lo.y - __fadd_rn(bc.y, bh.y)), 0.f);
-            const float gz = fmaxf(fmaxf(__fsub_rn(bc.z, bh.z) - hi.z, lo.z - __fadd_rn(bc.z, bh.z)), 0.f);
-            if (gx * gx + gy * gy + gz * gz >= tb * tb) continue;   // warp-uniform
+        for (int b0 = 0; b0 < n_aabb; b0 += 32) {
+            const float tb = P.B_world + 1e-3f;
+            bool nr = false;
+            if (b0 + lane < n_aabb) {
+                const float4 bc = S.aabb[2 * (b0 + lane)], bh = S.aabb[2 * (b0 + lane) + 1];
+                const float gx = fmaxf(fmaxf(__fsub_rn(bc.x, bh.x) - hi.x, lo.x - __fadd_rn(bc.x, bh.x)), 0.f);
+                const float gy = fmaxf(fmaxf(__fsub_rn(bc.y, bh.y) - hi.y, lo.y - __fadd_rn(bc.y, bh.y)), 0.f);
+                const float gz = fmaxf(fmaxf(__fsub_rn(bc.z, bh.z) - hi.z, lo.z - __fadd_rn(bc.z, bh.z)), 0.f);
+                nr = gx * gx + gy * gy + gz * gz < tb * tb;
+            }
+            unsigned box_near = __ballot_sync(0xffffffffu, nr);
+            while (box_near) {
+                const int b = b0 + __ffs(box_near) - 1;
+                box_near &= box_near - 1u;
+                const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
 #pragma unroll
-            for (int s = 0; s < SPG; ++s)
-                if (s < cnt)
-                    mbox = fminf(mbox, sphere_aabb(own_centre<NP>(MX, MY, MZ, s), S.sph[s0 + s].w,
-                                                   bc, bh));
+                for (int s = 0; s < SPG; ++s)
+                    if (s < cnt)
+                        mbox = fminf(mbox, sphere_aabb(own_centre<NP>(MX, MY, MZ, s), S.sph[s0 + s].w,
+                                                       bc, bh));
+            }
+        }
+        unsigned nb_near;   // at most 31 neighbours
+        {
+            const float tn = P.B + S.marg[1];
+            bool nr = false;
+            if (lane < n_nb) {
+                const float4 pl = S.nbbox[2 * lane], ph = S.nbbox[2 * lane + 1];
+                const float gx = fmaxf(fmaxf(pl.x - hi.x, lo.x - ph.x), 0.f);
+                const float gy = fmaxf(fmaxf(pl.y - hi.y, lo.y - ph.y), 0.f);
+                const float gz = fmaxf(fmaxf(pl.z - hi.z, lo.z - ph.z), 0.f);
+                nr = gx * gx + gy * gy + gz * gz < tn * tn;
+            }
+            nb_near = __ballot_sync(0xffffffffu, nr);
         }
         for (int ps = 0; ps <= n_nb; ++ps) {
             const bool world = ps == 0;
@@ -418,6 +456,9 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             // this neighbour's plan is at least B + margin skips the exact
             // pass (its coordination term is zero); a plan published without
             // joints always takes the exact pass
+            // a neighbour whose plan box is at least B + margin from the warp's
+            // box has every plan sphere culled: no candidate, no term
+            if (!world && !((nb_near >> (ps - 1)) & 1u)) continue;
             bool need = true;
             if (!world) {
                 const int ai = S.nb_arm[ps - 1];
@@ -427,7 +468,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                                               (long long)h * K + n] < P.B + A.pair_margin);
                 if (!__any_sync(0xffffffffu, need)) continue;
             }
-            const int nc = cull(S, k0, k1, Bp, 1e-3f + P.eps_g / Bp, box, lane, list);
+            const int nc = cull(S, k0, k1, Bp, world ? S.marg[0] : S.marg[1], box, lane, list);
             float m = nc > 0 ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
                              : kInf;   // nc is warp-uniform
             if (world) m = fminf(m, mbox);
@@ -519,8 +560,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
         S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
         S.nb_arm = (int *)p;       p += align16(sizeof(int) * MRS_MAX_ARMS);
-        S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
         S.sbox = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.max_ns);
+        S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
+        S.marg = (float *)p;       p += align16(sizeof(float) * 2);
+        S.nbbox = (float4 *)p;     p += align16(sizeof(float4) * 2 * NA);
         S.sc = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof * 32);
         S.dh = (float4 *)p;        p += align16(sizeof(float4) * kMaxDof);
         S.tw = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof);
@@ -543,6 +586,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     for (int k = threadIdx.x; k < 2 * kRedStride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
     __shared__ __align__(8) uint64_t s_bar;   // completion of the plan-slice copies
     uint32_t bar_phase = 0;
+    if (threadIdx.x == 1) {
+        S.marg[0] = 1e-3f + P.eps_g / P.B_world;
+        S.marg[1] = 1e-3f + P.eps_g / P.B;
+    }
     if (threadIdx.x == 0) {
         s_tile[0] = atomicAdd(&D.work[iter], 1);
         tc::mbar_init(&s_bar, 1);
@@ -653,7 +700,23 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             }
             bar_phase ^= 1u;
             for (int k = threadIdx.x; k < n_plan; k += blockDim.x)
-                put_other(S, n_world + k, S.other[n_world + k]);
+                put_derived(S, n_world + k, S.other[n_world + k]);
+            // box of each neighbour's plan spheres (centre +- radius), one warp
+            // per neighbour
+            for (int w = g; w < nnb; w += kGroups) {
+                float3 bl = make_float3(kInf, kInf, kInf), bh = make_float3(-kInf, -kInf, -kInf);
+                for (int k = S.nb_start[w] + lane; k < S.nb_start[w + 1]; k += 32) {
+                    const float4 q = S.other[k];
+                    bl.x = fminf(bl.x, q.x - q.w); bl.y = fminf(bl.y, q.y - q.w); bl.z = fminf(bl.z, q.z - q.w);
+                    bh.x = fmaxf(bh.x, q.x + q.w); bh.y = fmaxf(bh.y, q.y + q.w); bh.z = fmaxf(bh.z, q.z + q.w);
+                }
+                const float4 l4 = make_float4(warp_min(bl.x), warp_min(bl.y), warp_min(bl.z), 0.f);
+                const float4 h4 = make_float4(warp_max(bh.x), warp_max(bh.y), warp_max(bh.z), 0.f);
+                if (lane == 0) {
+                    S.nbbox[2 * w] = l4;
+                    S.nbbox[2 * w + 1] = h4;
+                }
+            }
         }
         __syncthreads();   // the unit's inputs are staged
         const int n_nb = nnb;
