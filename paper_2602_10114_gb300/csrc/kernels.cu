@@ -333,9 +333,13 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTile *tiles, int last)
+constexpr int kUpdateThreads = 256;
+constexpr size_t kUpdateSmem = sizeof(float) * (kMoments + 1) * (kUpdateThreads + 1);
+
+__global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, const UpdateTile *tiles,
+                                                           int last)
 {
-    constexpr int NT = 128;
+    constexpr int NT = kUpdateThreads;
     constexpr int kM2 = kMoments - kMaxDof;
     const UpdateTile T = tiles[blockIdx.x];
     const ArmDev &A = D.arms[T.arm];
@@ -346,7 +350,9 @@ __global__ void __launch_bounds__(128) k_update(Params P, Dev D, const UpdateTil
     __shared__ int s_i[32];
     __shared__ float s_beta, s_Z;
     __shared__ int s_best;
-    __shared__ float s_part[kMoments + 1][NT + 1];   // per-thread partial moments and Z
+    // per-thread partial moments and Z, [kMoments + 1][NT + 1] (dynamic)
+    extern __shared__ float s_dyn[];
+    float (*s_part)[NT + 1] = reinterpret_cast<float (*)[NT + 1]>(s_dyn);
     __shared__ float s_mom[kMoments + 1];
     pdl_wait();      // the totals come from the costs kernel
     pdl_trigger();
@@ -725,6 +731,9 @@ cudaError_t configure_kernels(const LaunchPlan &L)
     if ((e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)L.smem_prep)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kUpdateSmem)) != cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 
@@ -779,8 +788,8 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
             cudaSuccess)
             return rec;
         mark();
-        if ((rec = launch_k(k_update, L.n_update_tiles, 128, 0, s, pdl, P, D, L.update_tiles,
-                            last)) != cudaSuccess)
+        if ((rec = launch_k(k_update, L.n_update_tiles, kUpdateThreads, kUpdateSmem, s, pdl, P, D,
+                            L.update_tiles, last)) != cudaSuccess)
             return rec;
         mark();
     }
