@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        if (g == 0) {
+        if (g == 1) {   // warp 0 may still be in the previous unit's cost stage
             const int pos = __popc(mask & ((1u << lane) - 1u));
             if (ok) {
                 S.nb_start[pos] = n_world + incl - ns_i;
@@ -640,10 +640,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         // the neighbours' plan spheres at step h (one contiguous 16 N_S-byte
         // run per neighbour on the board, time-major) are copied into their
-        // slots of S.other by the bulk-copy engine, issued by one thread
-        // against one mbarrier; meanwhile the block stages the world
+        // slots of S.other by the bulk-copy engine, issued by one thread of
+        // warp 1 against one mbarrier; meanwhile the block stages the world
         const int n_plan = __shfl_sync(0xffffffffu, incl, 31);   // plan spheres of all neighbours
-        if (g == 0 && n_plan > 0) {
+        if (g == 1 && n_plan > 0) {
             if (lane == 0) {
                 tc::fence_async_smem();   // the previous unit's generic reads come first
                 fused_bar_expect(&s_bar, (uint32_t)n_plan * 16u);
@@ -658,17 +658,17 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 }
             }
         }
-        // the rest of the staging starts on warps 1 to 4 (warp 0 issues the
-        // plan copies, warp 7 claims the next unit)
+        // the rest of the staging starts on warps 2 to 6 and leaves warp 0
+        // out (warp 1 issues the plan copies, warp 7 claims the next unit)
         const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
-        for (int k = (threadIdx.x + 224) & 255; k < n_world; k += blockDim.x) {
+        for (int k = (threadIdx.x + 192) & 255; k < n_world; k += blockDim.x) {
             const float4 o = D.world[k], v = D.world_vel[k];
             put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
                                         __fmaf_rn(v.z, t_h, o.z), o.w));
         }
-        for (int k = (threadIdx.x + 160) & 255; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
+        for (int k = (threadIdx.x + 128) & 255; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
         {
-            const int k = (threadIdx.x + 128) & 255;
+            const int k = (threadIdx.x + 96) & 255;
             if (k < A.dof) {
                 S.dh[k] = A.dh[k];
                 S.tw[k] = A.twist[k];
@@ -677,13 +677,13 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             else if (k < 12) S.base[k] = A.base_t[k - 9];
             else if (k < 24) S.goal[k - 12] = D.input[A.off_in + 2 * A.dof + k - 12];
         }
-        for (int k = (threadIdx.x + 96) & 255; k < A.ns; k += blockDim.x) {
+        for (int k = (threadIdx.x + 64) & 255; k < A.ns; k += blockDim.x) {
             S.sph[k] = A.sph[k];
             S.frame[k] = A.frame[k];
         }
         // self pairs as byte offsets of both spheres in the own buffer, with
         // their squared ramp bound
-        for (int k = threadIdx.x; k < A.n_self; k += blockDim.x) {
+        for (int k = (int)threadIdx.x - 32; k >= 0 && k < A.n_self; k += blockDim.x - 32) {
             const int pr = D.self_pairs[A.self_off + k];
             S.pairs[k] = make_int2(((pr & 0xff) << 9) | ((pr >> 8) << 25),
                                    __float_as_int(D.self_t2[A.self_off + k]));
