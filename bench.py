@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "rollout trajectory-steps/s and control-cycle p50/p99 latency, learned vs exact"
 UNIT = "trajectory-steps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_rollout
+# launch on workload 2, from one ncu capture of the kernel as it stands; set
+# back to None whenever the kernel changes, until it is captured again
+ROLLOUT_TRAFFIC_BYTES = 2204160
 
 
 def measured_peaks():
@@ -629,7 +633,7 @@ def run(args):
         "kernel_ms": k_mean,
         "roofline": {"kernel": "k_rollout", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ROLLOUT_TRAFFIC_BYTES,
                      "peak_source": "FP32 FMA peak from unit counts and the maximum SM clock "
                                     "(152 SMs x 128 lanes x 2 x 2.07 GHz)",
                      "flops_per_launch": flops},
