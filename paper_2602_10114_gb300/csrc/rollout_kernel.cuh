@@ -688,6 +688,22 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             S.pairs[k] = make_int2(((pr & 0xff) << 9) | ((pr >> 8) << 25),
                                    __float_as_int(D.self_t2[A.self_off + k]));
         }
+        // the first sub-batch's joint sines and cosines (warp j takes joint j)
+        // are staged with the unit, so the staging barrier also serves them
+        if (it == 0) {     // the sampled trajectories and limit terms come from the sample kernel
+            pdl_wait();
+            pdl_trigger();
+        }
+        {
+            const int n = T.n0 + lane;
+            const bool valid = n < A.K;
+            for (int j = g; j < A.dof; j += kGroups) {
+                float sn, cs;
+                const float qj = D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
+                sincosf(__fadd_rn(qj, A.dh[j].w), &sn, &cs);
+                S.sc[j * 32 + lane] = make_float2(sn, cs);
+            }
+        }
         if (n_plan > 0) {
             // bounded wait for the plan copies, then the derived layouts; if
             // a copy did not land in time the block records the error, waits
@@ -720,10 +736,6 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         __syncthreads();   // the unit's inputs are staged
         const int n_nb = nnb;
-        if (it == 0) {     // the sampled trajectories and limit terms come from the sample kernel
-            pdl_wait();
-            pdl_trigger();
-        }
 
         for (int sb = 0; sb < T.nsub; ++sb, buf ^= 1) {
             RolloutSmem Sb = S;
@@ -737,14 +749,17 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 cp_async4(&s_lim[lane], D.stage_lim + A.off_kh + (long long)h * A.K + n);
             // sine and cosine of every joint angle of the sub-batch, once
             // (warp j takes joint j): the sphere groups' kinematic chains
-            // share them
-            for (int j = g; j < A.dof; j += kGroups) {
-                float sn, cs;
-                const float qj = D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
-                sincosf(__fadd_rn(qj, S.dh[j].w), &sn, &cs);
-                S.sc[j * 32 + lane] = make_float2(sn, cs);
+            // share them (the first sub-batch's came with the staging)
+            if (sb > 0) {
+                for (int j = g; j < A.dof; j += kGroups) {
+                    float sn, cs;
+                    const float qj =
+                        D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
+                    sincosf(__fadd_rn(qj, S.dh[j].w), &sn, &cs);
+                    S.sc[j * 32 + lane] = make_float2(sn, cs);
+                }
+                __syncthreads();
             }
-            __syncthreads();
             float pose = 0.f;
             switch (A.spg) {
                 case 1: rollout_group<1>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
