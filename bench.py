@@ -371,7 +371,7 @@ def plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, dev):
             "e2e": {"value": units * ws / e2e_s, "cycles": len(lat),
                     "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                     "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))},
-            "gpu_launches_per_step": int(A * (2 + 4 * sc.params["iterations"]))}
+            "gpu_launches_per_step": int(A * (1 + 4 * sc.params["iterations"]))}
 
 
 def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
@@ -643,7 +643,7 @@ def run(args):
         "learned": learned,
         "learned_pair": learned_pair,
         "other_workloads": others,
-        "gpu_launches": int((2 + 4 * sc.params["iterations"]) * args.steps),
+        "gpu_launches": int((1 + 4 * sc.params["iterations"]) * args.steps),
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -279,8 +279,10 @@ mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise);
  * captured graph).  mrs_kernel_times writes the durations (ms) of the last
  * cycle's stages, in launch order: prep, then per iteration sample,
  * surrogate (zero without a surrogate), rollout, costs, update, then toplan
- * (2 + 5 * iterations values); *n gives the capacity of ms on entry and the
- * count on return.  Waits for the cycle. */
+ * (2 + 5 * iterations values); prep is zero when Sense + Shift run inside the
+ * first sample launch (every arm with at most 32 blocks of 32 samples).  *n
+ * gives the capacity of ms on entry and the count on return.  Waits for the
+ * cycle. */
 mrs_status mrs_enable_timing(mrs_ctx *ctx, int on);
 mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
 

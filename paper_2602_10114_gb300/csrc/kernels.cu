@@ -1,11 +1,12 @@
 // kernels.cu -- the sm_103a kernels of one MR-STORM control cycle.
 //
 // Per cycle (Algorithm 1 of arxiv 2602.10114, all arms batched):
-//   k_prep     Sense + Shift: distance-to-goal, priority weights alpha^(j,i)
-//              (Sec. IV-B), left shift of phi (Sec. III-A), Cholesky L_h.
 //   per optimisation iteration:
 //     k_sample   SampleControls: Philox normals, eps = L_h z, U = mu + eps,
-//                semi-implicit Euler integration, stop/joint-limit terms.
+//                semi-implicit Euler integration, stop/joint-limit terms;
+//                on the first iteration also Sense + Shift: distance-to-goal,
+//                priority weights alpha^(j,i) (Sec. IV-B), left shift of phi
+//                (Sec. III-A), Cholesky L_h.
 //     k_rollout  Rollout: DH kinematics of the collision spheres and the
 //                world / self / coordination clearance terms (Eq. 5,
 //                Sec. IV-A), stage cost C_{n,h}.
@@ -108,6 +109,10 @@ __device__ __forceinline__ void cholesky_unrolled(int d, const float *S, float *
             if (i < d && j < d) Lout[i * d + j] = (j <= i) ? L[i][j] : 0.f;
 }
 
+// Sense + Shift as a kernel of its own (one block per arm), for workloads
+// whose arms have many sample blocks: distance-to-goal, priority weights
+// alpha^(j,i) (Sec. IV-B), the shifted state (Sec. III-A) into this cycle's
+// buffer and the Cholesky factors L_h.
 __global__ void k_prep(Params P, Dev D)
 {
     extern __shared__ float sm[];
@@ -137,11 +142,11 @@ __global__ void k_prep(Params P, Dev D)
         s_bvalid[t] = plan_usable(P, D.board_valid[t], D.board_stamp[t], cycle) ? 1 : 0;
         s_bdist[t] = D.board_dist[t];
     }
-    if (a == 0)   // rollout tile counters of this cycle's iterations
-        for (int i = t; i < P.iterations; i += blockDim.x) D.work[i] = 0;
     if (external) return;   // optimised elsewhere (uniform over the block)
-    float *Sig = D.Sigma + off_hdd;
-    float *mu = D.mu + off_hd;
+    const float *Sig = sigma_buf(D, cycle) + off_hdd;   // the previous cycle's state
+    const float *mu = mu_buf(D, cycle) + off_hd;
+    float *Sig_cur = sigma_buf(D, cycle + 1) + off_hdd;  // this cycle's
+    float *mu_cur = mu_buf(D, cycle + 1) + off_hd;
     float *sS = sm, *sL = sm + H * dd, *sM = sm + 2 * H * dd;
 
     // second wave: the shifted distribution (Shift, Sec. III-A: phi_h <-
@@ -161,10 +166,8 @@ __global__ void k_prep(Params P, Dev D)
     }
     if (t < 2 * d + 12) s_in[t] = D.input[off_in + t];
     __syncthreads();
-    if (shift) {
-        for (int i = t; i < H * dd; i += blockDim.x) Sig[i] = sS[i];
-        for (int i = t; i < H * d; i += blockDim.x) mu[i] = sM[i];
-    }
+    for (int i = t; i < H * dd; i += blockDim.x) Sig_cur[i] = sS[i];
+    for (int i = t; i < H * d; i += blockDim.x) mu_cur[i] = sM[i];
     // Cholesky factor of every step's covariance (in shared memory), and, on
     // the last thread, Sense: the end effector's distance to the goal
     for (int h = t; h < H; h += blockDim.x) cholesky_unrolled(d, sS + h * dd, sL + h * dd);
@@ -189,22 +192,37 @@ __global__ void k_prep(Params P, Dev D)
 }
 
 // ---------------------------------------------------------------------------
-// SampleControls + integration (one block per (arm, 32 samples))
+// SampleControls + integration (one block per (arm, 32 samples)).  With
+// with_prep (first iteration, arms of at most 32 sample blocks) the launch is
+// also the cycle's Sense + Shift: every block
+// shifts the previous state (Shift, Sec. III-A: phi_h <- phi_{h+1}, the last
+// step keeps its mean and restarts from sigma_init^2 I; not before the first
+// cycle) chunk by chunk into shared memory and factors each step's
+// covariance; the arm's first block (n0 = 0) publishes the shifted state
+// into the cycle's buffer and the factors, and computes the sensed distance
+// to the goal and the priorities alpha^(j,i) (Sec. IV-B).
 
 __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTile *tiles, int iter,
-                                                int smem_floats)
+                                                int smem_floats, int with_prep)
 {
     extern __shared__ float sm[];
+    __shared__ float s_bdist[MRS_MAX_ARMS];
+    __shared__ int s_bvalid[MRS_MAX_ARMS];   // usable: published and fresh enough
+    __shared__ float s_e;
     const SampleTile T = tiles[blockIdx.x];
     const long long cycle = *D.cycle;
     const ArmDev &A = D.arms[T.arm];
     const int d = A.dof, H = A.H, K = A.K, dd = d * d;
     const int off_hdd = A.off_hdd, off_hd = A.off_hd;
+    const bool prep = with_prep != 0, leader = prep && T.n0 == 0;
+    const float *mu_prev = mu_buf(D, cycle) + off_hd, *sig_prev = sigma_buf(D, cycle) + off_hdd;
+    float *mu_cur = mu_buf(D, cycle + 1) + off_hd, *sig_cur = sigma_buf(D, cycle + 1) + off_hdd;
     // the horizon in chunks of Hc steps that fit the block's shared memory
     const int Hc = max(1, min(H, smem_floats / (dd + d + 2 * d * 32)));
     float *sL = sm;                 // [Hc][d][d]
     float *sMu = sL + Hc * dd;      // [Hc][d]
-    float *sU = sMu + Hc * d;       // [Hc][d][32]: U, then the joint-limit terms
+    float *sU = sMu + Hc * d;       // [Hc][d][32]: U, then the joint-limit terms (the shifted
+                                    // covariances before that, on the first iteration)
     float *sS = sU + Hc * d * 32;   // [Hc][d][32]: stop terms
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -227,17 +245,48 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
         lo = __fadd_rn(A.q_lo[ij], P.q_margin);
         vmax = A.qd_max[ij];
     }
-    pdl_wait();      // L and mu come from the prep (or the previous update)
+    if (leader && ti < P.n_arms) {   // the board's published distances, for the priorities
+        s_bvalid[ti] = plan_usable(P, D.board_valid[ti], D.board_stamp[ti], cycle) ? 1 : 0;
+        s_bdist[ti] = D.board_dist[ti];
+    }
+    pdl_wait();      // later iterations: L and mu come from the previous update
     pdl_trigger();
+    const bool shift = cycle > 0;
+    const float s2 = P.sigma_init * P.sigma_init;
 
     for (int h0 = 0; h0 < H; h0 += Hc) {
         const int nh = min(Hc, H - h0);
+        if (prep) {
+            float *sSig = sU;   // [nh][dd] <= [nh][d][32]
 #pragma unroll 4
-        for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
-            sL[i] = D.L[off_hdd + (long long)h0 * dd + i];
-        for (int i = threadIdx.x; i < nh * d; i += blockDim.x)
-            sMu[i] = D.mu[off_hd + h0 * d + i];
-        __syncthreads();
+            for (int i = threadIdx.x; i < nh * dd; i += blockDim.x) {
+                const int hl = i / dd, k = i - hl * dd, h = h0 + hl;
+                sSig[i] = !shift ? sig_prev[h * dd + k]
+                                 : (h + 1 < H ? sig_prev[(h + 1) * dd + k]
+                                              : ((k % (d + 1) == 0) ? s2 : 0.f));
+            }
+            for (int i = threadIdx.x; i < nh * d; i += blockDim.x) {
+                const int h = h0 + i / d, src = h0 * d + i;
+                sMu[i] = (shift && h + 1 < H) ? mu_prev[src + d] : mu_prev[src];
+            }
+            __syncthreads();
+            for (int hl = threadIdx.x; hl < nh; hl += blockDim.x)
+                cholesky_unrolled(d, sSig + hl * dd, sL + hl * dd);
+            if (leader) {   // the cycle's shifted state
+                for (int i = threadIdx.x; i < nh * dd; i += blockDim.x) sig_cur[h0 * dd + i] = sSig[i];
+                for (int i = threadIdx.x; i < nh * d; i += blockDim.x) mu_cur[h0 * d + i] = sMu[i];
+            }
+            __syncthreads();
+            if (leader)
+                for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
+                    D.L[off_hdd + (long long)h0 * dd + i] = sL[i];
+        } else {
+#pragma unroll 4
+            for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
+                sL[i] = D.L[off_hdd + (long long)h0 * dd + i];
+            for (int i = threadIdx.x; i < nh * d; i += blockDim.x) sMu[i] = mu_cur[h0 * d + i];
+            __syncthreads();
+        }
 
         for (int hl = warp; hl < nh; hl += blockDim.x >> 5) {
             const int h = h0 + hl;
@@ -269,8 +318,24 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
                 sS[idx] = hinge2(__fsub_rn(fabsf(qd), vmax));
                 sU[idx] = __fadd_rn(hinge2(__fsub_rn(q, hi)), hinge2(__fsub_rn(lo, q)));
             }
+        } else if (leader && h0 == 0 && ti == blockDim.x - 1) {
+            // Sense, on an idle warp: the end effector's distance to the goal
+            Frame F;
+            frame_base(A, F);
+            for (int i = 0; i < d; ++i) frame_step(F, in[i], A.dh[i], A.twist[i]);
+            const float *gp = in + 2 * d;
+            const float dx = __fsub_rn(F.t[0], gp[0]), dy = __fsub_rn(F.t[1], gp[1]),
+                        dz = __fsub_rn(F.t[2], gp[2]);
+            s_e = sqrtf(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+            D.e_now[T.arm] = s_e;
         }
         __syncthreads();
+        if (leader && h0 == 0)
+            // Priority of every neighbour with a published plan (Sec. IV-B),
+            // from the own sensed distance and the neighbour's published one.
+            for (int i = ti; i < P.n_arms; i += blockDim.x)
+                D.alpha[T.arm * P.n_arms + i] =
+                    (i != T.arm && s_bvalid[i]) ? priority(s_e, s_bdist[i], P.tau) : 0.f;
         for (int t = threadIdx.x; t < 32 * nh; t += blockDim.x) {
             const int l = t & 31, hl = t >> 5;
             const int nn = T.n0 + l;
@@ -343,6 +408,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     constexpr int kM2 = kMoments - kMaxDof;
     const UpdateTile T = tiles[blockIdx.x];
     const ArmDev &A = D.arms[T.arm];
+    const long long cycle = *D.cycle;
     const int d = A.dof, K = A.K, h = T.h, dd = d * d;
     const float *C = D.costs + A.off_k;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT >> 5;
@@ -431,8 +497,8 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     __syncthreads();
 
     const float invZ = __frcp_rn(s_Z);
-    float *mu = D.mu + A.off_hd + h * d;
-    float *Sig = D.Sigma + A.off_hdd + h * dd;
+    float *mu = mu_buf(D, cycle + 1) + A.off_hd + h * d;          // the cycle's state
+    float *Sig = sigma_buf(D, cycle + 1) + A.off_hdd + h * dd;
     // PickBest on the last iteration: U_* = mu_1 + eps_{n*,1} (before the update)
     if (last && h == 0 && threadIdx.x < d) {
         const int j = threadIdx.x;
@@ -491,6 +557,7 @@ __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_count
     __shared__ float s_e;
     const int a = blockIdx.x, t = threadIdx.x;
     const ArmDev &A = D.arms[a];
+    const long long cyc = *D.cycle;
     // wave 1: header and constants (fixed extents, no dependence on the header)
     const int d = A.dof, H = A.H, ns = A.ns, off_hd = A.off_hd, off_in = A.off_in;
     const bool local = !A.external;   // external arms keep the plan they were given
@@ -516,7 +583,7 @@ __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_count
     pdl_wait();
     pdl_trigger();
     if (local) {
-        const float *mu = D.mu + off_hd;
+        const float *mu = mu_buf(D, cyc + 1) + off_hd;   // the cycle's updated mean
 #pragma unroll 4
         for (int i = t; i < Hd; i += blockDim.x) smu[i] = mu[i];
     }
@@ -583,6 +650,7 @@ __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_count
             *D.cycle = s_cycle + 1;
             *D.world_t = __fadd_rn(*D.world_t, P.dt);
             *done_counter = 0;
+            for (int i = 0; i < P.iterations; ++i) D.work[i] = 0;   // the next cycle's tile counters
         }
     }
 }
@@ -759,12 +827,14 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
     // with timing events between them)
     const bool pdl = events == nullptr;
     mark();
-    k_prep<<<L.n_arms, 512, L.smem_prep, s>>>(P, D);
-    mark();
+    if (!L.merge_prep) k_prep<<<L.n_arms, 512, L.smem_prep, s>>>(P, D);
+    mark();   // with merge_prep, Sense + Shift run in the first sample launch
     for (int it = 0; it < P.iterations; ++it) {
         const int last = (it == P.iterations - 1);
-        if ((rec = launch_k(k_sample, L.n_sample_tiles, 512, L.smem_sample, s, pdl, P, D,
-                            L.sample_tiles, it, (int)(L.smem_sample / sizeof(float)))) !=
+        // with merge_prep the first sample launch opens the cycle (no kernel before it)
+        const int with_prep = (it == 0 && L.merge_prep) ? 1 : 0;
+        if ((rec = launch_k(k_sample, L.n_sample_tiles, 512, L.smem_sample, s, pdl && !with_prep, P, D,
+                            L.sample_tiles, it, (int)(L.smem_sample / sizeof(float)), with_prep)) !=
             cudaSuccess)
             return rec;
         if (P.w_manip > 0.f)

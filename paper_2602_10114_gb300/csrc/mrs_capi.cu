@@ -121,8 +121,8 @@ static void build_layout(mrs_ctx *c)
     L.world_vel = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
     L.aabb = take(sizeof(float4) * 2 * MRS_MAX_AABBS);
     L.world_n = take(sizeof(int) * 2);
-    L.mu = take(sizeof(float) * c->sz.hd);
-    L.Sigma = take(sizeof(float) * c->sz.hdd);
+    L.mu = take(sizeof(float) * 2 * c->sz.hd);       // two buffers (cycle parity)
+    L.Sigma = take(sizeof(float) * 2 * c->sz.hdd);
     L.L = take(sizeof(float) * c->sz.hdd);
     L.board_sph = take(sizeof(float) * c->sz.hs);
     L.board_q = take(sizeof(float) * c->sz.hd);
@@ -217,6 +217,8 @@ static void fill_dev(mrs_ctx *c, char *base)
     D.world_n = (int *)(base + L.world_n);
     D.mu = (float *)(base + L.mu);
     D.Sigma = (float *)(base + L.Sigma);
+    D.st_hd = (long long)c->sz.hd;
+    D.st_hdd = (long long)c->sz.hdd;
     D.L = (float *)(base + L.L);
     D.board_sph = (float4 *)(base + L.board_sph);
     D.board_q = (float *)(base + L.board_q);
@@ -444,8 +446,12 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     L.n_update_tiles = (int)ctx->update_tiles.size();
     L.total_kh = (int)kh;
     size_t sp = 0, ss = 0, st2 = 0;
+    L.merge_prep = true;
     for (auto &A : ctx->arms) {
         sp = std::max(sp, sizeof(float) * (size_t)A.H * (2 * A.dof * A.dof + A.dof));
+        // the merged Sense + Shift repeats the arm's H factorisations in each of
+        // its sample blocks: worth a launch less only for a few blocks per arm
+        if (!A.external && (A.K + 31) / 32 > 32) L.merge_prep = false;
         // k_sample: the whole horizon, or chunks of it within 96 KB
         const size_t per_h = sizeof(float) * (size_t)(A.dof * A.dof + A.dof + 2 * A.dof * 32);
         ss = std::max(ss, std::min((size_t)A.H * per_h, std::max(per_h, (size_t)96 * 1024)));
@@ -879,14 +885,15 @@ mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes)
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
     const int A = ctx->A;
-    std::vector<float> mu(ctx->sz.hd), Sg(ctx->sz.hdd), sph(ctx->sz.hs), q(ctx->sz.hd), dist(A);
+    std::vector<float> mu2(2 * ctx->sz.hd), Sg2(2 * ctx->sz.hdd), sph(ctx->sz.hs), q(ctx->sz.hd),
+        dist(A);
     std::vector<int> valid(A);
     std::vector<long long> stamp(A);
     long long cycle = 0;
     float wt = 0.f;
     const Dev &D = ctx->D;
-    CK(cudaMemcpyAsync(mu.data(), D.mu, sizeof(float) * mu.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
-    CK(cudaMemcpyAsync(Sg.data(), D.Sigma, sizeof(float) * Sg.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(mu2.data(), D.mu, sizeof(float) * mu2.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
+    CK(cudaMemcpyAsync(Sg2.data(), D.Sigma, sizeof(float) * Sg2.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
     CK(cudaMemcpyAsync(sph.data(), D.board_sph, sizeof(float) * sph.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
     CK(cudaMemcpyAsync(q.data(), D.board_q, sizeof(float) * q.size(), cudaMemcpyDeviceToHost, ctx->stream), "save");
     CK(cudaMemcpyAsync(dist.data(), D.board_dist, sizeof(float) * A, cudaMemcpyDeviceToHost, ctx->stream), "save");
@@ -895,15 +902,18 @@ mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes)
     CK(cudaMemcpyAsync(&cycle, D.cycle, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream), "save");
     CK(cudaMemcpyAsync(&wt, D.world_t, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "save");
     CK(cudaStreamSynchronize(ctx->stream), "save sync");
+    // the current state is the buffer of the cycle's parity
+    const float *mu = mu2.data() + (cycle & 1) * ctx->sz.hd;
+    const float *Sg = Sg2.data() + (cycle & 1) * ctx->sz.hdd;
     char *p = (char *)blob;
     BlobHeader hdr{0x3152534du, 1u, (uint32_t)A, 0u, cycle, wt, 0.f};
     std::memcpy(p, &hdr, sizeof(hdr));
     p += sizeof(hdr);
     for (int a = 0; a < A; ++a) {
         const ArmDev &Ar = ctx->arms[a];
-        std::memcpy(p, mu.data() + Ar.off_hd, sizeof(float) * Ar.H * Ar.dof);
+        std::memcpy(p, mu + Ar.off_hd, sizeof(float) * Ar.H * Ar.dof);
         p += sizeof(float) * Ar.H * Ar.dof;
-        std::memcpy(p, Sg.data() + Ar.off_hdd, sizeof(float) * Ar.H * Ar.dof * Ar.dof);
+        std::memcpy(p, Sg + Ar.off_hdd, sizeof(float) * Ar.H * Ar.dof * Ar.dof);
         p += sizeof(float) * Ar.H * Ar.dof * Ar.dof;
     }
     for (int a = 0; a < A; ++a) {
@@ -969,8 +979,12 @@ mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
     const Dev &D = ctx->D;
     long long cycle = hdr.cycle;
     float wt = hdr.world_t;
-    CK(cudaMemcpyAsync(D.mu, mu.data(), sizeof(float) * mu.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
-    CK(cudaMemcpyAsync(D.Sigma, Sg.data(), sizeof(float) * Sg.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
+    // into the buffer of the cycle's parity (the state after cycle - 1)
+    CK(cudaMemcpyAsync(D.mu + (cycle & 1) * ctx->sz.hd, mu.data(), sizeof(float) * mu.size(),
+                       cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemcpyAsync(D.Sigma + (cycle & 1) * ctx->sz.hdd, Sg.data(), sizeof(float) * Sg.size(),
+                       cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(cudaMemsetAsync(D.work, 0, sizeof(int) * 64, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.board_sph, sph.data(), sizeof(float) * sph.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.board_q, q.data(), sizeof(float) * q.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.board_dist, dist.data(), sizeof(float) * A, cudaMemcpyHostToDevice, ctx->stream), "load");

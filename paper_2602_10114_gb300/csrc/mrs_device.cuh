@@ -72,7 +72,8 @@ struct Dev {
     float4 *world_vel;     // [kMaxWorld] velocity (w unused)
     float4 *aabb;          // [kMaxAabb][2] centre, half extents
     int *world_n;          // [2] spheres, boxes
-    float *mu, *Sigma, *L; // state: [hd], [hdd], [hdd]
+    float *mu, *Sigma, *L; // state: [2][hd], [2][hdd] (by cycle parity), [hdd]
+    long long st_hd, st_hdd;   // element offset of the second mu / Sigma buffer
     float4 *board_sph;     // plan board read by the cycle: [hs/4]
     float *board_q;        // [hd]
     int *board_valid;      // [A]
@@ -116,6 +117,18 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// mu and Sigma are double-buffered by cycle parity: the state after cycle
+// c - 1 (*D.cycle == c) is in buffer c & 1; cycle c reads it, writes the
+// shifted state into buffer (c + 1) & 1 and updates that one.
+__device__ __forceinline__ float *mu_buf(const Dev &D, long long parity)
+{
+    return D.mu + (parity & 1) * D.st_hd;
+}
+__device__ __forceinline__ float *sigma_buf(const Dev &D, long long parity)
+{
+    return D.Sigma + (parity & 1) * D.st_hdd;
 }
 
 // Work items of the launch-grid work lists.

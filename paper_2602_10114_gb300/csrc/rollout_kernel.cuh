@@ -611,14 +611,12 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         // every warp: lane i decides for arm i
         bool ok = false;
         int ns_i = 0;
-        float al = 0.f;
         {
             const int i = lane;
             if (i < NA && i != T.arm && h < D.arms[i].H &&   // min(H_j, H_i)
                 plan_usable(P, D.board_valid[i], D.board_stamp[i], cycle)) {
                 ok = true;
                 ns_i = D.arms[i].ns;
-                al = D.alpha[T.arm * NA + i];
             }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, ok);
@@ -629,12 +627,11 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
+        const int pos = __popc(mask & ((1u << lane) - 1u));   // this lane's neighbour slot
         if (g == 1) {   // warp 0 may still be in the previous unit's cost stage
-            const int pos = __popc(mask & ((1u << lane) - 1u));
             if (ok) {
                 S.nb_start[pos] = n_world + incl - ns_i;
                 S.nb_arm[pos] = lane;
-                S.nb_alpha[tp * MRS_MAX_ARMS + pos] = al;
             }
             if (lane == 31) S.nb_start[nnb] = n_world + incl;
         }
@@ -690,10 +687,11 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         // the first sub-batch's joint sines and cosines (warp j takes joint j)
         // are staged with the unit, so the staging barrier also serves them
-        if (it == 0) {     // the sampled trajectories and limit terms come from the sample kernel
-            pdl_wait();
+        if (it == 0) {     // the sampled trajectories, limit terms and priorities come from
+            pdl_wait();    // the sample kernel
             pdl_trigger();
         }
+        if (g == 1 && ok) S.nb_alpha[tp * MRS_MAX_ARMS + pos] = D.alpha[T.arm * NA + lane];
         {
             const int n = T.n0 + lane;
             const bool valid = n < A.K;
