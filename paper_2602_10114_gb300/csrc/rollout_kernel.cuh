@@ -577,6 +577,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     __shared__ int s_tile[2];
     __shared__ float s_pose[2][32];
     __shared__ float s_lim[32];   // the sub-batch's joint-limit terms, copied ahead by warp 0
+    __shared__ long long s_idx[32];   // and each sample's stage-cost offset
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
     const long long cycle = *D.cycle;
@@ -695,7 +696,9 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         {
             const int n = T.n0 + lane;
             const bool valid = n < A.K;
-            for (int j = g; j < A.dof; j += kGroups) {
+            // joint j on warp (j + 1) mod 8: warp 0, still in the previous
+            // unit's cost stage, takes a joint only for 8 or more
+            for (int j = (g + kGroups - 1) % kGroups; j < A.dof; j += kGroups) {
                 float sn, cs;
                 const float qj = D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
                 sincosf(__fadd_rn(qj, A.dh[j].w), &sn, &cs);
@@ -743,13 +746,16 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             const bool valid = n < A.K;
             // warp 0 uses the sub-batch's stop / joint-limit terms in its cost
             // stage: copied to shared memory now, behind the kinematics
-            if (g == 0 && valid)
-                cp_async4(&s_lim[lane], D.stage_lim + A.off_kh + (long long)h * A.K + n);
+            if (g == 0 && valid) {
+                const long long idx = A.off_kh + (long long)h * A.K + n;
+                cp_async4(&s_lim[lane], D.stage_lim + idx);
+                s_idx[lane] = idx;
+            }
             // sine and cosine of every joint angle of the sub-batch, once
             // (warp j takes joint j): the sphere groups' kinematic chains
             // share them (the first sub-batch's came with the staging)
             if (sb > 0) {
-                for (int j = g; j < A.dof; j += kGroups) {
+                for (int j = (g + kGroups - 1) % kGroups; j < A.dof; j += kGroups) {
                     float sn, cs;
                     const float qj =
                         D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
@@ -776,7 +782,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             if (g == 0) {
                 cp_async_wait_all();
                 if (valid) {
-                    const long long idx = A.off_kh + (long long)h * A.K + n;
+                    const long long idx = s_idx[lane];
                     const float dw = ordered_to_float(Sb.red[0 * 32 + lane]);
                     const float dsf = ordered_to_float(Sb.red[1 * 32 + lane]);
                     float dyn = 0.f;
