@@ -307,16 +307,27 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
         }
         __syncthreads();
 
-        // Integration, one thread per (sample, joint), sequential over the horizon.
+        // Integration, one thread per (sample, joint), sequential over the
+        // horizon; the controls are read 8 steps ahead, so that the chain
+        // does not wait on shared memory at every step.
         if (integrates) {
             const int nn = T.n0 + il;
-            for (int hl = 0; hl < nh; ++hl) {
-                const int h = h0 + hl;
-                const int idx = (hl * d + ij) * 32 + il;
-                integrate(q, qd, sU[idx], P.dt);
-                if (nn < K) traj[(long long)(h * d + ij) * K + nn] = q;
-                sS[idx] = hinge2(__fsub_rn(fabsf(qd), vmax));
-                sU[idx] = __fadd_rn(hinge2(__fsub_rn(q, hi)), hinge2(__fsub_rn(lo, q)));
+            for (int hb = 0; hb < nh; hb += 8) {
+                float u[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    u[k] = (hb + k < nh) ? sU[((hb + k) * d + ij) * 32 + il] : 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int hl = hb + k;
+                    if (hl >= nh) break;
+                    const int h = h0 + hl;
+                    const int idx = (hl * d + ij) * 32 + il;
+                    integrate(q, qd, u[k], P.dt);
+                    if (nn < K) traj[(long long)(h * d + ij) * K + nn] = q;
+                    sS[idx] = hinge2(__fsub_rn(fabsf(qd), vmax));
+                    sU[idx] = __fadd_rn(hinge2(__fsub_rn(q, hi)), hinge2(__fsub_rn(lo, q)));
+                }
             }
         } else if (leader && h0 == 0 && ti == blockDim.x - 1) {
             // Sense, on an idle warp: the end effector's distance to the goal
@@ -590,11 +601,19 @@ __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_count
     __syncthreads();
     if (local) {
         // integration, one thread per joint, sequential over the horizon
+        // (the mean read 8 steps ahead)
         if (t < d) {
             float q = s_in[t], qd = s_in[d + t];
-            for (int h = 0; h < H; ++h) {
-                integrate(q, qd, smu[h * d + t], P.dt);
-                sq[h * d + t] = q;
+            for (int hb = 0; hb < H; hb += 8) {
+                float u[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) u[k] = (hb + k < H) ? smu[(hb + k) * d + t] : 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (hb + k >= H) break;
+                    integrate(q, qd, u[k], P.dt);
+                    sq[(hb + k) * d + t] = q;
+                }
             }
         }
         for (int i = t; i < Hd; i += blockDim.x) D.out[D.out_mean + off_hd + i] = smu[i];
