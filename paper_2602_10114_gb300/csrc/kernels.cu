@@ -431,6 +431,14 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     extern __shared__ float s_dyn[];
     float (*s_part)[NT + 1] = reinterpret_cast<float (*)[NT + 1]>(s_dyn);
     __shared__ float s_mom[kMoments + 1];
+    // the first sample's noise of this thread (e_first) is loaded before the
+    // wait: the sample kernel that wrote it finished before the costs kernel
+    // could start, and the minimum below does not need it
+    const float *eps = D.eps + A.off_khd + (long long)h * d * K;
+    float e_first[kMaxDof];
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j)
+        e_first[j] = (j < d && (int)threadIdx.x < K) ? eps[(long long)j * K + threadIdx.x] : 0.f;
     pdl_wait();      // the totals come from the costs kernel
     pdl_trigger();
 
@@ -470,14 +478,14 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     for (int j = 0; j < kMaxDof; ++j) m1[j] = 0.f;
 #pragma unroll
     for (int k = 0; k < kM2; ++k) m2[k] = 0.f;
-    const float *eps = D.eps + A.off_khd + (long long)h * d * K;
 #pragma unroll 2
     for (int n = threadIdx.x; n < K; n += NT) {
         const float w = expf(-__fmul_rn(__fsub_rn(C[n], beta), inv_lambda));
         z = __fadd_rn(z, w);
         float e[kMaxDof];
 #pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) e[j] = (j < d) ? eps[(long long)j * K + n] : 0.f;
+        for (int j = 0; j < kMaxDof; ++j)
+            e[j] = (n == (int)threadIdx.x) ? e_first[j] : ((j < d) ? eps[(long long)j * K + n] : 0.f);
         int k = 0;
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) {
