@@ -439,6 +439,20 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
 #pragma unroll
     for (int j = 0; j < kMaxDof; ++j)
         e_first[j] = (j < d && (int)threadIdx.x < K) ? eps[(long long)j * K + threadIdx.x] : 0.f;
+    // so are this step's current mean and covariance entries (one per
+    // thread: mean j = thread, covariance entry (j, c) of the lower triangle
+    // number t = thread; d (d + 1) / 2 <= 45 < NT), written before the
+    // sample kernel ran
+    static_assert(kMaxDof * (kMaxDof + 1) / 2 <= NT, "one covariance entry per thread");
+    float *mu = mu_buf(D, cycle + 1) + A.off_hd + h * d;          // the cycle's state
+    float *Sig = sigma_buf(D, cycle + 1) + A.off_hdd + h * dd;
+    const int tcov = threadIdx.x;
+    int jt = 0;
+    while ((jt + 1) * (jt + 2) / 2 <= tcov && jt < kMaxDof) ++jt;
+    const int ct = tcov - jt * (jt + 1) / 2;
+    const bool has_cov = tcov < d * (d + 1) / 2;
+    const float mu_old = (int)threadIdx.x < d ? mu[threadIdx.x] : 0.f;
+    const float sig_old = has_cov ? Sig[jt * d + ct] : 0.f;
     pdl_wait();      // the totals come from the costs kernel
     pdl_trigger();
 
@@ -516,13 +530,11 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     __syncthreads();
 
     const float invZ = __frcp_rn(s_Z);
-    float *mu = mu_buf(D, cycle + 1) + A.off_hd + h * d;          // the cycle's state
-    float *Sig = sigma_buf(D, cycle + 1) + A.off_hdd + h * dd;
     // PickBest on the last iteration: U_* = mu_1 + eps_{n*,1} (before the update)
     if (last && h == 0 && threadIdx.x < d) {
         const int j = threadIdx.x;
         const float *e0 = D.eps + A.off_khd;
-        D.out[D.out_u + A.off_d + j] = __fadd_rn(mu[j], e0[(long long)j * K + s_best]);
+        D.out[D.out_u + A.off_d + j] = __fadd_rn(mu_old, e0[(long long)j * K + s_best]);
         if (j == 0) {
             D.out[D.out_min + T.arm] = beta;
             D.n_star[T.arm] = s_best;
@@ -532,15 +544,13 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     // Eq. 4 with Eq. 3 written through eps: delta = S1/Z, Sigma~ = S2/Z - delta delta^T
     if (threadIdx.x < d) {
         const int j = threadIdx.x;
-        mu[j] = __fmaf_rn(P.alpha_mu, __fmul_rn(s_mom[j], invZ), mu[j]);
+        mu[j] = __fmaf_rn(P.alpha_mu, __fmul_rn(s_mom[j], invZ), mu_old);
     }
-    for (int t = threadIdx.x; t < d * (d + 1) / 2; t += NT) {
-        int j = 0;
-        while ((j + 1) * (j + 2) / 2 <= t) ++j;
-        const int c = t - j * (j + 1) / 2;
+    if (has_cov) {
+        const int t = tcov, j = jt, c = ct;
         const float dj = __fmul_rn(s_mom[j], invZ), dc = __fmul_rn(s_mom[c], invZ);
         const float st = __fsub_rn(__fmul_rn(s_mom[kMaxDof + t], invZ), __fmul_rn(dj, dc));
-        const float nv = __fmaf_rn(P.alpha_sigma, st, __fmul_rn(1.f - P.alpha_sigma, Sig[j * d + c]));
+        const float nv = __fmaf_rn(P.alpha_sigma, st, __fmul_rn(1.f - P.alpha_sigma, sig_old));
         Sig[j * d + c] = nv;
         Sig[c * d + j] = nv;
     }
