@@ -487,8 +487,9 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         if (A.learned)
             need = valid && D.dhat[A.off_kh + (long long)h * K + n] < P.B_self + A.self_margin;
         const int np = (!A.learned || __any_sync(0xffffffffu, need)) ? A.n_self : 0;
-        const int p0 = (np * g) / kGroups, p1 = (np * (g + 1)) / kGroups;
-        // 32 pairs at a time, one per lane, tested on the two spheres' boxes
+        // warp g takes pairs g, g + 8, g + 16, ... (interleaved, so that the
+        // pairs near contact, which cluster in the list, spread over the
+        // warps); 32 pairs at a time, one per lane, tested on the two spheres' boxes
         // over the sub-batch: a pair whose boxes are at least B_self + 1 mm
         // apart has every sample's spheres that far apart (each ball lies in
         // its box), outside the ramp, and is skipped (no result changes); the
@@ -496,10 +497,11 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         float m = kInf;
         const unsigned char *ownb = reinterpret_cast<const unsigned char *>(S.own) + lane * 16;
         const float tb = P.B_self + 1e-3f;
-        for (int base = p0; base < p1; base += 32) {
+        for (int base = g; base < np; base += 32 * kGroups) {
             bool near = false;
-            if (base + lane < p1) {
-                const int o = S.pairs[base + lane].x;
+            const int ip = base + kGroups * lane;
+            if (ip < np) {
+                const int o = S.pairs[ip].x;
                 const int a1 = (o & 0xffff) >> 9, a2 = (int)((unsigned)o >> 25);
                 const float4 l1 = S.sbox[2 * a1], h1 = S.sbox[2 * a1 + 1];
                 const float4 l2 = S.sbox[2 * a2], h2 = S.sbox[2 * a2 + 1];
@@ -510,7 +512,7 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             }
             unsigned mk = __ballot_sync(0xffffffffu, near);
             while (mk) {
-                const int i = base + __ffs(mk) - 1;
+                const int i = base + kGroups * (__ffs(mk) - 1);
                 mk &= mk - 1u;
                 const int2 pr = S.pairs[i];
                 const float4 c1 = *reinterpret_cast<const float4 *>(ownb + (pr.x & 0xffff));
