@@ -320,6 +320,25 @@ __device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 
                        -0.5f * ((s & 1) ? z1 : z0));
 }
 
+// The same minimum for a single candidate k: its exact distance to every own
+// sphere, the square root only inside the ramp (the pre-test and the flags
+// of clearance_pass cost more than the exact tests for one candidate).
+template <int NP>
+__device__ __forceinline__ float one_candidate(const RolloutSmem &S, int k, float B, int s0, int cnt,
+                                               const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
+                                               const f32x2 (&MZ)[NP])
+{
+    const float4 p = S.other[k];
+    float m = kInf;
+#pragma unroll
+    for (int s = 0; s < 2 * NP; ++s)
+        if (s < cnt) {
+            const float r = S.sph[s0 + s].w;
+            pair_exact(own_centre<NP>(MX, MY, MZ, s), __fadd_rn(r, B), r, p, m);
+        }
+    return m;
+}
+
 template <int SPG>
 __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmDev &A,
                                               const RolloutSmem &S, int h, int n, bool valid,
@@ -469,8 +488,10 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 if (!__any_sync(0xffffffffu, need)) continue;
             }
             const int nc = cull(S, k0, k1, Bp, world ? S.marg[0] : S.marg[1], box, lane, list);
-            float m = nc > 0 ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
-                             : kInf;   // nc is warp-uniform
+            // nc is warp-uniform
+            float m = nc > 1    ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
+                      : nc == 1 ? one_candidate<NP>(S, list[0], Bp, s0, cnt, MX, MY, MZ)
+                                : kInf;
             if (world) m = fminf(m, mbox);
             if (need && m < Bp)
                 atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
