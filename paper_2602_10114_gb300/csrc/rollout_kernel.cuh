@@ -631,6 +631,43 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         const ArmDev &A = D.arms[T.arm];
         const int h = T.h;
 
+        // the world at the step's time, the boxes, the arm's constants and its
+        // self pairs, staged by warps 2 to 7 first (their loads overlap the
+        // neighbour list below); warp 0 may still be in the previous unit's
+        // cost stage and warp 1 issues the plan copies
+        if (g >= 2) {
+            constexpr int kStage = kRolloutThreads - 64;
+            const int tl = (int)threadIdx.x - 64;
+            const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
+            for (int k = tl; k < n_world; k += kStage) {
+                const float4 o = D.world[k], v = D.world_vel[k];
+                put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
+                                            __fmaf_rn(v.z, t_h, o.z), o.w));
+            }
+            for (int k = (tl + 128) % kStage; k < 2 * n_aabb; k += kStage) S.aabb[k] = D.aabb[k];
+            {
+                const int k = (tl + 96) % kStage;
+                if (k < A.dof) {
+                    S.dh[k] = A.dh[k];
+                    S.tw[k] = A.twist[k];
+                }
+                if (k < 9) S.base[k] = A.base_R[k];
+                else if (k < 12) S.base[k] = A.base_t[k - 9];
+                else if (k < 24) S.goal[k - 12] = D.input[A.off_in + 2 * A.dof + k - 12];
+            }
+            for (int k = (tl + 64) % kStage; k < A.ns; k += kStage) {
+                S.sph[k] = A.sph[k];
+                S.frame[k] = A.frame[k];
+            }
+            // self pairs as byte offsets of both spheres in the own buffer,
+            // with their squared ramp bound
+            for (int k = tl; k < A.n_self; k += kStage) {
+                const int pr = D.self_pairs[A.self_off + k];
+                S.pairs[k] = make_int2(((pr & 0xff) << 9) | ((pr >> 8) << 25),
+                                       __float_as_int(D.self_t2[A.self_off + k]));
+            }
+        }
+
         // neighbour list (published plans whose horizon reaches step h), in
         // every warp: lane i decides for arm i
         bool ok = false;
@@ -662,7 +699,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         // the neighbours' plan spheres at step h (one contiguous 16 N_S-byte
         // run per neighbour on the board, time-major) are copied into their
         // slots of S.other by the bulk-copy engine, issued by one thread of
-        // warp 1 against one mbarrier; meanwhile the block stages the world
+        // warp 1 against one mbarrier
         const int n_plan = __shfl_sync(0xffffffffu, incl, 31);   // plan spheres of all neighbours
         if (g == 1 && n_plan > 0) {
             if (lane == 0) {
@@ -678,36 +715,6 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                               (uint32_t)Ai.ns * 16u, &s_bar);
                 }
             }
-        }
-        // the rest of the staging starts on warps 2 to 6 and leaves warp 0
-        // out (warp 1 issues the plan copies, warp 7 claims the next unit)
-        const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
-        for (int k = (threadIdx.x + 192) & 255; k < n_world; k += blockDim.x) {
-            const float4 o = D.world[k], v = D.world_vel[k];
-            put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
-                                        __fmaf_rn(v.z, t_h, o.z), o.w));
-        }
-        for (int k = (threadIdx.x + 128) & 255; k < 2 * n_aabb; k += blockDim.x) S.aabb[k] = D.aabb[k];
-        {
-            const int k = (threadIdx.x + 96) & 255;
-            if (k < A.dof) {
-                S.dh[k] = A.dh[k];
-                S.tw[k] = A.twist[k];
-            }
-            if (k < 9) S.base[k] = A.base_R[k];
-            else if (k < 12) S.base[k] = A.base_t[k - 9];
-            else if (k < 24) S.goal[k - 12] = D.input[A.off_in + 2 * A.dof + k - 12];
-        }
-        for (int k = (threadIdx.x + 64) & 255; k < A.ns; k += blockDim.x) {
-            S.sph[k] = A.sph[k];
-            S.frame[k] = A.frame[k];
-        }
-        // self pairs as byte offsets of both spheres in the own buffer, with
-        // their squared ramp bound
-        for (int k = (int)threadIdx.x - 32; k >= 0 && k < A.n_self; k += blockDim.x - 32) {
-            const int pr = D.self_pairs[A.self_off + k];
-            S.pairs[k] = make_int2(((pr & 0xff) << 9) | ((pr >> 8) << 25),
-                                   __float_as_int(D.self_t2[A.self_off + k]));
         }
         // the first sub-batch's joint sines and cosines (warp j takes joint j)
         // are staged with the unit, so the staging barrier also serves them
