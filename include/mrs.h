@@ -216,6 +216,16 @@ mrs_status mrs_step_device(mrs_ctx *ctx, const float *d_input);
  * pointers into it. */
 mrs_status mrs_output_device(mrs_ctx *ctx, mrs_step_out *out);
 
+/* Host pointers into the context's pinned copy of that result buffer (the
+ * same layout, output_floats floats), which mrs_step refreshes on every call,
+ * also when its out argument is NULL.  out->* receive pointers into it, valid
+ * until the context is destroyed; they hold the results of the last
+ * mrs_step and are overwritten by the next one.  A caller that copies the
+ * results anyway can pass out = NULL to mrs_step and copy the block from
+ * here once, instead of having mrs_step copy each result into its own
+ * buffer first. */
+mrs_status mrs_output_host(mrs_ctx *ctx, mrs_step_out *out);
+
 /* Wait (bounded by timeout_s seconds) for the work enqueued on the context
  * stream; MRS_ETIMEOUT if it does not finish in time. */
 mrs_status mrs_sync(mrs_ctx *ctx, double timeout_s);

@@ -854,6 +854,20 @@ mrs_status mrs_output_device(mrs_ctx *ctx, mrs_step_out *out)
     return MRS_OK;
 }
 
+mrs_status mrs_output_host(mrs_ctx *ctx, mrs_step_out *out)
+{
+    if (!ctx || !out) return MRS_EINVAL;
+    const Dev &D = ctx->D;
+    float *o = ctx->pin_out;
+    out->mean_plan = o + D.out_mean;
+    out->plan_spheres = o + D.out_sph;
+    out->plan_q = o + D.out_q;
+    out->u_star = o + D.out_u;
+    out->dist_to_goal = o + D.out_dist;
+    out->min_cost = o + D.out_min;
+    return MRS_OK;
+}
+
 mrs_status mrs_sync(mrs_ctx *ctx, double timeout_s)
 {
     if (!ctx) return MRS_EINVAL;

@@ -76,6 +76,7 @@ SIGNATURES = {
     "mrs_step": (C.c_int, [C.c_void_p, C.POINTER(MrsArmState), C.POINTER(MrsStepOut)]),
     "mrs_step_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mrs_output_device": (C.c_int, [C.c_void_p, C.POINTER(MrsStepOut)]),
+    "mrs_output_host": (C.c_int, [C.c_void_p, C.POINTER(MrsStepOut)]),
     "mrs_sync": (C.c_int, [C.c_void_p, C.c_double]),
     "mrs_use_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "mrs_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -277,9 +278,9 @@ class Controller:
 
     def _step_buffers(self):
         """Built once per controller: one contiguous input array (per arm q,
-        qd, goal_p, goal_R) with the arm-state array pointing into it, one
-        contiguous output array with the output struct pointing into it, and
-        the slices of each output."""
+        qd, goal_p, goal_R) with the arm-state array pointing into it, a view
+        of the context's pinned result block (mrs_output_host) and the
+        slices of each output in it."""
         A = len(self.sc.arms)
         sz = self.sizes
         xin = np.zeros(sum(2 * a.dof + 12 for a in self.sc.arms), np.float32)
@@ -291,19 +292,22 @@ class Controller:
                      xin[off + 2 * d + 3:off + 2 * d + 12])
             states[i] = MrsArmState(*[_pf(x) for x in parts])
             off += 2 * d + 12
-        sizes = (sz.hd, sz.hs, sz.hd, sz.d, A, A)
-        bounds = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
-        obuf = np.zeros(int(bounds[-1]), np.float32)
-        sl = [slice(int(bounds[i]), int(bounds[i + 1])) for i in range(len(sizes))]
-        o = MrsStepOut(*[_pf(obuf[x]) for x in sl])
+        o = MrsStepOut()
+        self._check(self.L.mrs_output_host(self.h, C.byref(o)), "output_host")
+        ptrs = [C.cast(getattr(o, k), C.c_void_p).value for k in self._OUT_KEYS]
+        base = min(ptrs)
+        block = np.ctypeslib.as_array((C.c_float * int(sz.output_floats)).from_address(base))
+        lens = (sz.hd, sz.hs, sz.hd, sz.d, A, A)
+        keys = tuple((k, slice((p - base) // 4, (p - base) // 4 + int(n)))
+                     for k, p, n in zip(self._OUT_KEYS, ptrs, lens))
         self._dofs = tuple(a.dof for a in self.sc.arms)
-        self._sbuf = (xin, states, obuf, tuple(zip(self._OUT_KEYS, sl)), C.byref(o), o)
+        self._sbuf = (xin, states, block, keys)
         return self._sbuf
 
     def step(self, q, qd, goal_p, goal_R):
         """One control cycle with host inputs; returns a dict of host arrays
         (fresh copies)."""
-        xin, states, obuf, keys, oref, _ = getattr(self, "_sbuf", None) or self._step_buffers()
+        xin, states, block, keys = getattr(self, "_sbuf", None) or self._step_buffers()
         parts = []
         for a, d in enumerate(self._dofs):
             qa, qda, gpa, gRa = q[a], qd[a], np.ravel(goal_p[a]), np.ravel(goal_R[a])
@@ -311,10 +315,10 @@ class Controller:
                 raise ValueError(f"arm {a}: q, qd need {d} values, goal_p 3, goal_R 9")
             parts += (qa, qda, gpa, gRa)
         np.concatenate(parts, out=xin)
-        st = self.L.mrs_step(self.h, states, oref)
+        st = self.L.mrs_step(self.h, states, None)   # results stay in the pinned block
         if st != 0:
             self._check(st, "step")
-        oc = obuf.copy()
+        oc = block.copy()
         return {k: oc[s] for k, s in keys}
 
     def step_device(self, d_input):
