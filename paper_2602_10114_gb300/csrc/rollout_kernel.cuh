@@ -393,11 +393,13 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         *pose_out = pose_cost(F, S.goal, S.goal + 3, P.w_rot);
     }
 
+    // box bounding each own sphere (centre +- radius) over the warp's 32
+    // samples (warp-wide floating-point min / max), kept for the self pass,
+    // and their union: the warp's box
+    float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
+    unsigned short *list = S.cand + g * S.cand_cap;
+    float *box = S.box + g * 8;
     if (cnt > 0) {
-        // box bounding each own sphere (centre +- radius) over the warp's 32
-        // samples (warp-wide floating-point min / max), kept
-        // for the self pass, and their union: the warp's box
-        float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
 #pragma unroll
         for (int s = 0; s < SPG; ++s)
             if (s < cnt) {
@@ -412,13 +414,16 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 lo.x = fminf(lo.x, bl.x); lo.y = fminf(lo.y, bl.y); lo.z = fminf(lo.z, bl.z);
                 hi.x = fmaxf(hi.x, bh.x); hi.y = fmaxf(hi.y, bh.y); hi.z = fmaxf(hi.z, bh.z);
             }
-        unsigned short *list = S.cand + g * S.cand_cap;
-        float *box = S.box + g * 8;
         if (lane == 0) {
             box[0] = lo.x; box[1] = lo.y; box[2] = lo.z;
             box[3] = hi.x; box[4] = hi.y; box[5] = hi.z;
         }
-        __syncwarp();
+    }
+    // every group's centres and sphere boxes are in shared memory; the
+    // obstacle passes below need only the warp's own spheres, so they share
+    // the phase up to the next barrier with the self pass
+    __syncthreads();
+    if (cnt > 0) {
 
         // world boxes (exact), then one pre-tested pass per sphere set over its
         // candidates: the world spheres (slot 0, buffer B_world) and each
@@ -497,7 +502,6 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
         }
     }
-    __syncthreads();   // every group's centres are in shared memory
 
     // self collision: the arm's pair list, split evenly over the 8 warps.  With
     // a learned surrogate, a rollout step whose predicted clearance is at least
