@@ -320,21 +320,24 @@ __device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 
                        -0.5f * ((s & 1) ? z1 : z0));
 }
 
-// The same minimum for a single candidate k: its exact distance to every own
-// sphere, the square root only inside the ramp (the pre-test and the flags
-// of clearance_pass cost more than the exact tests for one candidate).
+// The same minimum for one or two candidates: their exact distances to every
+// own sphere, the square root only inside the ramp (the pre-test and the
+// flags of clearance_pass cost more than the exact tests for so few).
 template <int NP>
-__device__ __forceinline__ float one_candidate(const RolloutSmem &S, int k, float B, int s0, int cnt,
-                                               const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
-                                               const f32x2 (&MZ)[NP])
+__device__ __forceinline__ float few_candidates(const RolloutSmem &S, const unsigned short *list,
+                                                int nc, float B, int s0, int cnt,
+                                                const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
+                                                const f32x2 (&MZ)[NP])
 {
-    const float4 p = S.other[k];
+    const float4 p0 = S.other[list[0]], p1 = S.other[list[nc > 1 ? 1 : 0]];
     float m = kInf;
 #pragma unroll
     for (int s = 0; s < 2 * NP; ++s)
         if (s < cnt) {
-            const float r = S.sph[s0 + s].w;
-            pair_exact(own_centre<NP>(MX, MY, MZ, s), __fadd_rn(r, B), r, p, m);
+            const float r = S.sph[s0 + s].w, rB = __fadd_rn(r, B);
+            const float3 c = own_centre<NP>(MX, MY, MZ, s);
+            pair_exact(c, rB, r, p0, m);
+            if (nc > 1) pair_exact(c, rB, r, p1, m);
         }
     return m;
 }
@@ -494,9 +497,9 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             }
             const int nc = cull(S, k0, k1, Bp, world ? S.marg[0] : S.marg[1], box, lane, list);
             // nc is warp-uniform
-            float m = nc > 1    ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
-                      : nc == 1 ? one_candidate<NP>(S, list[0], Bp, s0, cnt, MX, MY, MZ)
-                                : kInf;
+            float m = nc > 2   ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
+                      : nc > 0 ? few_candidates<NP>(S, list, nc, Bp, s0, cnt, MX, MY, MZ)
+                               : kInf;
             if (world) m = fminf(m, mbox);
             if (need && m < Bp)
                 atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
