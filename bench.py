@@ -568,9 +568,9 @@ def run(args):
     ctl.sync()
     tune = None
     if not args.no_autotune:
-        best, table = ctl.autotune(reps=5)
+        best, table = ctl.autotune(reps=9)
         tune = {"chosen": best, "tried": len(table),
-                "default_ms": next(t["rollout_ms"] for t in table
+                "default_ms": next(t["cycle_ms"] for t in table
                                    if (t["tile_samples"], t["order"]) == (32, 0)
                                    and t["blocks_per_sm"] == max(x["blocks_per_sm"] for x in table))}
 

@@ -314,17 +314,19 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
  * returns MRS_EINVAL for a shape out of range. */
 typedef struct {
     int tile_samples, blocks_per_sm, order;
-    float rollout_ms;          /* mrs_autotune: median rollout time of the shape */
+    float cycle_ms;            /* mrs_autotune: median control-cycle time of the shape */
 } mrs_rollout_shape;
 mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
 
 /* Autotuner: times every shape of the grid {32, 64, 96, 128, 192, 256}
- * samples x 1 ..
- * max resident blocks per SM x {step-major, arm-major} over `reps` control
- * cycles each (rollout stage, CUDA events, median) on the context's current
- * inputs, and keeps the fastest.  The controller state is saved before and
- * restored after the trials, so the next cycle is unaffected.  Needs one
+ * samples x 1 .. max resident blocks per SM x {step-major, arm-major} over
+ * `reps` whole control cycles each (the cycle as mrs_step_device runs it:
+ * CUDA graph without per-stage timing, so programmatic launch overlaps the
+ * stages; CUDA events around each cycle on the context's stream, median) on
+ * the context's current inputs, and keeps the fastest.  The controller state
+ * is saved before and restored after the trials, so the next cycle is
+ * unaffected; per-stage timing is switched back on if it was on.  Needs one
  * earlier mrs_step / mrs_step_device (the inputs the trials use);
  * otherwise MRS_ESTATE.  `table` (host, capacity `cap`, may be null)
  * receives every shape tried with its time, *n_tried their count; `best`

@@ -1461,7 +1461,7 @@ mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *ma
         shape->tile_samples = ctx->tile_samples;
         shape->blocks_per_sm = ctx->blocks_per_sm;
         shape->order = ctx->tile_order;
-        shape->rollout_ms = 0.f;
+        shape->cycle_ms = 0.f;
     }
     if (max_blocks_per_sm) *max_blocks_per_sm = ctx->max_blocks_per_sm;
     return MRS_OK;
@@ -1476,27 +1476,40 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     if (st != MRS_OK) return st;
     std::vector<char> blob(ctx->sz.state_bytes);
     if ((st = mrs_save_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;
+    // Whole cycles are timed as they run in use: the graph without timing
+    // nodes, so that each kernel's prologue overlaps its predecessor's tail
+    // (programmatic launch).  A shape's rollout time alone misleads: per-stage
+    // timing serialises the stages, and a shape that is fast there can leave
+    // the following stages waiting under overlap.
     const bool timing = ctx->timing;
-    if ((st = mrs_enable_timing(ctx, 1)) != MRS_OK) return st;
-    const int stages = 2 + 5 * ctx->P.iterations;
+    if ((st = mrs_enable_timing(ctx, 0)) != MRS_OK) return st;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return fail(ctx, MRS_ECUDA, "autotune: event create");
+    }
     std::vector<mrs_rollout_shape> tried;
     mrs_rollout_shape keep{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
     float best_ms = INFINITY;
     for (int ts : {32, 64, 96, 128, 192, 256}) {
-        for (int bps = 1; bps <= ctx->max_blocks_per_sm; ++bps) {
-            for (int order = 0; order < 2; ++order) {
-                if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) return st;
+        for (int bps = 1; bps <= ctx->max_blocks_per_sm && st == MRS_OK; ++bps) {
+            for (int order = 0; order < 2 && st == MRS_OK; ++order) {
+                if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) break;
                 std::vector<float> t;
-                for (int r = 0; r <= reps; ++r) {   // the first cycle warms up
-                    if ((st = launch_cycle(ctx)) != MRS_OK) return st;
-                    float ms[64];
-                    int n = 64;
-                    if ((st = mrs_kernel_times(ctx, ms, &n)) != MRS_OK) return st;
-                    float roll = 0.f;
-                    for (int it = 0; it < ctx->P.iterations; ++it) roll += ms[1 + 5 * it + 2];
-                    if (r > 0) t.push_back(roll);
+                for (int r = 0; r <= reps; ++r) {   // the first cycle warms up (and instantiates)
+                    cudaError_t e = cudaEventRecord(t0, ctx->stream);
+                    if (e == cudaSuccess && (st = launch_cycle(ctx)) != MRS_OK) break;
+                    if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                    if (e != cudaSuccess) {
+                        st = cuda_fail(ctx, e, "autotune: cycle timing");
+                        break;
+                    }
+                    if (r > 0) t.push_back(ms);
                 }
-                (void)stages;
+                if (st != MRS_OK) break;
                 std::sort(t.begin(), t.end());
                 const float med = t[t.size() / 2];
                 tried.push_back(mrs_rollout_shape{ts, bps, order, med});
@@ -1507,6 +1520,9 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
             }
         }
     }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != MRS_OK) return st;
     if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order)) != MRS_OK) return st;
     if ((st = mrs_enable_timing(ctx, timing ? 1 : 0)) != MRS_OK) return st;
     if ((st = mrs_load_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;

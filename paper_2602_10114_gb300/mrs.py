@@ -53,7 +53,7 @@ class MrsStepOut(C.Structure):
 
 class MrsRolloutShape(C.Structure):
     _fields_ = [("tile_samples", C.c_int), ("blocks_per_sm", C.c_int), ("order", C.c_int),
-                ("rollout_ms", C.c_float)]
+                ("cycle_ms", C.c_float)]
 
 
 class MrsSizes(C.Structure):
@@ -363,14 +363,14 @@ class Controller:
 
     def autotune(self, reps=5):
         """Time every rollout shape, keep the fastest; returns (best, table)
-        as dicts with tile_samples, blocks_per_sm, order, rollout_ms."""
+        as dicts with tile_samples, blocks_per_sm, order, cycle_ms."""
         tab = (MrsRolloutShape * 64)()
         n = C.c_int()
         best = MrsRolloutShape()
         self._check(self.L.mrs_autotune(self.h, int(reps), tab, 64, C.byref(n), C.byref(best)),
                     "autotune")
         conv = lambda x: dict(tile_samples=x.tile_samples, blocks_per_sm=x.blocks_per_sm,
-                              order=x.order, rollout_ms=float(x.rollout_ms))
+                              order=x.order, cycle_ms=float(x.cycle_ms))
         return conv(best), [conv(tab[i]) for i in range(min(n.value, 64))]
 
     def save_state(self) -> bytes:

@@ -79,8 +79,8 @@ def test_autotune_keeps_the_fastest_and_restores_the_state():
     best, tab = ctl.autotune(reps=3)
     (_, _, _), mx = ctl.rollout_shape()
     assert len(tab) == 6 * mx * 2
-    assert all(t["rollout_ms"] > 0 for t in tab)
-    assert best["rollout_ms"] == min(t["rollout_ms"] for t in tab)
+    assert all(t["cycle_ms"] > 0 for t in tab)
+    assert best["cycle_ms"] == min(t["cycle_ms"] for t in tab)
     assert ctl.rollout_shape()[0] == (best["tile_samples"], best["blocks_per_sm"], best["order"])
     assert ctl.save_state() == blob
     # the next cycle equals the one the untuned controller runs
