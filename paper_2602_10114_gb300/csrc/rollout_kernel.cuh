@@ -39,6 +39,16 @@ namespace mrs {
 
 constexpr int kPretestUnroll = MRS_PRETEST_UNROLL;
 
+// The unit arm's scalars, staged in shared memory once per unit (the
+// ArmDev record in global memory would be re-read after the unit's stores)
+struct ArmHdr {
+    int dof, K, ns, n_self, learned, H;
+    unsigned pair_mask;
+    float pair_margin, self_margin;
+    int spg;
+    long long off_kh, off_khd;
+};
+
 struct RolloutSmem {
     float4 *other;     // world spheres at the step's time, then neighbours' plan spheres
     float *other_w;    // |p|^2 - r_p^2 of each
@@ -343,7 +353,7 @@ __device__ __forceinline__ float few_candidates(const RolloutSmem &S, const unsi
 }
 
 template <int SPG>
-__device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmDev &A,
+__device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmHdr &A,
                                               const RolloutSmem &S, int h, int n, bool valid,
                                               int g, int lane, int n_world, int n_aabb, int n_nb,
                                               float *pose_out)
@@ -608,6 +618,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     __shared__ float s_pose[2][32];
     __shared__ float s_lim[32];   // the sub-batch's joint-limit terms, copied ahead by warp 0
     __shared__ long long s_idx[32];   // and each sample's stage-cost offset
+    __shared__ ArmHdr s_ah[2];    // the unit arm's scalars, by unit parity
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
     const long long cycle = *D.cycle;
@@ -661,6 +672,14 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 if (k < 9) S.base[k] = A.base_R[k];
                 else if (k < 12) S.base[k] = A.base_t[k - 9];
                 else if (k < 24) S.goal[k - 12] = D.input[A.off_in + 2 * A.dof + k - 12];
+            }
+            if (tl == 191) {
+                ArmHdr hd;
+                hd.dof = A.dof; hd.K = A.K; hd.ns = A.ns; hd.n_self = A.n_self;
+                hd.learned = A.learned; hd.H = A.H; hd.pair_mask = A.pair_mask;
+                hd.pair_margin = A.pair_margin; hd.self_margin = A.self_margin; hd.spg = A.spg;
+                hd.off_kh = A.off_kh; hd.off_khd = A.off_khd;
+                s_ah[tp] = hd;
             }
             for (int k = (tl + 64) % kStage; k < A.ns; k += kStage) {
                 S.sph[k] = A.sph[k];
@@ -774,17 +793,18 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         __syncthreads();   // the unit's inputs are staged
         const int n_nb = nnb;
+        const ArmHdr &AH = s_ah[tp];   // staged above
 
         for (int sb = 0; sb < T.nsub; ++sb, buf ^= 1) {
             RolloutSmem Sb = S;
             Sb.own = S.own + buf * own_stride;
             Sb.red = S.red + buf * kRedStride;
             const int n = T.n0 + sb * 32 + lane;
-            const bool valid = n < A.K;
+            const bool valid = n < AH.K;
             // warp 0 uses the sub-batch's stop / joint-limit terms in its cost
             // stage: copied to shared memory now, behind the kinematics
             if (g == 0 && valid) {
-                const long long idx = A.off_kh + (long long)h * A.K + n;
+                const long long idx = AH.off_kh + (long long)h * AH.K + n;
                 cp_async4(&s_lim[lane], D.stage_lim + idx);
                 s_idx[lane] = idx;
             }
@@ -792,25 +812,25 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             // (warp j takes joint j): the sphere groups' kinematic chains
             // share them (the first sub-batch's came with the staging)
             if (sb > 0) {
-                for (int j = (g + kGroups - 1) % kGroups; j < A.dof; j += kGroups) {
+                for (int j = (g + kGroups - 1) % kGroups; j < AH.dof; j += kGroups) {
                     float sn, cs;
                     const float qj =
-                        D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
+                        D.traj[AH.off_khd + ((long long)h * AH.dof + j) * AH.K + (valid ? n : 0)];
                     sincosf(__fadd_rn(qj, S.dh[j].w), &sn, &cs);
                     S.sc[j * 32 + lane] = make_float2(sn, cs);
                 }
                 __syncthreads();
             }
             float pose = 0.f;
-            switch (A.spg) {
-                case 1: rollout_group<1>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 2: rollout_group<2>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 3: rollout_group<3>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 4: rollout_group<4>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 5: rollout_group<5>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 6: rollout_group<6>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 7: rollout_group<7>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                default: rollout_group<8>(P, D, A, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+            switch (AH.spg) {
+                case 1: rollout_group<1>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 2: rollout_group<2>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 3: rollout_group<3>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 4: rollout_group<4>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 5: rollout_group<5>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 6: rollout_group<6>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 7: rollout_group<7>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                default: rollout_group<8>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
             }
             if (g == kGroups - 1) s_pose[buf][lane] = pose;
             __syncthreads();   // every warp's minima and the pose cost are in
