@@ -30,12 +30,12 @@ struct mrs_ctx {
     bool own_ws = false;
     bool bound = false;
     float *pin_in = nullptr, *pin_out = nullptr;
-    int *pin_err = nullptr;
+    int *pin_err = nullptr;    // the word after the output block in pin_out
     cudaEvent_t done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // mrs_step's graph: the input upload from pin_in, the cycle, and the
-    // downloads of the outputs and the error word into pin_out / pin_err
+    // download of the output block and the error word after it into pin_out
     cudaGraph_t graph_io = nullptr;
     cudaGraphExec_t gexec_io = nullptr;
     bool use_graph = true;
@@ -46,7 +46,7 @@ struct mrs_ctx {
     struct Layout {
         size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
             board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
-            e_now, n_star, out, cycle, world_t, err, done_counter, sample_tiles, rollout_tiles,
+            e_now, n_star, out, cycle, world_t, done_counter, sample_tiles, rollout_tiles,
             cost_tiles, update_tiles, self_pairs, self_t2, work, dhat, total;
     } lay{};
     std::vector<SampleTile> sample_tiles;
@@ -137,10 +137,10 @@ static void build_layout(mrs_ctx *c)
     L.alpha = take(sizeof(float) * A * A);
     L.e_now = take(sizeof(float) * A);
     L.n_star = take(sizeof(int) * A);
-    L.out = take(sizeof(float) * c->sz.output_floats);
+    // the error word sits right after the output block: one download brings both
+    L.out = take(sizeof(float) * (c->sz.output_floats + 4));
     L.cycle = take(sizeof(long long));
     L.world_t = take(sizeof(float));
-    L.err = take(sizeof(int));
     L.done_counter = take(sizeof(int));
     L.sample_tiles = take(sizeof(SampleTile) * c->sample_tiles.size());
     L.rollout_tiles = take(sizeof(RolloutTile) * c->rollout_tiles.size());
@@ -238,7 +238,7 @@ static void fill_dev(mrs_ctx *c, char *base)
     D.out = (float *)(base + L.out);
     D.cycle = (long long *)(base + L.cycle);
     D.world_t = (float *)(base + L.world_t);
-    D.err = (int *)(base + L.err);
+    D.err = (int *)(D.out + c->sz.output_floats);
     c->L.done_counter = (int *)(base + L.done_counter);
     c->L.sample_tiles = (const SampleTile *)(base + L.sample_tiles);
     c->L.rollout_tiles = (const RolloutTile *)(base + L.rollout_tiles);
@@ -474,13 +474,13 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     }
     if (cudaHostAlloc((void **)&ctx->pin_in, sizeof(float) * in, cudaHostAllocDefault) !=
             cudaSuccess ||
-        cudaHostAlloc((void **)&ctx->pin_out, sizeof(float) * ctx->sz.output_floats,
+        cudaHostAlloc((void **)&ctx->pin_out, sizeof(float) * (ctx->sz.output_floats + 4),
                       cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&ctx->pin_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) != cudaSuccess) {
         mrs_destroy(ctx);
         return MRS_ENOMEM;
     }
+    ctx->pin_err = (int *)(ctx->pin_out + ctx->sz.output_floats);
     int dev = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -522,7 +522,6 @@ void mrs_destroy(mrs_ctx *ctx)
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->pin_in) cudaFreeHost(ctx->pin_in);
     if (ctx->pin_out) cudaFreeHost(ctx->pin_out);
-    if (ctx->pin_err) cudaFreeHost(ctx->pin_err);
     if (ctx->done) cudaEventDestroy(ctx->done);
     for (auto e : ctx->events) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -742,11 +741,9 @@ static mrs_status launch_cycle_io(mrs_ctx *ctx)
                                         cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = enqueue_cycle(ctx->P, ctx->D, ctx->L, ctx->stream, nullptr, true);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
+            e = cudaMemcpyAsync(ctx->pin_out, ctx->D.out,
+                                sizeof(float) * ctx->sz.output_floats + sizeof(int),
                                 cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ctx->pin_err, ctx->D.err, sizeof(int), cudaMemcpyDeviceToHost,
-                                ctx->stream);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -817,10 +814,9 @@ mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out
                            cudaMemcpyHostToDevice, ctx->stream), "input upload");
         st = launch_cycle(ctx);
         if (st != MRS_OK) return st;
-        CK(cudaMemcpyAsync(ctx->pin_out, ctx->D.out, sizeof(float) * ctx->sz.output_floats,
-                           cudaMemcpyDeviceToHost, ctx->stream), "output download");
-        CK(cudaMemcpyAsync(ctx->pin_err, ctx->D.err, sizeof(int), cudaMemcpyDeviceToHost,
-                           ctx->stream), "error word download");
+        CK(cudaMemcpyAsync(ctx->pin_out, ctx->D.out,
+                           sizeof(float) * ctx->sz.output_floats + sizeof(int),
+                           cudaMemcpyDeviceToHost, ctx->stream), "output and error word download");
     }
     ctx->has_input = true;
     st = wait_bounded(ctx, 10.0);
