@@ -330,7 +330,9 @@ mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *ma
  * earlier mrs_step / mrs_step_device (the inputs the trials use);
  * otherwise MRS_ESTATE.  `table` (host, capacity `cap`, may be null)
  * receives every shape tried with its time, *n_tried their count; `best`
- * (may be null) the one kept. */
+ * (may be null) the one kept.  If a trial fails, the earlier shape, timing
+ * switch and state are put back as far as the device allows and the
+ * trial's error is returned. */
 mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int cap, int *n_tried,
                         mrs_rollout_shape *best);
 

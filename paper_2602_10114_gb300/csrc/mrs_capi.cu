@@ -1485,7 +1485,8 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
         return fail(ctx, MRS_ECUDA, "autotune: event create");
     }
     std::vector<mrs_rollout_shape> tried;
-    mrs_rollout_shape keep{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
+    const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
+    mrs_rollout_shape keep = before;
     float best_ms = INFINITY;
     for (int ts : {32, 64, 96, 128, 192, 256}) {
         for (int bps = 1; bps <= ctx->max_blocks_per_sm && st == MRS_OK; ++bps) {
@@ -1518,7 +1519,16 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    if (st != MRS_OK) return st;
+    if (st != MRS_OK) {
+        // put back the shape, the timing switch and the state as far as the
+        // device still allows; the trial's error is the one reported
+        const std::string why = ctx->err;
+        apply_shape(ctx, before.tile_samples, before.blocks_per_sm, before.order);
+        mrs_enable_timing(ctx, timing ? 1 : 0);
+        mrs_load_state(ctx, blob.data(), blob.size());
+        ctx->err = why;
+        return st;
+    }
     if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order)) != MRS_OK) return st;
     if ((st = mrs_enable_timing(ctx, timing ? 1 : 0)) != MRS_OK) return st;
     if ((st = mrs_load_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;
