@@ -324,7 +324,9 @@ mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *ma
  * `reps` whole control cycles each (the cycle as mrs_step_device runs it:
  * CUDA graph without per-stage timing, so programmatic launch overlaps the
  * stages; CUDA events around each cycle on the context's stream, median) on
- * the context's current inputs, and keeps the fastest.  The controller state
+ * the context's current inputs, and keeps the fastest.  Each trial cycle
+ * starts from a cold L2: a temporary device buffer of twice the L2 size is
+ * written before it (without room for the buffer, the trials start warm).  The controller state
  * is saved before and restored after the trials, so the next cycle is
  * unaffected; per-stage timing is switched back on if it was on.  Needs one
  * earlier mrs_step / mrs_step_device (the inputs the trials use);

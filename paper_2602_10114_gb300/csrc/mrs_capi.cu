@@ -1484,6 +1484,20 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
         if (t0) cudaEventDestroy(t0);
         return fail(ctx, MRS_ECUDA, "autotune: event create");
     }
+    // Each trial cycle starts from a cold L2 (a write of twice its size just
+    // before), as a controller's cycle does when other work shares the GPU
+    // between cycles; without room for the buffer the trials start warm.
+    int dev = 0, l2 = 0;
+    void *evict = nullptr;
+    size_t evict_bytes = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess && l2 > 0) {
+        evict_bytes = 2 * (size_t)l2;
+        if (cudaMalloc(&evict, evict_bytes) != cudaSuccess) {
+            evict = nullptr;
+            cudaGetLastError();   // clear the allocation failure
+        }
+    }
     std::vector<mrs_rollout_shape> tried;
     const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
     mrs_rollout_shape keep = before;
@@ -1494,7 +1508,9 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
                 if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) break;
                 std::vector<float> t;
                 for (int r = 0; r <= reps; ++r) {   // the first cycle warms up (and instantiates)
-                    cudaError_t e = cudaEventRecord(t0, ctx->stream);
+                    cudaError_t e = evict ? cudaMemsetAsync(evict, r & 0xff, evict_bytes, ctx->stream)
+                                          : cudaSuccess;
+                    if (e == cudaSuccess) e = cudaEventRecord(t0, ctx->stream);
                     if (e == cudaSuccess && (st = launch_cycle(ctx)) != MRS_OK) break;
                     if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
                     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -1519,6 +1535,7 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    if (evict) cudaFree(evict);
     if (st != MRS_OK) {
         // put back the shape, the timing switch and the state as far as the
         // device still allows; the trial's error is the one reported
