@@ -79,40 +79,70 @@ __global__ void k_reset(Params P, Dev D, int total_hdd, int total_hd)
 // ---------------------------------------------------------------------------
 // Sense + Shift + Cholesky (one block per arm)
 
-// Cholesky factor L of S + 1e-8 I (row by row, the diagonal clamped at
-// 1e-6), held in registers with the indices unrolled to the build's DoF
-// limit so that no memory round trip sits on the dependent chain; S and
-// Lout are row-major [d][d], the upper triangle of Lout is zeroed.
-__device__ __forceinline__ void cholesky_unrolled(int d, const float *S, float *Lout)
+// Cholesky factor L of S + 1e-8 I (the diagonal clamped at 1e-6) by one
+// warp: lane l holds the lower-triangle elements e = l and l + 32 (e = i(i+1)/2
+// + j, i >= j) and the columns are finished left to right; after column k
+// every element (i, j) with j > k takes its update -L[i][k] L[j][k], the two
+// factors fetched from their lanes by shuffles.  Each element thus sees the
+// same fused multiply-adds in the same order (k ascending) as the row-by-row
+// algorithm, then the same correctly rounded square root or division: the
+// factor is bitwise the same, with a dependent chain of d columns instead of
+// d(d+1)/2 elements.  S and Lout are row-major [d][d] (S in shared or global
+// memory, visible to the whole warp); the upper triangle of Lout is zeroed.
+// All 32 lanes must call it together.
+__device__ __forceinline__ void cholesky_warp(int d, const float *S, float *Lout, int lane)
 {
-    float L[kMaxDof][kMaxDof];
+    constexpr unsigned kAll = 0xffffffffu;
+    const int nel = d * (d + 1) / 2;   // <= 45 for d <= 9
+    int ri[2], ci[2];
+    float v[2];
 #pragma unroll
-    for (int i = 0; i < kMaxDof; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            L[i][j] = 0.f;
-            if (i < d) {
-                float s = S[i * d + j];
-                if (i == j) s = __fadd_rn(s, 1e-8f);
-#pragma unroll
-                for (int k = 0; k < j; ++k) s = __fmaf_rn(-L[i][k], L[j][k], s);
-                if (i == j)
-                    L[i][i] = sqrtf(s > 1e-12f ? s : 1e-12f);
-                else
-                    L[i][j] = __fdiv_rn(s, L[j][j]);
-            }
+    for (int u = 0; u < 2; ++u) {
+        const int e = lane + 32 * u;
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        ri[u] = i;
+        ci[u] = e - i * (i + 1) / 2;
+        v[u] = 0.f;
+        if (e < nel) {
+            v[u] = S[i * d + ci[u]];
+            if (i == ci[u]) v[u] = __fadd_rn(v[u], 1e-8f);
         }
+    }
+    for (int k = 0; k < d; ++k) {
+        // the diagonal element (k, k), then the rest of column k
+        const int ekk = k * (k + 1) / 2 + k;
 #pragma unroll
-    for (int i = 0; i < kMaxDof; ++i)
+        for (int u = 0; u < 2; ++u)
+            if (lane + 32 * u == ekk) v[u] = sqrtf(v[u] > 1e-12f ? v[u] : 1e-12f);
+        const float a0 = __shfl_sync(kAll, v[0], ekk & 31), a1 = __shfl_sync(kAll, v[1], ekk & 31);
+        const float lkk = (ekk >> 5) ? a1 : a0;
 #pragma unroll
-        for (int j = 0; j < kMaxDof; ++j)
-            if (i < d && j < d) Lout[i * d + j] = (j <= i) ? L[i][j] : 0.f;
+        for (int u = 0; u < 2; ++u)
+            if (lane + 32 * u < nel && ci[u] == k && ri[u] > k) v[u] = __fdiv_rn(v[u], lkk);
+        // trailing update of the elements (i, j), j > k
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const bool upd = lane + 32 * u < nel && ci[u] > k;
+            const int ei = ri[u] * (ri[u] + 1) / 2 + k, ej = ci[u] * (ci[u] + 1) / 2 + k;
+            const int si = upd ? ei : 0, sj = upd ? ej : 0;
+            const float x0 = __shfl_sync(kAll, v[0], si & 31), x1 = __shfl_sync(kAll, v[1], si & 31);
+            const float y0 = __shfl_sync(kAll, v[0], sj & 31), y1 = __shfl_sync(kAll, v[1], sj & 31);
+            const float lik = (si >> 5) ? x1 : x0, ljk = (sj >> 5) ? y1 : y0;
+            if (upd) v[u] = __fmaf_rn(-lik, ljk, v[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (lane + 32 * u < nel) Lout[ri[u] * d + ci[u]] = v[u];
+    for (int e = lane; e < d * d; e += 32)
+        if (e % d > e / d) Lout[e] = 0.f;
 }
 
 // Sense + Shift as a kernel of its own (one block per arm), for workloads
 // whose arms have many sample blocks: distance-to-goal, priority weights
 // alpha^(j,i) (Sec. IV-B), the shifted state (Sec. III-A) into this cycle's
-// buffer and the Cholesky factors L_h.
+// buffer and the shifted Cholesky factors L_h.
 __global__ void k_prep(Params P, Dev D)
 {
     extern __shared__ float sm[];
@@ -151,13 +181,20 @@ __global__ void k_prep(Params P, Dev D)
 
     // second wave: the shifted distribution (Shift, Sec. III-A: phi_h <-
     // phi_{h+1}, the last step keeps its mean and restarts from
-    // sigma_init^2 I; not before the first cycle) and the sensed input
+    // sigma_init^2 I; not before the first cycle), with the state's Cholesky
+    // factors shifted alike (the restart's factor is diagonal, the value the
+    // factorisation gives), and the sensed input
     const bool shift = cycle > 0;
     const float s2 = P.sigma_init * P.sigma_init;
+    const float x2 = __fadd_rn(s2, 1e-8f), l_last = sqrtf(x2 > 1e-12f ? x2 : 1e-12f);
+    const float *Lf = lst_buf(D, cycle) + off_hdd;
 #pragma unroll 4
     for (int i = t; i < H * dd; i += blockDim.x) {
         const int h = i / dd, k = i % dd;
-        sS[i] = !shift ? Sig[i] : (h + 1 < H ? Sig[i + dd] : ((k % (d + 1) == 0) ? s2 : 0.f));
+        const int src = !shift ? i : (h + 1 < H ? i + dd : -1);
+        const bool dg = k % (d + 1) == 0;
+        sS[i] = src >= 0 ? Sig[src] : (dg ? s2 : 0.f);
+        sL[i] = src >= 0 ? Lf[src] : (dg ? l_last : 0.f);
     }
 #pragma unroll 4
     for (int i = t; i < H * d; i += blockDim.x) {
@@ -168,9 +205,7 @@ __global__ void k_prep(Params P, Dev D)
     __syncthreads();
     for (int i = t; i < H * dd; i += blockDim.x) Sig_cur[i] = sS[i];
     for (int i = t; i < H * d; i += blockDim.x) mu_cur[i] = sM[i];
-    // Cholesky factor of every step's covariance (in shared memory), and, on
-    // the last thread, Sense: the end effector's distance to the goal
-    for (int h = t; h < H; h += blockDim.x) cholesky_unrolled(d, sS + h * dd, sL + h * dd);
+    // Sense, on the last thread: the end effector's distance to the goal
     if (t == blockDim.x - 1) {
         Frame F;
         for (int k = 0; k < 9; ++k) F.R[k] = s_base[k];
@@ -197,10 +232,10 @@ __global__ void k_prep(Params P, Dev D)
 // also the cycle's Sense + Shift: every block
 // shifts the previous state (Shift, Sec. III-A: phi_h <- phi_{h+1}, the last
 // step keeps its mean and restarts from sigma_init^2 I; not before the first
-// cycle) chunk by chunk into shared memory and factors each step's
-// covariance; the arm's first block (n0 = 0) publishes the shifted state
-// into the cycle's buffer and the factors, and computes the sensed distance
-// to the goal and the priorities alpha^(j,i) (Sec. IV-B).
+// cycle) and the state's Cholesky factors with it, chunk by chunk, into
+// shared memory; the arm's first block (n0 = 0) publishes the shifted state
+// and factors into the cycle's buffers, and computes the sensed distance to
+// the goal and the priorities alpha^(j,i) (Sec. IV-B).
 
 __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTile *tiles, int iter,
                                                 int smem_floats, int with_prep)
@@ -221,8 +256,7 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
     const int Hc = max(1, min(H, smem_floats / (dd + d + 2 * d * 32)));
     float *sL = sm;                 // [Hc][d][d]
     float *sMu = sL + Hc * dd;      // [Hc][d]
-    float *sU = sMu + Hc * d;       // [Hc][d][32]: U, then the joint-limit terms (the shifted
-                                    // covariances before that, on the first iteration)
+    float *sU = sMu + Hc * d;       // [Hc][d][32]: U, then the joint-limit terms
     float *sS = sU + Hc * d * 32;   // [Hc][d][32]: stop terms
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,33 +287,33 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
     pdl_trigger();
     const bool shift = cycle > 0;
     const float s2 = P.sigma_init * P.sigma_init;
+    const float x2 = __fadd_rn(s2, 1e-8f), l_last = sqrtf(x2 > 1e-12f ? x2 : 1e-12f);
 
     for (int h0 = 0; h0 < H; h0 += Hc) {
         const int nh = min(Hc, H - h0);
         if (prep) {
-            float *sSig = sU;   // [nh][dd] <= [nh][d][32]
+            // the state's Cholesky factors (taken beside the previous ToPlan)
+            // shift with the covariances; the restart's factor is diagonal,
+            // the value the factorisation gives
+            const float *Lf = lst_buf(D, cycle) + off_hdd;
 #pragma unroll 4
             for (int i = threadIdx.x; i < nh * dd; i += blockDim.x) {
                 const int hl = i / dd, k = i - hl * dd, h = h0 + hl;
-                sSig[i] = !shift ? sig_prev[h * dd + k]
-                                 : (h + 1 < H ? sig_prev[(h + 1) * dd + k]
-                                              : ((k % (d + 1) == 0) ? s2 : 0.f));
+                const int src = !shift ? h * dd + k : (h + 1 < H ? (h + 1) * dd + k : -1);
+                const bool dg = k % (d + 1) == 0;
+                const float lf = src >= 0 ? Lf[src] : (dg ? l_last : 0.f);
+                sL[i] = lf;
+                if (leader) {   // the cycle's shifted state and factors
+                    sig_cur[h0 * dd + i] = src >= 0 ? sig_prev[src] : (dg ? s2 : 0.f);
+                    D.L[off_hdd + (long long)h0 * dd + i] = lf;
+                }
             }
             for (int i = threadIdx.x; i < nh * d; i += blockDim.x) {
                 const int h = h0 + i / d, src = h0 * d + i;
                 sMu[i] = (shift && h + 1 < H) ? mu_prev[src + d] : mu_prev[src];
+                if (leader) mu_cur[h0 * d + i] = sMu[i];
             }
             __syncthreads();
-            for (int hl = threadIdx.x; hl < nh; hl += blockDim.x)
-                cholesky_unrolled(d, sSig + hl * dd, sL + hl * dd);
-            if (leader) {   // the cycle's shifted state
-                for (int i = threadIdx.x; i < nh * dd; i += blockDim.x) sig_cur[h0 * dd + i] = sSig[i];
-                for (int i = threadIdx.x; i < nh * d; i += blockDim.x) mu_cur[h0 * d + i] = sMu[i];
-            }
-            __syncthreads();
-            if (leader)
-                for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
-                    D.L[off_hdd + (long long)h0 * dd + i] = sL[i];
         } else {
 #pragma unroll 4
             for (int i = threadIdx.x; i < nh * dd; i += blockDim.x)
@@ -556,8 +590,29 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
     }
     if (!last) {
         __syncthreads();
-        if (threadIdx.x == 0) cholesky_unrolled(d, Sig, D.L + A.off_hdd + h * dd);
+        if (warp == 0) cholesky_warp(d, Sig, D.L + A.off_hdd + h * dd, lane);
     }
+}
+
+// Cholesky factor of the state's covariance at work item w (arm, step) in
+// the buffers of the given parity, by one warp.  The cycle takes them in
+// ToPlan's launch, after the last update, and the next cycle's Shift moves
+// them with the covariances, so the sampling never factors on its critical
+// path; k_chol takes them after an initialisation or a state load.
+__device__ __forceinline__ void state_factor(const Dev &D, const UpdateTile *tiles, int w,
+                                             long long parity, int lane)
+{
+    const UpdateTile T = tiles[w];
+    const ArmDev &A = D.arms[T.arm];
+    const int d = A.dof;
+    const long long o = A.off_hdd + (long long)T.h * d * d;
+    cholesky_warp(d, sigma_buf(D, parity) + o, lst_buf(D, parity) + o, lane);
+}
+
+__global__ void __launch_bounds__(256) k_chol(Dev D, const UpdateTile *tiles, int n_tiles, int parity)
+{
+    const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (w < n_tiles) state_factor(D, tiles, w, parity, threadIdx.x & 31);   // uniform over the warp
 }
 
 // ---------------------------------------------------------------------------
@@ -573,8 +628,37 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(Params P, Dev D, cons
 // rollout's frame_step, so a zero-noise rollout still reproduces the plan
 // bit for bit.
 
-__global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_counter)
+// The last block of ToPlan's launch to finish advances the cycle counter and
+// the world clock and clears the next cycle's work counters.
+__device__ __forceinline__ void toplan_done(const Params &P, const Dev &D, int *done_counter,
+                                            long long cyc)
 {
+    __threadfence();
+    const int prev = atomicAdd(done_counter, 1);
+    if (prev == gridDim.x - 1) {
+        *D.cycle = cyc + 1;
+        *D.world_t = __fadd_rn(*D.world_t, P.dt);
+        *done_counter = 0;
+        for (int i = 0; i < P.iterations; ++i) D.work[i] = 0;   // the next cycle's tile counters
+    }
+}
+
+__global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_counter,
+                                                const UpdateTile *ftiles, int n_ftiles)
+{
+    if ((int)blockIdx.x >= P.n_arms) {   // uniform over the block
+        // the next cycle's factors: the state the update just wrote is in the
+        // buffer of parity cycle + 1 (the counter advances only once every
+        // block of this launch has passed its end)
+        const long long cyc = *D.cycle;
+        pdl_wait();
+        pdl_trigger();
+        const int w = ((int)blockIdx.x - P.n_arms) * 8 + (threadIdx.x >> 5);
+        if (w < n_ftiles) state_factor(D, ftiles, w, cyc + 1, threadIdx.x & 31);
+        __syncthreads();
+        if (threadIdx.x == 0) toplan_done(P, D, done_counter, cyc);
+        return;
+    }
     extern __shared__ float sq[];   // [H][d] plan joints, mean, sin(q + theta), cos(q + theta)
     __shared__ float4 s_sph[kMaxSpheres];
     __shared__ int s_frame[kMaxSpheres];
@@ -681,14 +765,7 @@ __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_count
             D.board_dist[a] = s_e;
             D.out[D.out_dist + a] = s_e;
         }
-        __threadfence();
-        const int prev = atomicAdd(done_counter, 1);
-        if (prev == gridDim.x - 1) {
-            *D.cycle = s_cycle + 1;
-            *D.world_t = __fadd_rn(*D.world_t, P.dt);
-            *done_counter = 0;
-            for (int i = 0; i < P.iterations; ++i) D.work[i] = 0;   // the next cycle's tile counters
-        }
+        toplan_done(P, D, done_counter, s_cycle);
     }
 }
 
@@ -850,6 +927,13 @@ cudaError_t enqueue_init(const Params &P, const Dev &D, int n_arms, int total_hd
     return cudaGetLastError();
 }
 
+cudaError_t enqueue_state_factors(const Dev &D, const LaunchPlan &L, int parity, cudaStream_t s)
+{
+    if (L.n_update_tiles > 0)
+        k_chol<<<(L.n_update_tiles + 7) / 8, 256, 0, s>>>(D, L.update_tiles, L.n_update_tiles, parity);
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cudaStream_t s,
                           cudaEvent_t *events, bool capturing)
 {
@@ -900,8 +984,9 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
             return rec;
         mark();
     }
-    if ((rec = launch_k(k_toplan, L.n_arms, 256, L.smem_toplan, s, pdl, P, D, L.done_counter)) !=
-        cudaSuccess)
+    // ToPlan on one block per arm, the next cycle's factors on the blocks after them
+    if ((rec = launch_k(k_toplan, L.n_arms + (L.n_update_tiles + 7) / 8, 256, L.smem_toplan, s, pdl,
+                        P, D, L.done_counter, L.update_tiles, L.n_update_tiles)) != cudaSuccess)
         return rec;
     mark();
     if (rec != cudaSuccess) return rec;

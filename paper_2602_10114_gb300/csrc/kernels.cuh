@@ -126,6 +126,9 @@ cudaError_t configure_kernels(const LaunchPlan &L);
 // Fill the derived per-arm constants and reset the controller state.
 cudaError_t enqueue_init(const Params &P, const Dev &D, int n_arms, int total_hdd, int total_hd,
                          cudaStream_t s);
+// Cholesky factors of the state's covariances in the buffers of the given
+// parity (after an initialisation or a state load)
+cudaError_t enqueue_state_factors(const Dev &D, const LaunchPlan &L, int parity, cudaStream_t s);
 cudaError_t enqueue_fk(const Dev &D, int arm, int n, const float *q, float *ee, float *spheres,
                        cudaStream_t s);
 cudaError_t enqueue_debug_spheres(const Dev &D, int n_req, const int *anh, float *out,

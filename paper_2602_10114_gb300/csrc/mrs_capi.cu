@@ -46,7 +46,7 @@ struct mrs_ctx {
     struct Layout {
         size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
             board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
-            e_now, n_star, out, cycle, world_t, done_counter, sample_tiles, rollout_tiles,
+            e_now, n_star, out, cycle, world_t, done_counter, Lst, sample_tiles, rollout_tiles,
             cost_tiles, update_tiles, self_pairs, self_t2, work, dhat, total;
     } lay{};
     std::vector<SampleTile> sample_tiles;
@@ -124,6 +124,7 @@ static void build_layout(mrs_ctx *c)
     L.mu = take(sizeof(float) * 2 * c->sz.hd);       // two buffers (cycle parity)
     L.Sigma = take(sizeof(float) * 2 * c->sz.hdd);
     L.L = take(sizeof(float) * c->sz.hdd);
+    L.Lst = take(sizeof(float) * 2 * c->sz.hdd);
     L.board_sph = take(sizeof(float) * c->sz.hs);
     L.board_q = take(sizeof(float) * c->sz.hd);
     L.board_valid = take(sizeof(int) * A);
@@ -220,6 +221,7 @@ static void fill_dev(mrs_ctx *c, char *base)
     D.st_hd = (long long)c->sz.hd;
     D.st_hdd = (long long)c->sz.hdd;
     D.L = (float *)(base + L.L);
+    D.Lst = (float *)(base + L.Lst);
     D.board_sph = (float4 *)(base + L.board_sph);
     D.board_q = (float *)(base + L.board_q);
     D.board_valid = (int *)(base + L.board_valid);
@@ -588,6 +590,7 @@ static mrs_status bind(mrs_ctx *ctx, void *dev, size_t bytes)
        "memset");
     CK(enqueue_init(ctx->P, ctx->D, ctx->A, (int)ctx->sz.hdd, (int)ctx->sz.hd, ctx->stream),
        "init kernels");
+    CK(enqueue_state_factors(ctx->D, ctx->L, 0, ctx->stream), "initial factors");
     CK(cudaStreamSynchronize(ctx->stream), "sync after init");
     ctx->bound = true;
     return MRS_OK;
@@ -1002,6 +1005,7 @@ mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
     CK(cudaMemcpyAsync(D.board_stamp, stamp.data(), sizeof(long long) * A, cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.cycle, &cycle, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.world_t, &wt, sizeof(float), cudaMemcpyHostToDevice, ctx->stream), "load");
+    CK(enqueue_state_factors(D, ctx->L, (int)(cycle & 1), ctx->stream), "load factors");
     CK(cudaStreamSynchronize(ctx->stream), "load sync");
     return MRS_OK;
 }

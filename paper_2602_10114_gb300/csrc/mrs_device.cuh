@@ -74,6 +74,8 @@ struct Dev {
     int *world_n;          // [2] spheres, boxes
     float *mu, *Sigma, *L; // state: [2][hd], [2][hdd] (by cycle parity), [hdd]
     long long st_hd, st_hdd;   // element offset of the second mu / Sigma buffer
+    float *Lst;                // [2][sum H d d]: Cholesky factors of the state's covariances,
+                               // by cycle parity like Sigma (taken in ToPlan's launch)
     float4 *board_sph;     // plan board read by the cycle: [hs/4]
     float *board_q;        // [hd]
     int *board_valid;      // [A]
@@ -129,6 +131,10 @@ __device__ __forceinline__ float *mu_buf(const Dev &D, long long parity)
 __device__ __forceinline__ float *sigma_buf(const Dev &D, long long parity)
 {
     return D.Sigma + (parity & 1) * D.st_hdd;
+}
+__device__ __forceinline__ float *lst_buf(const Dev &D, long long parity)
+{
+    return D.Lst + (parity & 1) * D.st_hdd;
 }
 
 // Work items of the launch-grid work lists.
