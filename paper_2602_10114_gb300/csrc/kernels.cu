@@ -237,8 +237,11 @@ __global__ void k_prep(Params P, Dev D)
 // and factors into the cycle's buffers, and computes the sensed distance to
 // the goal and the priorities alpha^(j,i) (Sec. IV-B).
 
-__global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTile *tiles, int iter,
-                                                int smem_floats, int with_prep)
+// NS = 32 runs on the large workloads, whose grids fill the GPU: two resident
+// blocks per SM (at most 64 registers).
+template <int NS>
+__global__ void __launch_bounds__(512, NS == 32 ? 2 : 1)
+    k_sample(Params P, Dev D, const SampleTile *tiles, int iter, int smem_floats, int with_prep)
 {
     extern __shared__ float sm[];
     __shared__ float s_bdist[MRS_MAX_ARMS];
@@ -253,14 +256,16 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
     const float *mu_prev = mu_buf(D, cycle) + off_hd, *sig_prev = sigma_buf(D, cycle) + off_hdd;
     float *mu_cur = mu_buf(D, cycle + 1) + off_hd, *sig_cur = sigma_buf(D, cycle + 1) + off_hdd;
     // the horizon in chunks of Hc steps that fit the block's shared memory
-    const int Hc = max(1, min(H, smem_floats / (dd + d + 2 * d * 32)));
+    const int Hc = max(1, min(H, smem_floats / (dd + d + 2 * d * NS)));
     float *sL = sm;                 // [Hc][d][d]
     float *sMu = sL + Hc * dd;      // [Hc][d]
-    float *sU = sMu + Hc * d;       // [Hc][d][32]: U, then the joint-limit terms
-    float *sS = sU + Hc * d * 32;   // [Hc][d][32]: stop terms
+    float *sU = sMu + Hc * d;       // [Hc][d][NS]: U, then the joint-limit terms
+    float *sS = sU + Hc * d * NS;   // [Hc][d][NS]: stop terms
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = T.n0 + lane;
+    // lane l draws sample n0 + l % NS at step slot warp * 32 / NS + l / NS
+    const int sl = lane % NS, slot = warp * (32 / NS) + lane / NS, nslot = 512 / NS;   // 512 threads
+    const int n = T.n0 + sl;
     const bool valid = n < K;
     float *eps_out = D.eps + A.off_khd;
     const float *in = D.input + A.off_in;
@@ -269,8 +274,8 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
 
     // integration state and constants of this thread's (sample, joint),
     // carried across chunks; loaded in the same wave as the first chunk
-    const int ti = threadIdx.x, il = ti & 31, ij = ti >> 5;
-    const bool integrates = ti < 32 * d;
+    const int ti = threadIdx.x, il = ti % NS, ij = ti / NS;
+    const bool integrates = ti < NS * d;
     float q = 0.f, qd = 0.f, hi = 0.f, lo = 0.f, vmax = 0.f;
     if (integrates) {
         q = in[ij];
@@ -322,7 +327,8 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
             __syncthreads();
         }
 
-        for (int hl = warp; hl < nh; hl += blockDim.x >> 5) {
+#pragma unroll 1
+        for (int hl = slot; hl < nh; hl += nslot) {
             const int h = h0 + hl;
             float z[kMaxDof];
             normals(P.seed, T.arm, cycle, iter, n, h, d, z);
@@ -334,7 +340,7 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
 #pragma unroll
                     for (int c = 0; c <= j; ++c) e = __fmaf_rn(Lh[j * d + c], z[c], e);
                     if (P.zero_noise) e = 0.f;
-                    sU[(hl * d + j) * 32 + lane] = __fadd_rn(sMu[hl * d + j], e);
+                    sU[(hl * d + j) * NS + sl] = __fadd_rn(sMu[hl * d + j], e);
                     if (valid) eps_out[(long long)(h * d + j) * K + n] = e;
                 }
             }
@@ -350,13 +356,13 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
                 float u[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
-                    u[k] = (hb + k < nh) ? sU[((hb + k) * d + ij) * 32 + il] : 0.f;
+                    u[k] = (hb + k < nh) ? sU[((hb + k) * d + ij) * NS + il] : 0.f;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int hl = hb + k;
                     if (hl >= nh) break;
                     const int h = h0 + hl;
-                    const int idx = (hl * d + ij) * 32 + il;
+                    const int idx = (hl * d + ij) * NS + il;
                     integrate(q, qd, u[k], P.dt);
                     if (nn < K) traj[(long long)(h * d + ij) * K + nn] = q;
                     sS[idx] = hinge2(__fsub_rn(fabsf(qd), vmax));
@@ -381,14 +387,14 @@ __global__ void __launch_bounds__(512) k_sample(Params P, Dev D, const SampleTil
             for (int i = ti; i < P.n_arms; i += blockDim.x)
                 D.alpha[T.arm * P.n_arms + i] =
                     (i != T.arm && s_bvalid[i]) ? priority(s_e, s_bdist[i], P.tau) : 0.f;
-        for (int t = threadIdx.x; t < 32 * nh; t += blockDim.x) {
-            const int l = t & 31, hl = t >> 5;
+        for (int t = threadIdx.x; t < NS * nh; t += blockDim.x) {
+            const int l = t % NS, hl = t / NS;
             const int nn = T.n0 + l;
             if (nn >= K) continue;
             float s = 0.f, jc = 0.f;
             for (int j = 0; j < d; ++j) {
-                s = __fadd_rn(s, sS[(hl * d + j) * 32 + l]);
-                jc = __fadd_rn(jc, sU[(hl * d + j) * 32 + l]);
+                s = __fadd_rn(s, sS[(hl * d + j) * NS + l]);
+                jc = __fadd_rn(jc, sU[(hl * d + j) * NS + l]);
             }
             lim[(long long)(h0 + hl) * K + nn] = __fmaf_rn(P.w_joint, jc, __fmul_rn(P.w_stop, s));
         }
@@ -907,8 +913,9 @@ cudaError_t configure_kernels(const LaunchPlan &L)
 {
     cudaError_t e;
     if ((e = configure_rollout(L)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)L.smem_sample)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(L.sample_tile == 16 ? k_sample<16> : k_sample<32>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_sample)) !=
+        cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)L.smem_prep)) != cudaSuccess)
@@ -954,7 +961,8 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
         const int last = (it == P.iterations - 1);
         // with merge_prep the first sample launch opens the cycle (no kernel before it)
         const int with_prep = (it == 0 && L.merge_prep) ? 1 : 0;
-        if ((rec = launch_k(k_sample, L.n_sample_tiles, 512, L.smem_sample, s, pdl && !with_prep, P, D,
+        if ((rec = launch_k(L.sample_tile == 16 ? k_sample<16> : k_sample<32>, L.n_sample_tiles,
+                            512, L.smem_sample, s, pdl && !with_prep, P, D,
                             L.sample_tiles, it, (int)(L.smem_sample / sizeof(float)), with_prep)) !=
             cudaSuccess)
             return rec;

@@ -42,6 +42,7 @@ struct LaunchPlan {
     const CostTile *cost_tiles;
     const UpdateTile *update_tiles;
     size_t smem_prep, smem_sample, smem_rollout, smem_toplan;
+    int sample_tile;    // samples per sampling block: 16 (every arm of at most 1024 samples) or 32
     bool merge_prep;    // Sense + Shift inside the first sample launch (every arm of at most
                         // 32 sample blocks) instead of a kernel of their own
     int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)

@@ -190,16 +190,26 @@ static void set_rollout_grid(mrs_ctx *c)
     c->L.rollout_variant = bps >= 3 ? 3 : 2;
 }
 
+// every optimised arm has at most kSmallArmK samples: Sense + Shift inside
+// the first sampling launch, and 16 samples per sampling block
+static bool small_arms(const mrs_ctx *c)
+{
+    for (auto &A : c->arms)
+        if (!A.external && A.K > kSmallArmK) return false;
+    return true;
+}
+
 static void build_work_lists(mrs_ctx *c)
 {
     c->sample_tiles.clear();
     c->rollout_tiles.clear();
     c->cost_tiles.clear();
     c->update_tiles.clear();
+    const int tile = small_arms(c) ? 16 : 32;
     for (int a = 0; a < c->A; ++a) {
         const ArmDev &A = c->arms[a];
         if (A.external) continue;   // optimised elsewhere
-        for (int n0 = 0; n0 < A.K; n0 += 32) c->sample_tiles.push_back({a, n0});
+        for (int n0 = 0; n0 < A.K; n0 += tile) c->sample_tiles.push_back({a, n0});
         for (int n0 = 0; n0 < A.K; n0 += 256) c->cost_tiles.push_back({a, n0});
         for (int h = 0; h < A.H; ++h) c->update_tiles.push_back({a, h});
     }
@@ -448,14 +458,15 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     L.n_update_tiles = (int)ctx->update_tiles.size();
     L.total_kh = (int)kh;
     size_t sp = 0, ss = 0, st2 = 0;
-    L.merge_prep = true;
+    // the merged Sense + Shift repeats the arm's shift in each of its sample
+    // blocks: worth a launch less only for a few blocks per arm
+    L.merge_prep = small_arms(ctx);
+    L.sample_tile = L.merge_prep ? 16 : 32;
     for (auto &A : ctx->arms) {
         sp = std::max(sp, sizeof(float) * (size_t)A.H * (2 * A.dof * A.dof + A.dof));
-        // the merged Sense + Shift repeats the arm's H factorisations in each of
-        // its sample blocks: worth a launch less only for a few blocks per arm
-        if (!A.external && (A.K + 31) / 32 > 32) L.merge_prep = false;
         // k_sample: the whole horizon, or chunks of it within 96 KB
-        const size_t per_h = sizeof(float) * (size_t)(A.dof * A.dof + A.dof + 2 * A.dof * 32);
+        const size_t per_h =
+            sizeof(float) * (size_t)(A.dof * A.dof + A.dof + 2 * A.dof * L.sample_tile);
         ss = std::max(ss, std::min((size_t)A.H * per_h, std::max(per_h, (size_t)96 * 1024)));
         st2 = std::max(st2, sizeof(float) * (size_t)A.H * 4 * A.dof);
     }

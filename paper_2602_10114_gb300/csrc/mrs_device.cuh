@@ -138,7 +138,12 @@ __device__ __forceinline__ float *lst_buf(const Dev &D, long long parity)
 }
 
 // Work items of the launch-grid work lists.
-struct SampleTile { int arm, n0; };
+// Samples per sampling block: 16 when every arm has at most 1024 samples
+// (a warp's two half-warps take two steps of the block's samples, so the
+// short sampling launch spans twice the SMs), else 32 (the larger grid
+// already fills the GPU, and fewer blocks re-read each step's factors).
+constexpr int kSmallArmK = 1024;
+struct SampleTile { int arm, n0; };   // samples n0 .. n0 + tile width - 1
 struct RolloutTile { int arm, h, n0, nsub; };   // samples n0 .. n0 + 32 nsub - 1 at step h
 struct CostTile { int arm, n0; };
 struct UpdateTile { int arm, h; };
