@@ -227,8 +227,8 @@ __global__ void k_prep(Params P, Dev D)
 }
 
 // ---------------------------------------------------------------------------
-// SampleControls + integration (one block per (arm, 32 samples)).  With
-// with_prep (first iteration, arms of at most 32 sample blocks) the launch is
+// SampleControls + integration (one block per (arm, NS samples)).  With
+// with_prep (first iteration, every arm of at most 1024 samples) the launch is
 // also the cycle's Sense + Shift: every block
 // shifts the previous state (Shift, Sec. III-A: phi_h <- phi_{h+1}, the last
 // step keeps its mean and restarts from sigma_init^2 I; not before the first

@@ -44,7 +44,7 @@ struct LaunchPlan {
     size_t smem_prep, smem_sample, smem_rollout, smem_toplan;
     int sample_tile;    // samples per sampling block: 16 (every arm of at most 1024 samples) or 32
     bool merge_prep;    // Sense + Shift inside the first sample launch (every arm of at most
-                        // 32 sample blocks) instead of a kernel of their own
+                        // 1024 samples) instead of a kernel of their own
     int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)
     int rollout_variant;   // register budget of the rollout kernel: 2 or 3 blocks per SM
     int *done_counter;  // last-block-done counter of k_toplan
