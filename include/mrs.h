@@ -308,7 +308,9 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
  *                  one built for three resident blocks;
  *   order          0 step-major work list (all arms' units of step h, then
  *                  h + 1: concurrent blocks share the step's plans), 1
- *                  arm-major.
+ *                  arm-major, 2 step-major from the last step (the later
+ *                  steps' wider spread of samples tends to cost more: the
+ *                  costlier units first leave a shorter tail).
  * Results do not depend on the shape (each sample's cost is reduced by its
  * own lane in every shape); only the time does.  mrs_set_rollout_shape
  * returns MRS_EINVAL for a shape out of range. */
@@ -320,11 +322,12 @@ mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
 
 /* Autotuner: times every shape of the grid {32, 64, 96, 128, 192, 256}
- * samples x 1 .. max resident blocks per SM x {step-major, arm-major} over
+ * samples x 1 .. max resident blocks per SM x orders {0, 1, 2} over
  * `reps` whole control cycles each (the cycle as mrs_step_device runs it:
  * CUDA graph without per-stage timing, so programmatic launch overlaps the
  * stages; CUDA events around each cycle on the context's stream, median) on
- * the context's current inputs, and keeps the fastest.  Each trial cycle
+ * the context's current inputs, every shape from the same saved state,
+ * and keeps the fastest.  Each trial cycle
  * starts from a cold L2: a temporary device buffer of twice the L2 size is
  * written before it (without room for the buffer, the trials start warm).  The controller state
  * is saved before and restored after the trials, so the next cycle is

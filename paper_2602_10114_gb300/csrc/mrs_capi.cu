@@ -172,6 +172,11 @@ static void build_rollout_tiles(mrs_ctx *c)
         for (int h = 0; h < Hmax; ++h)
             for (int a = 0; a < c->A; ++a)
                 if (h < c->arms[a].H && !c->arms[a].external) push(a, h);
+    } else if (c->tile_order == 2) {   // step-major from the last step: the later steps'
+                                        // wider sample spread tends to cost more, so they go first
+        for (int h = Hmax - 1; h >= 0; --h)
+            for (int a = 0; a < c->A; ++a)
+                if (h < c->arms[a].H && !c->arms[a].external) push(a, h);
     } else {
         for (int a = 0; a < c->A; ++a)
             if (!c->arms[a].external)
@@ -1460,7 +1465,7 @@ mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
     if (!ctx || !shape) return MRS_EINVAL;
     if (shape->tile_samples < 32 || shape->tile_samples > 256 || shape->tile_samples % 32 ||
         shape->blocks_per_sm < 0 || shape->blocks_per_sm > ctx->max_blocks_per_sm ||
-        (shape->order != 0 && shape->order != 1))
+        shape->order < 0 || shape->order > 2)
         return fail(ctx, MRS_EINVAL, "rollout shape out of range");
     return apply_shape(ctx, shape->tile_samples, shape->blocks_per_sm, shape->order);
 }
@@ -1519,8 +1524,12 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     float best_ms = INFINITY;
     for (int ts : {32, 64, 96, 128, 192, 256}) {
         for (int bps = 1; bps <= ctx->max_blocks_per_sm && st == MRS_OK; ++bps) {
-            for (int order = 0; order < 2 && st == MRS_OK; ++order) {
+            for (int order = 0; order < 3 && st == MRS_OK; ++order) {
                 if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) break;
+                // every shape's trials start from the same state (and draw the same
+                // samples): the controller's state drifts over the trials, and with
+                // it the work of a cycle
+                if ((st = mrs_load_state(ctx, blob.data(), blob.size())) != MRS_OK) break;
                 std::vector<float> t;
                 for (int r = 0; r <= reps; ++r) {   // the first cycle warms up (and instantiates)
                     cudaError_t e = evict ? cudaMemsetAsync(evict, r & 0xff, evict_bytes, ctx->stream)
