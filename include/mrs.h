@@ -239,7 +239,10 @@ mrs_status mrs_use_graph(mrs_ctx *ctx, int on);
  * endian): u32 magic 0x3152534d, u32 version 1, u32 n_arms, u32 pad,
  * i64 cycle, f32 world_t, f32 pad, then per arm mu[H][d], Sigma[H][d][d]
  * (f32), then per arm {i32 valid, i32 pad, i64 stamp, f32 dist, f32 pad,
- * plan_spheres[H][NS][4], plan_q[H][d]}.  Loading checks sizes and finiteness. */
+ * plan_spheres[H][NS][4], plan_q[H][d]}.  Loading checks sizes and finiteness
+ * and recomputes what derives from the state (the Cholesky factors of Sigma
+ * that the next cycle's Shift moves), so a loaded state continues bit for
+ * bit as the saved one would have. */
 mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes);
 mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes);
 
