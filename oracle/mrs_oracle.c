@@ -427,6 +427,37 @@ static int plan_usable(const orc_config *cfg, const orc_state *st, int i)
 static int arm_active(const orc_config *cfg, int a) { return !cfg->active || cfg->active[a]; }
 
 /* ------------------------------------------------------------------------ */
+/* Self-collision pair set of C_self (Eq. 5 names the term; the pair set is a
+ * reading).  Two spheres form a pair when their bodies are at least three
+ * apart along the chain (closer bodies share a joint and always touch), and
+ * when their clearance at the nominal pose -- every joint at zero -- is at
+ * least b_rest.  A pair that touches, or lies inside the safety band, with
+ * the arm at rest belongs to the arm's build rather than to a collision; arm
+ * models list such pairs as ignored, and so does this reading. */
+static void rest_spheres(const orc_arm *arm, double *S_rest)
+{
+    double q0[ORC_MAX_DOF];
+    for (int j = 0; j < arm->dof; ++j) q0[j] = 0.0;
+    orc_fk(arm, q0, NULL, S_rest);
+}
+
+static int self_pair_used(const orc_arm *arm, const double *S_rest, int s1, int s2,
+                          double b_rest)
+{
+    int gap = arm->sphere_body[s1] - arm->sphere_body[s2];
+    if (gap < 0) gap = -gap;
+    if (gap < 3) return 0;
+    return orc_sphere_sphere(S_rest + 4 * s1, S_rest + 4 * s2) >= b_rest;
+}
+
+int orc_self_pair_used(const orc_arm *arm, int s1, int s2, double b_rest)
+{
+    double S_rest[ORC_MAX_SPHERES * 4];
+    rest_spheres(arm, S_rest);
+    return self_pair_used(arm, S_rest, s1, s2, b_rest);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Rollout (Sec. III-A: [C_n, X_n] = f(U_n)).  Reading of the dynamics f:
  * U are joint accelerations, integrated by semi-implicit Euler,
  *   qd_h = qd_{h-1} + U_h dt,   q_h = q_{h-1} + qd_h dt,   h = 1..H,
@@ -448,6 +479,8 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
         qd[j] = in->qd[od + j];
     }
     const double *g_p = in->goal_p + 3 * arm, *g_R = in->goal_R + 9 * arm;
+    double S_rest[ORC_MAX_SPHERES * 4];
+    rest_spheres(A, S_rest);
     long long queries = 0;
     double total = 0.0, slope_total = 0.0;
     for (int h = 0; h < H; ++h) {
@@ -491,13 +524,11 @@ double orc_rollout(const orc_config *cfg, int arm, const orc_state *st, const or
             }
         double c_coll = (in->n_world + in->n_aabb > 0) ? orc_ramp(d_world, cfg->B_world) : 0.0;
 
-        /* self collision: sphere pairs on bodies at least three apart */
+        /* self collision: the pairs of the arm's self-collision set */
         double d_self = INFINITY;
         for (int s1 = 0; s1 < NS; ++s1)
             for (int s2 = s1 + 1; s2 < NS; ++s2) {
-                int gap = A->sphere_body[s1] - A->sphere_body[s2];
-                if (gap < 0) gap = -gap;
-                if (gap < 3) continue;
+                if (!self_pair_used(A, S_rest, s1, s2, cfg->B_self)) continue;
                 double dist = orc_sphere_sphere(S + 4 * s1, S + 4 * s2);
                 if (dist < d_self) d_self = dist;
             }
@@ -903,11 +934,6 @@ double orc_mlp_loss_grad_w(int in_dim, int in_pad, int width, int layers, const 
     return loss;
 }
 
-/* Exact self-collision clearance of joint vectors q [n][dof]: the minimum
- * over sphere pairs on bodies at least three apart of the centre distance
- * minus both radii (the quantity the self-collision term ramps, Eq. 5);
- * +infinity when the arm has no such pair.  The training label of the
- * learned surrogate. */
 void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *qa,
                        const double *qb, double *out)
 {
@@ -925,17 +951,21 @@ void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *
     }
 }
 
-void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out)
+/* Exact self-collision clearance of joint vectors q [n][dof]: the minimum
+ * over the self-collision pairs (self_pair_used, with the rest-pose band
+ * b_rest = B_self) of the centre distance minus both radii (the quantity the
+ * self-collision term ramps, Eq. 5); +infinity when the arm has no pair.  The
+ * training label of the learned surrogate. */
+void orc_self_distance(const orc_arm *arm, int n, const double *q, double b_rest, double *out)
 {
-    double S[ORC_MAX_SPHERES * 4];
+    double S[ORC_MAX_SPHERES * 4], S_rest[ORC_MAX_SPHERES * 4];
+    rest_spheres(arm, S_rest);
     for (int r = 0; r < n; ++r) {
         orc_fk(arm, q + (size_t)r * arm->dof, NULL, S);
         double m = INFINITY;
         for (int s1 = 0; s1 < arm->n_spheres; ++s1)
             for (int s2 = s1 + 1; s2 < arm->n_spheres; ++s2) {
-                int gap = arm->sphere_body[s1] - arm->sphere_body[s2];
-                if (gap < 0) gap = -gap;
-                if (gap < 3) continue;
+                if (!self_pair_used(arm, S_rest, s1, s2, b_rest)) continue;
                 double d = orc_sphere_sphere(S + 4 * s1, S + 4 * s2);
                 if (d < m) m = d;
             }

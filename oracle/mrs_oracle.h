@@ -166,9 +166,13 @@ double orc_mlp_loss_grad(int in_dim, int in_pad, int width, int layers, const do
 double orc_mlp_loss_grad_w(int in_dim, int in_pad, int width, int layers, const double *params,
                            int n, const double *x, const double *t, double over_weight,
                            double *grad, double *y_out);
-/* Exact self-collision clearance of joint vectors q [n][dof] (+inf if the
- * arm has no sphere pair on bodies at least three apart). */
-void orc_self_distance(const orc_arm *arm, int n, const double *q, double *out);
+/* Self-collision pair set (reading of C_self, Eq. 5): 1 when spheres s1 and
+ * s2 lie on bodies at least three apart and their clearance with every joint
+ * at zero (the nominal pose) is at least b_rest (B_self in the cycle). */
+int orc_self_pair_used(const orc_arm *arm, int s1, int s2, double b_rest);
+/* Exact self-collision clearance of joint vectors q [n][dof] over that pair
+ * set (+inf if the arm has no pair). */
+void orc_self_distance(const orc_arm *arm, int n, const double *q, double b_rest, double *out);
 
 /* Geometric Jacobian of the end-effector (the origin of frame d) in the world
  * frame, J [6][dof] row-major: for revolute joint i (axis z_{i-1} through

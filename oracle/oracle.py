@@ -121,7 +121,9 @@ def lib():
                                               _dp, C.c_double, _dp, _dp]
             L.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp,
                                             _dp, _dp, _dp]
-            L.orc_self_distance.argtypes = [C.POINTER(OrcArm), C.c_int, _dp, _dp]
+            L.orc_self_distance.argtypes = [C.POINTER(OrcArm), C.c_int, _dp, C.c_double, _dp]
+            L.orc_self_pair_used.restype = C.c_int
+            L.orc_self_pair_used.argtypes = [C.POINTER(OrcArm), C.c_int, C.c_int, C.c_double]
             L.orc_jacobian.argtypes = [C.POINTER(OrcArm), _dp, _dp]
             L.orc_manipulability.restype = C.c_double
             L.orc_manipulability.argtypes = [C.c_int, _dp]
@@ -348,11 +350,19 @@ class Oracle:
         return frames, sph
 
     def self_distance(self, arm: int, q):
-        """Exact self-collision clearance of joint vectors q [n][dof]."""
+        """Exact self-collision clearance of joint vectors q [n][dof] over the
+        arm's self-collision pair set (rest-pose band B_self)."""
         q, pq = _d(np.asarray(q, np.float64).reshape(-1, self.sc.arms[arm].dof))
         out = np.zeros(len(q))
-        lib().orc_self_distance(C.byref(self.arms[arm]), len(q), pq, _ptr(out))
+        lib().orc_self_distance(C.byref(self.arms[arm]), len(q), pq, self.cfg.B_self, _ptr(out))
         return out
+
+    def self_pairs(self, arm: int):
+        """The arm's self-collision pair set as (s1, s2) index pairs, s1 < s2."""
+        n = self.sc.arms[arm].n_spheres
+        f = lib().orc_self_pair_used
+        return [(i, j) for i in range(n) for j in range(i + 1, n)
+                if f(C.byref(self.arms[arm]), i, j, self.cfg.B_self)]
 
     def pair_distance(self, a: int, b: int, qa, qb, base_b=None, base_a=None):
         """Exact clearance between arm a at joints qa [n][d_a] and arm b at qb

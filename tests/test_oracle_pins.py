@@ -613,13 +613,50 @@ def test_self_distance_is_the_self_term_of_the_rollout(oracle_mod):
         q = rng.uniform(-2.8, 2.8, 7)
         d = orc.self_distance(0, q)[0]
         _, sph = orc.fk(0, q)
+        _, rest = orc.fk(0, np.zeros(7))
         body = arm.sphere_body
-        brute = min(np.linalg.norm(sph[i, :3] - sph[j, :3]) - sph[i, 3] - sph[j, 3]
+
+        def clear(S, i, j):
+            return np.linalg.norm(S[i, :3] - S[j, :3]) - S[i, 3] - S[j, 3]
+        brute = min(clear(sph, i, j)
                     for i in range(len(sph)) for j in range(i + 1, len(sph))
-                    if abs(int(body[i]) - int(body[j])) >= 3)
+                    if abs(int(body[i]) - int(body[j])) >= 3 and clear(rest, i, j) >= B)
         assert math.isclose(d, brute, rel_tol=1e-12, abs_tol=1e-15)
         _, stage, _, _ = orc.rollout(0, [q], [np.zeros(7)], gp, gR, np.zeros((2, 7)))
         assert math.isclose(stage[0], max(0.0, 1 - d / B), rel_tol=1e-12, abs_tol=1e-15)
+
+
+def test_self_pair_set_ignores_pairs_touching_at_rest(oracle_mod):
+    """The self-collision pair set (reading of C_self in Eq. 5): pairs on
+    bodies at least three apart, minus those inside the B_self band at the
+    rest pose.  A planar four-link arm (alpha = d = 0, a = 0.25 m) lies
+    straight along x at rest, so frame i sits at x = 0.25 i; every sphere has
+    r = 0.0625 m (all values exact in binary32).  Sphere 0 (body 1, frame-1
+    origin) and sphere 1 (body 4, frame-4 origin) are 0.625 m clear at rest:
+    kept.  Sphere 2 (body 4, 0.6875 m back along the link: x = 0.3125 at
+    rest) overlaps sphere 0 at rest; sphere 3 (x = 0.390625) is 1/64 m clear
+    of it, inside the 3 cm band: both dropped.  Sphere 4 (body 2) is only two
+    bodies from sphere 1: dropped by the chain rule.  The clearance at any
+    pose is then the planar closed form of the one kept pair."""
+    from oracle.oracle import Oracle
+    a, r = 0.25, 0.0625
+    spheres = [[0, 0, 0, r], [0, 0, 0, r], [-0.6875, 0, 0, r], [-0.609375, 0, 0, r],
+               [0, 0, 0, r]]
+    bodies = [1, 4, 4, 4, 2]
+    order = np.argsort(bodies, kind="stable")     # bodies must be non-decreasing
+    arm = dh_arm([[a, 0, 0, 0]] * 4, np.asarray(spheres)[order], np.asarray(bodies)[order])
+    orc = Oracle(tiny_scenario([arm]))
+    kept = {(int(order[i]), int(order[j])) for i, j in orc.self_pairs(0)}
+    kept = {tuple(sorted(p)) for p in kept}
+    assert kept == {(0, 1)}
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        q = rng.uniform(-2.8, 2.8, 4)
+        th = np.cumsum(q)
+        p1 = a * np.array([math.cos(th[0]), math.sin(th[0])])
+        p4 = a * np.array([np.sum(np.cos(th)), np.sum(np.sin(th))])
+        assert math.isclose(orc.self_distance(0, q)[0], np.linalg.norm(p4 - p1) - 2 * r,
+                            rel_tol=1e-12, abs_tol=1e-14)
 
 
 # ---------------------------------------------------------------------------
