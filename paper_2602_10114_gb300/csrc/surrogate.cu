@@ -11,9 +11,10 @@
 //                     to a neighbour's published plan (evaluation).
 // The surrogates' own inference (features, layers, output) is one fused
 // kernel of mlp_fused.cuh.
-// The clearance is the minimum over the arm's sphere pairs on bodies at least
-// three apart of sqrt(d2) - r1 - r2, with the rollout's kinematics and pair
-// arithmetic (same functions, same operation order).
+// The clearance is the minimum over the arm's self-collision pairs (bodies at
+// least three apart, clear of the B_self band at the rest pose) of
+// sqrt(d2) - r1 - r2, with the rollout's kinematics and pair arithmetic (same
+// functions, same operation order).
 #include "kernels.cuh"
 
 namespace mrs {

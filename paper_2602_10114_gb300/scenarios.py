@@ -156,7 +156,11 @@ def _world(rng, n_spheres, n_aabb, bases, lo, hi, speed=None):
 
 
 def _states(rng, arms):
-    q0 = [_f32(rng.uniform(-1.0, 1.0, a.dof)) for a in arms]
+    """Start state and goal joints: every arm starts at rest in its rest pose
+    (all joints zero, zero velocity), the pose at which the self-collision
+    pair set is taken, so no arm starts in self-contact; the goal joints are
+    uniform within the limits."""
+    q0 = [_f32(np.zeros(a.dof)) for a in arms]
     qd0 = [_f32(np.zeros(a.dof)) for a in arms]
     goal_q = [_f32(rng.uniform(a.q_lo, a.q_hi)) for a in arms]
     return q0, qd0, goal_q

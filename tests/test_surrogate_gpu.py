@@ -37,6 +37,19 @@ def test_dataset_labels_and_features_match_the_oracle():
     import torch
     t2 = ctl.self_distance(1, torch.from_numpy(q).cuda()).cpu().numpy()
     assert np.array_equal(t2, t)
+    # near the rest pose, where the pairs dropped by the rest-pose rule are
+    # closest: the library's pair set is the oracle's
+    for idx in (2, 4, 5):
+        sc = S.config(idx)
+        ctl = mrs.Controller(sc)
+        orc = Oracle(sc)
+        rng = np.random.default_rng(idx)
+        for arm in sorted({0, 1, 2} & set(range(sc.n_arms))):
+            d = sc.arms[arm].dof
+            qn = rng.uniform(-0.3, 0.3, (512, d)).astype(np.float32)
+            qn[0] = 0
+            got = ctl.self_distance(arm, torch.from_numpy(qn).cuda()).cpu().numpy()
+            assert np.abs(got - orc.self_distance(arm, qn.astype(np.float64))).max() < EPS_D
 
 
 def test_in_cycle_inference_matches_the_oracle_forward():
