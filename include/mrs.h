@@ -23,6 +23,9 @@
  *  - Floats are IEEE binary32.  Lengths are metres, angles radians, time
  *    seconds.  Non-finite inputs are rejected with MRS_EINVAL.
  *  - One context per host thread; calls on one context are not reentrant.
+ *  - A context belongs to the device of its stream.  Every call on a
+ *    context makes that device current for the call's duration and gives
+ *    the caller's current device back before it returns.
  */
 #ifndef MRS_H
 #define MRS_H
@@ -64,6 +67,12 @@ typedef enum {
  *  qd_max      [dof]      velocity limit of the safe-stopping cost.
  *  sphere_body [NS]       body of each sphere, 1..dof for link i, dof+1 for
  *                         the tool (carried by frame dof); non-decreasing.
+ *                         The self-collision term (C_self of Eq. 5) runs
+ *                         over the sphere pairs on bodies at least three
+ *                         apart whose clearance with every joint at zero
+ *                         (the rest pose) is at least B_self: pairs that
+ *                         touch, or lie in the safety band, at rest belong
+ *                         to the arm's build and are ignored.
  *  sphere_xyzr [NS][4]    centre in the body's frame and radius.
  *  base_pose   [7]        base position and unit quaternion (w, x, y, z).
  *  K, H                   samples per iteration and horizon.
@@ -97,7 +106,9 @@ typedef struct {
  *  q_margin     soft-limit margin of the joint cost.
  *  iterations   optimisation iterations per cycle (the paper's K).
  *  seed         Philox key of the sampling.
- *  mode         0 = exact costs (the only mode of this build).
+ *  reserved     must be 0.  (Exact or learned clearance terms are chosen
+ *               per arm after create: mrs_set_self_surrogate and
+ *               mrs_set_pair_surrogate; without them every term is exact.)
  *  max_plan_age a board entry older than this many cycles counts as not
  *               published and is ignored (Sec. IV-C); 0 = no limit.
  *  w_manip      weight of C_manip of Eq. 5 (singularity avoidance, Sec.
@@ -114,7 +125,7 @@ typedef struct {
     float B, B_world, B_self, tau, q_margin;
     int iterations;
     unsigned long long seed;
-    int mode;
+    int reserved;
     int max_plan_age;
     float w_manip, manip_w0;
 } mrs_config;
@@ -200,8 +211,11 @@ mrs_status mrs_share_plans(mrs_ctx *ctx, int arm, const float *plan_spheres, con
 /* One control cycle for every arm (Algorithm 1: Sense, Shift, `iterations`
  * x {SampleControls, Rollout, UpdateDistribution}, ToPlan, Publish to the
  * board for the next cycle, PickBest).  `states` [n_arms] host pointers.
- * Blocks until the results are in `out` or until the bounded wait gives up
- * (MRS_ETIMEOUT; the context must then be destroyed). */
+ * Blocks until the results are in `out` or until a bounded wait gives up
+ * (MRS_ETIMEOUT).  After a host-side timeout (the cycle did not finish within
+ * 10 s) the context must be destroyed; after a device-side one (see
+ * mrs_set_wait_limit) the outputs and the state are not valid until a state
+ * is loaded. */
 mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out);
 
 /* Same cycle with device-resident inputs, enqueued on the context stream
@@ -264,8 +278,9 @@ mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float
  *    requests fail with MRS_EINVAL before any device work.
  *  - The context must have a bound workspace (MRS_ESTATE otherwise: binding
  *    on demand would allocate).
- *  - The first call on each device looks up the array's device address on
- *    that device; make that first call before any stream capture.
+ *  - The first call on each device (the context's device) looks up the
+ *    array's device address on that device; make that first call before any
+ *    stream capture.
  *  - All calls in the process share the one array and it keeps the last
  *    call's contents (nothing in it needs to start at zero: every value
  *    returned is written by the call).  Calls that overlap on the GPU, from
@@ -283,6 +298,17 @@ mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee
 mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs);
 mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out);
 mrs_status mrs_debug_alpha(mrs_ctx *ctx, float *alpha);
+
+/* Test hook of the device-side bounded waits: the number of polls the
+ * rollout's wait for its staged plan copies may take before it gives up
+ * (polls < 0: the default, 2^22; 0: give up at once).  A wait that gives up
+ * sets the context's error word, waits with the default limit for its copies
+ * still in flight, and ends its block; mrs_step then returns MRS_ETIMEOUT.
+ * After MRS_ETIMEOUT from a device-side wait the cycle's outputs and the
+ * controller state are not valid: mrs_load_state (which also clears the
+ * error word) or mrs_bind_workspace makes the context usable again.  Errors:
+ * MRS_EINVAL for polls above the default. */
+mrs_status mrs_set_wait_limit(mrs_ctx *ctx, long long polls);
 
 /* Debug switch: zero_noise = 1 samples eps = 0 (every rollout is the mean). */
 mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise);
@@ -399,8 +425,9 @@ mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float mar
 /* Training data for an arm's surrogate, on the device: n joint vectors
  * uniform within the joint limits (Philox, `seed`), their features d_x
  * [n][2 dof] (sin, cos per joint) and exact self-collision clearance d_t [n]
- * (the minimum over sphere pairs on bodies at least three apart of centre
- * distance minus radii); d_q [n][dof] receives the joint vectors (may be NULL). */
+ * (the minimum over the arm's self-collision pairs, see mrs_arm_desc, of
+ * centre distance minus radii); d_q [n][dof] receives the joint vectors (may
+ * be NULL). */
 mrs_status mrs_self_dataset(mrs_ctx *ctx, int arm, int n, unsigned long long seed, float *d_x,
                             float *d_t, float *d_q);
 /* Exact self-collision clearance of joint vectors d_q [n][dof] -> d_out [n]. */

@@ -135,11 +135,11 @@ cudaError_t enqueue_fk(const Dev &D, int arm, int n, const float *q, float *ee, 
 cudaError_t enqueue_debug_spheres(const Dev &D, int n_req, const int *anh, float *out,
                                   cudaStream_t s);
 cudaError_t enqueue_philox(int n, const uint4 *ctr, uint2 key, uint4 *out, cudaStream_t s);
-// Forward kinematics staged in the library's static device scratch
-// (mrs_fk_static.cu); no device memory is allocated.
-cudaError_t fk_static(const Dev &D, int arm, int dof, int ns, int n, const float *q_host,
-                      float *ee_host, float *spheres_host, cudaStream_t s, std::string &why,
-                      bool &too_large);
+// Forward kinematics staged in the library's static device scratch of
+// `device` (mrs_fk_static.cu); no device memory is allocated.
+cudaError_t fk_static(const Dev &D, int device, int arm, int dof, int ns, int n,
+                      const float *q_host, float *ee_host, float *spheres_host, cudaStream_t s,
+                      std::string &why, bool &too_large);
 size_t fk_static_capacity_floats();
 
 }  // namespace mrs

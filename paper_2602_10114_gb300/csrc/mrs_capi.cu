@@ -17,6 +17,7 @@
 using namespace mrs;
 
 struct mrs_ctx {
+    int device = 0;            // the device of the context's stream, made current by every call
     Params P{};
     Dev D{};
     LaunchPlan L{};
@@ -89,6 +90,25 @@ static mrs_status cuda_fail(mrs_ctx *c, cudaError_t e, const char *where)
         cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
     } while (0)
+
+// Makes the context's device current for one call and gives the caller's
+// current device back at its end: a thread may call into a context while
+// another device is current, and the context's stream, workspace, graph and
+// static scratch all belong to the context's device.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(const mrs_ctx *c)
+    {
+        int cur = 0;
+        if (c && cudaGetDevice(&cur) == cudaSuccess && cur != c->device &&
+            cudaSetDevice(c->device) == cudaSuccess)
+            prev = cur;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 static bool finite_arr(const float *p, size_t n)
 {
@@ -308,7 +328,7 @@ static mrs_status validate(const mrs_config *cfg, std::string &why)
     if (!(cfg->w_manip >= 0.f) || !std::isfinite(cfg->w_manip) ||
         (cfg->w_manip > 0.f && !(cfg->manip_w0 > 0.f && std::isfinite(cfg->manip_w0))))
         return why = "w_manip must be >= 0, and manip_w0 > 0 when w_manip > 0", MRS_EINVAL;
-    if (cfg->mode != 0) return why = "only exact mode (0) is built", MRS_EUNSUPPORTED;
+    if (cfg->reserved != 0) return why = "mrs_config.reserved must be 0", MRS_EINVAL;
     for (int a = 0; a < cfg->n_arms; ++a) {
         const mrs_arm_desc &d = cfg->arms[a];
         if (d.dof < 1 || d.dof > MRS_MAX_DOF) return why = "dof out of range", MRS_EINVAL;
@@ -348,6 +368,63 @@ static void invalidate_graph(mrs_ctx *ctx)
     ctx->graph_io = nullptr;
 }
 
+// Sphere centres and radii of an arm with every joint at zero (its rest
+// pose), in double precision: standard DH frames T_i = T_{i-1} Rz(theta_i)
+// Tz(d_i) Tx(a_i) Rx(alpha_i) from the base pose.  Used once at set-up, to
+// drop the self-collision pairs that touch or lie inside the B_self band at
+// rest: they belong to the arm's build (Eq. 5's C_self is over the others).
+static void rest_pose_spheres(const mrs_arm_desc &d, std::vector<double> &out)
+{
+    const float *b = d.base_pose;
+    double w = b[3], x = b[4], y = b[5], z = b[6];
+    const double n = std::sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    // rotation R (row-major) and translation t of the current frame
+    double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                   2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                   2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    double t[3] = {b[0], b[1], b[2]};
+    std::vector<double> frames((size_t)(d.dof + 1) * 12);
+    auto keep = [&](int f) {
+        for (int k = 0; k < 9; ++k) frames[12 * f + k] = R[k];
+        for (int k = 0; k < 3; ++k) frames[12 * f + 9 + k] = t[k];
+    };
+    keep(0);
+    for (int j = 0; j < d.dof; ++j) {
+        const double a = d.dh[4 * j], dd = d.dh[4 * j + 1], al = d.dh[4 * j + 2],
+                     th = d.dh[4 * j + 3];
+        const double ct = std::cos(th), st = std::sin(th), ca = std::cos(al), sa = std::sin(al);
+        // local transform Rz(th) Tz(dd) Tx(a) Rx(al): rotation M, offset (a ct, a st, dd)
+        const double M[9] = {ct, -st * ca, st * sa, st, ct * ca, -ct * sa, 0.0, sa, ca};
+        const double o[3] = {a * ct, a * st, dd};
+        double Rn[9], tn[3];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c)
+                Rn[3 * r + c] = R[3 * r] * M[c] + R[3 * r + 1] * M[3 + c] + R[3 * r + 2] * M[6 + c];
+            tn[r] = t[r] + R[3 * r] * o[0] + R[3 * r + 1] * o[1] + R[3 * r + 2] * o[2];
+        }
+        std::memcpy(R, Rn, sizeof R);
+        std::memcpy(t, tn, sizeof t);
+        keep(j + 1);
+    }
+    out.assign((size_t)d.n_spheres * 4, 0.0);
+    for (int s = 0; s < d.n_spheres; ++s) {
+        const int f = std::min(d.sphere_body[s], d.dof);
+        const double *F = frames.data() + 12 * f;
+        const float *p = d.sphere_xyzr + 4 * s;
+        for (int r = 0; r < 3; ++r)
+            out[4 * s + r] = F[9 + r] + F[3 * r] * p[0] + F[3 * r + 1] * p[1] + F[3 * r + 2] * p[2];
+        out[4 * s + 3] = p[3];
+    }
+}
+
+static double rest_clearance(const std::vector<double> &S, int s1, int s2)
+{
+    const double *a = S.data() + 4 * s1, *b = S.data() + 4 * s2;
+    const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return std::sqrt(dx * dx + dy * dy + dz * dz) - a[3] - b[3];
+}
+
 extern "C" {
 
 mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
@@ -367,7 +444,6 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     Params &P = ctx->P;
     P.n_arms = cfg->n_arms;
     P.iterations = cfg->iterations;
-    P.mode = cfg->mode;
     P.zero_noise = 0;
     P.dt = cfg->dt; P.lambda = cfg->lambda; P.gamma = cfg->gamma;
     P.alpha_mu = cfg->alpha_mu; P.alpha_sigma = cfg->alpha_sigma; P.sigma_init = cfg->sigma_init;
@@ -378,6 +454,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     P.max_plan_age = cfg->max_plan_age;
     P.w_manip = cfg->w_manip;
     P.manip_w0 = cfg->manip_w0;
+    P.wait_polls = tc::kWaitLimit;
 
     size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
     long long khd = 0, kh = 0;
@@ -405,11 +482,15 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
             A.body[s] = d.sphere_body[s];
             A.frame[s] = std::min(d.sphere_body[s], d.dof);
         }
-        // self-collision pairs: bodies at least three apart
+        // self-collision pairs: bodies at least three apart and clear of the
+        // B_self band with every joint at zero (the rest-pose ignore rule)
         A.self_off = (int)ctx->self_pairs.size();
+        std::vector<double> rest;
+        rest_pose_spheres(d, rest);
         for (int s1 = 0; s1 < d.n_spheres; ++s1)
             for (int s2 = s1 + 1; s2 < d.n_spheres; ++s2)
-                if (std::abs(d.sphere_body[s1] - d.sphere_body[s2]) >= 3) {
+                if (std::abs(d.sphere_body[s1] - d.sphere_body[s2]) >= 3 &&
+                    rest_clearance(rest, s1, s2) >= (double)cfg->B_self) {
                     ctx->self_pairs.push_back(s1 | (s2 << 8));
                     // binary32 sums in the device's order: (r1 + B_self) + r2, squared
                     const float t = (d.sphere_xyzr[4 * s1 + 3] + cfg->B_self) + d.sphere_xyzr[4 * s2 + 3];
@@ -482,7 +563,17 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
 
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
+        if (cudaStreamGetDevice(ctx->stream, &ctx->device) != cudaSuccess) {
+            delete ctx;
+            g_create_err = "the stream's device could not be read";
+            return MRS_ECUDA;
+        }
     } else {
+        if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+            delete ctx;
+            g_create_err = "no CUDA device";
+            return MRS_ECUDA;
+        }
         cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             delete ctx;
@@ -490,6 +581,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         }
         ctx->own_stream = true;
     }
+    DeviceScope dev_scope(ctx);
     if (cudaHostAlloc((void **)&ctx->pin_in, sizeof(float) * in, cudaHostAllocDefault) !=
             cudaSuccess ||
         cudaHostAlloc((void **)&ctx->pin_out, sizeof(float) * (ctx->sz.output_floats + 4),
@@ -499,9 +591,8 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
         return MRS_ENOMEM;
     }
     ctx->pin_err = (int *)(ctx->pin_out + ctx->sz.output_floats);
-    int dev = 0, smem_optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+    int dev = ctx->device, smem_optin = 0;
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess) {
         mrs_destroy(ctx);
@@ -532,6 +623,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
 
 void mrs_destroy(mrs_ctx *ctx)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->rhohat) cudaFree(ctx->rhohat);
@@ -614,6 +706,7 @@ static mrs_status bind(mrs_ctx *ctx, void *dev, size_t bytes)
 
 mrs_status mrs_bind_workspace(mrs_ctx *ctx, void *dev_ptr, size_t bytes)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (!dev_ptr || bytes < ctx->sz.workspace_bytes || ((uintptr_t)dev_ptr & 255))
         return fail(ctx, MRS_EINVAL, "workspace null, too small or not 256-byte aligned");
@@ -637,6 +730,7 @@ static mrs_status ensure_bound(mrs_ctx *ctx)
 mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, int n_spheres,
                          const float *aabbs, int n_aabbs)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (n_spheres < 0 || n_spheres > MRS_MAX_WORLD_SPHERES || n_aabbs < 0 ||
         n_aabbs > MRS_MAX_AABBS || (n_spheres && !spheres) || (n_aabbs && !aabbs))
@@ -699,6 +793,7 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
 mrs_status mrs_share_plans(mrs_ctx *ctx, int arm, const float *plan_spheres, const float *plan_q,
                            float dist_to_goal, long long cycle)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "arm out of range");
     if (!std::isfinite(dist_to_goal)) return fail(ctx, MRS_EINVAL, "non-finite distance");
@@ -796,6 +891,7 @@ static mrs_status wait_bounded(mrs_ctx *ctx, double timeout_s)
 
 mrs_status mrs_step_device(mrs_ctx *ctx, const float *d_input)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !d_input) return fail(ctx, MRS_EINVAL, "null argument");
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
@@ -807,6 +903,7 @@ mrs_status mrs_step_device(mrs_ctx *ctx, const float *d_input)
 
 mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !states) return fail(ctx, MRS_EINVAL, "null argument");
     float *p = ctx->pin_in;
     for (int a = 0; a < ctx->A; ++a) {
@@ -856,6 +953,7 @@ mrs_status mrs_step(mrs_ctx *ctx, const mrs_arm_state *states, mrs_step_out *out
 
 mrs_status mrs_output_device(mrs_ctx *ctx, mrs_step_out *out)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !out) return MRS_EINVAL;
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
@@ -871,6 +969,7 @@ mrs_status mrs_output_device(mrs_ctx *ctx, mrs_step_out *out)
 
 mrs_status mrs_output_host(mrs_ctx *ctx, mrs_step_out *out)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !out) return MRS_EINVAL;
     const Dev &D = ctx->D;
     float *o = ctx->pin_out;
@@ -885,12 +984,14 @@ mrs_status mrs_output_host(mrs_ctx *ctx, mrs_step_out *out)
 
 mrs_status mrs_sync(mrs_ctx *ctx, double timeout_s)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     return wait_bounded(ctx, timeout_s);
 }
 
 mrs_status mrs_use_graph(mrs_ctx *ctx, int on)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     ctx->use_graph = on != 0;
     return MRS_OK;
@@ -909,6 +1010,7 @@ struct BlobHeader {
 
 mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !blob) return MRS_EINVAL;
     if (bytes < ctx->sz.state_bytes) return fail(ctx, MRS_EINVAL, "state buffer too small");
     mrs_status st = ensure_bound(ctx);
@@ -963,6 +1065,7 @@ mrs_status mrs_save_state(mrs_ctx *ctx, void *blob, size_t bytes)
 
 mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !blob) return MRS_EINVAL;
     if (bytes < ctx->sz.state_bytes) return fail(ctx, MRS_EINVAL, "state blob too small");
     const char *p = (const char *)blob;
@@ -1014,6 +1117,7 @@ mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
     CK(cudaMemcpyAsync(D.Sigma + (cycle & 1) * ctx->sz.hdd, Sg.data(), sizeof(float) * Sg.size(),
                        cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemsetAsync(D.work, 0, sizeof(int) * 64, ctx->stream), "load");
+    CK(cudaMemsetAsync(D.err, 0, sizeof(int), ctx->stream), "load");   // a loaded state is clean
     CK(cudaMemcpyAsync(D.board_sph, sph.data(), sizeof(float) * sph.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.board_q, q.data(), sizeof(float) * q.size(), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.board_dist, dist.data(), sizeof(float) * A, cudaMemcpyHostToDevice, ctx->stream), "load");
@@ -1031,6 +1135,7 @@ mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
 
 mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (arm < 0 || arm >= ctx->A || n < 0 || (n && (!q || !ee)))
         return fail(ctx, MRS_EINVAL, "bad fk arguments");
@@ -1060,6 +1165,7 @@ mrs_status mrs_fk(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float
 
 mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee, float *spheres)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (arm < 0 || arm >= ctx->A || n < 0 || (n && (!q || !ee)))
         return fail(ctx, MRS_EINVAL, "bad fk arguments");
@@ -1070,8 +1176,8 @@ mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee
     if (!finite_arr(q, (size_t)n * A.dof)) return fail(ctx, MRS_EINVAL, "non-finite q");
     std::string why;
     bool too_large = false;
-    cudaError_t e = fk_static(ctx->D, arm, A.dof, A.ns, n, q, ee, spheres, ctx->stream, why,
-                              too_large);
+    cudaError_t e = fk_static(ctx->D, ctx->device, arm, A.dof, A.ns, n, q, ee, spheres,
+                              ctx->stream, why, too_large);
     if (too_large) return fail(ctx, MRS_EINVAL, why);
     if (e != cudaSuccess) return cuda_fail(ctx, e, ("mrs_fk_static: " + why).c_str());
     return MRS_OK;
@@ -1079,6 +1185,7 @@ mrs_status mrs_fk_static(mrs_ctx *ctx, int arm, int n, const float *q, float *ee
 
 mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float margin)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "arm out of range");
     ArmDev &A = ctx->arms[arm];
@@ -1132,6 +1239,7 @@ mrs_status mrs_set_self_surrogate(mrs_ctx *ctx, int arm, mrs_mlp *net, float mar
 mrs_status mrs_self_dataset(mrs_ctx *ctx, int arm, int n, unsigned long long seed, float *d_x,
                             float *d_t, float *d_q)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || arm < 0 || arm >= ctx->A || n < 1 || !d_x || !d_t)
         return fail(ctx, MRS_EINVAL, "bad dataset arguments");
     mrs_status st = ensure_bound(ctx);
@@ -1143,6 +1251,7 @@ mrs_status mrs_self_dataset(mrs_ctx *ctx, int arm, int n, unsigned long long see
 
 mrs_status mrs_self_distance(mrs_ctx *ctx, int arm, int n, const float *d_q, float *d_out)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || arm < 0 || arm >= ctx->A || n < 1 || !d_q || !d_out)
         return fail(ctx, MRS_EINVAL, "bad arguments");
     mrs_status st = ensure_bound(ctx);
@@ -1154,6 +1263,7 @@ mrs_status mrs_self_distance(mrs_ctx *ctx, int arm, int n, const float *d_q, flo
 
 mrs_status mrs_debug_self(mrs_ctx *ctx, int arm, float *dhat, float *exact)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "bad arguments");
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
@@ -1213,6 +1323,7 @@ static void relative_pose(const ArmDev &A, const ArmDev &B, float out[7])
 
 mrs_status mrs_relative_pose(mrs_ctx *ctx, int a, int b, float *pose)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !pose || a < 0 || a >= ctx->A || b < 0 || b >= ctx->A)
         return fail(ctx, MRS_EINVAL, "bad arguments");
     relative_pose(ctx->arms[a], ctx->arms[b], pose);
@@ -1251,6 +1362,7 @@ static void rebuild_pair_groups(mrs_ctx *ctx)
 
 mrs_status mrs_set_pair_surrogate(mrs_ctx *ctx, int a, int b, mrs_mlp *net, float margin)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (a < 0 || a >= ctx->A || b < -1 || b >= ctx->A || b == a)
         return fail(ctx, MRS_EINVAL, "arm out of range");
@@ -1303,6 +1415,7 @@ mrs_status mrs_pair_dataset(mrs_ctx *ctx, int a, int b, int n, unsigned long lon
                             const float *poses, int n_pose, float jit_t, float jit_yaw, float *d_x,
                             float *d_t, float *d_qa, float *d_qb, float *d_pose)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || a < 0 || a >= ctx->A || b < 0 || b >= ctx->A || n < 1 || !d_x || !d_t ||
         (poses && n_pose < 1) || !(jit_t >= 0.f) || !(jit_yaw >= 0.f))
         return fail(ctx, MRS_EINVAL, "bad dataset arguments");
@@ -1332,6 +1445,7 @@ mrs_status mrs_pair_dataset(mrs_ctx *ctx, int a, int b, int n, unsigned long lon
 
 mrs_status mrs_debug_pair(mrs_ctx *ctx, int a, int b, float *rhohat, float *exact)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || a < 0 || a >= ctx->A || b < 0 || b >= ctx->A || a == b)
         return fail(ctx, MRS_EINVAL, "bad arguments");
     mrs_status st = ensure_bound(ctx);
@@ -1359,6 +1473,7 @@ mrs_status mrs_debug_pair(mrs_ctx *ctx, int a, int b, float *rhohat, float *exac
 
 mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !costs || arm < 0 || arm >= ctx->A) return fail(ctx, MRS_EINVAL, "bad arguments");
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
@@ -1371,6 +1486,7 @@ mrs_status mrs_debug_costs(mrs_ctx *ctx, int arm, float *costs)
 
 mrs_status mrs_debug_alpha(mrs_ctx *ctx, float *alpha)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !alpha) return fail(ctx, MRS_EINVAL, "bad arguments");
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
@@ -1382,6 +1498,7 @@ mrs_status mrs_debug_alpha(mrs_ctx *ctx, float *alpha)
 
 mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || n_req < 0 || (n_req && (!anh || !out))) return fail(ctx, MRS_EINVAL, "bad arguments");
     if (n_req == 0) return MRS_OK;
     for (int r = 0; r < n_req; ++r) {
@@ -1410,6 +1527,7 @@ mrs_status mrs_debug_spheres(mrs_ctx *ctx, int n_req, const int *anh, float *out
 
 mrs_status mrs_enable_timing(mrs_ctx *ctx, int on)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     const size_t need = 3 + 5 * (size_t)ctx->P.iterations;   // one more than the stages
     if (on && ctx->events.size() < need) {
@@ -1426,6 +1544,7 @@ mrs_status mrs_enable_timing(mrs_ctx *ctx, int on)
 
 mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !ms || !n) return MRS_EINVAL;
     if (!ctx->timing) return fail(ctx, MRS_ESTATE, "timing is not enabled");
     const int cnt = 2 + 5 * ctx->P.iterations;                 // stages of one cycle
@@ -1462,6 +1581,7 @@ static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm,
 
 mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || !shape) return MRS_EINVAL;
     if (shape->tile_samples < 32 || shape->tile_samples > 256 || shape->tile_samples % 32 ||
         shape->blocks_per_sm < 0 || shape->blocks_per_sm > ctx->max_blocks_per_sm ||
@@ -1472,6 +1592,7 @@ mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
 
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     if (shape) {
         shape->tile_samples = ctx->tile_samples;
@@ -1486,6 +1607,7 @@ mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *ma
 mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int cap, int *n_tried,
                         mrs_rollout_shape *best)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx || reps < 1 || reps > 1000 || cap < 0) return fail(ctx, MRS_EINVAL, "bad arguments");
     if (!ctx->has_input) return fail(ctx, MRS_ESTATE, "autotune needs the inputs of an earlier step");
     mrs_status st = ensure_bound(ctx);
@@ -1580,8 +1702,21 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     return MRS_OK;
 }
 
+mrs_status mrs_set_wait_limit(mrs_ctx *ctx, long long polls)
+{
+    DeviceScope dev_scope(ctx);
+    if (!ctx) return MRS_EINVAL;
+    if (polls > (long long)tc::kWaitLimit)
+        return fail(ctx, MRS_EINVAL, "wait limit above the default " +
+                                         std::to_string(tc::kWaitLimit) + " polls");
+    ctx->P.wait_polls = polls < 0 ? tc::kWaitLimit : (unsigned)polls;
+    invalidate_graph(ctx);
+    return MRS_OK;
+}
+
 mrs_status mrs_set_zero_noise(mrs_ctx *ctx, int zero_noise)
 {
+    DeviceScope dev_scope(ctx);
     if (!ctx) return MRS_EINVAL;
     ctx->P.zero_noise = zero_noise ? 1 : 0;
     invalidate_graph(ctx);

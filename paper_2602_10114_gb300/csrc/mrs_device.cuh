@@ -44,7 +44,7 @@ struct __align__(16) ArmDev {
 };
 
 struct Params {
-    int n_arms, iterations, mode, zero_noise;
+    int n_arms, iterations, zero_noise;
     float dt, lambda, gamma, alpha_mu, alpha_sigma, sigma_init;
     float w_pose, w_rot, w_stop, w_joint, w_coll, w_self, w_dyn;
     float B, B_world, B_self, tau, q_margin;
@@ -54,6 +54,7 @@ struct Params {
     float eps_g;                  // cancellation margin of the expanded pair pre-test (m^2)
     int max_plan_age;             // board entries older than this are ignored (0: no limit)
     float w_manip, manip_w0;      // C_manip weight (0: off) and manipulability threshold
+    unsigned wait_polls;          // polls of the rollout's bounded wait for its plan copies
 };
 
 // A neighbour's board entry is used when it is published and, with a
@@ -95,7 +96,8 @@ struct Dev {
     long long *cycle;      // completed cycles
     float *world_t;        // seconds since the world was set
     int *err;              // device error word (bounded waits)
-    int *self_pairs;       // per arm, packed s1 | s2 << 8, bodies >= 3 apart
+    int *self_pairs;       // per arm, packed s1 | s2 << 8: bodies >= 3 apart,
+                           // clear of the B_self band at the rest pose
     float *self_t2;        // (r1 + B_self + r2)^2 of each self pair, the sums in this order
     float *dhat;           // [sum K*H] surrogate self clearance of every rollout step, [h][n]
     float *rhohat;         // [sum K*H][A] surrogate clearance of every rollout step to each

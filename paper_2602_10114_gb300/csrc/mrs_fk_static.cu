@@ -27,41 +27,16 @@ static std::mutex g_scratch_mu;
 
 static size_t pad4(size_t n) { return (n + 3) / 4 * 4; }
 
-// Same arithmetic, in the same order, as the rollout's kinematics.
-__global__ void k_fk_static(Dev D, int arm, int n, const float *q, float *ee, float4 *spheres)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const ArmDev &A = D.arms[arm];
-    const int d = A.dof;
-    Frame F;
-    frame_base(A, F);
-    int f = 0;
-    for (int s = 0; s < A.ns; ++s) {
-        const int fs = A.frame[s];
-        while (f < fs) {
-            frame_step(F, q[(size_t)i * d + f], A.dh[f], A.twist[f]);
-            ++f;
-        }
-        const float4 p = A.sph[s];
-        const float3 c = sphere_centre(F, p);
-        spheres[(size_t)i * A.ns + s] = make_float4(c.x, c.y, c.z, p.w);
-    }
-    while (f < d) {
-        frame_step(F, q[(size_t)i * d + f], A.dh[f], A.twist[f]);
-        ++f;
-    }
-    for (int k = 0; k < 9; ++k) ee[(size_t)i * 12 + k] = F.R[k];
-    for (int k = 0; k < 3; ++k) ee[(size_t)i * 12 + 9 + k] = F.t[k];
-}
-
 size_t fk_static_capacity_floats() { return kFkStaticFloats; }
 
-// Host side of mrs_fk_static.  Returns cudaSuccess, or an error with `why`
-// set; a request larger than the scratch is rejected before any CUDA call.
-cudaError_t fk_static(const Dev &D, int arm, int dof, int ns, int n, const float *q_host,
-                      float *ee_host, float *spheres_host, cudaStream_t s, std::string &why,
-                      bool &too_large)
+// Host side of mrs_fk_static, on `device` (the context's device, current
+// during the call).  The kinematics are mrs_fk's own kernel (enqueue_fk) run
+// on slices of the static scratch.  Returns cudaSuccess, or an error with
+// `why` set; a request larger than the scratch is rejected before any CUDA
+// call.
+cudaError_t fk_static(const Dev &D, int device, int arm, int dof, int ns, int n,
+                      const float *q_host, float *ee_host, float *spheres_host, cudaStream_t s,
+                      std::string &why, bool &too_large)
 {
     too_large = false;
     const size_t nq = pad4((size_t)n * dof), ne = (size_t)n * 12, nsph = (size_t)n * ns * 4;
@@ -71,16 +46,15 @@ cudaError_t fk_static(const Dev &D, int arm, int dof, int ns, int n, const float
               "limit is " + std::to_string(kFkStaticFloats);
         return cudaErrorInvalidValue;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return why = "cudaGetDevice", e;
+    const int dev = device;
+    cudaError_t e = cudaSuccess;
     if (dev < 0 || dev >= kMaxDevices) return why = "device ordinal out of range", cudaErrorInvalidDevice;
     float *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
         if (!g_scratch_ptr[dev]) {
-            // first call on this device (the device is current): look up the
-            // device address of the static array
+            // first call on this device (made current by the caller): look
+            // up the device address of the static array
             float *p = nullptr;
             e = cudaGetSymbolAddress((void **)&p, g_fk_scratch);
             if (e != cudaSuccess) return why = "cudaGetSymbolAddress", e;
@@ -95,8 +69,8 @@ cudaError_t fk_static(const Dev &D, int arm, int dof, int ns, int n, const float
     if ((e = cudaMemcpyAsync(dq, q_host, sizeof(float) * n * dof, cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
         return why = "upload", e;
-    k_fk_static<<<(n + 127) / 128, 128, 0, s>>>(D, arm, n, dq, dee, dsph);
-    if ((e = cudaGetLastError()) != cudaSuccess) return why = "launch", e;
+    if ((e = enqueue_fk(D, arm, n, dq, dee, (float *)dsph, s)) != cudaSuccess)
+        return why = "launch", e;
     if ((e = cudaMemcpyAsync(ee_host, dee, sizeof(float) * ne, cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
         return why = "download", e;

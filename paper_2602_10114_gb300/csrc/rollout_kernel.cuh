@@ -762,10 +762,11 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             }
         }
         if (n_plan > 0) {
-            // bounded wait for the plan copies, then the derived layouts; if
-            // a copy did not land in time the block records the error, waits
-            // (bounded) for the copies still in flight and stops
-            const bool landed = tc::mbar_wait(&s_bar, bar_phase);
+            // bounded wait (P.wait_polls polls) for the plan copies, then the
+            // derived layouts; if a copy did not land in time the block
+            // records the error, waits (bounded, the full default limit) for
+            // the copies still in flight and stops
+            const bool landed = tc::mbar_wait(&s_bar, bar_phase, P.wait_polls);
             if (__syncthreads_or(!landed)) {
                 if (threadIdx.x == 0) atomicExch(D.err, 1);
                 tc::mbar_wait(&s_bar, bar_phase);

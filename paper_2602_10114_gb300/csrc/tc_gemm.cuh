@@ -57,11 +57,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// true when phase `parity` of the barrier has completed; bounded
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// true when phase `parity` of the barrier has completed within `limit`
+// polls (none at all for limit = 0); bounded
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned limit = kWaitLimit)
 {
     const uint32_t a = smem_u32(bar);
-    for (unsigned it = 0; it < kWaitLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}"

@@ -38,7 +38,7 @@ class MrsConfig(C.Structure):
                 ("w_joint", C.c_float), ("w_coll", C.c_float), ("w_self", C.c_float),
                 ("w_dyn", C.c_float), ("B", C.c_float), ("B_world", C.c_float),
                 ("B_self", C.c_float), ("tau", C.c_float), ("q_margin", C.c_float),
-                ("iterations", C.c_int), ("seed", C.c_ulonglong), ("mode", C.c_int),
+                ("iterations", C.c_int), ("seed", C.c_ulonglong), ("reserved", C.c_int),
                 ("max_plan_age", C.c_int), ("w_manip", C.c_float), ("manip_w0", C.c_float)]
 
 
@@ -87,6 +87,7 @@ SIGNATURES = {
     "mrs_debug_spheres": (C.c_int, [C.c_void_p, C.c_int, _ip, _fp]),
     "mrs_debug_alpha": (C.c_int, [C.c_void_p, _fp]),
     "mrs_set_zero_noise": (C.c_int, [C.c_void_p, C.c_int]),
+    "mrs_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
     "mrs_enable_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "mrs_kernel_times": (C.c_int, [C.c_void_p, _fp, C.POINTER(C.c_int)]),
     "mrs_set_rollout_shape": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -339,6 +340,11 @@ class Controller:
 
     def set_zero_noise(self, on: bool):
         self._check(self.L.mrs_set_zero_noise(self.h, 1 if on else 0), "zero_noise")
+
+    def set_wait_limit(self, polls: int):
+        """Polls of the rollout's bounded wait for its plan copies (< 0: the
+        default)."""
+        self._check(self.L.mrs_set_wait_limit(self.h, int(polls)), "set_wait_limit")
 
     def enable_timing(self, on: bool):
         self._check(self.L.mrs_enable_timing(self.h, 1 if on else 0), "enable_timing")

@@ -46,7 +46,7 @@ def test_argument_errors_without_a_device(lib):
     assert lib.mrs_query_sizes(None, None) == 1
 
 
-def test_unsupported_mode_and_bad_arm(lib):
+def test_reserved_field_and_bad_arm(lib):
     import numpy as np
     from paper_2602_10114_gb300 import mrs, scenarios
     sc = scenarios.config(1)
@@ -65,8 +65,9 @@ def test_unsupported_mode_and_bad_arm(lib):
                         p["w_coll"], p["w_self"], p["w_dyn"], p["B"], p["B_world"], p["B_self"],
                         p["tau"], p["q_margin"], 1, 0, 1)
     h = C.c_void_p()
-    assert lib.mrs_create(C.byref(cfg), None, C.byref(h)) == 6       # learned mode not built
-    cfg.mode = 0
+    assert lib.mrs_create(C.byref(cfg), None, C.byref(h)) == 1       # reserved must be 0
+    assert b"reserved" in lib.mrs_last_error(None)
+    cfg.reserved = 0
     cfg.lambda_ = float("nan")
     assert lib.mrs_create(C.byref(cfg), None, C.byref(h)) == 1
     cfg.lambda_ = 10.0

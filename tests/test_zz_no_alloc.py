@@ -2,7 +2,12 @@
 memory (a hard-period control loop, or a process whose device memory belongs
 to another allocator).  Its results must equal those of mrs_fk, the entry
 point that allocates its staging buffers, on consecutive calls that reuse the
-static scratch.  This file is collected last on purpose."""
+static scratch.
+
+The file is collected last (pytest collects test files in name order) so
+that a run stopping at its first failure has run every other test before
+this one; the tests here also pass when run alone in a fresh process, since
+they depend on no earlier call."""
 import numpy as np
 import pytest
 
