@@ -136,6 +136,36 @@ def update_tolerance(exp, orc, arm, lam, alpha_mu, alpha_sigma, floor=1e-5):
     return tol_mu, tol_sig
 
 
+def fp32_update_bound(exp, orc, arm, lam, alpha_mu, alpha_sigma):
+    """Conditioning of one arm's update in FP32, from the oracle alone: the
+    first-order change of the updated mean [H][d] and covariance [H][d][d]
+    when each total cost C_n carries a realistic FP32 error
+      e_n = 2^-22 |C_n| + (EPS_D / 4) S_n
+    (four units in the last place of the stored cost, plus the sphere error
+    the sphere parity checks enforce, EPS_D / 4, times the cost's ramp
+    sensitivity S_n).  To first order in the cost errors dC_n, Eq. 2 moves the
+    weights by dw_n = w_n (sum_m w_m dC_m - dC_n) / lambda, and since
+    sum_n w_n (U_n - mu~) = 0 the common part cancels in Eq. 3:
+      d mu~ = -(1/lambda) sum_n w_n dC_n (U_n - mu~),
+    so |d mu~| <= (1/lambda) sum_n w_n e_n |U_n - mu~| (likewise for Sigma~
+    with D_n - Sigma~), scaled by the EMA step of Eq. 4.  Where this bound
+    exceeds 1e-5 the weights resolve cost differences finer than the FP32
+    costs carry: the costs are large against lambda (contact ramps, priority
+    weights of up to 1e6 on the coordination term) and several samples keep
+    weight, so no FP32 evaluation of the costs can hold the mean to 1e-5."""
+    c = orc.split(exp["costs"], "k", arm)
+    w = oracle_weights(c, lam)
+    e = 2.0 ** -22 * np.abs(c) + EPS_D / 4 * orc.split(exp["sens"], "k", arm)
+    U = orc.split(exp["U"], "U", arm)
+    mt = np.einsum("n,nhj->hj", w, U)
+    dev = U - mt[None]
+    b_mu = alpha_mu / lam * np.einsum("n,nhj->hj", w * e, np.abs(dev))
+    D = np.einsum("nhj,nhk->nhjk", dev, dev)
+    St = np.einsum("n,nhjk->hjk", w, D)
+    b_sig = alpha_sigma / lam * np.einsum("n,nhjk->hjk", w * e, np.abs(D - St[None]))
+    return float(b_mu.max()), float(b_sig.max())
+
+
 def plan_tolerance(sc, arm, tol_mu, floor=1e-5, mu_floor=1e-5):
     """Tolerance of the published plan's sphere positions [H]: 1e-5 m plus the
     part of the mean's tolerance above its floor carried through ToPlan.  The

@@ -38,7 +38,7 @@ def _replay(sc, cycles=2):
     for _ in range(cycles):
         d = _dump(sc)
         got, gc, ga, gs, exp = R.cycle(d)
-        _check_cycle(R, got, gc, ga, gs, exp, d)
+        _check_cycle(R, got, gc, ga, gs, exp, d, label="limits")
         R.advance(exp)
 
 
