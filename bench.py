@@ -1,16 +1,26 @@
 """Benchmark of the batched multi-arm MPPI control cycle on GB300.
 
 One "step" is one control cycle of every arm (Algorithm 1: sense, shift,
-sample, rollout, update, ToPlan/publish) on the four-arm workload (4 arms x 7
-DoF, 40 spheres each, K=512 samples, H=30 steps, 32 world spheres + 4 boxes,
-all plans shared, exact costs).  The metric is rollout trajectory-steps per
-second: sum_a K_a H_a x iterations / cycle time.
+sample, rollout, update, ToPlan/publish).  The default workload is the
+largest single-GPU one, workload 5: 8 arms x 7 DoF, 40 spheres each,
+K = 4096 samples, H = 64 steps, dt = 0.01 s, 256 moving world spheres,
+every arm costed against the other 7 arms' shared plans (2,097,152 rollout
+steps per cycle).  The metric is rollout trajectory-steps per second:
+sum_a K_a H_a x iterations / cycle time.
 
-  value : device-resident inputs, per-cycle CUDA-event time on the
-          library's stream, L2 flushed (256 MiB write) between timed cycles.
+  value : exact costs, device-resident inputs, per-cycle CUDA-event time on
+          the library's stream, L2 flushed (256 MiB write) before every
+          timed cycle.
   e2e   : the same cycles through mrs_step with host buffers (H2D of the
-          sensed state, D2H of the results inside the timed region), wall
-          clock per call, closed loop (the host plant integrates U_*).
+          sensed state and D2H of the results inside the timed region),
+          wall clock per call, closed loop (the host plant integrates U_*,
+          goals drift), 5 seeded scenes x 200 cycles, p50 / p99 latency.
+
+Also reported: the plain form (one context per arm, no graph), the learned
+form (self and arm-pair networks trained here on the device), the other
+workloads (2, 3 = 2 with the learned self network, 4, and 2 in the paper's M
+setting), the rollout kernel's roofline, and the FP64 oracle timed on a
+bounded sample of the same workload on the host cores.
 
 `--impl reference` times the FP64 CPU oracle on the host cores instead.
 With torchrun (N > 1) every rank runs an independent replica on its own GPU
@@ -21,10 +31,13 @@ rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -35,10 +48,38 @@ sys.path.insert(0, ROOT)
 METRIC = "rollout trajectory-steps/s and control-cycle p50/p99 latency, learned vs exact"
 UNIT = "trajectory-steps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_rollout
-# launch on workload 2, from one ncu capture of the kernel as it stands; set
-# back to None whenever the kernel changes, until it is captured again
-ROLLOUT_TRAFFIC_BYTES = 2204160
+CSRC = os.path.join(ROOT, "paper_2602_10114_gb300", "csrc")
+# the rollout kernel's sources: an ncu summary applies while their hash matches
+ROLLOUT_SOURCES = ["rollout_kernel.cuh", "rollout.cu", "rollout_mb2.cu", "mrs_device.cuh",
+                   "tc_gemm.cuh"]
+ROLLOUT_PROFILE = os.path.join(ROOT, "profiles", "k_rollout_8arms_K4096_H64.md")
+CPU_SAMPLE_K = 32        # samples per arm of the oracle's bounded sample
+
+
+def rollout_source_hash():
+    h = hashlib.sha256()
+    for f in ROLLOUT_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_figures(path=ROLLOUT_PROFILE):
+    """The `key: value` lines of the ncu summary's figures block, or None with
+    the reason when the file is missing or was taken from other sources."""
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None, "no ncu summary"
+    fig = {}
+    for ln in lines:
+        ln = ln.strip()
+        if ln.startswith("figure "):
+            k, _, v = ln[len("figure "):].partition(":")
+            fig[k.strip()] = v.strip()
+    if fig.get("source_sha256") != rollout_source_hash():
+        return None, "the rollout kernel changed since its ncu capture"
+    return fig, os.path.relpath(path, ROOT)
 
 
 def measured_peaks():
@@ -47,9 +88,11 @@ def measured_peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
         return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
                 "source": "measured"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "fallback"}
 
 
 def mlp_flops(rows, in_pad, width, layers):
@@ -58,23 +101,24 @@ def mlp_flops(rows, in_pad, width, layers):
     return 2.0 * rows * (in_pad * width + (layers - 1) * width * width + width)
 
 
-def workload(idx):
+def workload(idx, run=0):
     """Workload 1..5, or "M": workload 2 in the paper's M setting (5
     optimisation iterations per cycle, Sec. V-A) with the manipulability term
     on (w_manip = 10)."""
     from paper_2602_10114_gb300 import scenarios as S
     if str(idx) == "M":
-        sc = S.config(2, iterations=5, w_manip=10.0)
+        sc = S.config(2, run=run, iterations=5, w_manip=10.0)
         sc.name = "cfg2 in the M setting: 4 arms x 7 DoF, K=512, H=30, 5 iterations, C_manip"
         return sc
-    return S.config(int(idx))
+    return S.config(int(idx), run=run)
 
 
 def rollout_flops(sc):
     """Algorithmic FP32 work of one rollout launch, counted brute force as the
-    paper counts distance queries: 10 flops (+1 sqrt) per sphere pair (world,
-    self, every other arm's plan at the same step), plus 60 d + 18 N_S per
-    rollout step for the kinematics."""
+    paper counts distance queries (Sec. IV-A, N_Q): 10 flops (+1 sqrt) per
+    sphere pair (world, self on bodies at least three apart, every other
+    arm's plan at the same step), plus 60 d + 18 N_S per rollout step for the
+    kinematics."""
     total = 0.0
     n_obst = len(sc.world) + len(sc.aabb)
     for j, a in enumerate(sc.arms):
@@ -88,7 +132,20 @@ def rollout_flops(sc):
     return total * sc.params["iterations"]
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the
+    timed region runs (into a temporary file)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -96,12 +153,11 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                                 else "_build", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="mrs_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}",
                                           f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
@@ -131,6 +187,10 @@ class ClockSampler:
             for k, name in enumerate(names):
                 if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
                     reasons.add(name)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
@@ -167,29 +227,51 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def cpu_baseline(sc, budget_s=12.0, threads=None):
-    """The FP64 oracle, as it stands, on the host cores: full control cycles of
-    the same workload until `budget_s` of wall time is spent (>= 1 cycle)."""
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (a baseline, not the target)
+
+def oracle_sample(sc):
+    """The bounded sample of a workload the oracle is timed on: the same arms,
+    horizon, world and plans, CPU_SAMPLE_K samples per arm instead of K (a
+    rollout's cost does not depend on K; the update's share is small)."""
+    from paper_2602_10114_gb300 import scenarios as S
+    return S.shrink(sc, K=min(CPU_SAMPLE_K, min(a.K for a in sc.arms)))
+
+
+def time_oracle(sc, threads, budget_s, min_cycles=1):
+    """Closed-loop oracle cycles of `sc` until budget_s of wall time is spent;
+    returns (trajectory-steps/s, cycles, seconds)."""
     from oracle.oracle import Oracle
-    threads = threads or os.cpu_count()
     orc = Oracle(sc, threads=threads)
     gp, gR = zip(*[orc.goal_pose(a, sc.goal_q[a]) for a in range(sc.n_arms)])
     gp, gR = np.asarray(gp), np.asarray(gR)
-    cycles, t0 = 0, time.perf_counter()
-    times = []
-    while True:
+    orc.cycle(sc.q0, sc.qd0, gp, gR, want_costs=False)     # cycle 0: publishes the plans
+    cycles, el = 0, 0.0
+    while cycles < min_cycles or el < budget_s:
         t = time.perf_counter()
         orc.cycle(sc.q0, sc.qd0, gp, gR, want_costs=False)
-        times.append(time.perf_counter() - t)
+        el += time.perf_counter() - t
         cycles += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = sum(times)
-    return {"value": sc.rollout_steps() * sc.params["iterations"] * cycles / el, "unit": UNIT,
-            "cores": threads, "kind": "oracle",
-            "sample": f"{cycles} full control cycles of the workload (FP64 oracle, OpenMP over "
-                      f"samples, {threads} threads)",
-            "ms_per_cycle": 1e3 * el / cycles}
+    return sc.rollout_steps() * sc.params["iterations"] * cycles / el, cycles, el
+
+
+def cpu_baseline(sc, budget_s=12.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the workload (oracle_sample), all cores (OpenMP over samples) and one
+    thread."""
+    smp = oracle_sample(sc)
+    threads = os.cpu_count() or 1
+    v_all, n_all, t_all = time_oracle(smp, threads, budget_s * 0.4)
+    v_one, n_one, t_one = time_oracle(smp, 1, budget_s * 0.6)
+    what = (f"{smp.arms[0].K} of the {sc.arms[0].K} samples per arm of the workload's "
+            f"cycle (all {sc.n_arms} arms, H={sc.arms[0].H}, the same world and shared "
+            f"plans), FP64 oracle")
+    return {"value": v_all, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_all} cycles of {what}, OpenMP over samples, {threads} threads",
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": f"{n_one} cycles of the same sample, 1 thread",
+                              "seconds": t_one},
+            "cpu_model": cpu_model(), "seconds": t_all}
 
 
 def run_reference(args):
@@ -197,19 +279,23 @@ def run_reference(args):
     if rank != 0:
         return
     sc = workload(args.workload)
+    smp = oracle_sample(sc)
     from oracle.oracle import Oracle
-    threads = os.cpu_count()
-    orc = Oracle(sc, threads=threads)
-    gp, gR = zip(*[orc.goal_pose(a, sc.goal_q[a]) for a in range(sc.n_arms)])
+    threads = os.cpu_count() or 1
+    orc = Oracle(smp, threads=threads)
+    gp, gR = zip(*[orc.goal_pose(a, smp.goal_q[a]) for a in range(smp.n_arms)])
     gp, gR = np.asarray(gp), np.asarray(gR)
-    for _ in range(args.warmup):
-        orc.cycle(sc.q0, sc.qd0, gp, gR, want_costs=False)
+    for _ in range(max(args.warmup, 1)):
+        orc.cycle(smp.q0, smp.qd0, gp, gR, want_costs=False)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        orc.cycle(sc.q0, sc.qd0, gp, gR, want_costs=False)
+        orc.cycle(smp.q0, smp.qd0, gp, gR, want_costs=False)
     el = time.perf_counter() - t0
-    units = sc.rollout_steps() * sc.params["iterations"] * args.steps
+    units = smp.rollout_steps() * smp.params["iterations"] * args.steps
     value = units / el
+    sample = (f"each step one control cycle with {smp.arms[0].K} of the {sc.arms[0].K} samples "
+              f"per arm (all {sc.n_arms} arms, H={sc.arms[0].H}, same world and plans), FP64 "
+              f"oracle, {threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -217,13 +303,45 @@ def run_reference(args):
             "config": {"workload": sc.name + ", exact costs, 1 iteration", "arms": sc.n_arms,
                        "K": sc.arms[0].K, "H": sc.arms[0].H},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"each step one full control cycle of the workload "
-                                       f"(FP64 oracle, {threads} threads)"},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def time_device(ctl, d_in, steps, warmup, flush, ws, local=0, sample_clocks=False):
+# ---------------------------------------------------------------------------
+# GPU timing
+
+def make_controller(sc, dev, shape=None):
+    """A context with the world set, the goal poses, and the packed
+    device-resident input of the scene's start state."""
+    import torch
+    from paper_2602_10114_gb300 import mrs
+    ctl = mrs.Controller(sc, device=dev)
+    ctl.set_world()
+    gp, gR = [], []
+    for a in range(sc.n_arms):
+        p, R = ctl.goal_pose(a, sc.goal_q[a])
+        gp.append(p)
+        gR.append(R)
+    if shape is not None:
+        ctl.set_rollout_shape(shape["tile_samples"], shape["blocks_per_sm"], shape["order"])
+    d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
+    ctl.step_device(d_in)
+    ctl.sync()
+    return ctl, gp, gR, d_in
+
+
+def stage_names(sc):
+    return ["prep"] + ["sample", "surrogate", "rollout", "costs", "update"] * \
+        sc.params["iterations"] + ["toplan"]
+
+
+def launches_per_cycle(kt):
+    """Kernels of one cycle: the stages with a non-zero time."""
+    return int(np.sum(np.asarray(kt).mean(axis=0) > 0))
+
+
+def time_device(ctl, d_in, steps, warmup, flush, ws):
     """Per-cycle CUDA-event times (ms) of device-resident cycles, L2 flushed
     before each, with the cycle's graph as a user runs it (no timing nodes);
     then the per-stage times from a second run of the same cycles with event
@@ -256,15 +374,10 @@ def time_device(ctl, d_in, steps, warmup, flush, ws, local=0, sample_clocks=Fals
         barrier(ws)
         return [x.elapsed_time(y) for x, y in zip(starts, ends)], kt
 
-    clk = ClockSampler(local) if sample_clocks else None
-    if clk:
-        clk.__enter__()
     step_ms, _ = loop(steps, False)
     _, kt = loop(min(steps, 20), True)
-    if clk:
-        clk.__exit__()
     ctl.enable_timing(False)
-    return step_ms, np.asarray(kt), clk
+    return step_ms, np.asarray(kt)
 
 
 def time_e2e(ctls, sc, gp, gR, cycles, warmup, flush, ws, episode=50):
@@ -325,7 +438,67 @@ def time_e2e(ctls, sc, gp, gR, cycles, warmup, flush, ws, episode=50):
     return lat
 
 
-def plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, dev):
+def e2e_over_seeds(idx, runs, cycles, shape, args, flush, ws, dev, first=None):
+    """mrs_step latency over `runs` seeded scenes of workload idx, `cycles`
+    closed-loop cycles each (one episode per scene); `first` = an existing
+    (ctl, sc, gp, gR) for run 0."""
+    lat = []
+    for run in range(runs):
+        if run == 0 and first is not None:
+            ctl, sc, gp, gR = first
+            lat += time_e2e(ctl, sc, gp, gR, cycles, args.warmup, flush, ws, episode=cycles)
+            continue
+        sc = workload(idx, run)
+        ctl, gp, gR, _ = make_controller(sc, dev, shape)
+        lat += time_e2e(ctl, sc, gp, gR, cycles, args.warmup, flush, ws, episode=cycles)
+        ctl.close()
+    return lat
+
+
+def e2e_summary(lat, units, ws, ctl, runs, cycles):
+    e2e_s = max_over_ranks(float(np.mean(lat)), ws)
+    return {"value": units * ws / e2e_s, "unit": UNIT,
+            "h2d_bytes_per_step": int(4 * ctl.sizes.input_floats),
+            "d2h_bytes_per_step": int(4 * ctl.sizes.output_floats + 4),
+            "cycles": len(lat), "scenes": runs, "cycles_per_scene": cycles,
+            "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+            "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+
+
+def rollout_roofline(sc, kt):
+    """FP32 roofline of one k_rollout launch: algorithmic work (the paper's
+    brute-force pair count) over the live CUDA-event duration, against the
+    FP32 peak from unit counts; executed-work figures and DRAM traffic from
+    the committed ncu summary of the same kernel source (else null)."""
+    names = stage_names(sc)
+    roll_ms = float(np.mean([kt[:, i] for i, n in enumerate(names) if n == "rollout"]))
+    flops = rollout_flops(sc) / sc.params["iterations"]
+    achieved = flops / (roll_ms / 1e3) / 1e12
+    fig, src = profile_figures()
+    out = {"kernel": "k_rollout", "bound": "alu", "achieved": achieved,
+           "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+           "frac_brute_force": achieved / FP32_PEAK_TFLOPS,
+           "frac_note": "achieved counts every sphere pair brute force (Sec. IV-A's N_Q); the "
+                        "kernel's box culls skip most of them, so this fraction can exceed 1; "
+                        "'executed' gives the hardware's own use of the FP32 pipe and issue "
+                        "slots from ncu",
+           "traffic": None, "peak_source": "FP32 FMA peak from unit counts and the maximum SM "
+                                          "clock (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+           "flops_per_launch": flops, "launch_ms": roll_ms}
+    if fig is not None:
+        out["traffic"] = float(fig["dram_bytes_per_launch"])
+        out["executed"] = {k: float(fig[k]) for k in fig
+                           if k not in ("source_sha256", "dram_bytes_per_launch", "workload")}
+        out["executed"]["source"] = src
+    else:
+        out["executed"] = {"source": None, "why": src}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# forms of the cycle
+
+def plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, dev, e2e_cycles):
     """The same kernels in exact mode, one arm at a time: one context per arm
     (the other arms external, their plans shared), all on one stream, each
     cycle launched kernel by kernel without a CUDA graph."""
@@ -346,10 +519,11 @@ def plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, dev):
         for c in ctls:
             c.step_device(d_in)
     torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    steps = max(5, args.steps // 5)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     barrier(ws)
-    for i in range(args.steps):
+    for i in range(steps):
         with torch.cuda.stream(s):
             flush.zero_()
             starts[i].record(s)
@@ -361,20 +535,19 @@ def plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, dev):
     barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms = max_over_ranks(float(np.mean(step_ms)), ws)
-    lat = time_e2e(ctls, sc, gp, gR, args.latency_cycles, args.warmup, flush, ws)
+    lat = time_e2e(ctls, sc, gp, gR, e2e_cycles, args.warmup, flush, ws, episode=e2e_cycles)
     e2e_s = max_over_ranks(float(np.mean(lat)), ws)
     for c in ctls:
         c.close()
-    return {"value": units * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+    return {"value": units * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "device_p50": float(np.percentile(step_ms, 50)),
             "device_p99": float(np.percentile(step_ms, 99)),
             "e2e": {"value": units * ws / e2e_s, "cycles": len(lat),
                     "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
-                    "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))},
-            "gpu_launches_per_step": int(A * (1 + 4 * sc.params["iterations"]))}
+                    "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}}
 
 
-def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
+def learned_self_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     """The same cycle with the self-collision surrogate (trained here, on the
     device, by the library's kernels): throughput, latency, false negatives,
     skip fraction and cost deviation against exact mode."""
@@ -408,7 +581,7 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     ev = surrogate.evaluate(np.concatenate([r[0].ravel() for r in roll]),
                             np.concatenate([r[1].ravel() for r in roll]),
                             float(np.float32(sc.params["B_self"])), 0.03)
-    step_ms, kt, _ = time_device(ctl, d_in, args.steps, args.warmup, flush, ws)
+    step_ms, kt = time_device(ctl, d_in, args.steps, args.warmup, flush, ws)
     ms = max_over_ranks(float(np.mean(step_ms)), ws)
     lat = time_e2e(ctl, sc, gp, gR, args.latency_cycles, args.warmup, flush, ws)
     e2e_s = max_over_ranks(float(np.mean(lat)), ws)
@@ -421,7 +594,8 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     return {
         "value": units * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
         "speedup_vs_exact": exact_ms / ms,
-        "e2e": {"value": units * ws / e2e_s, "cycles": len(lat), "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+        "e2e": {"value": units * ws / e2e_s, "cycles": len(lat),
+                "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                 "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))},
         "surrogate_ms": sur_ms, "rollout_ms": float(kt[:, 3].mean()),
         "roofline": {"kernel": "k_mlp_fused", "bound": "tensor",
@@ -440,29 +614,15 @@ def learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, exact_ms):
     }
 
 
-def learned_pair_mode(args, flush, ws, dev):
-    """Workload 5 with both learned clearances: the self-collision network and
-    the arm-pair network (asymmetric loss, fallback margin calibrated on half
-    of the held-out pairs to a 7e-4 false-negative rate, so that the other
-    half stays within the 1e-3 target), trained on the device;
-    throughput against exact mode, false negatives on held-out samples and on
-    every rollout step of a cycle, skip fractions, cost deviation."""
-    import torch
-    from paper_2602_10114_gb300 import mrs, surrogate
-    sc = workload(5)
-    ctl = mrs.Controller(sc, device=dev)
-    ctl.set_world()
-    gp, gR = [], []
-    for a in range(sc.n_arms):
-        p, R = ctl.goal_pose(a, sc.goal_q[a])
-        gp.append(p)
-        gR.append(R)
-    d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
-    ctl.step_device(d_in)
-    ctl.sync()
-    best, _ = ctl.autotune(reps=3)
-    steps = max(5, args.steps // 5)
-    ex_ms, _, _ = time_device(ctl, d_in, steps, 3, flush, ws)
+def learned_pair_mode(ctl, sc, d_in, args, flush, ws, exact_ms):
+    """The headline workload with both learned clearances: the self-collision
+    network and the arm-pair network (asymmetric loss, fallback margin
+    calibrated on half of the held-out pairs to a 7e-4 false-negative rate,
+    so that the other half stays within the 1e-3 target), trained on the
+    device; throughput against exact mode, false negatives on held-out
+    samples and on every rollout step of a cycle, skip fractions, cost
+    deviation."""
+    from paper_2602_10114_gb300 import surrogate
     t0 = time.perf_counter()
     snet, sst = surrogate.train_self_surrogate(ctl, 0, n_train=args.surrogate_samples, n_val=200_000,
                                                epochs=8, lr=2e-3)
@@ -489,16 +649,19 @@ def learned_pair_mode(args, flush, ws, dev):
     ev_self = surrogate.evaluate(np.concatenate([r[0].ravel() for r in sr]),
                                  np.concatenate([r[1].ravel() for r in sr]),
                                  float(np.float32(sc.params["B_self"])), 0.03)
-    ln_ms, kt, _ = time_device(ctl, d_in, steps, 3, flush, ws)
-    ctl.close()
-    ex = max_over_ranks(float(np.mean(ex_ms)), ws)
+    steps = max(5, args.steps // 5)
+    ln_ms, kt = time_device(ctl, d_in, steps, 3, flush, ws)
     ln = max_over_ranks(float(np.mean(ln_ms)), ws)
+    for a in range(sc.n_arms):
+        ctl.set_self_surrogate(a, None)
+        ctl.set_pair_surrogate(a, -1, None)
+    ctl.load_state(blob)
     units = sc.rollout_steps() * sc.params["iterations"]
     dev_ = np.abs(c_learned - c_exact)
     keep = ("fn_rate", "fn_rate_active", "skip_fraction", "mae", "colliding", "samples")
     return {"workload": sc.name + ", learned self + arm-pair clearance",
             "value": units * ws / (ln / 1e3), "unit": UNIT, "ms_per_step": ln,
-            "exact_ms_per_step": ex, "speedup_vs_exact": ex / ln, "steps": steps,
+            "exact_ms_per_step": exact_ms, "speedup_vs_exact": exact_ms / ln, "steps": steps,
             "surrogate_ms": float(kt[:, 2].mean()), "rollout_ms": float(kt[:, 3].mean()),
             "pair_margin": pst["margin"],
             "held_out": {"self": {k: sst[k] for k in keep}, "pair": {k: pst[k] for k in keep}},
@@ -509,114 +672,103 @@ def learned_pair_mode(args, flush, ws, dev):
             "train": {"self_samples": args.surrogate_samples, "pair_samples": args.pair_samples,
                       "seconds": train_s,
                       "architecture": "self 14 -> 3 x 256 SiLU -> 1; pair 35 -> 4 x 256 SiLU "
-                                      "-> 1, BF16"},
-            "rollout_shape": best}
+                                      "-> 1, BF16"}}
 
 
 def other_workload(idx, args, flush, ws, dev):
     """Device-timed cycles of another workload (exact costs, autotuned shape):
-    throughput, cycle time, rollout time and its FP32 roofline fraction."""
-    import torch
-    from paper_2602_10114_gb300 import mrs
-    sc = workload(idx)
-    ctl = mrs.Controller(sc, device=dev)
-    ctl.set_world()
-    gp, gR = [], []
-    for a in range(sc.n_arms):
-        p, R = ctl.goal_pose(a, sc.goal_q[a])
-        gp.append(p)
-        gR.append(R)
-    d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
-    ctl.step_device(d_in)
-    ctl.sync()
+    throughput, cycle time, rollout time and its FP32 roofline fraction; for
+    workload 2 also its mrs_step latency over 20 scenes x 50 cycles; "3" is
+    workload 2 with the learned self network."""
+    learned = str(idx) == "3"
+    sc = workload(2 if learned else idx)
+    ctl, gp, gR, d_in = make_controller(sc, dev)
     best, table = ctl.autotune(reps=3)
-    steps = max(5, args.steps // 5)
-    step_ms, kt, _ = time_device(ctl, d_in, steps, 3, flush, ws)
+    steps = max(5, args.steps // 2)
+    step_ms, kt = time_device(ctl, d_in, steps, 3, flush, ws)
     ms = max_over_ranks(float(np.mean(step_ms)), ws)
+    units = sc.rollout_steps() * sc.params["iterations"]
     it = sc.params["iterations"]
     roll = float(np.mean([kt[:, 3 + 5 * i] for i in range(it)]))     # one rollout launch
     fl = rollout_flops(sc) / it
+    res = {"workload": sc.name, "value": units * ws / (ms / 1e3), "unit": UNIT,
+           "ms_per_step": ms, "steps": steps, "rollout_ms": roll,
+           "rollout_shape": best, "roofline_frac_brute_force": fl / (roll / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+           "flops_per_launch": fl}
+    if learned:
+        res = {"workload": sc.name + ", learned self-collision clearance (workload 3)",
+               "exact": res}
+        res.update(learned_self_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units, ms))
+    elif str(idx) == "2" and not args.no_e2e_others:
+        lat = e2e_over_seeds(2, 20, 50, best, args, flush, ws, dev, first=(ctl, sc, gp, gR))
+        res["e2e"] = e2e_summary(lat, units, ws, ctl, 20, 50)
     ctl.close()
-    units = sc.rollout_steps() * sc.params["iterations"]
-    return {"workload": sc.name, "value": units * ws / (ms / 1e3), "unit": UNIT,
-            "ms_per_step": ms, "steps": steps, "rollout_ms": roll,
-            "rollout_shape": best, "roofline_frac": fl / (roll / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-            "flops_per_launch": fl}
+    return res
 
 
 def run(args):
     import torch
 
-    from paper_2602_10114_gb300 import build, mrs
+    from paper_2602_10114_gb300 import build
 
     ws, rank, local = dist_setup()
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     build.build()
     sc = workload(args.workload)
-    ctl = mrs.Controller(sc, device=dev)
-    ctl.set_world()
-    gp, gR = [], []
-    for a in range(sc.n_arms):
-        p, R = ctl.goal_pose(a, sc.goal_q[a])
-        gp.append(p)
-        gR.append(R)
     units_per_step = sc.rollout_steps() * sc.params["iterations"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
-    ctl.step_device(d_in)
-    ctl.sync()
+    ctl, gp, gR, d_in = make_controller(sc, dev)
     tune = None
-    if not args.no_autotune:
-        best, table = ctl.autotune(reps=9)
-        tune = {"chosen": best, "tried": len(table),
-                "default_ms": next(t["cycle_ms"] for t in table
-                                   if (t["tile_samples"], t["order"]) == (32, 0)
-                                   and t["blocks_per_sm"] == max(x["blocks_per_sm"] for x in table))}
+    if args.rollout_shape:
+        t, b, o = (int(x) for x in args.rollout_shape.split(","))
+        ctl.set_rollout_shape(t, b, o)
+        tune = {"given": {"tile_samples": t, "blocks_per_sm": b, "order": o}}
+    elif not args.no_autotune:
+        best, table = ctl.autotune(reps=5)
+        tune = {"chosen": best, "tried": len(table)}
+    shape = dict(zip(("tile_samples", "blocks_per_sm", "order"), ctl.rollout_shape()[0]))
 
     # ---- device-resident cycles (exact costs) ------------------------------
     clk = ClockSampler(local)
     clk.__enter__()
-    step_ms, kt, _ = time_device(ctl, d_in, args.steps, args.warmup, flush, ws)
-    ms = float(np.mean(step_ms))
-    ms_max = max_over_ranks(ms, ws)
+    step_ms, kt = time_device(ctl, d_in, args.steps, args.warmup, flush, ws)
+    ms_max = max_over_ranks(float(np.mean(step_ms)), ws)
     value = units_per_step * ws / (ms_max / 1e3)
-    names = ["prep"] + ["sample", "surrogate", "rollout", "costs", "update"] * sc.params["iterations"] + ["toplan"]
-    k_mean = {n: float(kt[:, i].mean()) for i, n in enumerate(names[:kt.shape[1]]) if n != "surrogate"}
-    roll_ms = float(np.mean([kt[:, i] for i, n in enumerate(names) if n == "rollout"]))
-    flops = rollout_flops(sc) / sc.params["iterations"]
-    achieved = flops / (roll_ms / 1e3) / 1e12
+    names = stage_names(sc)
+    k_mean = {n: float(kt[:, i].mean()) for i, n in enumerate(names[:kt.shape[1]])
+              if n != "surrogate"}
+    roof = rollout_roofline(sc, kt)
 
     # ---- end to end through mrs_step with host buffers ---------------------
-    lat = time_e2e(ctl, sc, gp, gR, args.latency_cycles, args.warmup, flush, ws)
-    e2e_s = max_over_ranks(float(np.mean(lat)), ws)
-    e2e = {"value": units_per_step * ws / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(4 * ctl.sizes.input_floats),
-           "d2h_bytes_per_step": int(4 * ctl.sizes.output_floats + 4),
-           "cycles": len(lat), "episode": 50,
-           "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
-           "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+    runs = args.e2e_scenes
+    per = max(1, args.latency_cycles // runs)
+    lat = e2e_over_seeds(args.workload, runs, per, shape, args, flush, ws, dev,
+                         first=(ctl, sc, gp, gR))
+    e2e = e2e_summary(lat, units_per_step, ws, ctl, runs, per)
+    clk.__exit__()
+    clocks = clk.summary()
 
     plain = None
     if not args.no_plain:
-        plain = plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, dev)
+        plain = plain_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, dev,
+                           args.plain_cycles)
     learned = None
     if not args.no_learned:
-        learned = learned_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step, ms_max)
-
+        if len(sc.arms) > 1 and str(args.workload) == "5":
+            learned = learned_pair_mode(ctl, sc, d_in, args, flush, ws, ms_max)
+        else:
+            learned = learned_self_mode(ctl, sc, gp, gR, d_in, args, flush, ws, units_per_step,
+                                        ms_max)
+    ctl.close()
     others = {}
     for idx in args.other_workloads:
         others[f"cfg{idx}"] = other_workload(idx, args, flush, ws, dev)
-    learned_pair = None
-    if not args.no_learned and not args.no_learned_pair:
-        learned_pair = learned_pair_mode(args, flush, ws, dev)
-    clk.__exit__()
     if rank != 0:
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, budget_s=args.cpu_budget)
-        cpu.pop("ms_per_cycle", None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True,
@@ -624,27 +776,22 @@ def run(args):
         "config": {"workload": sc.name + ", exact costs, 1 iteration", "arms": sc.n_arms,
                    "K": sc.arms[0].K, "H": sc.arms[0].H, "dof": sc.arms[0].dof,
                    "spheres": sc.arms[0].n_spheres, "world_spheres": int(len(sc.world)),
-                   "boxes": int(len(sc.aabb)), "mode": "exact",
+                   "moving_world": sc.world_vel is not None, "boxes": int(len(sc.aabb)),
+                   "rollout_steps_per_cycle": units_per_step, "mode": "exact",
                    "l2": "flushed (256 MiB write) before every timed cycle",
                    "parallelism": f"replicas x{ws}", "graph": True,
                    "rollout_shape": tune},
         "latency_ms": {"device_p50": float(np.percentile(step_ms, 50)),
                        "device_p99": float(np.percentile(step_ms, 99))},
         "kernel_ms": k_mean,
-        "roofline": {"kernel": "k_rollout", "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ROLLOUT_TRAFFIC_BYTES,
-                     "peak_source": "FP32 FMA peak from unit counts and the maximum SM clock "
-                                    "(152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                     "flops_per_launch": flops},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "plain": plain,
         "learned": learned,
-        "learned_pair": learned_pair,
         "other_workloads": others,
-        "gpu_launches": int((1 + 4 * sc.params["iterations"]) * args.steps),
-        "clocks": clk.summary(),
+        "gpu_launches": launches_per_cycle(kt) * args.steps,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -655,23 +802,32 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2")
+    ap.add_argument("--workload", default="5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle time for the CPU baseline (both legs)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-surrogate comparison")
     ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
     ap.add_argument("--pair-samples", type=int, default=5_000_000)
-    ap.add_argument("--no-learned-pair", action="store_true",
-                    help="skip the eight-arm learned self + arm-pair leg")
-    ap.add_argument("--other-workloads", nargs="*", default=["4", "5", "M"],
-                    help="also time these workloads (device-resident, exact, autotuned)")
+    ap.add_argument("--other-workloads", nargs="*", default=["2", "3", "4", "M"],
+                    help="also time these workloads (device-resident, autotuned; 3 = workload "
+                         "2 with the learned self network)")
+    ap.add_argument("--no-e2e-others", action="store_true",
+                    help="skip the mrs_step latency of the other workloads")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rollout shape")
+    ap.add_argument("--rollout-shape", default="",
+                    help="tile_samples,blocks_per_sm,order: use this rollout shape instead of "
+                         "the autotuner's (e.g. to profile the shape a run chose)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-arm-at-a-time, graph-free comparison")
+    ap.add_argument("--plain-cycles", type=int, default=200,
+                    help="closed-loop cycles of the plain form's latency")
     ap.add_argument("--latency-cycles", type=int, default=1000,
                     help="closed-loop mrs_step calls for the latency percentiles")
+    ap.add_argument("--e2e-scenes", type=int, default=5,
+                    help="seeded scenes the latency cycles are spread over")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
