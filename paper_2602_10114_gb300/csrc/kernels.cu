@@ -17,6 +17,8 @@
 //              anticipated plan on the board (Sec. IV-A).
 #include <cstdio>
 
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace mrs {
@@ -909,20 +911,25 @@ __global__ void k_manip(Params P, Dev D, int total_kh)
     D.stage_lim[A.off_kh + (long long)h * K + n] += P.w_manip * c;
 }
 
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t configure_kernels(const LaunchPlan &L)
 {
     cudaError_t e;
     if ((e = configure_rollout(L)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(L.sample_tile == 16 ? k_sample<16> : k_sample<32>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_sample)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)L.smem_prep)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kUpdateSmem)) != cudaSuccess)
-        return e;
+    const void *sample = L.sample_tile == 16 ? (const void *)k_sample<16> : (const void *)k_sample<32>;
+    if ((e = raise_smem_limit(sample, L.smem_sample)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void *)k_prep, L.smem_prep)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void *)k_update, kUpdateSmem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

@@ -108,6 +108,12 @@ cudaError_t launch_k(void (*k)(KArgs...), int grid, int block, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
 }
 
+// A kernel's dynamic shared-memory limit belongs to the process (on the
+// current device), not to a context: contexts of different sizes launch the
+// same kernels with different amounts.  Raise the limit of `kernel` to at
+// least `bytes`, never lower it (serialised over threads).
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes);
+
 // The rollout kernel (rollout.cu): shared-memory size for the given
 // capacities, attribute set-up and launch.
 size_t rollout_smem_bytes(const Params &P, int n_arms);

@@ -307,8 +307,7 @@ static cudaError_t configure_fused(mrs_mlp *m, int *per_sm)
     if ((size_t)(max_ctas + 1) * (smem + reserve) <= sm_bytes)
         need = sm_bytes / (size_t)(max_ctas + 1) - reserve + 16;
     need = (need + 15) / 16 * 16;
-    cudaError_t e = cudaFuncSetAttribute(fused::k_mlp_fused<In>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    cudaError_t e = raise_smem_limit((const void *)fused::k_mlp_fused<In>, need);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fused::k_mlp_fused<In>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout,

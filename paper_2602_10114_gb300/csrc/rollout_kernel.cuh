@@ -869,8 +869,7 @@ template <int MB>
 int rollout_occupancy_t(size_t smem)
 {
     cudaFuncAttributes fa{};
-    if (cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
+    if (raise_smem_limit((const void *)k_rollout<MB>, smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
         cudaFuncGetAttributes(&fa, k_rollout<MB>) != cudaSuccess)
@@ -886,8 +885,7 @@ int rollout_occupancy_t(size_t smem)
 template <int MB>
 cudaError_t rollout_configure_t(size_t smem)
 {
-    return cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return raise_smem_limit((const void *)k_rollout<MB>, smem);
 }
 
 template <int MB>

@@ -85,3 +85,25 @@ def test_dropped_stale_and_corrupt_plans():
     r = c.step(q, qd, gp, gR)
     assert np.all(c.debug_alpha()[:3, 3] == 0)
     assert np.all(np.isfinite(r["mean_plan"]))
+
+
+def test_a_smaller_context_made_later_leaves_a_larger_one_runnable():
+    """The kernels' dynamic shared-memory limits are per process, not per
+    context: a context whose rollout stages 256 world spheres keeps running
+    after contexts with smaller staging (the initial 64-sphere capacity) are
+    created, and computes what it computed before them."""
+    from paper_2602_10114_gb300 import mrs
+    big = S.shrink(S.config(5), K=32, H=8)
+    q, qd, gp, gR = _inputs(big)
+    ctl = mrs.Controller(big)
+    ctl.set_world()                          # 256 spheres: the staging grows
+    blob = ctl.save_state()
+    ref = ctl.step(q, qd, gp, gR)
+    small = [mrs.Controller(S.shrink(S.config(2), K=32, H=8)) for _ in range(2)]
+    small.append(mrs.Controller(big, external=set(range(1, big.n_arms))))
+    ctl.load_state(blob)
+    got = ctl.step(q, qd, gp, gR)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    for c in small:
+        c.close()
