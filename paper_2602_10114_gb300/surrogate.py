@@ -53,8 +53,11 @@ def calibrate_margin(pred, exact, B, target_fn):
 
 def train_self_surrogate(ctl, arm, n_train=2_000_000, n_val=200_000, epochs=8, batch=4096,
                          lr=1e-3, width=256, layers=3, seed=0, margin=0.03, over_weight=1.0,
-                         log=None):
-    """Train a surrogate for `arm` of controller `ctl`; returns (net, stats)."""
+                         target_fn=None, log=None):
+    """Train a surrogate for `arm` of controller `ctl`; returns (net, stats)
+    with the held-out false-negative rate at `margin`, or, with target_fn,
+    at the margin calibrated on the first half of the held-out samples to
+    that rate and evaluated on the second half (stats["margin"])."""
     t0 = time.perf_counter()
     x, t, _ = ctl.self_dataset(arm, n_train + n_val, seed)
     xt, tt = x[:n_train], t[:n_train]
@@ -72,8 +75,15 @@ def train_self_surrogate(ctl, arm, n_train=2_000_000, n_val=200_000, epochs=8, b
             log(f"epoch {ep}: loss {np.mean(losses[-steps:]):.3e}")
     train_s = time.perf_counter() - t0
     pred = net.forward(xv).cpu().numpy()
-    stats = evaluate(pred, tv.cpu().numpy(), float(np.float32(ctl.sc.params["B_self"])), margin)
-    stats.update(train_seconds=train_s, final_loss=float(np.mean(losses[-steps:])),
+    tvn = tv.cpu().numpy()
+    B = float(np.float32(ctl.sc.params["B_self"]))
+    if target_fn is not None:
+        h = len(pred) // 2
+        margin = calibrate_margin(pred[:h], tvn[:h], B, target_fn)
+        stats = evaluate(pred[h:], tvn[h:], B, margin)
+    else:
+        stats = evaluate(pred, tvn, B, margin)
+    stats.update(margin=margin, train_seconds=train_s, final_loss=float(np.mean(losses[-steps:])),
                  n_train=n_train, epochs=epochs)
     return net, stats
 

@@ -119,11 +119,11 @@ def test_fallback_rule_extremes():
         assert np.all(np.abs(gc[a] - ce) <= cost_tol(ce))
 
 
-def test_trained_surrogate_false_negatives():
-    """Trained on-GPU with the library's kernels; on held-out samples and on
-    every rollout step of a cycle, collisions the surrogate would skip are
-    rare (spec target 1e-3 with the full 2M-sample training; this test
-    trains on 400k samples)."""
+def test_small_training_smoke_false_negatives():
+    """Smoke test of the training path on 400k samples: on held-out samples
+    and on every rollout step of a cycle, collisions the surrogate would skip
+    are rare (5e-3 at this size).  The 1e-3 target is asserted with the full
+    training in test_learned_gain_gpu."""
     from paper_2602_10114_gb300 import mrs, surrogate
     from parity_utils import goals
     from oracle.oracle import Oracle
@@ -258,12 +258,13 @@ def test_pair_fallback_rule_extremes():
         R2.advance(exp)
 
 
-def test_trained_pair_surrogate_false_negatives():
-    """Trained on the device over the layout's relative poses with the
-    asymmetric loss, the fallback margin calibrated on held-out samples to a
-    1e-3 false-negative rate: on the other held-out samples and on every
-    rollout step of a cycle, colliding arm pairs the surrogate would skip stay
-    rare (this test trains on 400k samples)."""
+def test_small_training_smoke_pair_false_negatives():
+    """Smoke test of the arm-pair training path on 400k samples (the layout's
+    relative poses, asymmetric loss, margin calibrated on held-out samples to
+    1e-3): on the other held-out samples and on every rollout step of a
+    cycle, colliding pairs the surrogate would skip stay rare (5e-3 at this
+    size).  The 1e-3 target is asserted with the full training in
+    test_learned_gain_gpu."""
     from paper_2602_10114_gb300 import mrs, surrogate
     from parity_utils import goals
     from oracle.oracle import Oracle
