@@ -937,8 +937,11 @@ double orc_mlp_loss_grad_w(int in_dim, int in_pad, int width, int layers, const 
 void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *qa,
                        const double *qb, double *out)
 {
-    double Sa[ORC_MAX_SPHERES * 4], Sb[ORC_MAX_SPHERES * 4];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
     for (int r = 0; r < n; ++r) {
+        double Sa[ORC_MAX_SPHERES * 4], Sb[ORC_MAX_SPHERES * 4];
         orc_fk(a, qa + (size_t)r * a->dof, NULL, Sa);
         orc_fk(b, qb + (size_t)r * b->dof, NULL, Sb);
         double m = INFINITY;
@@ -951,6 +954,27 @@ void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *
     }
 }
 
+/* The same clearance with arm a at the identity (its own base frame) and
+ * arm b at pose_b[r] (xyz, quaternion w x y z in a's base frame), one pose
+ * per row: the label of the arm-pair surrogate, whose relative poses are
+ * drawn per sample. */
+void orc_pair_distance_posed(const orc_arm *a, const orc_arm *b, int n, const double *qa,
+                             const double *qb, const double *pose_b, double *out)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
+    for (int r = 0; r < n; ++r) {
+        orc_arm A = *a, B = *b;
+        const double ident[7] = {0, 0, 0, 1, 0, 0, 0};
+        for (int k = 0; k < 7; ++k) {
+            A.base_pose[k] = ident[k];
+            B.base_pose[k] = pose_b[(size_t)r * 7 + k];
+        }
+        orc_pair_distance(&A, &B, 1, qa + (size_t)r * a->dof, qb + (size_t)r * b->dof, out + r);
+    }
+}
+
 /* Exact self-collision clearance of joint vectors q [n][dof]: the minimum
  * over the self-collision pairs (self_pair_used, with the rest-pose band
  * b_rest = B_self) of the centre distance minus both radii (the quantity the
@@ -958,9 +982,13 @@ void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *
  * training label of the learned surrogate. */
 void orc_self_distance(const orc_arm *arm, int n, const double *q, double b_rest, double *out)
 {
-    double S[ORC_MAX_SPHERES * 4], S_rest[ORC_MAX_SPHERES * 4];
+    double S_rest[ORC_MAX_SPHERES * 4];
     rest_spheres(arm, S_rest);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
     for (int r = 0; r < n; ++r) {
+        double S[ORC_MAX_SPHERES * 4];
         orc_fk(arm, q + (size_t)r * arm->dof, NULL, S);
         double m = INFINITY;
         for (int s1 = 0; s1 < arm->n_spheres; ++s1)

@@ -193,6 +193,10 @@ double orc_manip_cost(double w, double w0);
  * label; negative when the arms overlap. */
 void orc_pair_distance(const orc_arm *a, const orc_arm *b, int n, const double *qa,
                        const double *qb, double *out);
+/* orc_pair_distance with arm a at the identity and arm b at pose_b [n][7]
+ * (xyz, quaternion w x y z in a's base frame), one pose per row. */
+void orc_pair_distance_posed(const orc_arm *a, const orc_arm *b, int n, const double *qa,
+                             const double *qb, const double *pose_b, double *out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

@@ -131,6 +131,8 @@ def lib():
             L.orc_manip_cost.argtypes = [C.c_double, C.c_double]
             L.orc_pair_distance.argtypes = [C.POINTER(OrcArm), C.POINTER(OrcArm), C.c_int, _dp,
                                             _dp, _dp]
+            L.orc_pair_distance_posed.argtypes = [C.POINTER(OrcArm), C.POINTER(OrcArm), C.c_int,
+                                                  _dp, _dp, _dp, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -381,6 +383,18 @@ class Oracle:
         arm_a, arm_b = with_base(a, base_a), with_base(b, base_b)
         out = np.zeros(len(qa))
         lib().orc_pair_distance(C.byref(arm_a), C.byref(arm_b), len(qa), pqa, pqb, _ptr(out))
+        return out
+
+    def pair_distance_posed(self, a: int, b: int, qa, qb, pose_b):
+        """Clearance of arm a (at its own base frame) at joints qa [n][d_a] and
+        arm b at joints qb [n][d_b] placed at pose_b [n][7] in a's frame."""
+        qa, pqa = _d(np.asarray(qa, np.float64).reshape(-1, self.sc.arms[a].dof))
+        qb, pqb = _d(np.asarray(qb, np.float64).reshape(-1, self.sc.arms[b].dof))
+        po, ppo = _d(np.asarray(pose_b, np.float64).reshape(-1, 7))
+        assert len(qa) == len(qb) == len(po)
+        out = np.zeros(len(qa))
+        lib().orc_pair_distance_posed(C.byref(self.arms[a]), C.byref(self.arms[b]), len(qa), pqa,
+                                      pqb, ppo, _ptr(out))
         return out
 
     def jacobian(self, arm: int, q):

@@ -674,6 +674,33 @@ def _planar_tip_arm(a1, a2, r, base_xyz, yaw):
                                     np.float32))
 
 
+def test_pair_distance_with_per_row_poses_equals_the_fixed_pose_form(oracle_mod):
+    """The per-row-pose clearance (arm a at the identity, arm b at a pose per
+    row) equals the fixed-pose clearance of the planar closed-form pin when
+    every row carries b's pose in a's frame, and a rigid motion applied to
+    both arms (here: a at a yawed, shifted base) leaves it unchanged."""
+    from oracle.oracle import Oracle
+    A = _planar_tip_arm(0.5, 0.25, 0.05, (0.0, 0.0, 0.0), 0.0)
+    Bm = _planar_tip_arm(0.375, 0.5, 0.0625, (1.5, 0.25, 0.125), math.pi)
+    orc = Oracle(tiny_scenario([A, Bm]))
+    rng = np.random.default_rng(3)
+    qa, qb = rng.uniform(-2.8, 2.8, (40, 2)), rng.uniform(-2.8, 2.8, (40, 2))
+    ref = orc.pair_distance(0, 1, qa, qb)
+    pose = np.tile(Bm.base_pose.astype(np.float64), (40, 1))
+    got = orc.pair_distance_posed(0, 1, qa, qb, pose)
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
+    # the same relative placement with a moved: yaw 0.7 about z, shifted
+    yaw, t = 0.7, np.array([0.3, -0.2, 0.05])
+    Rz = Rotation.from_euler("z", yaw)
+    qa_w = Rotation.from_quat([0, 0, math.sin(yaw / 2), math.cos(yaw / 2)])
+    pb = Bm.base_pose.astype(np.float64)
+    rb = Rotation.from_quat([pb[4], pb[5], pb[6], pb[3]])
+    base_b = np.concatenate([Rz.apply(pb[:3]) + t, np.roll((qa_w * rb).as_quat(), 1)])
+    moved = orc.pair_distance(0, 1, qa, qb, base_b=base_b,
+                              base_a=[*t, math.cos(yaw / 2), 0, 0, math.sin(yaw / 2)])
+    assert np.allclose(moved, ref, rtol=0, atol=1e-12)
+
+
 def test_pair_distance_planar_closed_form(oracle_mod):
     """Two planar two-link arms facing each other: the clearance of their tip
     spheres is |tip_a - tip_b| - r_a - r_b with tip = base + R_yaw (a1 c1 +
