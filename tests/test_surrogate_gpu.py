@@ -285,3 +285,39 @@ def test_small_training_smoke_pair_false_negatives():
     ev = surrogate.evaluate(rh, ex, float(np.float32(0.03)), stats["margin"])
     print("rollout steps:", ev)
     assert ev["fn_rate"] <= 5e-3
+
+
+def test_training_labels_equal_the_oracle_over_the_full_datasets():
+    """The networks are trained on labels the library's exact kernels
+    compute on the device; over every sample of the datasets the benchmark
+    trains on (the same sizes, seeds and poses: workload 3's and 5's self
+    data, 2.2M and 2.4M joint vectors; each of workload 4's three DoF
+    classes, 2.4M; workload 5's arm-pair data, 5.4M pairs at jittered
+    relative poses), each label lies within EPS_D of the FP64 oracle's
+    clearance of the same joints, so training on them is training on the
+    oracle's labels to within the FP32 distance error."""
+    from oracle.oracle import Oracle
+    from paper_2602_10114_gb300 import mrs
+    from parity_utils import EPS_D
+    worst = {}
+    for idx, arms, n in ((3, (0,), 2_200_000), (5, (0,), 2_400_000), (4, (0, 1, 2), 2_400_000)):
+        sc = S.config(idx)
+        ctl = mrs.Controller(sc)
+        orc = Oracle(sc, threads=16)
+        for a in arms:
+            _, t, q = ctl.self_dataset(a, n, 0)
+            exp = orc.self_distance(a, q.cpu().numpy().astype(np.float64))
+            worst[f"self cfg{idx} arm {a}"] = float(np.abs(t.cpu().numpy() - exp).max())
+            del t, q
+        ctl.close()
+    sc = S.config(5)
+    ctl = mrs.Controller(sc)
+    orc = Oracle(sc, threads=16)
+    poses = np.stack([ctl.relative_pose(0, i) for i in range(1, sc.n_arms)])
+    x, t, qa, qb, po = ctl.pair_dataset(0, 1, 5_400_000, 0, poses, 0.02, 0.05)
+    del x
+    exp = orc.pair_distance_posed(0, 1, qa.cpu().numpy(), qb.cpu().numpy(), po.cpu().numpy())
+    worst["pair cfg5"] = float(np.abs(t.cpu().numpy() - exp).max())
+    print("largest label difference (m):", worst)
+    for k, v in worst.items():
+        assert v < EPS_D, k
