@@ -80,6 +80,14 @@ struct RolloutSmem {
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Capacity of a warp's candidate list: the largest single pass (the world
+// spheres, or one neighbour's plan slice), rounded up to 8.
+__host__ __device__ inline int rollout_cand_cap(const Params &P)
+{
+    const int m = P.world_cap > P.max_ns ? P.world_cap : P.max_ns;
+    return (m + 7) & ~7;
+}
+
 // packed binary32 pairs (Blackwell f32x2 FMA: two lanes, each rounded exactly
 // like the scalar instruction)
 typedef unsigned long long f32x2;
@@ -562,13 +570,16 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
     }
 }
 
-// Per-block shared state that changes with the sub-batch (own centres, the
+// Per-block shared state read after the barrier that ends a sub-batch (the
 // per-lane minima, the end-effector pose cost) is double-buffered by
 // sub-batch parity, and the neighbour weights by work-unit parity, so that
 // warp 0's per-sample cost of one sub-batch overlaps the other warps' next
 // sub-batch (or the staging of the next unit) without a barrier between
-// them: three block barriers per sub-batch of 32 samples (inputs staged,
-// own centres written, minima complete).  The next work unit's index is
+// them; the own centres are read only before that barrier and need one
+// buffer.  The joint sines and cosines are double-buffered as well: each
+// sub-batch computes the next one's behind its passes.  Two block barriers
+// per sub-batch of 32 samples (own centres written; minima complete), one
+// more per work unit (inputs staged).  The next work unit's index is
 // fetched one unit ahead.
 //
 // The kernel is built for two register budgets: MB resident blocks per SM
@@ -582,15 +593,14 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     extern __shared__ __align__(16) unsigned char smraw[];
     const int NA = P.n_arms;
     RolloutSmem S;
-    const int own_stride = P.max_ns * 32;
-    constexpr int kRedStride = (2 + MRS_MAX_ARMS) * 32;
+    const int red_stride = (2 + NA) * 32;
     {
         unsigned char *p = smraw;
         const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * NA;
         S.other = (float4 *)p;     p += align16(sizeof(float4) * n_other);
         S.aabb = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.aabb_cap);
         S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
-        S.own = (float4 *)p;       p += align16(sizeof(float4) * 2 * own_stride);
+        S.own = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns * 32);
         S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
         S.pa = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
         S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
@@ -604,20 +614,22 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
         S.marg = (float *)p;       p += align16(sizeof(float) * 2);
         S.nbbox = (float4 *)p;     p += align16(sizeof(float4) * 2 * NA);
-        S.sc = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof * 32);
+        S.sc = (float2 *)p;        p += align16(sizeof(float2) * 2 * kMaxDof * 32);
         S.dh = (float4 *)p;        p += align16(sizeof(float4) * kMaxDof);
         S.tw = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof);
         S.base = (float *)p;       p += align16(sizeof(float) * 12);
         S.goal = (float *)p;       p += align16(sizeof(float) * 12);
         S.cand = (unsigned short *)p;
-        S.cand_cap = (int)((n_other + 7) & ~size_t(7));
+        S.cand_cap = rollout_cand_cap(P);
         p += align16(sizeof(unsigned short) * kGroups * S.cand_cap);
         S.red = (int *)p;
     }
+    float2 *const sc_base = S.sc;   // [2][kMaxDof][32] by sub-batch parity
     __shared__ int s_tile[2];
     __shared__ float s_pose[2][32];
     __shared__ float s_lim[32];   // the sub-batch's joint-limit terms, copied ahead by warp 0
     __shared__ long long s_idx[32];   // and each sample's stage-cost offset
+    __shared__ float s_qn[kMaxDof * 32];   // the next sub-batch's joint angles, copied ahead
     __shared__ ArmHdr s_ah[2];    // the unit arm's scalars, by unit parity
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
@@ -625,7 +637,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
 
     // both minima buffers start at +inf; every sub-batch's cost stage resets
     // the entries it used, so they are +inf again when reused
-    for (int k = threadIdx.x; k < 2 * kRedStride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
+    for (int k = threadIdx.x; k < 2 * red_stride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
     __shared__ __align__(8) uint64_t s_bar;   // completion of the plan-slice copies
     uint32_t bar_phase = 0;
     if (threadIdx.x == 1) {
@@ -752,13 +764,14 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         {
             const int n = T.n0 + lane;
             const bool valid = n < A.K;
+            float2 *sc = sc_base + buf * (kMaxDof * 32);
             // joint j on warp (j + 1) mod 8: warp 0, still in the previous
             // unit's cost stage, takes a joint only for 8 or more
             for (int j = (g + kGroups - 1) % kGroups; j < A.dof; j += kGroups) {
                 float sn, cs;
                 const float qj = D.traj[A.off_khd + ((long long)h * A.dof + j) * A.K + (valid ? n : 0)];
                 sincosf(__fadd_rn(qj, A.dh[j].w), &sn, &cs);
-                S.sc[j * 32 + lane] = make_float2(sn, cs);
+                sc[j * 32 + lane] = make_float2(sn, cs);
             }
         }
         if (n_plan > 0) {
@@ -798,8 +811,8 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
 
         for (int sb = 0; sb < T.nsub; ++sb, buf ^= 1) {
             RolloutSmem Sb = S;
-            Sb.own = S.own + buf * own_stride;
-            Sb.red = S.red + buf * kRedStride;
+            Sb.red = S.red + buf * red_stride;
+            Sb.sc = sc_base + buf * (kMaxDof * 32);
             const int n = T.n0 + sb * 32 + lane;
             const bool valid = n < AH.K;
             // warp 0 uses the sub-batch's stop / joint-limit terms in its cost
@@ -809,18 +822,19 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 cp_async4(&s_lim[lane], D.stage_lim + idx);
                 s_idx[lane] = idx;
             }
-            // sine and cosine of every joint angle of the sub-batch, once
-            // (warp j takes joint j): the sphere groups' kinematic chains
-            // share them (the first sub-batch's came with the staging)
-            if (sb > 0) {
-                for (int j = (g + kGroups - 1) % kGroups; j < AH.dof; j += kGroups) {
-                    float sn, cs;
-                    const float qj =
-                        D.traj[AH.off_khd + ((long long)h * AH.dof + j) * AH.K + (valid ? n : 0)];
-                    sincosf(__fadd_rn(qj, S.dh[j].w), &sn, &cs);
-                    S.sc[j * 32 + lane] = make_float2(sn, cs);
-                }
-                __syncthreads();
+            // the next sub-batch's joint angles (warp j takes joint j), loaded
+            // now and turned into sines and cosines after this sub-batch's
+            // passes, into the other parity's buffer: the barrier that ends
+            // this sub-batch publishes them (the first sub-batch's came with
+            // the staging)
+            const bool next = sb + 1 < T.nsub;
+            if (next) {
+                const int n_next = n + 32;
+                const bool valid_next = n_next < AH.K;
+                for (int j = (g + kGroups - 1) % kGroups; j < AH.dof; j += kGroups)
+                    cp_async4(&s_qn[j * 32 + lane],
+                              D.traj + AH.off_khd + ((long long)h * AH.dof + j) * AH.K +
+                                  (valid_next ? n_next : 0));
             }
             float pose = 0.f;
             switch (AH.spg) {
@@ -834,7 +848,16 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 default: rollout_group<8>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
             }
             if (g == kGroups - 1) s_pose[buf][lane] = pose;
-            __syncthreads();   // every warp's minima and the pose cost are in
+            if (next) {
+                float2 *sc = sc_base + (buf ^ 1) * (kMaxDof * 32);
+                cp_async_wait_all();
+                for (int j = (g + kGroups - 1) % kGroups; j < AH.dof; j += kGroups) {
+                    float sn, cs;
+                    sincosf(__fadd_rn(s_qn[j * 32 + lane], S.dh[j].w), &sn, &cs);
+                    sc[j * 32 + lane] = make_float2(sn, cs);
+                }
+            }
+            __syncthreads();   // every warp's minima, the pose cost and the next sines are in
 
             // stage cost of Eq. 5 plus the prioritised coordination term (Eq. 9)
             if (g == 0) {

@@ -1,5 +1,6 @@
 """The largest sizes include/mrs.h allows, each on its own, against the
-oracle, and a combination whose shared-memory staging cannot fit one block."""
+oracle; 32 arms of 64 spheres together; and a combination whose
+shared-memory staging cannot fit one block."""
 import math
 
 import numpy as np
@@ -74,16 +75,22 @@ def test_most_samples():
 
 
 def test_staging_beyond_one_block_is_unsupported():
-    """32 arms of 64 spheres with a full world cannot stage a step's plans in
-    one block's shared memory: mrs_create refuses with MRS_EUNSUPPORTED and
-    says why."""
+    """32 arms of 64 spheres stage a step's plans (31 x 64 spheres) in one
+    block's shared memory and run a replayed cycle; with a full world of 1024
+    spheres on top the staging no longer fits: mrs_set_world refuses with
+    MRS_EUNSUPPORTED, says why, and the context keeps its previous world."""
     from paper_2602_10114_gb300 import mrs
     rng = np.random.default_rng(3)
     geo = S.random_geometry(rng, 9, per_link=7, tool_spheres=1)
     arms = [S._make_arm(geo, 9, 32, 4, (2.0 * math.cos(2 * math.pi * a / 32),
                                         2.0 * math.sin(2 * math.pi * a / 32), 0.0), 0.0)
             for a in range(32)]
-    sc = _scenario(arms, np.zeros((0, 4)), np.zeros((0, 6)))
+    world = np.concatenate([rng.uniform([-2.5, -2.5, 0.0], [2.5, 2.5, 1.5], (1024, 3)),
+                            rng.uniform(0.02, 0.05, (1024, 1))], axis=1)
+    sc = _scenario(arms, world[:16], np.zeros((0, 6)))
+    _replay(sc, cycles=2)              # the second cycle stages 31 published plans
+    ctl = mrs.Controller(sc)
+    ctl.set_world()
     with pytest.raises(mrs.MrsError) as e:
-        mrs.Controller(sc)
+        ctl.set_world(world.astype(np.float32), None, np.zeros((0, 6), np.float32))
     assert e.value.status == 6 and "shared memory" in str(e.value)

@@ -98,8 +98,12 @@ def _check_cycle(R, got, gc, ga, gs, exp, dump, label=""):
     if dump is not None:
         for i, (a, n, h) in enumerate(dump):
             ns = sc.arms[a].n_spheres
-            e = np.abs(gs[i, :ns] - exp["dump_spheres"][i, :ns]).max()
-            assert e < SPHERE_TOL and e < EPS_D / 4
+            ref = exp["dump_spheres"][i, :ns]
+            e = np.abs(gs[i, :ns] - ref).max()
+            # the FP32 error model (EPS_D / 4 for coordinates within a metre)
+            # scales with the coordinates' magnitude, as rounding does
+            scale = max(1.0, float(np.abs(ref[:, :3]).max()))
+            assert e < SPHERE_TOL and e < EPS_D / 4 * scale
 
 
 def _dump(sc):
