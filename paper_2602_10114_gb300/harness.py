@@ -11,7 +11,11 @@ period (the integrator of the rollout), and reports the paper's scores
     and arms, the goals drifting at constant velocity and reset to their
     start when they leave the arm's reach;
   * reaching task: the goals reached (end-effector within 5 cm), each arm then
-    getting the next goal of its seeded list.
+    getting the next goal of its seeded list; "reaching_central" draws every
+    goal position near the centre the arms share (the paper's hard level,
+    goals sampled centrally to maximise interaction), uniform in a ball of
+    0.2 m radius at 0.4 m height, the orientation kept as the end
+    effector's at the time the goal is set; a goal also resets after 1 s.
 
 Variants (Sec. V-A): M (5 iterations per cycle), M_fast (1 iteration),
 M_tau (tau = 0: plans shared, no priority), S_d (independent controllers that
@@ -71,6 +75,125 @@ def contacts(spheres, world, aabb):
     return arm, wc
 
 
+def planar_arm(links, per_link, radius, base_xyz, yaw, K, H):
+    """A planar arm (alpha = d = 0: every joint axis vertical) of the given
+    link lengths, `per_link` spheres of `radius` evenly spaced on each link
+    segment (the frame-(i-1) origin end excluded), base at base_xyz turned by
+    yaw about z."""
+    dof = len(links)
+    dh = np.zeros((dof, 4))
+    dh[:, 0] = links
+    bodies, xyzr = [], []
+    for i, a in enumerate(links):
+        for k in range(per_link):
+            t = (k + 1) / per_link                 # from the joint to the link's end
+            bodies.append(i + 1)
+            xyzr.append([-(1.0 - t) * a, 0.0, 0.0, radius])
+    return S.Arm(dof=dof, n_spheres=len(bodies), K=K, H=H, dh=dh.astype(np.float32),
+                 q_lo=np.full(dof, -2.8, np.float32), q_hi=np.full(dof, 2.8, np.float32),
+                 qd_max=np.full(dof, 2.0, np.float32), sphere_body=np.asarray(bodies, np.int32),
+                 sphere_xyzr=np.asarray(xyzr, np.float32),
+                 base_pose=np.asarray([*base_xyz, *S.yaw_quat(yaw)], np.float32))
+
+
+_LINKS = (0.35, 0.35, 0.2)
+
+
+def _reach_to(x_local, links=_LINKS):
+    """Joints of a planar 3-link arm whose end effector lies on its base's x
+    axis at x_local: shoulder turned so that the elbow, folded, brings the
+    straight forearm and hand back onto the axis (wrist at zero)."""
+    f = links[1] + links[2]
+    c = np.clip((x_local ** 2 - links[0] ** 2 - f ** 2) / (2 * links[0] * f), -1, 1)
+    q2 = np.arccos(c)
+    q1 = -np.arctan2(f * np.sin(q2), links[0] + f * np.cos(q2))
+    return np.array([q1, q2, 0.0], np.float32)
+
+
+def livelock_scenario(tau, offset=0.05, lead=0.0, K=256, H=30, dt=0.02, **params):
+    """The conflict of Sec. IV-B (Fig. 1): two planar 3-link arms on opposite
+    sides of a shared workspace, 1.5 m apart and facing each other, each
+    reaching for a goal just past the middle (+-offset from it on its own
+    side's far edge), so that both end effectors cannot be at their goals at
+    once.  Both start stretched out towards the middle, arm 0 `lead` metres
+    closer to its goal; no world obstacles.  tau is the priority exponent."""
+    links = list(_LINKS)
+    arms = [planar_arm(links, 4, 0.04, (-0.75, 0.0, 0.3), 0.0, K, H),
+            planar_arm(links, 4, 0.04, (0.75, 0.0, 0.3), np.pi, K, H)]
+    p = dict(S.DEFAULT_PARAMS)
+    p.update(dt=dt, tau=tau, seed=7)
+    p.update(params)
+    reach = sum(links)
+    # goal joints: the end effector `offset` past the middle; the start:
+    # folded back at the elbow, arm 0 `lead` further out than arm 1
+    goal_q = [_reach_to(0.75 + offset), _reach_to(0.75 + offset)]
+    start_x = 0.75 + offset - 0.35
+    q0 = [_reach_to(start_x + lead), _reach_to(start_x)]
+    qd0 = [np.zeros(3, np.float32), np.zeros(3, np.float32)]
+    assert reach > 0.75 + offset
+    return S.Scenario("livelock: two planar arms reaching past the middle", arms, p,
+                      np.zeros((0, 4), np.float32), None, np.zeros((0, 6), np.float32),
+                      q0, qd0, goal_q, np.zeros((2, 3), np.float32), cycles=300)
+
+
+def priority_decision(tau, gaps=(0.02, 0.09), w_pose=1000.0, seed=0, cycles=6, K=1024,
+                      device="cuda"):
+    """The decision of Fig. 1 (C-D): both arms of livelock_scenario stretched
+    towards one shared goal point (offset 0), arm 0 gaps[0] and arm 1
+    gaps[1] from it, their anticipated plans overlapping.  `cycles` control
+    cycles at that fixed state (the board carries each cycle's plans to the
+    next); returns, per arm, the distance to the goal now and at the end of
+    its last published plan (the plan's end effector).  Without priority
+    (tau = 0) the arm nearer its goal does not advance either; with it, the
+    nearer arm plans to advance and the other to retreat."""
+    sc = livelock_scenario(tau, offset=0.0, lead=0.0, K=K, w_pose=w_pose, seed=seed)
+    sc.q0 = [_reach_to(0.75 - gaps[0]), _reach_to(0.75 - gaps[1])]
+    ctl = mrs.Controller(sc, device=device)
+    ctl.set_world()
+    goals = [ctl.goal_pose(a, sc.goal_q[a]) for a in range(2)]
+    gp = [g[0] for g in goals]
+    gR = [g[1] for g in goals]
+    for _ in range(cycles):
+        out = ctl.step(sc.q0, sc.qd0, gp, gR)
+    now, end = [], []
+    for a in range(2):
+        pq = ctl.split(out["plan_q"], "hd", a)
+        now.append(float(out["dist_to_goal"][a]))
+        end.append(float(np.linalg.norm(ctl.fk(a, pq[-1])[0][0, 9:12] - gp[a])))
+    ctl.close()
+    return now, end
+
+
+def livelock_episode(sc, cycles=300, device="cuda"):
+    """Closed loop of the two-arm conflict on the kinematic plant: the
+    distance of each end effector to its goal after every cycle [cycles][2],
+    and the cycles with the two arms in contact."""
+    ctl = mrs.Controller(sc, device=device)
+    ctl.set_world()
+    dt = np.float32(sc.params["dt"])
+    q = [np.asarray(x, np.float32).copy() for x in sc.q0]
+    qd = [np.asarray(x, np.float32).copy() for x in sc.qd0]
+    goals = [ctl.goal_pose(a, sc.goal_q[a]) for a in range(2)]
+    gp = [g[0] for g in goals]
+    gR = [g[1] for g in goals]
+    dist = np.zeros((cycles, 2))
+    contact = 0
+    for t in range(cycles):
+        out = ctl.step(q, qd, gp, gR)
+        for a in range(2):
+            u = ctl.split(out["u_star"], "d", a)
+            qd[a] = (qd[a] + u * dt).astype(np.float32)
+            q[a] = (q[a] + qd[a] * dt).astype(np.float32)
+        sph = []
+        for a in range(2):
+            e, sp = ctl.fk(a, q[a])
+            dist[t, a] = float(np.linalg.norm(e[0, 9:12] - gp[a]))
+            sph.append(sp[0].astype(np.float64))
+        contact += contacts(sph, np.zeros((0, 4)), np.zeros((0, 6)))[0]
+    ctl.close()
+    return dist, contact
+
+
 def run_episode(sc, variant, cycles=500, task="following", device="cuda", reach_tol=0.05,
                 goal_seed=0):
     """One episode of `variant` on scenario `sc`; returns the scores."""
@@ -98,6 +221,17 @@ def run_episode(sc, variant, cycles=500, task="following", device="cuda", reach_
     start = [ref.goal_pose(a, s.goal_q[a]) for a in range(A)]
     gp = [p.copy() for p, _ in start]
     gR = [R.copy() for _, R in start]
+    centre = np.mean(base, axis=0) + np.array([0.0, 0.0, 0.4])
+
+    def central_goal(a):
+        v = rng.normal(size=3)
+        v *= 0.2 * rng.uniform() ** (1 / 3) / np.linalg.norm(v)
+        e, _ = ref.fk(a, q[a])
+        return (centre + v).astype(np.float32), e[0, :9].reshape(3, 3).astype(np.float32)
+    set_at = [0] * A
+    if task == "reaching_central":
+        for a in range(A):
+            gp[a], gR[a] = central_goal(a)
     goals_reached = 0
     err = 0.0
     coll_steps = arm_steps = world_steps = 0
@@ -134,7 +268,13 @@ def run_episode(sc, variant, cycles=500, task="following", device="cuda", reach_
         for a in range(A):
             dist = float(np.linalg.norm(ee[a] - gp[a]))
             err += dist
-            if task == "reaching" and dist < reach_tol:
+            if task == "reaching_central":
+                if dist < reach_tol:
+                    goals_reached += 1
+                if dist < reach_tol or (t + 1 - set_at[a]) * float(dt) >= 1.0:
+                    gp[a], gR[a] = central_goal(a)
+                    set_at[a] = t + 1
+            elif task == "reaching" and dist < reach_tol:
                 goals_reached += 1
                 qg = rng.uniform(s.arms[a].q_lo, s.arms[a].q_hi).astype(np.float32)
                 gp[a], gR[a] = ref.goal_pose(a, qg)
@@ -154,7 +294,8 @@ def main():
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--cycles", type=int, default=500)
     ap.add_argument("--runs", type=int, default=3, help="seeded scenarios per variant")
-    ap.add_argument("--task", default="following", choices=["following", "reaching"])
+    ap.add_argument("--task", default="following",
+                    choices=["following", "reaching", "reaching_central"])
     ap.add_argument("--variants", nargs="*", default=list(VARIANTS))
     ap.add_argument("--n-world", type=int, default=None,
                     help="keep only this many world spheres and no boxes (difficulty level)")
