@@ -440,10 +440,11 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             box[3] = hi.x; box[4] = hi.y; box[5] = hi.z;
         }
     }
-    // every group's centres and sphere boxes are in shared memory; the
-    // obstacle passes below need only the warp's own spheres, so they share
-    // the phase up to the next barrier with the self pass
-    __syncthreads();
+    // the obstacle passes below need only the warp's own spheres and box:
+    // they run before the barrier that publishes every group's centres to
+    // the self pass, so a warp with a short kinematic chain spends the wait
+    // for the longest one on its passes
+    __syncwarp();
     if (cnt > 0) {
 
         // world boxes (exact), then one pre-tested pass per sphere set over its
@@ -523,6 +524,9 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
         }
     }
+
+    // every group's centres and sphere boxes are in shared memory
+    __syncthreads();
 
     // self collision: the arm's pair list, split evenly over the 8 warps.  With
     // a learned surrogate, a rollout step whose predicted clearance is at least
