@@ -339,19 +339,25 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
  *                  h + 1: concurrent blocks share the step's plans), 1
  *                  arm-major, 2 step-major from the last step (the later
  *                  steps' wider spread of samples tends to cost more: the
- *                  costlier units first leave a shorter tail).
+ *                  costlier units first leave a shorter tail);
+ *   exact_max      0 .. 64: a clearance pass left with at most this many
+ *                  candidate spheres after the box culls tests every pair
+ *                  exactly; with more it pre-tests them first (the default,
+ *                  2, suits dense candidate sets; sparse ones, as when arms
+ *                  meet only at a few spheres, run faster with more).
  * Results do not depend on the shape (each sample's cost is reduced by its
  * own lane in every shape); only the time does.  mrs_set_rollout_shape
  * returns MRS_EINVAL for a shape out of range. */
 typedef struct {
-    int tile_samples, blocks_per_sm, order;
+    int tile_samples, blocks_per_sm, order, exact_max;
     float cycle_ms;            /* mrs_autotune: median control-cycle time of the shape */
 } mrs_rollout_shape;
 mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
 
 /* Autotuner: times every shape of the grid {32, 64, 96, 128, 192, 256}
- * samples x 1 .. max resident blocks per SM x orders {0, 1, 2} over
+ * samples x 1 .. max resident blocks per SM x orders {0, 1, 2} x exact_max
+ * {2, 8, 32} over
  * `reps` whole control cycles each (the cycle as mrs_step_device runs it:
  * CUDA graph without per-stage timing, so programmatic launch overlaps the
  * stages; CUDA events around each cycle on the context's stream, median) on

@@ -455,6 +455,7 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     P.w_manip = cfg->w_manip;
     P.manip_w0 = cfg->manip_w0;
     P.wait_polls = tc::kWaitLimit;
+    P.exact_max = 2;
 
     size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
     long long khd = 0, kh = 0;
@@ -1559,13 +1560,15 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
 // ---------------------------------------------------------------------------
 // rollout launch shape and its autotuner
 
-static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm, int order)
+static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm, int order,
+                              int exact_max)
 {
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
     ctx->tile_samples = tile_samples;
     ctx->blocks_per_sm = blocks_per_sm;
     ctx->tile_order = order;
+    ctx->P.exact_max = exact_max;
     build_rollout_tiles(ctx);
     LaunchPlan &L = ctx->L;
     L.n_rollout_tiles = (int)ctx->rollout_tiles.size();
@@ -1585,9 +1588,10 @@ mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
     if (!ctx || !shape) return MRS_EINVAL;
     if (shape->tile_samples < 32 || shape->tile_samples > 256 || shape->tile_samples % 32 ||
         shape->blocks_per_sm < 0 || shape->blocks_per_sm > ctx->max_blocks_per_sm ||
-        shape->order < 0 || shape->order > 2)
+        shape->order < 0 || shape->order > 2 || shape->exact_max < 0 || shape->exact_max > 64)
         return fail(ctx, MRS_EINVAL, "rollout shape out of range");
-    return apply_shape(ctx, shape->tile_samples, shape->blocks_per_sm, shape->order);
+    return apply_shape(ctx, shape->tile_samples, shape->blocks_per_sm, shape->order,
+                       shape->exact_max);
 }
 
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm)
@@ -1598,6 +1602,7 @@ mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *ma
         shape->tile_samples = ctx->tile_samples;
         shape->blocks_per_sm = ctx->blocks_per_sm;
         shape->order = ctx->tile_order;
+        shape->exact_max = ctx->P.exact_max;
         shape->cycle_ms = 0.f;
     }
     if (max_blocks_per_sm) *max_blocks_per_sm = ctx->max_blocks_per_sm;
@@ -1641,13 +1646,16 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
         }
     }
     std::vector<mrs_rollout_shape> tried;
-    const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
+    const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order,
+                                   ctx->P.exact_max, 0.f};
     mrs_rollout_shape keep = before;
     float best_ms = INFINITY;
     for (int ts : {32, 64, 96, 128, 192, 256}) {
         for (int bps = 1; bps <= ctx->max_blocks_per_sm && st == MRS_OK; ++bps) {
-            for (int order = 0; order < 3 && st == MRS_OK; ++order) {
-                if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) break;
+            for (int combo = 0; combo < 9 && st == MRS_OK; ++combo) {
+                static const int kExactMax[3] = {2, 8, 32};
+                const int order = combo % 3, exact_max = kExactMax[combo / 3];
+                if ((st = apply_shape(ctx, ts, bps, order, exact_max)) != MRS_OK) break;
                 // every shape's trials start from the same state (and draw the same
                 // samples): the controller's state drifts over the trials, and with
                 // it the work of a cycle
@@ -1671,7 +1679,7 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
                 if (st != MRS_OK) break;
                 std::sort(t.begin(), t.end());
                 const float med = t[t.size() / 2];
-                tried.push_back(mrs_rollout_shape{ts, bps, order, med});
+                tried.push_back(mrs_rollout_shape{ts, bps, order, exact_max, med});
                 if (med < best_ms) {
                     best_ms = med;
                     keep = tried.back();
@@ -1686,13 +1694,15 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
         // put back the shape, the timing switch and the state as far as the
         // device still allows; the trial's error is the one reported
         const std::string why = ctx->err;
-        apply_shape(ctx, before.tile_samples, before.blocks_per_sm, before.order);
+        apply_shape(ctx, before.tile_samples, before.blocks_per_sm, before.order, before.exact_max);
         mrs_enable_timing(ctx, timing ? 1 : 0);
         mrs_load_state(ctx, blob.data(), blob.size());
         ctx->err = why;
         return st;
     }
-    if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order)) != MRS_OK) return st;
+    if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order, keep.exact_max)) !=
+        MRS_OK)
+        return st;
     if ((st = mrs_enable_timing(ctx, timing ? 1 : 0)) != MRS_OK) return st;
     if ((st = mrs_load_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;
     if (n_tried) *n_tried = (int)tried.size();

@@ -55,6 +55,8 @@ struct Params {
     int max_plan_age;             // board entries older than this are ignored (0: no limit)
     float w_manip, manip_w0;      // C_manip weight (0: off) and manipulability threshold
     unsigned wait_polls;          // polls of the rollout's bounded wait for its plan copies
+    int exact_max;                // a clearance pass with at most this many candidates
+                                  // tests every pair exactly (no pre-test)
 };
 
 // A neighbour's board entry is used when it is published and, with a

@@ -338,25 +338,26 @@ __device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 
                        -0.5f * ((s & 1) ? z1 : z0));
 }
 
-// The same minimum for one or two candidates: their exact distances to every
-// own sphere, the square root only inside the ramp (the pre-test and the
-// flags of clearance_pass cost more than the exact tests for so few).
+// The same minimum for a few candidates: their exact distances to every own
+// sphere, the square root only inside the ramp (for few candidates the
+// pre-test and the flags of clearance_pass cost more than the exact tests;
+// how few is the launch shape's exact_max).
 template <int NP>
 __device__ __forceinline__ float few_candidates(const RolloutSmem &S, const unsigned short *list,
                                                 int nc, float B, int s0, int cnt,
                                                 const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
                                                 const f32x2 (&MZ)[NP])
 {
-    const float4 p0 = S.other[list[0]], p1 = S.other[list[nc > 1 ? 1 : 0]];
     float m = kInf;
+    for (int j = 0; j < nc; ++j) {
+        const float4 p = S.other[list[j]];
 #pragma unroll
-    for (int s = 0; s < 2 * NP; ++s)
-        if (s < cnt) {
-            const float r = S.sph[s0 + s].w, rB = __fadd_rn(r, B);
-            const float3 c = own_centre<NP>(MX, MY, MZ, s);
-            pair_exact(c, rB, r, p0, m);
-            if (nc > 1) pair_exact(c, rB, r, p1, m);
-        }
+        for (int s = 0; s < 2 * NP; ++s)
+            if (s < cnt) {
+                const float r = S.sph[s0 + s].w, rB = __fadd_rn(r, B);
+                pair_exact(own_centre<NP>(MX, MY, MZ, s), rB, r, p, m);
+            }
+    }
     return m;
 }
 
@@ -516,7 +517,8 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
             }
             const int nc = cull(S, k0, k1, Bp, world ? S.marg[0] : S.marg[1], box, lane, list);
             // nc is warp-uniform
-            float m = nc > 2   ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
+            float m = nc > P.exact_max
+                          ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
                       : nc > 0 ? few_candidates<NP>(S, list, nc, Bp, s0, cnt, MX, MY, MZ)
                                : kInf;
             if (world) m = fminf(m, mbox);
