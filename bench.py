@@ -330,8 +330,7 @@ def make_controller(sc, dev, shape=None):
         gp.append(p)
         gR.append(R)
     if shape is not None:
-        ctl.set_rollout_shape(shape["tile_samples"], shape["blocks_per_sm"], shape["order"],
-                              shape.get("exact_max", 2))
+        ctl.set_rollout_shape(shape["tile_samples"], shape["blocks_per_sm"], shape["order"])
     d_in = torch.from_numpy(ctl.pack_input(sc.q0, sc.qd0, gp, gR)).to(dev)
     ctl.step_device(d_in)
     ctl.sync()
@@ -764,15 +763,13 @@ def run(args):
     ctl, gp, gR, d_in = make_controller(sc, dev)
     tune = None
     if args.rollout_shape:
-        v = [int(x) for x in args.rollout_shape.split(",")]
-        t, b, o, x = (v + [2])[:4]
-        ctl.set_rollout_shape(t, b, o, x)
-        tune = {"given": {"tile_samples": t, "blocks_per_sm": b, "order": o, "exact_max": x}}
+        t, b, o = (int(x) for x in args.rollout_shape.split(","))
+        ctl.set_rollout_shape(t, b, o)
+        tune = {"given": {"tile_samples": t, "blocks_per_sm": b, "order": o}}
     elif not args.no_autotune:
         best, table = ctl.autotune(reps=5)
         tune = {"chosen": best, "tried": len(table)}
-    shape = dict(zip(("tile_samples", "blocks_per_sm", "order", "exact_max"),
-                     ctl.rollout_shape()[0]))
+    shape = dict(zip(("tile_samples", "blocks_per_sm", "order"), ctl.rollout_shape()[0]))
 
     # ---- device-resident cycles (exact costs) ------------------------------
     clk = ClockSampler(local)
@@ -864,8 +861,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rollout shape")
     ap.add_argument("--rollout-shape", default="",
-                    help="tile_samples,blocks_per_sm,order[,exact_max]: use this rollout shape "
-                         "instead of the autotuner's (e.g. to profile the shape a run chose)")
+                    help="tile_samples,blocks_per_sm,order: use this rollout shape instead of "
+                         "the autotuner's (e.g. to profile the shape a run chose)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-arm-at-a-time, graph-free comparison")
     ap.add_argument("--plain-cycles", type=int, default=200,

@@ -176,8 +176,10 @@ void mrs_destroy(mrs_ctx *ctx);
 /* One-line reason of the last failure on ctx ("" if none); with ctx NULL,
  * the reason of the last failed mrs_create on this thread.  mrs_create
  * returns MRS_EUNSUPPORTED when the rollout's shared-memory staging (world
- * spheres + n_arms x the largest sphere count) exceeds the device's per-block
- * limit, and mrs_set_world when a larger world would. */
+ * spheres + n_arms x the largest sphere count, their clusters and candidate
+ * lists) exceeds the device's per-block limit, and mrs_set_world when a
+ * larger world would; within this header's limits the staging needs at most
+ * about 180 KB, so on a device with 227 KB per block neither happens. */
 const char *mrs_last_error(const mrs_ctx *ctx);
 
 mrs_status mrs_query_sizes(const mrs_ctx *ctx, mrs_sizes *out);
@@ -192,7 +194,9 @@ mrs_status mrs_bind_workspace(mrs_ctx *ctx, void *dev_ptr, size_t bytes);
 /* World obstacles (Sec. III-A Sense: the obstacle representation; treated
  * as static over the horizon unless velocities are given, in which case a
  * sphere is predicted at constant velocity: centre + vel * (t + h dt), t
- * being the time since this call).  Host pointers:
+ * being the time since this call; the rollout reads a copy of the spheres
+ * in a spatial order, refreshed every cycle, which changes no result).
+ * Host pointers:
  *  spheres [n][4] centre + radius; vel [n][3] or NULL; aabbs [m][6] centre
  *  and half extents.  n <= MRS_MAX_WORLD_SPHERES, m <= MRS_MAX_AABBS. */
 mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, int n_spheres,
@@ -339,25 +343,19 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
  *                  h + 1: concurrent blocks share the step's plans), 1
  *                  arm-major, 2 step-major from the last step (the later
  *                  steps' wider spread of samples tends to cost more: the
- *                  costlier units first leave a shorter tail);
- *   exact_max      0 .. 64: a clearance pass left with at most this many
- *                  candidate spheres after the box culls tests every pair
- *                  exactly; with more it pre-tests them first (the default,
- *                  2, suits dense candidate sets; sparse ones, as when arms
- *                  meet only at a few spheres, run faster with more).
+ *                  costlier units first leave a shorter tail).
  * Results do not depend on the shape (each sample's cost is reduced by its
  * own lane in every shape); only the time does.  mrs_set_rollout_shape
  * returns MRS_EINVAL for a shape out of range. */
 typedef struct {
-    int tile_samples, blocks_per_sm, order, exact_max;
+    int tile_samples, blocks_per_sm, order;
     float cycle_ms;            /* mrs_autotune: median control-cycle time of the shape */
 } mrs_rollout_shape;
 mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
 
 /* Autotuner: times every shape of the grid {32, 64, 96, 128, 192, 256}
- * samples x 1 .. max resident blocks per SM x orders {0, 1, 2} x exact_max
- * {2, 8, 32} over
+ * samples x 1 .. max resident blocks per SM x orders {0, 1, 2} over
  * `reps` whole control cycles each (the cycle as mrs_step_device runs it:
  * CUDA graph without per-stage timing, so programmatic launch overlaps the
  * stages; CUDA events around each cycle on the context's stream, median) on

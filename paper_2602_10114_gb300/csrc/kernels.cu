@@ -651,9 +651,114 @@ __device__ __forceinline__ void toplan_done(const Params &P, const Dev &D, int *
     }
 }
 
+// The rollout's copy of the world (Dev::world_s, world_vel_s): the spheres
+// sorted by the Morton code of their centres at the next cycle's
+// mid-horizon time (t_next: the next cycle's world time), so that the
+// rollout's clusters of 8 consecutive spheres are compact.  Only the order
+// changes, never a sphere, so no result depends on it.  One block of 256
+// threads: block-wide bounding box, 10-bit codes per axis, a bitonic sort of
+// (code, index) keys in shared memory, then the gather.
+__device__ void world_order_block(const Params &P, const Dev &D, float t_next)
+{
+    __shared__ unsigned long long key[MRS_MAX_WORLD_SPHERES];
+    __shared__ float s_box[8][6];
+    const int n = D.world_n[0], t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (n <= 0) return;
+    int hmax = 1;
+    for (int i = 0; i < P.n_arms; ++i) hmax = max(hmax, D.arms[i].H);
+    const float tr = t_next + P.dt * (0.5f * (float)hmax + 1.f);
+    auto pos = [&](int k) {
+        const float4 o = D.world[k], v = D.world_vel[k];
+        return make_float3(o.x + v.x * tr, o.y + v.y * tr, o.z + v.z * tr);
+    };
+    float lo[3] = {kInf, kInf, kInf}, hi[3] = {-kInf, -kInf, -kInf};
+    for (int k = t; k < n; k += blockDim.x) {
+        const float3 p = pos(k);
+        lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        if (lane == 0) {
+            s_box[w][a] = lo[a];
+            s_box[w][3 + a] = hi[a];
+        }
+    }
+    __syncthreads();
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            lo[a] = fminf(lo[a], s_box[i][a]);
+            hi[a] = fmaxf(hi[a], s_box[i][3 + a]);
+        }
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int k = t; k < n2; k += blockDim.x) {
+        unsigned long long kk = ~0ull;
+        if (k < n) {
+            const float3 p = pos(k);
+            const float c[3] = {p.x, p.y, p.z};
+            unsigned code = 0;
+            for (int a = 0; a < 3; ++a) {
+                const float ext = fmaxf(hi[a] - lo[a], 1e-6f);
+                const unsigned q = (unsigned)fminf(fmaxf((c[a] - lo[a]) * (1023.f / ext), 0.f), 1023.f);
+                for (int b = 0; b < 10; ++b) code |= ((q >> b) & 1u) << (3 * b + a);
+            }
+            kk = ((unsigned long long)code << 32) | (unsigned)k;
+        }
+        key[k] = kk;
+    }
+    __syncthreads();
+    for (int size = 2; size <= n2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = t; i < n2 / 2; i += blockDim.x) {
+                const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
+                const unsigned long long ka = key[a], kb = key[b];
+                if ((ka > kb) == ((a & size) == 0)) {
+                    key[a] = kb;
+                    key[b] = ka;
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = t; i < n; i += blockDim.x) {
+        const int k = (int)(unsigned)(key[i] & 0xffffffffull);
+        D.world_s[i] = D.world[k];
+        D.world_vel_s[i] = D.world_vel[k];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_world_order(Params P, Dev D)
+{
+    world_order_block(P, D, *D.world_t);
+}
+
+cudaError_t enqueue_world_order(const Params &P, const Dev &D, cudaStream_t s)
+{
+    k_world_order<<<1, 256, 0, s>>>(P, D);
+    return cudaGetLastError();
+}
+
+// ToPlan (one block per arm), the next cycle's state factors (the blocks
+// after them) and the world's order for the next cycle (the last block)
 __global__ void __launch_bounds__(256) k_toplan(Params P, Dev D, int *done_counter,
                                                 const UpdateTile *ftiles, int n_ftiles)
 {
+    if ((int)blockIdx.x == (int)gridDim.x - 1) {   // uniform over the block
+        // the world time is advanced only by the last block past toplan_done,
+        // so it is still this cycle's here; the current rollout has finished
+        // with the copy (the wait below covers every earlier kernel)
+        const long long cyc = *D.cycle;
+        const float t_next = __fadd_rn(*D.world_t, P.dt);
+        pdl_wait();
+        pdl_trigger();
+        world_order_block(P, D, t_next);
+        __syncthreads();
+        if (threadIdx.x == 0) toplan_done(P, D, done_counter, cyc);
+        return;
+    }
     if ((int)blockIdx.x >= P.n_arms) {   // uniform over the block
         // the next cycle's factors: the state the update just wrote is in the
         // buffer of parity cycle + 1 (the counter advances only once every
@@ -999,8 +1104,9 @@ cudaError_t enqueue_cycle(const Params &P, const Dev &D, const LaunchPlan &L, cu
             return rec;
         mark();
     }
-    // ToPlan on one block per arm, the next cycle's factors on the blocks after them
-    if ((rec = launch_k(k_toplan, L.n_arms + (L.n_update_tiles + 7) / 8, 256, L.smem_toplan, s, pdl,
+    // ToPlan on one block per arm, the next cycle's factors on the blocks after them, the
+    // world's order for the next cycle on the last
+    if ((rec = launch_k(k_toplan, L.n_arms + (L.n_update_tiles + 7) / 8 + 1, 256, L.smem_toplan, s, pdl,
                         P, D, L.done_counter, L.update_tiles, L.n_update_tiles)) != cudaSuccess)
         return rec;
     mark();

@@ -135,6 +135,9 @@ cudaError_t enqueue_init(const Params &P, const Dev &D, int n_arms, int total_hd
                          cudaStream_t s);
 // Cholesky factors of the state's covariances in the buffers of the given
 // parity (after an initialisation or a state load)
+// the rollout's copy of the world in spatial order (one block), at the
+// current world time
+cudaError_t enqueue_world_order(const Params &P, const Dev &D, cudaStream_t s);
 cudaError_t enqueue_state_factors(const Dev &D, const LaunchPlan &L, int parity, cudaStream_t s);
 cudaError_t enqueue_fk(const Dev &D, int arm, int n, const float *q, float *ee, float *spheres,
                        cudaStream_t s);

@@ -45,7 +45,7 @@ struct mrs_ctx {
     std::string err;
     // workspace offsets (bytes)
     struct Layout {
-        size_t arms, input, world, world_vel, aabb, world_n, mu, Sigma, L, board_sph, board_q,
+        size_t arms, input, world, world_vel, world_s, world_vel_s, aabb, world_n, mu, Sigma, L, board_sph, board_q,
             board_valid, board_stamp, board_dist, traj, eps, stage_lim, stage, costs, alpha,
             e_now, n_star, out, cycle, world_t, done_counter, Lst, sample_tiles, rollout_tiles,
             cost_tiles, update_tiles, self_pairs, self_t2, work, dhat, total;
@@ -139,6 +139,8 @@ static void build_layout(mrs_ctx *c)
     L.input = take(sizeof(float) * c->sz.input_floats);
     L.world = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
     L.world_vel = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
+    L.world_s = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
+    L.world_vel_s = take(sizeof(float4) * MRS_MAX_WORLD_SPHERES);
     L.aabb = take(sizeof(float4) * 2 * MRS_MAX_AABBS);
     L.world_n = take(sizeof(int) * 2);
     L.mu = take(sizeof(float) * 2 * c->sz.hd);       // two buffers (cycle parity)
@@ -249,6 +251,8 @@ static void fill_dev(mrs_ctx *c, char *base)
     D.input = (float *)(base + L.input);
     D.world = (float4 *)(base + L.world);
     D.world_vel = (float4 *)(base + L.world_vel);
+    D.world_s = (float4 *)(base + L.world_s);
+    D.world_vel_s = (float4 *)(base + L.world_vel_s);
     D.aabb = (float4 *)(base + L.aabb);
     D.world_n = (int *)(base + L.world_n);
     D.mu = (float *)(base + L.mu);
@@ -455,12 +459,10 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     P.w_manip = cfg->w_manip;
     P.manip_w0 = cfg->manip_w0;
     P.wait_polls = tc::kWaitLimit;
-    P.exact_max = 2;
 
     size_t hd = 0, hdd = 0, hs = 0, dsum = 0, ksum = 0, in = 0;
     long long khd = 0, kh = 0;
     int max_ns = 0, max_pairs = 0;
-    float ws_radius = 0.f;
     ctx->arms.resize(ctx->A);
     for (int a = 0; a < ctx->A; ++a) {
         const mrs_arm_desc &d = cfg->arms[a];
@@ -499,16 +501,6 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
                 }
         A.n_self = (int)ctx->self_pairs.size() - A.self_off;
         max_pairs = std::max(max_pairs, A.n_self);
-        // workspace radius for the cancellation margin of the pair pre-test
-        float reach = 0.f, tool = 0.f;
-        for (int j = 0; j < d.dof; ++j) reach += std::fabs(d.dh[4 * j]) + std::fabs(d.dh[4 * j + 1]);
-        for (int s2 = 0; s2 < d.n_spheres; ++s2) {
-            const float *v = d.sphere_xyzr + 4 * s2;
-            tool = std::max(tool, std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + v[3]);
-        }
-        const float *b = d.base_pose;
-        ws_radius = std::max(ws_radius, std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]) +
-                                            reach + tool + 0.3f);
         hd += (size_t)d.H * d.dof;
         hdd += (size_t)d.H * d.dof * d.dof;
         hs += (size_t)d.H * d.n_spheres * 4;
@@ -523,10 +515,6 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     P.max_pairs = std::max(max_pairs, 1);
     P.world_cap = 64;
     P.aabb_cap = 8;
-    // The expanded pre-test g = |c-p|^2 - t^2 carries rounding of order
-    // 2^-24 times the squared coordinates (<= ws_radius^2, four FMAs and two
-    // precomputed terms); 64 units of it is a safe margin.
-    P.eps_g = std::max(1e-6f, 64.f * 5.9604645e-8f * ws_radius * ws_radius);
     ctx->sz.n_arms = ctx->A;
     ctx->sz.hd = hd; ctx->sz.hdd = hdd; ctx->sz.hs = hs; ctx->sz.d = dsum; ctx->sz.k = ksum;
     ctx->sz.input_floats = in;
@@ -787,6 +775,7 @@ mrs_status mrs_set_world(mrs_ctx *ctx, const float *spheres, const float *vel, i
        "set_world");
     CK(cudaMemcpyAsync(ctx->D.world_t, &zero, sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
        "set_world");
+    CK(enqueue_world_order(ctx->P, ctx->D, ctx->stream), "set_world order");
     CK(cudaStreamSynchronize(ctx->stream), "set_world sync");
     return MRS_OK;
 }
@@ -1127,6 +1116,7 @@ mrs_status mrs_load_state(mrs_ctx *ctx, const void *blob, size_t bytes)
     CK(cudaMemcpyAsync(D.cycle, &cycle, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(cudaMemcpyAsync(D.world_t, &wt, sizeof(float), cudaMemcpyHostToDevice, ctx->stream), "load");
     CK(enqueue_state_factors(D, ctx->L, (int)(cycle & 1), ctx->stream), "load factors");
+    CK(enqueue_world_order(ctx->P, D, ctx->stream), "load world order");
     CK(cudaStreamSynchronize(ctx->stream), "load sync");
     return MRS_OK;
 }
@@ -1560,15 +1550,13 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n)
 // ---------------------------------------------------------------------------
 // rollout launch shape and its autotuner
 
-static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm, int order,
-                              int exact_max)
+static mrs_status apply_shape(mrs_ctx *ctx, int tile_samples, int blocks_per_sm, int order)
 {
     mrs_status st = ensure_bound(ctx);
     if (st != MRS_OK) return st;
     ctx->tile_samples = tile_samples;
     ctx->blocks_per_sm = blocks_per_sm;
     ctx->tile_order = order;
-    ctx->P.exact_max = exact_max;
     build_rollout_tiles(ctx);
     LaunchPlan &L = ctx->L;
     L.n_rollout_tiles = (int)ctx->rollout_tiles.size();
@@ -1588,10 +1576,9 @@ mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
     if (!ctx || !shape) return MRS_EINVAL;
     if (shape->tile_samples < 32 || shape->tile_samples > 256 || shape->tile_samples % 32 ||
         shape->blocks_per_sm < 0 || shape->blocks_per_sm > ctx->max_blocks_per_sm ||
-        shape->order < 0 || shape->order > 2 || shape->exact_max < 0 || shape->exact_max > 64)
+        shape->order < 0 || shape->order > 2)
         return fail(ctx, MRS_EINVAL, "rollout shape out of range");
-    return apply_shape(ctx, shape->tile_samples, shape->blocks_per_sm, shape->order,
-                       shape->exact_max);
+    return apply_shape(ctx, shape->tile_samples, shape->blocks_per_sm, shape->order);
 }
 
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm)
@@ -1602,7 +1589,6 @@ mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *ma
         shape->tile_samples = ctx->tile_samples;
         shape->blocks_per_sm = ctx->blocks_per_sm;
         shape->order = ctx->tile_order;
-        shape->exact_max = ctx->P.exact_max;
         shape->cycle_ms = 0.f;
     }
     if (max_blocks_per_sm) *max_blocks_per_sm = ctx->max_blocks_per_sm;
@@ -1646,16 +1632,13 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
         }
     }
     std::vector<mrs_rollout_shape> tried;
-    const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order,
-                                   ctx->P.exact_max, 0.f};
+    const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
     mrs_rollout_shape keep = before;
     float best_ms = INFINITY;
     for (int ts : {32, 64, 96, 128, 192, 256}) {
         for (int bps = 1; bps <= ctx->max_blocks_per_sm && st == MRS_OK; ++bps) {
-            for (int combo = 0; combo < 9 && st == MRS_OK; ++combo) {
-                static const int kExactMax[3] = {2, 8, 32};
-                const int order = combo % 3, exact_max = kExactMax[combo / 3];
-                if ((st = apply_shape(ctx, ts, bps, order, exact_max)) != MRS_OK) break;
+            for (int order = 0; order < 3 && st == MRS_OK; ++order) {
+                if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) break;
                 // every shape's trials start from the same state (and draw the same
                 // samples): the controller's state drifts over the trials, and with
                 // it the work of a cycle
@@ -1679,7 +1662,7 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
                 if (st != MRS_OK) break;
                 std::sort(t.begin(), t.end());
                 const float med = t[t.size() / 2];
-                tried.push_back(mrs_rollout_shape{ts, bps, order, exact_max, med});
+                tried.push_back(mrs_rollout_shape{ts, bps, order, med});
                 if (med < best_ms) {
                     best_ms = med;
                     keep = tried.back();
@@ -1694,15 +1677,13 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
         // put back the shape, the timing switch and the state as far as the
         // device still allows; the trial's error is the one reported
         const std::string why = ctx->err;
-        apply_shape(ctx, before.tile_samples, before.blocks_per_sm, before.order, before.exact_max);
+        apply_shape(ctx, before.tile_samples, before.blocks_per_sm, before.order);
         mrs_enable_timing(ctx, timing ? 1 : 0);
         mrs_load_state(ctx, blob.data(), blob.size());
         ctx->err = why;
         return st;
     }
-    if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order, keep.exact_max)) !=
-        MRS_OK)
-        return st;
+    if ((st = apply_shape(ctx, keep.tile_samples, keep.blocks_per_sm, keep.order)) != MRS_OK) return st;
     if ((st = mrs_enable_timing(ctx, timing ? 1 : 0)) != MRS_OK) return st;
     if ((st = mrs_load_state(ctx, blob.data(), blob.size())) != MRS_OK) return st;
     if (n_tried) *n_tried = (int)tried.size();

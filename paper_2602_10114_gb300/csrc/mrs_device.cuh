@@ -51,12 +51,9 @@ struct Params {
     unsigned long long seed;
     int max_ns, max_pairs;        // largest sphere and self-pair counts of any arm
     int world_cap, aabb_cap;      // shared-memory capacity of the rollout for the world
-    float eps_g;                  // cancellation margin of the expanded pair pre-test (m^2)
     int max_plan_age;             // board entries older than this are ignored (0: no limit)
     float w_manip, manip_w0;      // C_manip weight (0: off) and manipulability threshold
     unsigned wait_polls;          // polls of the rollout's bounded wait for its plan copies
-    int exact_max;                // a clearance pass with at most this many candidates
-                                  // tests every pair exactly (no pre-test)
 };
 
 // A neighbour's board entry is used when it is published and, with a
@@ -73,6 +70,8 @@ struct Dev {
     float *input;          // packed per arm: q(d) qd(d) goal_p(3) goal_R(9)
     float4 *world;         // [kMaxWorld] centre + radius
     float4 *world_vel;     // [kMaxWorld] velocity (w unused)
+    float4 *world_s;       // the same spheres in a spatial (Morton) order at the next
+    float4 *world_vel_s;   // cycle's mid-horizon time, and their velocities: the rollout's copy
     float4 *aabb;          // [kMaxAabb][2] centre, half extents
     int *world_n;          // [2] spheres, boxes
     float *mu, *Sigma, *L; // state: [2][hd], [2][hdd] (by cycle parity), [hdd]

@@ -7,21 +7,21 @@ namespace mrs {
 
 size_t rollout_smem_bytes(const Params &P, int n_arms)
 {
+    // the layout of k_rollout's dynamic shared memory, in its order
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
-    const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * n_arms;
+    const size_t n_other = (size_t)rollout_other_cap(P, n_arms);
+    const size_t n_cl = (size_t)rollout_cluster_cap(P, n_arms);
     return a16(sizeof(float4) * n_other) + a16(sizeof(float4) * 2 * P.aabb_cap) +
            a16(sizeof(float4) * P.max_ns) + a16(sizeof(float4) * P.max_ns * 32) +
-           a16(sizeof(float) * n_other) + 2 * a16(sizeof(ulonglong2) * n_other) +
-           a16(sizeof(unsigned long long) * n_other) + a16(sizeof(int) * P.max_ns) +
-           a16(sizeof(int2) * P.max_pairs) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +
-           a16(sizeof(float) * 2 * MRS_MAX_ARMS) + a16(sizeof(int) * MRS_MAX_ARMS) +
-           a16(sizeof(float) * kGroups * 8) + a16(sizeof(float) * 2) +
-           a16(sizeof(float4) * 2 * n_arms) +
-           a16(sizeof(float4) * 2 * P.max_ns) +
-           a16(sizeof(float2) * 2 * kMaxDof * 32) + a16(sizeof(float4) * kMaxDof) +
-           a16(sizeof(float2) * kMaxDof) + 2 * a16(sizeof(float) * 12) +
-           a16(sizeof(unsigned short) * kGroups * (size_t)rollout_cand_cap(P)) +
-           sizeof(int) * 2 * (2 + (size_t)n_arms) * 32;
+           a16(sizeof(float4) * 2 * n_cl) + a16(sizeof(float4) * 2 * P.max_ns) +
+           a16(sizeof(int) * P.max_ns) + a16(sizeof(int2) * P.max_pairs) +
+           a16(sizeof(int) * n_cl) + a16(sizeof(int) * (MRS_MAX_ARMS + 1)) +
+           a16(sizeof(int) * MRS_MAX_ARMS) + a16(sizeof(float) * 2 * MRS_MAX_ARMS) +
+           a16(sizeof(int) * MRS_MAX_ARMS) + a16(sizeof(float2) * 2 * kMaxDof * 32) +
+           a16(sizeof(float4) * kMaxDof) + a16(sizeof(float2) * kMaxDof) +
+           2 * a16(sizeof(float) * 12) + a16(n_other) +
+           a16(sizeof(unsigned short) * kGroups * (size_t)rollout_cand_cap(P, n_arms)) +
+           a16(sizeof(int2) * kObstaclePairCap) + sizeof(int) * 2 * (2 + (size_t)n_arms) * 32;
 }
 
 cudaError_t configure_rollout(const LaunchPlan &L)

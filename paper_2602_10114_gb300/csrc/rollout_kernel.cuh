@@ -9,20 +9,23 @@
 // mbarrier -- and the arm's constants) once; the samples then pass through in
 // sub-batches of 32.  Warp g of a block owns sphere group g (spheres [g*spg, (g+1)*spg),
 // spg = ceil(N_S / 8)) of the sub-batch's 32 rollout steps, one sample per
-// lane; its centres stay in registers.  The samples per tile, the tile order
-// and the resident blocks per SM are chosen at run time (mrs_autotune).
+// lane.  The samples per tile, the tile order and the resident blocks per SM
+// are chosen at run time (mrs_autotune).
 //
-// Pair test.  A pair (own sphere c, radius r; other sphere p, radius r_p) can
-// change a ramp cost max(0, 1 - dist/B) only if |c - p| < r + r_p + B.  With
-//   g = |c - p|^2 - (r + B + r_p)^2
-//     = [|p|^2 - r_p^2] - 2 c.p - 2 (r + B) r_p + [|c|^2 - (r + B)^2]
-// the bracketed per-sphere terms are precomputed, so the inner loop is four
-// FMAs and a min per pair, without branches, issued as packed f32x2
-// instructions on two own spheres at a time.  An own sphere whose minimum g
-// falls below eps_g (the FP32 cancellation margin of this expansion over the
-// workspace) gets an exact pass: direct squared distance, and the square root
-// only for pairs inside the ramp.  Since the cost is zero outside the ramp,
-// the result equals the brute-force minimum of Eq. 6 restricted to the ramp.
+// Pair tests.  A pair (own sphere c, radius r; other sphere p, radius r_p)
+// can change a ramp cost max(0, 1 - dist/B) only if |c - p| < r + r_p + B.
+// The other spheres of a unit -- the world at the step's time, then each
+// neighbour's plan slice -- form clusters of up to 8 consecutive spheres,
+// each with its box (the world is kept in a spatial order, refreshed every
+// cycle, so that its clusters are compact).  A warp narrows the pairs in
+// three box tests, each conservative (it never drops a pair inside the
+// ramp): the cluster boxes against the box of the warp's own spheres over
+// its 32 samples; the spheres of the near clusters against that box; every
+// (candidate, own sphere) pair against that own sphere's box over the
+// samples.  The pairs left get the exact distance of every sample, the
+// square root only inside the ramp.  Since the cost is zero outside the
+// ramp, the result equals the brute-force minimum of Eq. 6 restricted to the
+// ramp, whatever the order of the spheres.
 #pragma once
 
 #include <algorithm>
@@ -30,14 +33,16 @@
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
 
-// build-time knob of the pre-test loop
-#ifndef MRS_PRETEST_UNROLL
-#define MRS_PRETEST_UNROLL 1
-#endif
-
 namespace mrs {
 
-constexpr int kPretestUnroll = MRS_PRETEST_UNROLL;
+// slack of every box test (m): far above the rounding of the coordinates
+// (a few 1e-7 m over the workspace), so that no test drops a pair the exact
+// distance keeps
+constexpr float kCullMargin = 1e-3f;
+
+// capacity of the block's list of obstacle pairs per sub-batch (a warp tests
+// the pairs that do not fit itself)
+constexpr int kObstaclePairCap = 512;
 
 // The unit arm's scalars, staged in shared memory once per unit (the
 // ArmDev record in global memory would be re-read after the unit's stores)
@@ -51,10 +56,9 @@ struct ArmHdr {
 
 struct RolloutSmem {
     float4 *other;     // world spheres at the step's time, then neighbours' plan spheres
-    float *other_w;    // |p|^2 - r_p^2 of each
-    ulonglong2 *pa;    // packed pairs for the f32x2 pre-test: (x, x), (y, y)
-    ulonglong2 *pb;    //                                      (z, z), (r, r)
-    unsigned long long *pc;   //                               (w, w)
+    unsigned char *seg;     // [n_other] set of each plan sphere: 2 + its neighbour slot
+    float4 *cbox;      // [2 * n_cl] box of each cluster: lo, hi (w unused)
+    int *cinfo;        // [n_cl] first sphere | count << 16 | set << 20 (0 world, 2 + nb)
     float4 *aabb;      // [2 * n_aabb] centre, half extents
     float4 *sph;       // [ns] local centre + radius
     int *frame;        // [ns]
@@ -63,14 +67,15 @@ struct RolloutSmem {
     float4 *own;       // [ns][32] own sphere centre and radius of each sample
     int *red;          // [(2 + n_nb) * 32] ordered-int minima: world, self, neighbours
     int *nb_start;     // [n_nb + 1] ranges in `other` (after the world spheres)
+    int *nb_cstart;    // [n_nb] first cluster of each neighbour
     float *nb_alpha;   // [n_nb]
     int *nb_arm;       // [n_nb] arm index of each neighbour
     unsigned short *cand;   // [kGroups][cand_cap] per-warp candidate lists
     int cand_cap;
+    int2 *opairs;           // [kObstaclePairCap] the sub-batch's obstacle pairs left by the
+                            // box tests: own sphere | other << 6 | set << 18, (r + B + r_p)^2
+    int *opn;               // the count of opairs entries this sub-batch (by sub-batch parity)
     float4 *sbox;           // [ns][2] per-sphere bounding box over the sub-batch: lo, hi
-    float *box;             // [kGroups][8] per-warp bounding box: lo xyz, hi xyz
-    float *marg;            // [2] cull margins 1 mm + eps_g / B of the world and plan passes
-    float4 *nbbox;          // [2 * n_arms] box of each neighbour's plan spheres at the unit's step
     float2 *sc;             // [dof][32] sin, cos of q_j + theta_j of the sub-batch's samples
     float4 *dh;             // [kMaxDof] the arm's DH rows (a, d, alpha, theta)
     float2 *tw;             // [kMaxDof] sin, cos of the twists
@@ -80,40 +85,20 @@ struct RolloutSmem {
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Capacity of a warp's candidate list: the largest single pass (the world
-// spheres, or one neighbour's plan slice), rounded up to 8.
-__host__ __device__ inline int rollout_cand_cap(const Params &P)
+// Other spheres of a unit at most (the world, every other arm's plan slice),
+// their clusters, and the capacity of a warp's candidate list (all of them,
+// rounded up to 8).
+__host__ __device__ inline int rollout_other_cap(const Params &P, int n_arms)
 {
-    const int m = P.world_cap > P.max_ns ? P.world_cap : P.max_ns;
-    return (m + 7) & ~7;
+    return P.world_cap + P.max_ns * n_arms;
 }
-
-// packed binary32 pairs (Blackwell f32x2 FMA: two lanes, each rounded exactly
-// like the scalar instruction)
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pack2(float a, float b)
+__host__ __device__ inline int rollout_cluster_cap(const Params &P, int n_arms)
 {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
+    return (P.world_cap + 7) / 8 + n_arms * ((P.max_ns + 7) / 8);
 }
-__device__ __forceinline__ void unpack2(f32x2 v, float &a, float &b)
+__host__ __device__ inline int rollout_cand_cap(const Params &P, int n_arms)
 {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
-{
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// minimum of three (sm_100+ three-input min; exact, like fminf twice)
-__device__ __forceinline__ float min3(float a, float b, float c)
-{
-    float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
+    return (rollout_other_cap(P, n_arms) + 7) & ~7;
 }
 
 // mbarrier arrive with an expected transaction count (the bytes of the bulk
@@ -147,30 +132,6 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// store one other sphere (and its |p|^2 - r^2) in every layout the passes read
-__device__ __forceinline__ void put_other(const RolloutSmem &S, int k, float4 w)
-{
-    const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
-                                -__fmul_rn(w.w, w.w))));
-    S.other[k] = w;
-    S.other_w[k] = pw;
-    S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
-    S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
-    S.pc[k] = pack2(pw, pw);
-}
-
-// the derived layouts of a sphere already in S.other[k] (a plan sphere
-// copied there by the bulk-copy engine)
-__device__ __forceinline__ void put_derived(const RolloutSmem &S, int k, float4 w)
-{
-    const float pw = __fmaf_rn(w.z, w.z, __fmaf_rn(w.y, w.y, __fmaf_rn(w.x, w.x,
-                                -__fmul_rn(w.w, w.w))));
-    S.other_w[k] = pw;
-    S.pa[k] = make_ulonglong2(pack2(w.x, w.x), pack2(w.y, w.y));
-    S.pb[k] = make_ulonglong2(pack2(w.z, w.z), pack2(w.w, w.w));
-    S.pc[k] = pack2(pw, pw);
-}
-
 // exact distance of a candidate pair, as in the oracle: sqrt(d2) - r - r_p
 __device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p, float &m)
 {
@@ -195,6 +156,30 @@ __device__ __forceinline__ float warp_max(float v)
     return r;
 }
 
+// box lo / hi reduced over aligned groups of 8 lanes (every lane gets its
+// group's; exact)
+__device__ __forceinline__ void cluster_box(float3 &lo, float3 &hi)
+{
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+}
+
+// squared gap between a point and a box (0 inside)
+__device__ __forceinline__ float gap2(float4 p, float3 lo, float3 hi)
+{
+    const float gx = fmaxf(fmaxf(lo.x - p.x, p.x - hi.x), 0.f);
+    const float gy = fmaxf(fmaxf(lo.y - p.y, p.y - hi.y), 0.f);
+    const float gz = fmaxf(fmaxf(lo.z - p.z, p.z - hi.z), 0.f);
+    return gx * gx + gy * gy + gz * gz;
+}
+
 // The same test for a self pair whose squared ramp bound (r1 + B + r2)^2 was
 // computed beforehand with the same sums: sqrt(d2) - r1 - r2 when inside
 __device__ __forceinline__ void pair_exact_t2(float4 c1, float4 c2, float t2, float &m)
@@ -204,207 +189,188 @@ __device__ __forceinline__ void pair_exact_t2(float4 c1, float4 c2, float t2, fl
     if (d2 < t2) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), c1.w), c2.w));
 }
 
-// Candidates of one pass: the other spheres in [k0, k1) that come within
-// r_p + B + margin of the box bounding the warp's own spheres (each centre
-// +- its radius, over the 32 lanes).  A sphere outside is farther than
-// r + r_p + B + margin from every own sphere, so its pairs are outside the
-// ramp and, with margin >= eps_g / B, also fail the pre-test: dropping them
-// changes no result.  Warp-cooperative; returns the count (warp-uniform).
-__device__ __forceinline__ int cull(const RolloutSmem &S, int k0, int k1, float B, float margin,
-                                    const float *box, int lane, unsigned short *list)
+// Candidates of a warp: the other spheres (every set) within r_p + B + margin
+// of the warp's box [lo, hi] (each own centre +- its radius over the 32
+// lanes), found cluster by cluster.  A cluster whose box is farther than
+// B + margin from the warp's box holds no candidate: each of its spheres
+// lies in the cluster box by its radius, so its centre is farther than
+// r_p + B + margin from the warp's box.  Near clusters are taken four at a
+// time, lanes 8i .. 8i + 7 on the i-th, their spheres tested one per lane.
+// Sets that no lane of the warp needs (skip_nb, bit nb for neighbour nb) are
+// left out.  The candidates come in increasing index order, so each set's
+// are contiguous; returns their number (warp-uniform).  tw, tn: B + margin of
+// the world and of the plan sets.
+__device__ __forceinline__ int cull_clusters(const RolloutSmem &S, float3 lo, float3 hi,
+                                             int n_cl, int n_world, float tw, float tn,
+                                             unsigned skip_nb, int lane, unsigned short *list)
 {
-    const float3 lo = make_float3(box[0], box[1], box[2]), hi = make_float3(box[3], box[4], box[5]);
+    const float tc = fmaxf(tw, tn);
+    const float tc2 = tc * tc;
+    const unsigned below = (1u << lane) - 1u;
     int nc = 0;
-    for (int base = k0; base < k1; base += 32) {
-        const int k = base + lane;
-        bool keep = false;
-        if (k < k1) {
-            const float4 p = S.other[k];
-            const float dx = fmaxf(fmaxf(lo.x - p.x, p.x - hi.x), 0.f);
-            const float dy = fmaxf(fmaxf(lo.y - p.y, p.y - hi.y), 0.f);
-            const float dz = fmaxf(fmaxf(lo.z - p.z, p.z - hi.z), 0.f);
-            const float t = p.w + B + margin;
-            keep = dx * dx + dy * dy + dz * dz < t * t;
+    for (int c0 = 0; c0 < n_cl; c0 += 32) {
+        const int c = c0 + lane;
+        bool near = false;
+        if (c < n_cl) {
+            const float4 cl = S.cbox[2 * c], ch = S.cbox[2 * c + 1];
+            const float gx = fmaxf(fmaxf(cl.x - hi.x, lo.x - ch.x), 0.f);
+            const float gy = fmaxf(fmaxf(cl.y - hi.y, lo.y - ch.y), 0.f);
+            const float gz = fmaxf(fmaxf(cl.z - hi.z, lo.z - ch.z), 0.f);
+            near = gx * gx + gy * gy + gz * gz < tc2;
+            if (skip_nb) {
+                const int set = S.cinfo[c] >> 20;
+                if (set >= 2 && ((skip_nb >> (set - 2)) & 1u)) near = false;
+            }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) list[nc + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
-        nc += __popc(m);
+        unsigned mc = __ballot_sync(0xffffffffu, near);
+        while (mc) {
+            // the (lane / 8)-th lowest near cluster left, then drop four
+            unsigned x = mc;
+            const int i = lane >> 3;
+            if (i >= 1) x &= x - 1u;
+            if (i >= 2) x &= x - 1u;
+            if (i >= 3) x &= x - 1u;
+            mc &= mc - 1u;
+            mc &= mc - 1u;
+            mc &= mc - 1u;
+            mc &= mc - 1u;
+            bool keep = false;
+            int k = 0;
+            if (x) {
+                const int info = S.cinfo[c0 + __ffs(x) - 1];
+                const int r = lane & 7;
+                if (r < ((info >> 16) & 15)) {
+                    k = (info & 0xffff) + r;
+                    const float4 p = S.other[k];
+                    const float t = p.w + (k < n_world ? tw : tn);
+                    keep = gap2(p, lo, hi) < t * t;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) list[nc + __popc(m & below)] = (unsigned short)k;
+            nc += __popc(m);
+        }
     }
     __syncwarp();
     return nc;
 }
 
-// Minimum signed distance, inside the ramp of buffer B, between the warp's
-// own spheres and the candidates other[list[0 .. nc)).  Returns +inf when no
-// pair is in the ramp.
-// Own sphere centres arrive packed in pairs as -2c (NP = ceil(SPG / 2)); the
-// pre-test runs on both spheres of a pair with one f32x2 FMA chain.
-template <int NP>
-__device__ __forceinline__ float clearance_pass(const RolloutSmem &S, const unsigned short *list,
-                                                int nc, float B, float eps_g, int s0, int cnt,
-                                                int lane, const f32x2 (&MX)[NP],
-                                                const f32x2 (&MY)[NP], const f32x2 (&MZ)[NP])
+// Exact distance of one obstacle pair (own sphere, other sphere p) for this
+// lane's sample, the square root only inside the ramp, and its minimum into
+// the set's slot of the per-lane minima (world 0, neighbour nb at 2 + nb)
+// when inside the set's buffer and the lane needs the set (need_nb: bit nb
+// for neighbour nb).  code: own sphere | other << 6 | set << 18; t2: the
+// squared ramp bound (r + B + r_p)^2 with the sums in this order.
+__device__ __forceinline__ void obstacle_pair(const Params &P, const RolloutSmem &S, int code,
+                                              float t2, int lane, unsigned need_nb)
 {
-    f32x2 MR[NP];
-    float gmin[2 * NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const int a = 2 * q, b = 2 * q + 1;
-        const float ra = (a < cnt) ? -2.f * __fadd_rn(S.sph[s0 + a].w, B) : 0.f;
-        const float rb = (b < cnt) ? -2.f * __fadd_rn(S.sph[s0 + b].w, B) : 0.f;
-        MR[q] = pack2(ra, rb);
-        gmin[a] = gmin[b] = kInf;
+    const int set = code >> 18;
+    const float4 c = S.own[(code & 63) * 32 + lane];
+    const float4 p = S.other[(code >> 6) & 4095];
+    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    if (d2 < t2) {
+        const float dist = __fsub_rn(__fsub_rn(sqrtf(d2), c.w), p.w);
+        const bool need = set == 0 || ((need_nb >> (set - 2)) & 1u);
+        if (need && dist < (set == 0 ? P.B_world : P.B))
+            atomicMin(&S.red[set * 32 + lane], float_to_ordered(dist));
     }
-    // two candidates per step: their values meet the running minimum in one
-    // three-input min
-    int i = 0;
-#pragma unroll kPretestUnroll
-    for (; i + 1 < nc; i += 2) {
-        const int k = list[i], k1 = list[i + 1];
-        const ulonglong2 A0 = S.pa[k], B0 = S.pb[k], A1 = S.pa[k1], B1 = S.pb[k1];
-        const f32x2 W0 = S.pc[k], W1 = S.pc[k1];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            float g0, g1, h0, h1;
-            unpack2(fma2(MX[q], A0.x, fma2(MY[q], A0.y, fma2(MZ[q], B0.x, fma2(MR[q], B0.y, W0)))),
-                    g0, g1);
-            unpack2(fma2(MX[q], A1.x, fma2(MY[q], A1.y, fma2(MZ[q], B1.x, fma2(MR[q], B1.y, W1)))),
-                    h0, h1);
-            gmin[2 * q] = min3(gmin[2 * q], g0, h0);
-            gmin[2 * q + 1] = min3(gmin[2 * q + 1], g1, h1);
-        }
-    }
-    if (i < nc) {
-        const int k = list[i];
-        const ulonglong2 A = S.pa[k], Bv = S.pb[k];
-        const f32x2 W = S.pc[k];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            float g0, g1;
-            unpack2(fma2(MX[q], A.x, fma2(MY[q], A.y, fma2(MZ[q], Bv.x, fma2(MR[q], Bv.y, W)))),
-                    g0, g1);
-            gmin[2 * q] = fminf(gmin[2 * q], g0);
-            gmin[2 * q + 1] = fminf(gmin[2 * q + 1], g1);
-        }
-    }
-    // own spheres whose pre-test minimum is within the margin of the ramp
-    unsigned flagged = 0u;
-#pragma unroll
-    for (int s = 0; s < 2 * NP; ++s) {
-        if (s < cnt) {
-            // g = gmin + |c|^2 - (r + B)^2 with c = -m/2
-            float x0, x1, y0, y1, z0, z1;
-            unpack2(MX[s / 2], x0, x1);
-            unpack2(MY[s / 2], y0, y1);
-            unpack2(MZ[s / 2], z0, z1);
-            const float cx = -0.5f * ((s & 1) ? x1 : x0), cy = -0.5f * ((s & 1) ? y1 : y0),
-                        cz = -0.5f * ((s & 1) ? z1 : z0);
-            const float rB = __fadd_rn(S.sph[s0 + s].w, B);
-            const float ac = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmaf_rn(cx, cx, -__fmul_rn(rB, rB))));
-            if (__fadd_rn(gmin[s], ac) < eps_g) flagged |= 1u << s;
-        }
-    }
-    // exact pass (rare): one loop for all flagged spheres, centres read back
-    // from the warp's shared-memory copy
-    float m = kInf;
-    unsigned any = __ballot_sync(0xffffffffu, flagged != 0u);
-    while (any) {
-        unsigned bits = flagged;
-        flagged = 0u;
-        if (bits) {
-            const int s = __ffs(bits) - 1;
-            flagged = bits & (bits - 1u);
-            const float4 o = S.own[(s0 + s) * 32 + lane];
-            const float3 c = make_float3(o.x, o.y, o.z);
-            const float r = S.sph[s0 + s].w;
-            const float rB = __fadd_rn(r, B);
-            for (int j = 0; j < nc; ++j) pair_exact(c, rB, r, S.other[list[j]], m);
-        }
-        any = __ballot_sync(0xffffffffu, flagged != 0u);
-    }
-    return m;
 }
 
-// centre of own sphere s from the packed -2c registers
-template <int NP>
-__device__ __forceinline__ float3 own_centre(const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
-                                             const f32x2 (&MZ)[NP], int s)
+// The warp's obstacle pairs left by the box tests: each (candidate, own
+// sphere) pair, one per lane, is tested against that own sphere's box over
+// the sub-batch; the pairs within r_p + B + margin of it are appended to the
+// block's list, whose exact distances all warps share after the block
+// barrier.  Pairs that do not fit the list are done here.
+template <int SPG>
+__device__ __forceinline__ void near_pairs(const Params &P, const RolloutSmem &S,
+                                           const unsigned short *list, int nc, int n_world,
+                                           float tw, float tn, int s0, int cnt, int lane,
+                                           unsigned need_nb)
 {
-    float x0, x1, y0, y1, z0, z1;
-    unpack2(MX[s / 2], x0, x1);
-    unpack2(MY[s / 2], y0, y1);
-    unpack2(MZ[s / 2], z0, z1);
-    return make_float3(-0.5f * ((s & 1) ? x1 : x0), -0.5f * ((s & 1) ? y1 : y0),
-                       -0.5f * ((s & 1) ? z1 : z0));
-}
-
-// The same minimum for a few candidates: their exact distances to every own
-// sphere, the square root only inside the ramp (for few candidates the
-// pre-test and the flags of clearance_pass cost more than the exact tests;
-// how few is the launch shape's exact_max).
-template <int NP>
-__device__ __forceinline__ float few_candidates(const RolloutSmem &S, const unsigned short *list,
-                                                int nc, float B, int s0, int cnt,
-                                                const f32x2 (&MX)[NP], const f32x2 (&MY)[NP],
-                                                const f32x2 (&MZ)[NP])
-{
-    float m = kInf;
-    for (int j = 0; j < nc; ++j) {
-        const float4 p = S.other[list[j]];
-#pragma unroll
-        for (int s = 0; s < 2 * NP; ++s)
+    const unsigned below = (1u << lane) - 1u;
+    const int np = nc * SPG;
+    for (int base = 0; base < np; base += 32) {
+        const int e = base + lane;
+        bool near = false;
+        int code = 0;
+        float t2 = 0.f;
+        if (e < np) {
+            const int j = e / SPG, s = e - j * SPG;
             if (s < cnt) {
-                const float r = S.sph[s0 + s].w, rB = __fadd_rn(r, B);
-                pair_exact(own_centre<NP>(MX, MY, MZ, s), rB, r, p, m);
+                const int k = list[j];
+                const float4 p = S.other[k];
+                const float4 bl = S.sbox[2 * (s0 + s)], bh = S.sbox[2 * (s0 + s) + 1];
+                const bool w = k < n_world;
+                const float t = p.w + (w ? tw : tn);
+                near = gap2(p, make_float3(bl.x, bl.y, bl.z), make_float3(bh.x, bh.y, bh.z)) < t * t;
+                const float tb = __fadd_rn(__fadd_rn(S.sph[s0 + s].w, w ? P.B_world : P.B), p.w);
+                t2 = __fmul_rn(tb, tb);
+                code = (s0 + s) | (k << 6) | ((w ? 0 : (int)S.seg[k]) << 18);
             }
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, near);
+        if (!mk) continue;
+        int at = 0;
+        if (lane == 0) at = atomicAdd(S.opn, __popc(mk));
+        at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & below);
+        const bool stored = near && at < kObstaclePairCap;
+        if (stored) S.opairs[at] = make_int2(code, __float_as_int(t2));
+        unsigned left = __ballot_sync(0xffffffffu, near && !stored);
+        while (left) {
+            const int b = __ffs(left) - 1;
+            left &= left - 1u;
+            obstacle_pair(P, S, __shfl_sync(0xffffffffu, code, b),
+                          __shfl_sync(0xffffffffu, t2, b), lane, need_nb);
+        }
     }
-    return m;
 }
 
 template <int SPG>
 __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmHdr &A,
                                               const RolloutSmem &S, int h, int n, bool valid,
                                               int g, int lane, int n_world, int n_aabb, int n_nb,
-                                              float *pose_out)
+                                              int n_cl, float *pose_out)
 {
     const int d = A.dof, K = A.K;
     const int s0 = g * SPG;
     const int cnt = max(0, min(SPG, A.ns - s0));
 
     // DH chain up to the last frame this group needs; the last warp always
-    // runs to the end effector for the pose cost.  Own centres are kept as
-    // packed pairs of -2c (padding far away, never tested).
-    constexpr int NP = (SPG + 1) / 2;
-    f32x2 MX[NP], MY[NP], MZ[NP];
+    // runs to the end effector for the pose cost.  Each own centre goes to
+    // shared memory, and its box over the warp's 32 samples (centre +-
+    // radius, warp-wide floating-point min / max, exact) to the sphere
+    // boxes; their union is the warp's box.
     Frame F;
 #pragma unroll
     for (int k = 0; k < 9; ++k) F.R[k] = S.base[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) F.t[k] = S.base[9 + k];
+    float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
     int f = 0;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        float cx[2], cy[2], cz[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int s = 2 * q + u;
-            if (s < cnt) {
-                const int fs = S.frame[s0 + s];
-                while (f < fs) {
-                    const float2 sc = S.sc[f * 32 + lane];
-                    frame_step_sc(F, sc.x, sc.y, S.dh[f], S.tw[f]);
-                    ++f;
-                }
-                const float3 c = sphere_centre(F, S.sph[s0 + s]);
-                cx[u] = -2.f * c.x; cy[u] = -2.f * c.y; cz[u] = -2.f * c.z;
-                S.own[(s0 + s) * 32 + lane] = make_float4(c.x, c.y, c.z, S.sph[s0 + s].w);
-            } else {
-                cx[u] = cy[u] = cz[u] = -2e15f;
+    for (int s = 0; s < SPG; ++s) {
+        if (s < cnt) {
+            const int fs = S.frame[s0 + s];
+            while (f < fs) {
+                const float2 sc = S.sc[f * 32 + lane];
+                frame_step_sc(F, sc.x, sc.y, S.dh[f], S.tw[f]);
+                ++f;
             }
+            const float4 sp = S.sph[s0 + s];
+            const float3 c = sphere_centre(F, sp);
+            S.own[(s0 + s) * 32 + lane] = make_float4(c.x, c.y, c.z, sp.w);
+            const float4 bl = make_float4(warp_min(c.x - sp.w), warp_min(c.y - sp.w),
+                                          warp_min(c.z - sp.w), 0.f);
+            const float4 bh = make_float4(warp_max(c.x + sp.w), warp_max(c.y + sp.w),
+                                          warp_max(c.z + sp.w), 0.f);
+            if (lane == 0) {
+                S.sbox[2 * (s0 + s)] = bl;
+                S.sbox[2 * (s0 + s) + 1] = bh;
+            }
+            lo.x = fminf(lo.x, bl.x); lo.y = fminf(lo.y, bl.y); lo.z = fminf(lo.z, bl.z);
+            hi.x = fmaxf(hi.x, bh.x); hi.y = fmaxf(hi.y, bh.y); hi.z = fmaxf(hi.z, bh.z);
         }
-        MX[q] = pack2(cx[0], cx[1]);
-        MY[q] = pack2(cy[0], cy[1]);
-        MZ[q] = pack2(cz[0], cz[1]);
     }
     if (g == kGroups - 1) {
         while (f < d) {
@@ -414,50 +380,34 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         }
         *pose_out = pose_cost(F, S.goal, S.goal + 3, P.w_rot);
     }
-
-    // box bounding each own sphere (centre +- radius) over the warp's 32
-    // samples (warp-wide floating-point min / max), kept for the self pass,
-    // and their union: the warp's box
-    float3 lo = make_float3(kInf, kInf, kInf), hi = make_float3(-kInf, -kInf, -kInf);
-    unsigned short *list = S.cand + g * S.cand_cap;
-    float *box = S.box + g * 8;
-    if (cnt > 0) {
-#pragma unroll
-        for (int s = 0; s < SPG; ++s)
-            if (s < cnt) {
-                const float3 c = own_centre<NP>(MX, MY, MZ, s);
-                const float r = S.sph[s0 + s].w;
-                const float4 bl = make_float4(warp_min(c.x - r), warp_min(c.y - r), warp_min(c.z - r), 0.f);
-                const float4 bh = make_float4(warp_max(c.x + r), warp_max(c.y + r), warp_max(c.z + r), 0.f);
-                if (lane == 0) {
-                    S.sbox[2 * (s0 + s)] = bl;
-                    S.sbox[2 * (s0 + s) + 1] = bh;
-                }
-                lo.x = fminf(lo.x, bl.x); lo.y = fminf(lo.y, bl.y); lo.z = fminf(lo.z, bl.z);
-                hi.x = fmaxf(hi.x, bh.x); hi.y = fmaxf(hi.y, bh.y); hi.z = fmaxf(hi.z, bh.z);
+    // with an arm-pair surrogate, a step whose predicted clearance to a
+    // neighbour's plan is at least B + margin needs no exact pass for it
+    // (its coordination term is zero); a plan published without joints
+    // always takes the exact pass.  need_nb: the neighbours this lane needs
+    // (the same in every warp); skip_nb: those no lane needs.
+    unsigned need_nb = ~0u, skip_nb = 0u;
+    if (A.pair_mask) {
+        for (int nb = 0; nb < n_nb; ++nb) {
+            const int ai = S.nb_arm[nb];
+            if ((A.pair_mask >> ai) & 1u) {
+                const bool need = valid && (D.board_valid[ai] != 1 ||
+                                            D.rhohat[A.off_kh * P.n_arms + (long long)ai * A.H * K +
+                                                     (long long)h * K + n] < P.B + A.pair_margin);
+                if (!need) need_nb &= ~(1u << nb);
+                if (!__any_sync(0xffffffffu, need)) skip_nb |= 1u << nb;
             }
-        if (lane == 0) {
-            box[0] = lo.x; box[1] = lo.y; box[2] = lo.z;
-            box[3] = hi.x; box[4] = hi.y; box[5] = hi.z;
         }
     }
-    // the obstacle passes below need only the warp's own spheres and box:
+    // the obstacle passes below need only the warp's own spheres and boxes:
     // they run before the barrier that publishes every group's centres to
     // the self pass, so a warp with a short kinematic chain spends the wait
     // for the longest one on its passes
     __syncwarp();
     if (cnt > 0) {
-
-        // world boxes (exact), then one pre-tested pass per sphere set over its
-        // candidates: the world spheres (slot 0, buffer B_world) and each
-        // published neighbour plan at this step (slot 2 + nb, buffer B)
-        // A box whose gap to the warp's bounding box is at least B_world +
-        // 1 mm is skipped: the signed distance of every own sphere to it is
-        // at least that gap (the sphere lies inside the warp box by its
-        // radius along each separating axis), so it is outside the ramp and
-        // changes no result.
-        // the world boxes and the neighbours' plan boxes near enough to
-        // matter, tested one per lane; the others are skipped
+        // world boxes (exact): a box whose gap to the warp's box is at least
+        // B_world + 1 mm is skipped (the signed distance of every own sphere
+        // to it is at least that gap, outside the ramp); the others are
+        // tested one per lane, then against every own sphere
         float mbox = kInf;
         for (int b0 = 0; b0 < n_aabb; b0 += 32) {
             const float tb = P.B_world + 1e-3f;
@@ -476,60 +426,32 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
                 const float4 bc = S.aabb[2 * b], bh = S.aabb[2 * b + 1];
 #pragma unroll
                 for (int s = 0; s < SPG; ++s)
-                    if (s < cnt)
-                        mbox = fminf(mbox, sphere_aabb(own_centre<NP>(MX, MY, MZ, s), S.sph[s0 + s].w,
-                                                       bc, bh));
+                    if (s < cnt) {
+                        const float4 o = S.own[(s0 + s) * 32 + lane];
+                        mbox = fminf(mbox, sphere_aabb(make_float3(o.x, o.y, o.z), o.w, bc, bh));
+                    }
             }
         }
-        unsigned nb_near;   // at most 31 neighbours
-        {
-            const float tn = P.B + S.marg[1];
-            bool nr = false;
-            if (lane < n_nb) {
-                const float4 pl = S.nbbox[2 * lane], ph = S.nbbox[2 * lane + 1];
-                const float gx = fmaxf(fmaxf(pl.x - hi.x, lo.x - ph.x), 0.f);
-                const float gy = fmaxf(fmaxf(pl.y - hi.y, lo.y - ph.y), 0.f);
-                const float gz = fmaxf(fmaxf(pl.z - hi.z, lo.z - ph.z), 0.f);
-                nr = gx * gx + gy * gy + gz * gz < tn * tn;
-            }
-            nb_near = __ballot_sync(0xffffffffu, nr);
-        }
-        for (int ps = 0; ps <= n_nb; ++ps) {
-            const bool world = ps == 0;
-            const int k0 = world ? 0 : S.nb_start[ps - 1];
-            const int k1 = world ? n_world : S.nb_start[ps];
-            const float Bp = world ? P.B_world : P.B;
-            // with an arm-pair surrogate, a step whose predicted clearance to
-            // this neighbour's plan is at least B + margin skips the exact
-            // pass (its coordination term is zero); a plan published without
-            // joints always takes the exact pass
-            // a neighbour whose plan box is at least B + margin from the warp's
-            // box has every plan sphere culled: no candidate, no term
-            if (!world && !((nb_near >> (ps - 1)) & 1u)) continue;
-            bool need = true;
-            if (!world) {
-                const int ai = S.nb_arm[ps - 1];
-                if ((A.pair_mask >> ai) & 1u)
-                    need = valid && (D.board_valid[ai] != 1 ||
-                                     D.rhohat[A.off_kh * P.n_arms + (long long)ai * A.H * K +
-                                              (long long)h * K + n] < P.B + A.pair_margin);
-                if (!__any_sync(0xffffffffu, need)) continue;
-            }
-            const int nc = cull(S, k0, k1, Bp, world ? S.marg[0] : S.marg[1], box, lane, list);
-            // nc is warp-uniform
-            float m = nc > P.exact_max
-                          ? clearance_pass<NP>(S, list, nc, Bp, P.eps_g, s0, cnt, lane, MX, MY, MZ)
-                      : nc > 0 ? few_candidates<NP>(S, list, nc, Bp, s0, cnt, MX, MY, MZ)
-                               : kInf;
-            if (world) m = fminf(m, mbox);
-            if (need && m < Bp)
-                atomicMin(&S.red[(world ? 0 : ps + 1) * 32 + lane], float_to_ordered(m));
-        }
+        if (mbox < P.B_world) atomicMin(&S.red[lane], float_to_ordered(mbox));
+
+        const float tw = __fadd_rn(P.B_world, kCullMargin), tn = __fadd_rn(P.B, kCullMargin);
+        unsigned short *list = S.cand + g * S.cand_cap;
+        const int nc = cull_clusters(S, lo, hi, n_cl, n_world, tw, tn, skip_nb, lane, list);
+        if (nc > 0) near_pairs<SPG>(P, S, list, nc, n_world, tw, tn, s0, cnt, lane, need_nb);
     }
 
-    // every group's centres and sphere boxes are in shared memory
+    // every group's centres and sphere boxes, and the block's obstacle pairs,
+    // are in shared memory
     __syncthreads();
 
+    // the obstacle pairs of every warp, split evenly over the warps
+    {
+        const int no = min(*S.opn, kObstaclePairCap);
+        for (int i = g; i < no; i += kGroups) {
+            const int2 e = S.opairs[i];
+            obstacle_pair(P, S, e.x, __int_as_float(e.y), lane, need_nb);
+        }
+    }
     // self collision: the arm's pair list, split evenly over the 8 warps.  With
     // a learned surrogate, a rollout step whose predicted clearance is at least
     // B_self + margin skips the exact pass (its self term is zero); the warp
@@ -601,33 +523,33 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     RolloutSmem S;
     const int red_stride = (2 + NA) * 32;
     {
+        // the same layout as rollout_smem_bytes
         unsigned char *p = smraw;
-        const size_t n_other = (size_t)P.world_cap + (size_t)P.max_ns * NA;
+        const size_t n_other = (size_t)rollout_other_cap(P, NA);
+        const size_t n_cl = (size_t)rollout_cluster_cap(P, NA);
         S.other = (float4 *)p;     p += align16(sizeof(float4) * n_other);
         S.aabb = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.aabb_cap);
         S.sph = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns);
         S.own = (float4 *)p;       p += align16(sizeof(float4) * P.max_ns * 32);
-        S.other_w = (float *)p;    p += align16(sizeof(float) * n_other);
-        S.pa = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
-        S.pb = (ulonglong2 *)p;    p += align16(sizeof(ulonglong2) * n_other);
-        S.pc = (unsigned long long *)p; p += align16(sizeof(unsigned long long) * n_other);
+        S.cbox = (float4 *)p;      p += align16(sizeof(float4) * 2 * n_cl);
+        S.sbox = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.max_ns);
         S.frame = (int *)p;        p += align16(sizeof(int) * P.max_ns);
         S.pairs = (int2 *)p;       p += align16(sizeof(int2) * P.max_pairs);
+        S.cinfo = (int *)p;        p += align16(sizeof(int) * n_cl);
         S.nb_start = (int *)p;     p += align16(sizeof(int) * (MRS_MAX_ARMS + 1));
+        S.nb_cstart = (int *)p;    p += align16(sizeof(int) * MRS_MAX_ARMS);
         S.nb_alpha = (float *)p;   p += align16(sizeof(float) * 2 * MRS_MAX_ARMS);
         S.nb_arm = (int *)p;       p += align16(sizeof(int) * MRS_MAX_ARMS);
-        S.sbox = (float4 *)p;      p += align16(sizeof(float4) * 2 * P.max_ns);
-        S.box = (float *)p;        p += align16(sizeof(float) * kGroups * 8);
-        S.marg = (float *)p;       p += align16(sizeof(float) * 2);
-        S.nbbox = (float4 *)p;     p += align16(sizeof(float4) * 2 * NA);
         S.sc = (float2 *)p;        p += align16(sizeof(float2) * 2 * kMaxDof * 32);
         S.dh = (float4 *)p;        p += align16(sizeof(float4) * kMaxDof);
         S.tw = (float2 *)p;        p += align16(sizeof(float2) * kMaxDof);
         S.base = (float *)p;       p += align16(sizeof(float) * 12);
         S.goal = (float *)p;       p += align16(sizeof(float) * 12);
+        S.seg = p;                 p += align16(n_other);
         S.cand = (unsigned short *)p;
-        S.cand_cap = rollout_cand_cap(P);
+        S.cand_cap = rollout_cand_cap(P, NA);
         p += align16(sizeof(unsigned short) * kGroups * S.cand_cap);
+        S.opairs = (int2 *)p;      p += align16(sizeof(int2) * kObstaclePairCap);
         S.red = (int *)p;
     }
     float2 *const sc_base = S.sc;   // [2][kMaxDof][32] by sub-batch parity
@@ -637,19 +559,18 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     __shared__ long long s_idx[32];   // and each sample's stage-cost offset
     __shared__ float s_qn[kMaxDof * 32];   // the next sub-batch's joint angles, copied ahead
     __shared__ ArmHdr s_ah[2];    // the unit arm's scalars, by unit parity
+    __shared__ int s_opn[2];      // obstacle pairs listed, by sub-batch parity
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
+    const int ncw = (n_world + 7) >> 3;   // world clusters
     const long long cycle = *D.cycle;
 
     // both minima buffers start at +inf; every sub-batch's cost stage resets
     // the entries it used, so they are +inf again when reused
     for (int k = threadIdx.x; k < 2 * red_stride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
+    if (threadIdx.x < 2) s_opn[threadIdx.x] = 0;
     __shared__ __align__(8) uint64_t s_bar;   // completion of the plan-slice copies
     uint32_t bar_phase = 0;
-    if (threadIdx.x == 1) {
-        S.marg[0] = 1e-3f + P.eps_g / P.B_world;
-        S.marg[1] = 1e-3f + P.eps_g / P.B;
-    }
     if (threadIdx.x == 0) {
         s_tile[0] = atomicAdd(&D.work[iter], 1);
         tc::mbar_init(&s_bar, 1);
@@ -675,10 +596,26 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             constexpr int kStage = kRolloutThreads - 64;
             const int tl = (int)threadIdx.x - 64;
             const float t_h = __fmaf_rn((float)(h + 1), P.dt, *D.world_t);
-            for (int k = tl; k < n_world; k += kStage) {
-                const float4 o = D.world[k], v = D.world_vel[k];
-                put_other(S, k, make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
-                                            __fmaf_rn(v.z, t_h, o.z), o.w));
+            // the world spheres at the step's time, and the box of each
+            // cluster of 8 (aligned groups of 8 lanes: the 192 staging
+            // threads keep a sphere's index and its lane congruent mod 32)
+            for (int k0 = tl - lane; k0 < n_world; k0 += kStage) {
+                const int k = k0 + lane;
+                float3 bl = make_float3(kInf, kInf, kInf), bh = make_float3(-kInf, -kInf, -kInf);
+                if (k < n_world) {
+                    const float4 o = D.world_s[k], v = D.world_vel_s[k];
+                    const float4 w = make_float4(__fmaf_rn(v.x, t_h, o.x), __fmaf_rn(v.y, t_h, o.y),
+                                                 __fmaf_rn(v.z, t_h, o.z), o.w);
+                    S.other[k] = w;
+                    bl = make_float3(w.x - w.w, w.y - w.w, w.z - w.w);
+                    bh = make_float3(w.x + w.w, w.y + w.w, w.z + w.w);
+                }
+                cluster_box(bl, bh);
+                if ((lane & 7) == 0 && k < n_world) {
+                    S.cbox[2 * (k >> 3)] = make_float4(bl.x, bl.y, bl.z, 0.f);
+                    S.cbox[2 * (k >> 3) + 1] = make_float4(bh.x, bh.y, bh.z, 0.f);
+                    S.cinfo[k >> 3] = k | (min(8, n_world - k) << 16);
+                }
             }
             for (int k = (tl + 128) % kStage; k < 2 * n_aabb; k += kStage) S.aabb[k] = D.aabb[k];
             {
@@ -726,16 +663,23 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
         }
         const unsigned mask = __ballot_sync(0xffffffffu, ok);
         const int nnb = __popc(mask);
-        int incl = ns_i;
+        const int ncl_i = (ns_i + 7) >> 3;   // clusters of the neighbour's plan slice
+        int incl = ns_i, inclc = ncl_i;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+            const int vc = __shfl_up_sync(0xffffffffu, inclc, o);
+            if (lane >= o) {
+                incl += v;
+                inclc += vc;
+            }
         }
         const int pos = __popc(mask & ((1u << lane) - 1u));   // this lane's neighbour slot
+        const int n_cl = ncw + __shfl_sync(0xffffffffu, inclc, 31);
         if (g == 1) {   // warp 0 may still be in the previous unit's cost stage
             if (ok) {
                 S.nb_start[pos] = n_world + incl - ns_i;
+                S.nb_cstart[pos] = ncw + inclc - ncl_i;
                 S.nb_arm[pos] = lane;
             }
             if (lane == 31) S.nb_start[nnb] = n_world + incl;
@@ -792,22 +736,27 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                 return;
             }
             bar_phase ^= 1u;
-            for (int k = threadIdx.x; k < n_plan; k += blockDim.x)
-                put_derived(S, n_world + k, S.other[n_world + k]);
-            // box of each neighbour's plan spheres (centre +- radius), one warp
-            // per neighbour
+            // the set of each neighbour's plan spheres and the box of each of
+            // its clusters of 8 (counted from the slice's start), one warp per
+            // neighbour
             for (int w = g; w < nnb; w += kGroups) {
-                float3 bl = make_float3(kInf, kInf, kInf), bh = make_float3(-kInf, -kInf, -kInf);
-                for (int k = S.nb_start[w] + lane; k < S.nb_start[w + 1]; k += 32) {
-                    const float4 q = S.other[k];
-                    bl.x = fminf(bl.x, q.x - q.w); bl.y = fminf(bl.y, q.y - q.w); bl.z = fminf(bl.z, q.z - q.w);
-                    bh.x = fmaxf(bh.x, q.x + q.w); bh.y = fmaxf(bh.y, q.y + q.w); bh.z = fmaxf(bh.z, q.z + q.w);
-                }
-                const float4 l4 = make_float4(warp_min(bl.x), warp_min(bl.y), warp_min(bl.z), 0.f);
-                const float4 h4 = make_float4(warp_max(bh.x), warp_max(bh.y), warp_max(bh.z), 0.f);
-                if (lane == 0) {
-                    S.nbbox[2 * w] = l4;
-                    S.nbbox[2 * w + 1] = h4;
+                const int st = S.nb_start[w], en = S.nb_start[w + 1], cs = S.nb_cstart[w];
+                for (int k0 = st; k0 < en; k0 += 32) {
+                    const int k = k0 + lane;
+                    float3 bl = make_float3(kInf, kInf, kInf), bh = make_float3(-kInf, -kInf, -kInf);
+                    if (k < en) {
+                        const float4 q = S.other[k];
+                        S.seg[k] = (unsigned char)(2 + w);
+                        bl = make_float3(q.x - q.w, q.y - q.w, q.z - q.w);
+                        bh = make_float3(q.x + q.w, q.y + q.w, q.z + q.w);
+                    }
+                    cluster_box(bl, bh);
+                    if ((lane & 7) == 0 && k < en) {
+                        const int c = cs + ((k - st) >> 3);
+                        S.cbox[2 * c] = make_float4(bl.x, bl.y, bl.z, 0.f);
+                        S.cbox[2 * c + 1] = make_float4(bh.x, bh.y, bh.z, 0.f);
+                        S.cinfo[c] = k | (min(8, en - k) << 16) | ((2 + w) << 20);
+                    }
                 }
             }
         }
@@ -819,6 +768,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             RolloutSmem Sb = S;
             Sb.red = S.red + buf * red_stride;
             Sb.sc = sc_base + buf * (kMaxDof * 32);
+            Sb.opn = s_opn + buf;
             const int n = T.n0 + sb * 32 + lane;
             const bool valid = n < AH.K;
             // warp 0 uses the sub-batch's stop / joint-limit terms in its cost
@@ -844,14 +794,14 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             }
             float pose = 0.f;
             switch (AH.spg) {
-                case 1: rollout_group<1>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 2: rollout_group<2>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 3: rollout_group<3>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 4: rollout_group<4>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 5: rollout_group<5>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 6: rollout_group<6>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                case 7: rollout_group<7>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
-                default: rollout_group<8>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, &pose); break;
+                case 1: rollout_group<1>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 2: rollout_group<2>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 3: rollout_group<3>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 4: rollout_group<4>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 5: rollout_group<5>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 6: rollout_group<6>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 7: rollout_group<7>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                default: rollout_group<8>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
             }
             if (g == kGroups - 1) s_pose[buf][lane] = pose;
             if (next) {
@@ -884,8 +834,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                     c = __fmaf_rn(P.w_dyn, dyn, c);
                     D.stage[idx] = c;
                 }
-                // this lane's minima are read: +inf again for their next use
+                // this lane's minima are read: +inf again for their next use,
+                // and the obstacle-pair list of this parity is empty again
                 for (int k = lane; k < (2 + n_nb) * 32; k += 32) Sb.red[k] = float_to_ordered(kInf);
+                if (lane == 0) *Sb.opn = 0;
             }
         }
     }

@@ -53,7 +53,7 @@ class MrsStepOut(C.Structure):
 
 class MrsRolloutShape(C.Structure):
     _fields_ = [("tile_samples", C.c_int), ("blocks_per_sm", C.c_int), ("order", C.c_int),
-                ("exact_max", C.c_int), ("cycle_ms", C.c_float)]
+                ("cycle_ms", C.c_float)]
 
 
 class MrsSizes(C.Structure):
@@ -356,29 +356,28 @@ class Controller:
         self._check(self.L.mrs_kernel_times(self.h, _pf(ms), C.byref(n)), "kernel_times")
         return ms[:n.value].copy()
 
-    def set_rollout_shape(self, tile_samples=32, blocks_per_sm=0, order=0, exact_max=2):
-        sh = MrsRolloutShape(tile_samples, blocks_per_sm, order, exact_max, 0.0)
+    def set_rollout_shape(self, tile_samples=32, blocks_per_sm=0, order=0):
+        sh = MrsRolloutShape(tile_samples, blocks_per_sm, order, 0.0)
         self._check(self.L.mrs_set_rollout_shape(self.h, C.byref(sh)), "set_rollout_shape")
 
     def rollout_shape(self):
-        """(tile_samples, blocks_per_sm, order, exact_max) and the maximum
-        blocks per SM."""
+        """(tile_samples, blocks_per_sm, order) and the maximum blocks per SM."""
         sh = MrsRolloutShape()
         mx = C.c_int()
         self._check(self.L.mrs_get_rollout_shape(self.h, C.byref(sh), C.byref(mx)), "get_rollout_shape")
-        return (sh.tile_samples, sh.blocks_per_sm, sh.order, sh.exact_max), mx.value
+        return (sh.tile_samples, sh.blocks_per_sm, sh.order), mx.value
 
     def autotune(self, reps=5):
         """Time every rollout shape, keep the fastest; returns (best, table)
         as dicts with tile_samples, blocks_per_sm, order, cycle_ms."""
-        tab = (MrsRolloutShape * 256)()
+        tab = (MrsRolloutShape * 64)()
         n = C.c_int()
         best = MrsRolloutShape()
-        self._check(self.L.mrs_autotune(self.h, int(reps), tab, 256, C.byref(n), C.byref(best)),
+        self._check(self.L.mrs_autotune(self.h, int(reps), tab, 64, C.byref(n), C.byref(best)),
                     "autotune")
         conv = lambda x: dict(tile_samples=x.tile_samples, blocks_per_sm=x.blocks_per_sm,
-                              order=x.order, exact_max=x.exact_max, cycle_ms=float(x.cycle_ms))
-        return conv(best), [conv(tab[i]) for i in range(min(n.value, 256))]
+                              order=x.order, cycle_ms=float(x.cycle_ms))
+        return conv(best), [conv(tab[i]) for i in range(min(n.value, 64))]
 
     def save_state(self) -> bytes:
         buf = (C.c_char * int(self.sizes.state_bytes))()

@@ -1,6 +1,5 @@
-"""The largest sizes include/mrs.h allows, each on its own, against the
-oracle; 32 arms of 64 spheres together; and a combination whose
-shared-memory staging cannot fit one block."""
+"""The largest sizes include/mrs.h allows, each on its own and all at once,
+against the oracle."""
 import math
 
 import numpy as np
@@ -74,23 +73,20 @@ def test_most_samples():
     _replay(sc, cycles=1)
 
 
-def test_staging_beyond_one_block_is_unsupported():
-    """32 arms of 64 spheres stage a step's plans (31 x 64 spheres) in one
-    block's shared memory and run a replayed cycle; with a full world of 1024
-    spheres on top the staging no longer fits: mrs_set_world refuses with
-    MRS_EUNSUPPORTED, says why, and the context keeps its previous world."""
-    from paper_2602_10114_gb300 import mrs
+def test_every_limit_at_once():
+    """32 arms of 64 spheres (9 DoF) among MRS_MAX_WORLD_SPHERES spheres and
+    MRS_MAX_AABBS boxes: the largest staging the header allows (a step's 31
+    published plans of 64 spheres and the full world, with their clusters and
+    candidate lists) fits one block's shared memory, and two replayed cycles
+    (the second stages the published plans) match the oracle."""
     rng = np.random.default_rng(3)
     geo = S.random_geometry(rng, 9, per_link=7, tool_spheres=1)
+    assert len(geo["sphere_body"]) == 64
     arms = [S._make_arm(geo, 9, 32, 4, (2.0 * math.cos(2 * math.pi * a / 32),
                                         2.0 * math.sin(2 * math.pi * a / 32), 0.0), 0.0)
             for a in range(32)]
     world = np.concatenate([rng.uniform([-2.5, -2.5, 0.0], [2.5, 2.5, 1.5], (1024, 3)),
                             rng.uniform(0.02, 0.05, (1024, 1))], axis=1)
-    sc = _scenario(arms, world[:16], np.zeros((0, 6)))
-    _replay(sc, cycles=2)              # the second cycle stages 31 published plans
-    ctl = mrs.Controller(sc)
-    ctl.set_world()
-    with pytest.raises(mrs.MrsError) as e:
-        ctl.set_world(world.astype(np.float32), None, np.zeros((0, 6), np.float32))
-    assert e.value.status == 6 and "shared memory" in str(e.value)
+    boxes = np.concatenate([rng.uniform([-2.5, -2.5, 0.0], [2.5, 2.5, 1.5], (64, 3)),
+                            rng.uniform(0.02, 0.06, (64, 3))], axis=1)
+    _replay(_scenario(arms, world, boxes), cycles=2)

@@ -34,16 +34,15 @@ def _controller(sc):
 def test_every_shape_gives_the_same_cycle():
     """Sixteen uneven arms, with ragged sample counts (K = 16, 80, 100, ...):
     outputs and per-sample costs of one cycle from the same state are bitwise
-    equal under every shape, including every exact_max (pre-tested or
-    all-exact clearance passes give the same minima)."""
+    equal under every shape."""
     sc = S.shrink(S.config(4), K_div=16)
     sc.arms[1].K, sc.arms[5].K = 80, 100
     ctl, gp, gR = _controller(sc)
     ctl.step(sc.q0, sc.qd0, gp, gR)
     blob = ctl.save_state()
-    _, mx = ctl.rollout_shape()
+    (_, _, _), mx = ctl.rollout_shape()
     shapes = [(32, 0, 0), (64, 0, 0), (128, 0, 1), (96, 1, 1), (256, min(2, mx), 0), (32, 1, 1),
-              (64, 0, 2), (32, 0, 0, 0), (64, 0, 1, 8), (128, 0, 2, 32), (256, 1, 0, 64)]
+              (64, 0, 2)]
     ref = None
     for sh in shapes:
         ctl.load_state(blob)
@@ -62,9 +61,8 @@ def test_every_shape_gives_the_same_cycle():
 def test_shape_out_of_range_is_rejected():
     from paper_2602_10114_gb300 import mrs
     ctl, _, _ = _controller(S.config(1))
-    _, mx = ctl.rollout_shape()
-    for sh in [(16, 0, 0), (48, 0, 0), (288, 0, 0), (32, mx + 1, 0), (32, 0, 3), (32, -1, 0),
-               (32, 0, 0, -1), (32, 0, 0, 65)]:
+    (_, _, _), mx = ctl.rollout_shape()
+    for sh in [(16, 0, 0), (48, 0, 0), (288, 0, 0), (32, mx + 1, 0), (32, 0, 3), (32, -1, 0)]:
         with pytest.raises(mrs.MrsError) as e:
             ctl.set_rollout_shape(*sh)
         assert e.value.status == 1
@@ -80,12 +78,11 @@ def test_autotune_keeps_the_fastest_and_restores_the_state():
     ctl.step(sc.q0, sc.qd0, gp, gR)
     blob = ctl.save_state()
     best, tab = ctl.autotune(reps=3)
-    _, mx = ctl.rollout_shape()
-    assert len(tab) == 6 * mx * 3 * 3
+    (_, _, _), mx = ctl.rollout_shape()
+    assert len(tab) == 6 * mx * 3
     assert all(t["cycle_ms"] > 0 for t in tab)
     assert best["cycle_ms"] == min(t["cycle_ms"] for t in tab)
-    assert ctl.rollout_shape()[0] == (best["tile_samples"], best["blocks_per_sm"], best["order"],
-                                      best["exact_max"])
+    assert ctl.rollout_shape()[0] == (best["tile_samples"], best["blocks_per_sm"], best["order"])
     assert ctl.save_state() == blob
     # the next cycle equals the one the untuned controller runs
     ref, _, _ = _controller(sc)
