@@ -336,9 +336,10 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
  *                  at the step) are staged once, the samples pass through
  *                  in groups of 32;
  *   blocks_per_sm  resident blocks of the persistent grid per SM, 1 ..
- *                  max_blocks_per_sm (0 = the maximum); up to two use the
- *                  kernel built with the larger register budget, three the
- *                  one built for three resident blocks;
+ *                  max_blocks_per_sm (0 = the maximum, at most 4, set by
+ *                  the rollout's shared memory); up to two use the kernel
+ *                  built with the largest register budget, three and four
+ *                  the ones built for three and four resident blocks;
  *   order          0 step-major work list (all arms' units of step h, then
  *                  h + 1: concurrent blocks share the step's plans), 1
  *                  arm-major, 2 step-major from the last step (the later

@@ -46,7 +46,7 @@ struct LaunchPlan {
     bool merge_prep;    // Sense + Shift inside the first sample launch (every arm of at most
                         // 1024 samples) instead of a kernel of their own
     int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)
-    int rollout_variant;   // register budget of the rollout kernel: 2 or 3 blocks per SM
+    int rollout_variant;   // register budget of the rollout kernel: 2, 3 or 4 blocks per SM
     int *done_counter;  // last-block-done counter of k_toplan
     int n_surrogates;
     SurrogateSlot surrogates[MRS_MAX_ARMS];

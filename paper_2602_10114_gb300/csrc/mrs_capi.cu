@@ -214,7 +214,7 @@ static void set_rollout_grid(mrs_ctx *c)
     const int bps = c->blocks_per_sm > 0 ? std::min(c->blocks_per_sm, c->max_blocks_per_sm)
                                          : c->max_blocks_per_sm;
     c->L.rollout_grid = bps * c->num_sms;
-    c->L.rollout_variant = bps >= 3 ? 3 : 2;
+    c->L.rollout_variant = bps >= 4 ? 4 : bps >= 3 ? 3 : 2;
 }
 
 // every optimised arm has at most kSmallArmK samples: Sense + Shift inside

@@ -26,21 +26,24 @@ size_t rollout_smem_bytes(const Params &P, int n_arms)
 
 cudaError_t configure_rollout(const LaunchPlan &L)
 {
-    const cudaError_t e = rollout_configure_t<3>(L.smem_rollout);
-    return e != cudaSuccess ? e : rollout_configure_mb2(L.smem_rollout);
+    cudaError_t e = rollout_configure_t<3>(L.smem_rollout);
+    if (e == cudaSuccess) e = rollout_configure_mb2(L.smem_rollout);
+    return e != cudaSuccess ? e : rollout_configure_mb4(L.smem_rollout);
 }
 
-// Resident blocks per SM: the larger of the two variants' (the three-block
+// Resident blocks per SM: the largest of the variants' (the four-block
 // variant's, unless its shared memory does not fit)
 int rollout_blocks_per_sm(size_t smem)
 {
-    return std::max(rollout_occupancy_t<3>(smem), rollout_occupancy_mb2(smem));
+    return std::max(std::max(rollout_occupancy_t<3>(smem), rollout_occupancy_mb2(smem)),
+                    std::min(4, rollout_occupancy_mb4(smem)));
 }
 
 cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                            cudaStream_t s, bool pdl)
 {
     if (L.rollout_variant == 2) return rollout_launch_mb2(P, D, L, iter, s, pdl);
+    if (L.rollout_variant == 4) return rollout_launch_mb4(P, D, L, iter, s, pdl);
     return rollout_launch_t<3>(P, D, L, iter, s, pdl);
 }
 

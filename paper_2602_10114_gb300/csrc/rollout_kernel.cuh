@@ -86,8 +86,7 @@ struct RolloutSmem {
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Other spheres of a unit at most (the world, every other arm's plan slice),
-// their clusters, and the capacity of a warp's candidate list (all of them,
-// rounded up to 8).
+// their clusters, and the capacity of a warp's candidate list.
 __host__ __device__ inline int rollout_other_cap(const Params &P, int n_arms)
 {
     return P.world_cap + P.max_ns * n_arms;
@@ -96,9 +95,9 @@ __host__ __device__ inline int rollout_cluster_cap(const Params &P, int n_arms)
 {
     return (P.world_cap + 7) / 8 + n_arms * ((P.max_ns + 7) / 8);
 }
-__host__ __device__ inline int rollout_cand_cap(const Params &P, int n_arms)
+__host__ __device__ inline int rollout_cand_cap(const Params &, int)
 {
-    return (rollout_other_cap(P, n_arms) + 7) & ~7;
+    return 128;   // a warp's candidate list; when full, its pairs are taken at once
 }
 
 // mbarrier arrive with an expected transaction count (the bytes of the bulk
@@ -189,72 +188,6 @@ __device__ __forceinline__ void pair_exact_t2(float4 c1, float4 c2, float t2, fl
     if (d2 < t2) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), c1.w), c2.w));
 }
 
-// Candidates of a warp: the other spheres (every set) within r_p + B + margin
-// of the warp's box [lo, hi] (each own centre +- its radius over the 32
-// lanes), found cluster by cluster.  A cluster whose box is farther than
-// B + margin from the warp's box holds no candidate: each of its spheres
-// lies in the cluster box by its radius, so its centre is farther than
-// r_p + B + margin from the warp's box.  Near clusters are taken four at a
-// time, lanes 8i .. 8i + 7 on the i-th, their spheres tested one per lane.
-// Sets that no lane of the warp needs (skip_nb, bit nb for neighbour nb) are
-// left out.  The candidates come in increasing index order, so each set's
-// are contiguous; returns their number (warp-uniform).  tw, tn: B + margin of
-// the world and of the plan sets.
-__device__ __forceinline__ int cull_clusters(const RolloutSmem &S, float3 lo, float3 hi,
-                                             int n_cl, int n_world, float tw, float tn,
-                                             unsigned skip_nb, int lane, unsigned short *list)
-{
-    const float tc = fmaxf(tw, tn);
-    const float tc2 = tc * tc;
-    const unsigned below = (1u << lane) - 1u;
-    int nc = 0;
-    for (int c0 = 0; c0 < n_cl; c0 += 32) {
-        const int c = c0 + lane;
-        bool near = false;
-        if (c < n_cl) {
-            const float4 cl = S.cbox[2 * c], ch = S.cbox[2 * c + 1];
-            const float gx = fmaxf(fmaxf(cl.x - hi.x, lo.x - ch.x), 0.f);
-            const float gy = fmaxf(fmaxf(cl.y - hi.y, lo.y - ch.y), 0.f);
-            const float gz = fmaxf(fmaxf(cl.z - hi.z, lo.z - ch.z), 0.f);
-            near = gx * gx + gy * gy + gz * gz < tc2;
-            if (skip_nb) {
-                const int set = S.cinfo[c] >> 20;
-                if (set >= 2 && ((skip_nb >> (set - 2)) & 1u)) near = false;
-            }
-        }
-        unsigned mc = __ballot_sync(0xffffffffu, near);
-        while (mc) {
-            // the (lane / 8)-th lowest near cluster left, then drop four
-            unsigned x = mc;
-            const int i = lane >> 3;
-            if (i >= 1) x &= x - 1u;
-            if (i >= 2) x &= x - 1u;
-            if (i >= 3) x &= x - 1u;
-            mc &= mc - 1u;
-            mc &= mc - 1u;
-            mc &= mc - 1u;
-            mc &= mc - 1u;
-            bool keep = false;
-            int k = 0;
-            if (x) {
-                const int info = S.cinfo[c0 + __ffs(x) - 1];
-                const int r = lane & 7;
-                if (r < ((info >> 16) & 15)) {
-                    k = (info & 0xffff) + r;
-                    const float4 p = S.other[k];
-                    const float t = p.w + (k < n_world ? tw : tn);
-                    keep = gap2(p, lo, hi) < t * t;
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) list[nc + __popc(m & below)] = (unsigned short)k;
-            nc += __popc(m);
-        }
-    }
-    __syncwarp();
-    return nc;
-}
-
 // Exact distance of one obstacle pair (own sphere, other sphere p) for this
 // lane's sample, the square root only inside the ramp, and its minimum into
 // the set's slot of the per-lane minima (world 0, neighbour nb at 2 + nb)
@@ -324,6 +257,80 @@ __device__ __forceinline__ void near_pairs(const Params &P, const RolloutSmem &S
                           __shfl_sync(0xffffffffu, t2, b), lane, need_nb);
         }
     }
+}
+
+// The warp's obstacle pairs: candidates first, the other spheres (every set)
+// within r_p + B + margin of the warp's box [lo, hi] (each own centre +- its
+// radius over the 32 lanes), found cluster by cluster.  A cluster whose box is farther than
+// B + margin from the warp's box holds no candidate: each of its spheres
+// lies in the cluster box by its radius, so its centre is farther than
+// r_p + B + margin from the warp's box.  Near clusters are taken four at a
+// time, lanes 8i .. 8i + 7 on the i-th, their spheres tested one per lane.
+// Sets that no lane of the warp needs (skip_nb, bit nb for neighbour nb) are
+// left out.  The candidates go through near_pairs whenever the warp's list
+// is full, and at the end.  tw, tn: B + margin of the world and of the plan
+// sets.
+template <int SPG>
+__device__ __forceinline__ void obstacle_pairs(const Params &P, const RolloutSmem &S, float3 lo,
+                                               float3 hi, int n_cl, int n_world, float tw,
+                                               float tn, unsigned skip_nb, int s0, int cnt,
+                                               int lane, unsigned need_nb, unsigned short *list)
+{
+    const float tc = fmaxf(tw, tn);
+    const float tc2 = tc * tc;
+    const unsigned below = (1u << lane) - 1u;
+    int nc = 0;
+    for (int c0 = 0; c0 < n_cl; c0 += 32) {
+        const int c = c0 + lane;
+        bool near = false;
+        if (c < n_cl) {
+            const float4 cl = S.cbox[2 * c], ch = S.cbox[2 * c + 1];
+            const float gx = fmaxf(fmaxf(cl.x - hi.x, lo.x - ch.x), 0.f);
+            const float gy = fmaxf(fmaxf(cl.y - hi.y, lo.y - ch.y), 0.f);
+            const float gz = fmaxf(fmaxf(cl.z - hi.z, lo.z - ch.z), 0.f);
+            near = gx * gx + gy * gy + gz * gz < tc2;
+            if (skip_nb) {
+                const int set = S.cinfo[c] >> 20;
+                if (set >= 2 && ((skip_nb >> (set - 2)) & 1u)) near = false;
+            }
+        }
+        unsigned mc = __ballot_sync(0xffffffffu, near);
+        while (mc) {
+            // the (lane / 8)-th lowest near cluster left, then drop four
+            unsigned x = mc;
+            const int i = lane >> 3;
+            if (i >= 1) x &= x - 1u;
+            if (i >= 2) x &= x - 1u;
+            if (i >= 3) x &= x - 1u;
+            mc &= mc - 1u;
+            mc &= mc - 1u;
+            mc &= mc - 1u;
+            mc &= mc - 1u;
+            bool keep = false;
+            int k = 0;
+            if (x) {
+                const int info = S.cinfo[c0 + __ffs(x) - 1];
+                const int r = lane & 7;
+                if (r < ((info >> 16) & 15)) {
+                    k = (info & 0xffff) + r;
+                    const float4 p = S.other[k];
+                    const float t = p.w + (k < n_world ? tw : tn);
+                    keep = gap2(p, lo, hi) < t * t;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) list[nc + __popc(m & below)] = (unsigned short)k;
+            nc += __popc(m);
+            if (nc > S.cand_cap - 32) {   // no room for another step: take these now
+                __syncwarp();
+                near_pairs<SPG>(P, S, list, nc, n_world, tw, tn, s0, cnt, lane, need_nb);
+                __syncwarp();
+                nc = 0;
+            }
+        }
+    }
+    __syncwarp();
+    if (nc > 0) near_pairs<SPG>(P, S, list, nc, n_world, tw, tn, s0, cnt, lane, need_nb);
 }
 
 template <int SPG>
@@ -435,9 +442,8 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         if (mbox < P.B_world) atomicMin(&S.red[lane], float_to_ordered(mbox));
 
         const float tw = __fadd_rn(P.B_world, kCullMargin), tn = __fadd_rn(P.B, kCullMargin);
-        unsigned short *list = S.cand + g * S.cand_cap;
-        const int nc = cull_clusters(S, lo, hi, n_cl, n_world, tw, tn, skip_nb, lane, list);
-        if (nc > 0) near_pairs<SPG>(P, S, list, nc, n_world, tw, tn, s0, cnt, lane, need_nb);
+        obstacle_pairs<SPG>(P, S, lo, hi, n_cl, n_world, tw, tn, skip_nb, s0, cnt, lane, need_nb,
+                            S.cand + g * S.cand_cap);
     }
 
     // every group's centres and sphere boxes, and the block's obstacle pairs,
@@ -510,9 +516,9 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
 // more per work unit (inputs staged).  The next work unit's index is
 // fetched one unit ahead.
 //
-// The kernel is built for two register budgets: MB resident blocks per SM
-// (MB = 3: 80 registers per thread; MB = 2: up to 128, no spills), compiled
-// in separate translation units; the launch shape picks one.
+// The kernel is built for three register budgets: MB resident blocks per SM
+// (MB = 4: 64 registers per thread; MB = 3: 80; MB = 2: up to 128; none
+// spills), compiled in separate translation units; the launch shape picks one.
 template <int MB>
 __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D,
                                                                 const RolloutTile *tiles,
@@ -878,10 +884,14 @@ cudaError_t rollout_launch_t(const Params &P, const Dev &D, const LaunchPlan &L,
                     L.rollout_tiles, L.n_rollout_tiles, iter);
 }
 
-// the two-blocks-per-SM variant (rollout_mb2.cu)
+// the two- and four-blocks-per-SM variants (rollout_mb2.cu, rollout_mb4.cu)
 int rollout_occupancy_mb2(size_t smem);
 cudaError_t rollout_configure_mb2(size_t smem);
 cudaError_t rollout_launch_mb2(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
+                               cudaStream_t s, bool pdl);
+int rollout_occupancy_mb4(size_t smem);
+cudaError_t rollout_configure_mb4(size_t smem);
+cudaError_t rollout_launch_mb4(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                                cudaStream_t s, bool pdl);
 
 }  // namespace mrs

@@ -370,14 +370,15 @@ class Controller:
     def autotune(self, reps=5):
         """Time every rollout shape, keep the fastest; returns (best, table)
         as dicts with tile_samples, blocks_per_sm, order, cycle_ms."""
-        tab = (MrsRolloutShape * 64)()
+        cap = 6 * 4 * 3   # tile sizes x resident blocks (at most 4) x orders
+        tab = (MrsRolloutShape * cap)()
         n = C.c_int()
         best = MrsRolloutShape()
-        self._check(self.L.mrs_autotune(self.h, int(reps), tab, 64, C.byref(n), C.byref(best)),
+        self._check(self.L.mrs_autotune(self.h, int(reps), tab, cap, C.byref(n), C.byref(best)),
                     "autotune")
         conv = lambda x: dict(tile_samples=x.tile_samples, blocks_per_sm=x.blocks_per_sm,
                               order=x.order, cycle_ms=float(x.cycle_ms))
-        return conv(best), [conv(tab[i]) for i in range(min(n.value, 64))]
+        return conv(best), [conv(tab[i]) for i in range(min(n.value, cap))]
 
     def save_state(self) -> bytes:
         buf = (C.c_char * int(self.sizes.state_bytes))()

@@ -34,15 +34,16 @@ def _controller(sc):
 def test_every_shape_gives_the_same_cycle():
     """Sixteen uneven arms, with ragged sample counts (K = 16, 80, 100, ...):
     outputs and per-sample costs of one cycle from the same state are bitwise
-    equal under every shape."""
+    equal under every shape, including each number of resident blocks."""
     sc = S.shrink(S.config(4), K_div=16)
     sc.arms[1].K, sc.arms[5].K = 80, 100
     ctl, gp, gR = _controller(sc)
     ctl.step(sc.q0, sc.qd0, gp, gR)
     blob = ctl.save_state()
     (_, _, _), mx = ctl.rollout_shape()
+    # every register budget the context can launch (1-2, 3 and 4 blocks per SM)
     shapes = [(32, 0, 0), (64, 0, 0), (128, 0, 1), (96, 1, 1), (256, min(2, mx), 0), (32, 1, 1),
-              (64, 0, 2)]
+              (64, 0, 2)] + [(64, b, 1) for b in range(1, mx + 1)]
     ref = None
     for sh in shapes:
         ctl.load_state(blob)
