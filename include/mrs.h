@@ -331,7 +331,7 @@ mrs_status mrs_kernel_times(mrs_ctx *ctx, float *ms, int *n);
 
 /* Launch shape of the rollout (the kernel that runs FK, the collision passes
  * and the stage cost of every sampled step; the paper fixes no GPU mapping):
- *   tile_samples   samples per work unit, a multiple of 32 in [32, 256]: the
+ *   tile_samples   samples per work unit, a multiple of 32 in [32, 1024]: the
  *                  unit's inputs (world at the step's time, neighbour plans
  *                  at the step) are staged once, the samples pass through
  *                  in groups of 32;
@@ -355,7 +355,7 @@ typedef struct {
 mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape);
 mrs_status mrs_get_rollout_shape(mrs_ctx *ctx, mrs_rollout_shape *shape, int *max_blocks_per_sm);
 
-/* Autotuner: times every shape of the grid {32, 64, 96, 128, 192, 256}
+/* Autotuner: times every shape of the grid {32, 64, 128, 256, 512, 1024}
  * samples x 1 .. max resident blocks per SM x orders {0, 1, 2} over
  * `reps` whole control cycles each (the cycle as mrs_step_device runs it:
  * CUDA graph without per-stage timing, so programmatic launch overlaps the

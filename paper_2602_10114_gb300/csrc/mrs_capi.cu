@@ -207,8 +207,8 @@ static void build_rollout_tiles(mrs_ctx *c)
 }
 
 // persistent rollout grid and kernel variant for the shape's blocks per SM
-// (0 = the maximum): up to two blocks the variant with the larger register
-// budget, three the other
+// (0 = the maximum): up to two blocks the variant with the largest register
+// budget, three and four the variants built for them
 static void set_rollout_grid(mrs_ctx *c)
 {
     const int bps = c->blocks_per_sm > 0 ? std::min(c->blocks_per_sm, c->max_blocks_per_sm)
@@ -1574,7 +1574,7 @@ mrs_status mrs_set_rollout_shape(mrs_ctx *ctx, const mrs_rollout_shape *shape)
 {
     DeviceScope dev_scope(ctx);
     if (!ctx || !shape) return MRS_EINVAL;
-    if (shape->tile_samples < 32 || shape->tile_samples > 256 || shape->tile_samples % 32 ||
+    if (shape->tile_samples < 32 || shape->tile_samples > 1024 || shape->tile_samples % 32 ||
         shape->blocks_per_sm < 0 || shape->blocks_per_sm > ctx->max_blocks_per_sm ||
         shape->order < 0 || shape->order > 2)
         return fail(ctx, MRS_EINVAL, "rollout shape out of range");
@@ -1635,7 +1635,7 @@ mrs_status mrs_autotune(mrs_ctx *ctx, int reps, mrs_rollout_shape *table, int ca
     const mrs_rollout_shape before{ctx->tile_samples, ctx->blocks_per_sm, ctx->tile_order, 0.f};
     mrs_rollout_shape keep = before;
     float best_ms = INFINITY;
-    for (int ts : {32, 64, 96, 128, 192, 256}) {
+    for (int ts : {32, 64, 128, 256, 512, 1024}) {
         for (int bps = 1; bps <= ctx->max_blocks_per_sm && st == MRS_OK; ++bps) {
             for (int order = 0; order < 3 && st == MRS_OK; ++order) {
                 if ((st = apply_shape(ctx, ts, bps, order)) != MRS_OK) break;

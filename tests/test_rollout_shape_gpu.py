@@ -43,7 +43,7 @@ def test_every_shape_gives_the_same_cycle():
     (_, _, _), mx = ctl.rollout_shape()
     # every register budget the context can launch (1-2, 3 and 4 blocks per SM)
     shapes = [(32, 0, 0), (64, 0, 0), (128, 0, 1), (96, 1, 1), (256, min(2, mx), 0), (32, 1, 1),
-              (64, 0, 2)] + [(64, b, 1) for b in range(1, mx + 1)]
+              (64, 0, 2), (512, 0, 1), (1024, 0, 2)] + [(64, b, 1) for b in range(1, mx + 1)]
     ref = None
     for sh in shapes:
         ctl.load_state(blob)
@@ -63,7 +63,7 @@ def test_shape_out_of_range_is_rejected():
     from paper_2602_10114_gb300 import mrs
     ctl, _, _ = _controller(S.config(1))
     (_, _, _), mx = ctl.rollout_shape()
-    for sh in [(16, 0, 0), (48, 0, 0), (288, 0, 0), (32, mx + 1, 0), (32, 0, 3), (32, -1, 0)]:
+    for sh in [(16, 0, 0), (48, 0, 0), (1056, 0, 0), (32, mx + 1, 0), (32, 0, 3), (32, -1, 0)]:
         with pytest.raises(mrs.MrsError) as e:
             ctl.set_rollout_shape(*sh)
         assert e.value.status == 1
