@@ -828,7 +828,8 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                     const long long idx = s_idx[lane];
                     const float dw = ordered_to_float(Sb.red[0 * 32 + lane]);
                     const float dsf = ordered_to_float(Sb.red[1 * 32 + lane]);
-                    float dyn = 0.f;
+                    float dyn = 0.f;   // neighbours in order; four loads in flight
+#pragma unroll 4
                     for (int nb = 0; nb < n_nb; ++nb) {
                         const float rho = fmaxf(ordered_to_float(Sb.red[(2 + nb) * 32 + lane]), 0.f);
                         dyn = __fmaf_rn(S.nb_alpha[tp * MRS_MAX_ARMS + nb], ramp(rho, P.B), dyn);
