@@ -23,9 +23,6 @@
 
 namespace mrs {
 
-constexpr int kMaxWorld = MRS_MAX_WORLD_SPHERES;
-constexpr int kMaxAabb = MRS_MAX_AABBS;
-
 // ---------------------------------------------------------------------------
 // set-up
 

@@ -68,11 +68,11 @@ __device__ __forceinline__ bool plan_usable(const Params &P, int valid, long lon
 struct Dev {
     ArmDev *arms;
     float *input;          // packed per arm: q(d) qd(d) goal_p(3) goal_R(9)
-    float4 *world;         // [kMaxWorld] centre + radius
-    float4 *world_vel;     // [kMaxWorld] velocity (w unused)
+    float4 *world;         // [MRS_MAX_WORLD_SPHERES] centre + radius
+    float4 *world_vel;     // [MRS_MAX_WORLD_SPHERES] velocity (w unused)
     float4 *world_s;       // the same spheres in a spatial (Morton) order at the next
     float4 *world_vel_s;   // cycle's mid-horizon time, and their velocities: the rollout's copy
-    float4 *aabb;          // [kMaxAabb][2] centre, half extents
+    float4 *aabb;          // [MRS_MAX_AABBS][2] centre, half extents
     int *world_n;          // [2] spheres, boxes
     float *mu, *Sigma, *L; // state: [2][hd], [2][hdd] (by cycle parity), [hdd]
     long long st_hd, st_hdd;   // element offset of the second mu / Sigma buffer

@@ -519,7 +519,10 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
 // The kernel is built for three register budgets: MB resident blocks per SM
 // (MB = 4: 64 registers per thread; MB = 3: 80; MB = 2: up to 128; none
 // spills), compiled in separate translation units; the launch shape picks one.
-template <int MB>
+// SPG > 0 builds it for one sphere-group size only (every arm's spg equal):
+// the code of one group routine instead of eight keeps the hot instruction
+// footprint small; SPG = 0 dispatches on each arm's size.
+template <int MB, int SPG>
 __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D,
                                                                 const RolloutTile *tiles,
                                                                 int n_tiles, int iter)
@@ -799,7 +802,10 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                                   (valid_next ? n_next : 0));
             }
             float pose = 0.f;
-            switch (AH.spg) {
+            if constexpr (SPG > 0)
+                rollout_group<SPG>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl,
+                                   &pose);
+            else switch (AH.spg) {
                 case 1: rollout_group<1>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
                 case 2: rollout_group<2>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
                 case 3: rollout_group<3>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
@@ -857,10 +863,10 @@ template <int MB>
 int rollout_occupancy_t(size_t smem)
 {
     cudaFuncAttributes fa{};
-    if (raise_smem_limit((const void *)k_rollout<MB>, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_rollout<MB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    if (raise_smem_limit((const void *)k_rollout<MB, 0>, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rollout<MB, 0>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_rollout<MB>) != cudaSuccess)
+        cudaFuncGetAttributes(&fa, k_rollout<MB, 0>) != cudaSuccess)
         return 1;
     const int warps = kRolloutThreads / 32;
     const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
@@ -870,20 +876,32 @@ int rollout_occupancy_t(size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-template <int MB>
+template <int MB, int SPG>
 cudaError_t rollout_configure_t(size_t smem)
 {
-    return raise_smem_limit((const void *)k_rollout<MB>, smem);
+    const cudaError_t e = raise_smem_limit((const void *)k_rollout<MB, SPG>, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_rollout<MB, SPG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared);
 }
 
-template <int MB>
+template <int MB, int SPG>
 cudaError_t rollout_launch_t(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                              cudaStream_t s, bool pdl)
 {
     const int grid = L.n_rollout_tiles < L.rollout_grid ? L.n_rollout_tiles : L.rollout_grid;
-    return launch_k(k_rollout<MB>, grid, kRolloutThreads, L.smem_rollout, s, pdl, P, D,
+    return launch_k(k_rollout<MB, SPG>, grid, kRolloutThreads, L.smem_rollout, s, pdl, P, D,
                     L.rollout_tiles, L.n_rollout_tiles, iter);
 }
+
+// the builds for one sphere-group size (rollout_spg4.cu, rollout_spg5.cu):
+// all three register budgets of each, chosen by the launch's variant
+cudaError_t rollout_configure_spg4(size_t smem);
+cudaError_t rollout_launch_spg4(int variant, const Params &P, const Dev &D, const LaunchPlan &L,
+                                int iter, cudaStream_t s, bool pdl);
+cudaError_t rollout_configure_spg5(size_t smem);
+cudaError_t rollout_launch_spg5(int variant, const Params &P, const Dev &D, const LaunchPlan &L,
+                                int iter, cudaStream_t s, bool pdl);
 
 // the two- and four-blocks-per-SM variants (rollout_mb2.cu, rollout_mb4.cu)
 int rollout_occupancy_mb2(size_t smem);
