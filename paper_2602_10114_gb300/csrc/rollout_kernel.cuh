@@ -131,15 +131,6 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// exact distance of a candidate pair, as in the oracle: sqrt(d2) - r - r_p
-__device__ __forceinline__ void pair_exact(float3 c, float rB, float r, float4 p, float &m)
-{
-    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
-    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float t = __fadd_rn(rB, p.w);
-    if (d2 < __fmul_rn(t, t)) m = fminf(m, __fsub_rn(__fsub_rn(sqrtf(d2), r), p.w));
-}
-
 // minimum / maximum of a float over the full warp (sm_100+ floating-point
 // warp reduction; exact)
 __device__ __forceinline__ float warp_min(float v)
@@ -505,14 +496,15 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
 }
 
 // Per-block shared state read after the barrier that ends a sub-batch (the
-// per-lane minima, the end-effector pose cost) is double-buffered by
-// sub-batch parity, and the neighbour weights by work-unit parity, so that
-// warp 0's per-sample cost of one sub-batch overlaps the other warps' next
-// sub-batch (or the staging of the next unit) without a barrier between
-// them; the own centres are read only before that barrier and need one
-// buffer.  The joint sines and cosines are double-buffered as well: each
-// sub-batch computes the next one's behind its passes.  Two block barriers
-// per sub-batch of 32 samples (own centres written; minima complete), one
+// per-lane minima, the end-effector pose cost, the obstacle-pair count) is
+// double-buffered by sub-batch parity, and the neighbour weights by
+// work-unit parity, so that warp 0's per-sample cost of one sub-batch
+// overlaps the other warps' next sub-batch (or the staging of the next
+// unit) without a barrier between them; the own centres and the obstacle
+// pairs are read only before that barrier and need one buffer.  The joint
+// sines and cosines are double-buffered as well: each sub-batch computes the
+// next one's behind its passes.  Two block barriers per sub-batch of 32
+// samples (own centres and obstacle pairs written; minima complete), one
 // more per work unit (inputs staged).  The next work unit's index is
 // fetched one unit ahead.
 //
