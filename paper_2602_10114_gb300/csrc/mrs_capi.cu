@@ -204,6 +204,23 @@ static void build_rollout_tiles(mrs_ctx *c)
             if (!c->arms[a].external)
                 for (int h = 0; h < c->arms[a].H; ++h) push(a, h);
     }
+    // The list's last units (as many as the largest persistent grid has
+    // blocks) in quarters: the blocks take their last units at different
+    // times, and smaller pieces there even out when they finish.  Samples
+    // keep their lanes, so no result changes; the list stays shorter than
+    // the 32-sample one the workspace holds.
+    if (nsub >= 4 && c->num_sms > 0) {
+        auto &t = c->rollout_tiles;
+        const int tail = std::min((int)t.size(), 4 * c->num_sms);
+        std::vector<RolloutTile> out(t.begin(), t.end() - tail);
+        out.reserve(t.size() + 3 * (size_t)tail);
+        for (auto it = t.end() - tail; it != t.end(); ++it) {
+            const int q = (it->nsub + 3) / 4;
+            for (int k = 0; k < it->nsub; k += q)
+                out.push_back({it->arm, it->h, it->n0 + 32 * k, std::min(q, it->nsub - k)});
+        }
+        t.swap(out);
+    }
 }
 
 // persistent rollout grid and kernel variant for the shape's blocks per SM
