@@ -51,7 +51,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 CSRC = os.path.join(ROOT, "paper_2602_10114_gb300", "csrc")
 # the rollout kernel's sources: an ncu summary applies while their hash matches
 ROLLOUT_SOURCES = ["rollout_kernel.cuh", "rollout.cu", "rollout_mb2.cu", "rollout_mb4.cu",
-                   "rollout_spg4.cu", "rollout_spg5.cu", "mrs_device.cuh", "tc_gemm.cuh"]
+                   "rollout_spg4.cu", "rollout_spg5.cu", "rollout_spg57.cu", "mrs_device.cuh",
+                   "tc_gemm.cuh"]
 ROLLOUT_PROFILE = os.path.join(ROOT, "profiles", "k_rollout_8arms_K4096_H64.md")
 CPU_SAMPLE_K = 32        # samples per arm of the oracle's bounded sample
 

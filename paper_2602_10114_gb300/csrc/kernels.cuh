@@ -47,7 +47,7 @@ struct LaunchPlan {
                         // 1024 samples) instead of a kernel of their own
     int rollout_grid;   // persistent rollout blocks (resident blocks per SM x SMs)
     int rollout_variant;   // register budget of the rollout kernel: 2, 3 or 4 blocks per SM
-    int rollout_spg;       // the arms' common sphere-group size when a build for it exists, else 0
+    unsigned rollout_sizes;   // sphere-group sizes of the arms that roll out (bit s for size s)
     int *done_counter;  // last-block-done counter of k_toplan
     int n_surrogates;
     SurrogateSlot surrogates[MRS_MAX_ARMS];

@@ -566,14 +566,11 @@ mrs_status mrs_create(const mrs_config *cfg, void *stream, mrs_ctx **out)
     L.smem_sample = ss;
     L.smem_toplan = st2;
     L.smem_rollout = rollout_smem_bytes(P, ctx->A);
-    // the sphere-group size every rolled-out arm shares, when the rollout has
-    // a build for it (else the build that dispatches on each arm's size)
-    {
-        int common = -1;
-        for (const ArmDev &A : ctx->arms)
-            if (!A.external) common = (common == -1 || common == A.spg) ? A.spg : 0;
-        L.rollout_spg = (common == 4 || common == 5) ? common : 0;
-    }
+    // the sphere-group sizes of the arms that roll out: the launch takes the
+    // smallest rollout build that holds them all
+    L.rollout_sizes = 0;
+    for (const ArmDev &A : ctx->arms)
+        if (!A.external) L.rollout_sizes |= 1u << A.spg;
 
     if (stream) {
         ctx->stream = (cudaStream_t)stream;

@@ -26,11 +26,12 @@ size_t rollout_smem_bytes(const Params &P, int n_arms)
 
 cudaError_t configure_rollout(const LaunchPlan &L)
 {
-    cudaError_t e = rollout_configure_t<3, 0>(L.smem_rollout);
+    cudaError_t e = rollout_configure_t<3, kAllSizes>(L.smem_rollout);
     if (e == cudaSuccess) e = rollout_configure_mb2(L.smem_rollout);
     if (e == cudaSuccess) e = rollout_configure_mb4(L.smem_rollout);
     if (e == cudaSuccess) e = rollout_configure_spg4(L.smem_rollout);
-    return e != cudaSuccess ? e : rollout_configure_spg5(L.smem_rollout);
+    if (e == cudaSuccess) e = rollout_configure_spg5(L.smem_rollout);
+    return e != cudaSuccess ? e : rollout_configure_spg57(L.smem_rollout);
 }
 
 // Resident blocks per SM: the largest of the variants' (the four-block
@@ -44,11 +45,15 @@ int rollout_blocks_per_sm(size_t smem)
 cudaError_t launch_rollout(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                            cudaStream_t s, bool pdl)
 {
-    if (L.rollout_spg == 5) return rollout_launch_spg5(L.rollout_variant, P, D, L, iter, s, pdl);
-    if (L.rollout_spg == 4) return rollout_launch_spg4(L.rollout_variant, P, D, L, iter, s, pdl);
+    // the smallest build that holds the size of every arm that rolls out
+    const unsigned m = L.rollout_sizes;
+    if (m == kSizes5) return rollout_launch_spg5(L.rollout_variant, P, D, L, iter, s, pdl);
+    if (m == kSizes4) return rollout_launch_spg4(L.rollout_variant, P, D, L, iter, s, pdl);
+    if (m && (m & ~kSizes57) == 0)
+        return rollout_launch_spg57(L.rollout_variant, P, D, L, iter, s, pdl);
     if (L.rollout_variant == 2) return rollout_launch_mb2(P, D, L, iter, s, pdl);
     if (L.rollout_variant == 4) return rollout_launch_mb4(P, D, L, iter, s, pdl);
-    return rollout_launch_t<3, 0>(P, D, L, iter, s, pdl);
+    return rollout_launch_t<3, kAllSizes>(P, D, L, iter, s, pdl);
 }
 
 }  // namespace mrs

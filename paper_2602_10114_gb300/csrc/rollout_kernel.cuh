@@ -40,6 +40,17 @@ namespace mrs {
 // distance keeps
 constexpr float kCullMargin = 1e-3f;
 
+// every sphere-group size (bits 1 .. 8) for the build that serves any arms
+constexpr unsigned kAllSizes = 0x1FEu;
+
+// the size of a build that holds one sphere-group size, else 0
+constexpr int single_size(unsigned sizes)
+{
+    for (int s = 1; s <= 8; ++s)
+        if (sizes == (1u << s)) return s;
+    return 0;
+}
+
 // capacity of the block's list of obstacle pairs per sub-batch (a warp tests
 // the pairs that do not fit itself)
 constexpr int kObstaclePairCap = 512;
@@ -511,10 +522,11 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
 // The kernel is built for three register budgets: MB resident blocks per SM
 // (MB = 4: 64 registers per thread; MB = 3: 80; MB = 2: up to 128; none
 // spills), compiled in separate translation units; the launch shape picks one.
-// SPG > 0 builds it for one sphere-group size only (every arm's spg equal):
-// the code of one group routine instead of eight keeps the hot instruction
-// footprint small; SPG = 0 dispatches on each arm's size.
-template <int MB, int SPG>
+// SIZES is the set of sphere-group sizes the build holds (bit s for size s):
+// a build for the sizes the context's arms have (one or two group routines
+// instead of eight) keeps the hot instruction footprint small; kAllSizes
+// holds every size.
+template <int MB, unsigned SIZES>
 __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D,
                                                                 const RolloutTile *tiles,
                                                                 int n_tiles, int iter)
@@ -794,19 +806,24 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                                   (valid_next ? n_next : 0));
             }
             float pose = 0.f;
-            if constexpr (SPG > 0)
-                rollout_group<SPG>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl,
-                                   &pose);
+            // the group routine of the arm's size (only the sizes the build holds)
+#define MRS_GROUP(SZ)                                                                          \
+    if constexpr ((SIZES >> SZ) & 1u)                                                           \
+        rollout_group<SZ>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose)
+            if constexpr (single_size(SIZES) > 0)
+                rollout_group<single_size(SIZES)>(P, D, AH, Sb, h, n, valid, g, lane, n_world,
+                                                  n_aabb, n_nb, n_cl, &pose);
             else switch (AH.spg) {
-                case 1: rollout_group<1>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                case 2: rollout_group<2>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                case 3: rollout_group<3>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                case 4: rollout_group<4>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                case 5: rollout_group<5>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                case 6: rollout_group<6>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                case 7: rollout_group<7>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
-                default: rollout_group<8>(P, D, AH, Sb, h, n, valid, g, lane, n_world, n_aabb, n_nb, n_cl, &pose); break;
+                case 1: MRS_GROUP(1); break;
+                case 2: MRS_GROUP(2); break;
+                case 3: MRS_GROUP(3); break;
+                case 4: MRS_GROUP(4); break;
+                case 5: MRS_GROUP(5); break;
+                case 6: MRS_GROUP(6); break;
+                case 7: MRS_GROUP(7); break;
+                default: MRS_GROUP(8); break;
             }
+#undef MRS_GROUP
             if (g == kGroups - 1) s_pose[buf][lane] = pose;
             if (next) {
                 float2 *sc = sc_base + (buf ^ 1) * (kMaxDof * 32);
@@ -855,10 +872,10 @@ template <int MB>
 int rollout_occupancy_t(size_t smem)
 {
     cudaFuncAttributes fa{};
-    if (raise_smem_limit((const void *)k_rollout<MB, 0>, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_rollout<MB, 0>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    if (raise_smem_limit((const void *)k_rollout<MB, kAllSizes>, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rollout<MB, kAllSizes>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_rollout<MB, 0>) != cudaSuccess)
+        cudaFuncGetAttributes(&fa, k_rollout<MB, kAllSizes>) != cudaSuccess)
         return 1;
     const int warps = kRolloutThreads / 32;
     const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
@@ -868,32 +885,37 @@ int rollout_occupancy_t(size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-template <int MB, int SPG>
+template <int MB, unsigned SIZES>
 cudaError_t rollout_configure_t(size_t smem)
 {
-    const cudaError_t e = raise_smem_limit((const void *)k_rollout<MB, SPG>, smem);
+    const cudaError_t e = raise_smem_limit((const void *)k_rollout<MB, SIZES>, smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_rollout<MB, SPG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_rollout<MB, SIZES>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 cudaSharedmemCarveoutMaxShared);
 }
 
-template <int MB, int SPG>
+template <int MB, unsigned SIZES>
 cudaError_t rollout_launch_t(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                              cudaStream_t s, bool pdl)
 {
     const int grid = L.n_rollout_tiles < L.rollout_grid ? L.n_rollout_tiles : L.rollout_grid;
-    return launch_k(k_rollout<MB, SPG>, grid, kRolloutThreads, L.smem_rollout, s, pdl, P, D,
+    return launch_k(k_rollout<MB, SIZES>, grid, kRolloutThreads, L.smem_rollout, s, pdl, P, D,
                     L.rollout_tiles, L.n_rollout_tiles, iter);
 }
 
-// the builds for one sphere-group size (rollout_spg4.cu, rollout_spg5.cu):
-// all three register budgets of each, chosen by the launch's variant
+// the builds for a few sphere-group sizes (rollout_spg4.cu: 4, rollout_spg5.cu:
+// 5, rollout_spg57.cu: 5 and 7), all three register budgets of each, chosen by
+// the launch's variant; each build is used when it holds every arm's size
+constexpr unsigned kSizes4 = 1u << 4, kSizes5 = 1u << 5, kSizes57 = (1u << 5) | (1u << 7);
 cudaError_t rollout_configure_spg4(size_t smem);
 cudaError_t rollout_launch_spg4(int variant, const Params &P, const Dev &D, const LaunchPlan &L,
                                 int iter, cudaStream_t s, bool pdl);
 cudaError_t rollout_configure_spg5(size_t smem);
 cudaError_t rollout_launch_spg5(int variant, const Params &P, const Dev &D, const LaunchPlan &L,
                                 int iter, cudaStream_t s, bool pdl);
+cudaError_t rollout_configure_spg57(size_t smem);
+cudaError_t rollout_launch_spg57(int variant, const Params &P, const Dev &D, const LaunchPlan &L,
+                                 int iter, cudaStream_t s, bool pdl);
 
 // the two- and four-blocks-per-SM variants (rollout_mb2.cu, rollout_mb4.cu)
 int rollout_occupancy_mb2(size_t smem);

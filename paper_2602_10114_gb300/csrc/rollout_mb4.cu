@@ -7,12 +7,12 @@ namespace mrs {
 
 int rollout_occupancy_mb4(size_t smem) { return rollout_occupancy_t<4>(smem); }
 
-cudaError_t rollout_configure_mb4(size_t smem) { return rollout_configure_t<4, 0>(smem); }
+cudaError_t rollout_configure_mb4(size_t smem) { return rollout_configure_t<4, kAllSizes>(smem); }
 
 cudaError_t rollout_launch_mb4(const Params &P, const Dev &D, const LaunchPlan &L, int iter,
                                cudaStream_t s, bool pdl)
 {
-    return rollout_launch_t<4, 0>(P, D, L, iter, s, pdl);
+    return rollout_launch_t<4, kAllSizes>(P, D, L, iter, s, pdl);
 }
 
 }  // namespace mrs
