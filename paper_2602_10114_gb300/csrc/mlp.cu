@@ -268,6 +268,11 @@ struct mrs_mlp {
 
 static size_t pad16(size_t x) { return (x + 15) / 16 * 16; }
 
+// K chunks of 16 per weight-ring slot of the fused inference kernel: the
+// chunks of a slot share one barrier wait and one commit of the thread that
+// issues the MMAs
+static constexpr int kFusedGroup = 2;
+
 static mrs_status mlp_fail(mrs_mlp *m, mrs_status s, const std::string &why)
 {
     if (m) m->msg = why;
@@ -541,13 +546,15 @@ mrs_status mrs_mlp_create(int in_dim, int width, int layers, unsigned long long 
         n.width = width;
         n.layers = layers;
         n.chunk_bytes = (unsigned)width * 32u;
+        n.group = kFusedGroup;
+        n.slot_bytes = (unsigned)n.group * n.chunk_bytes;
         n.a_bytes = 128u * 2u * (unsigned)std::max(m->in_pad, width);
         n.tmem_cols = 32;
         while ((int)n.tmem_cols < width) n.tmem_cols *= 2;
         n.p_floats = (unsigned)(layers * width + width + 1);
         const long budget = 110 * 1024 - (long)n.a_bytes - (long)sizeof(fused::Ctl) -
                             (long)n.p_floats * 4 - 16;
-        n.slots = (int)std::max(2L, std::min((long)fused::kMaxSlots, budget / (long)n.chunk_bytes));
+        n.slots = (int)std::max(2L, std::min((long)fused::kMaxSlots, budget / (long)n.slot_bytes));
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||

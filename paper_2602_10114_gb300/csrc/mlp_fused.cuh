@@ -5,19 +5,24 @@
 // Per 128-row tile the CTA keeps the layer input A [128][K] (BF16, canonical
 // K-major layout without swizzle) in shared memory and the layer's
 // accumulator [128][width] (FP32) in tensor memory.  The weights stream
-// through a ring of shared-memory slots, one 16-wide K chunk of one layer per
-// slot, pre-packed in global memory in the same canonical layout so that
-// one cp.async.bulk moves a chunk.  Warp roles (320 threads):
+// through a ring of shared-memory slots, each holding `group` consecutive
+// 16-wide K chunks of one layer (fewer at the end of a layer), pre-packed in
+// global memory in the same canonical layout so that one cp.async.bulk
+// fills a slot.  One thread issues every MMA of the CTA, and each chunk costs
+// it a few hundred cycles of dependent instruction latency when it waits and
+// commits per chunk, longer than the tensor core takes for the chunk
+// (M = 128, N = 256, K = 16): a slot's chunks share one wait and one commit.
+// Warp roles (320 threads):
 //   warps 0-7  features of the tile into A; after each layer, bias + SiLU
 //              of the accumulator back into A (hidden layers) or the dot
 //              product with the output weights (last layer).  Warp w reads
 //              TMEM lanes 32 (w % 4) .. + 31 (one row per thread) and every
 //              other 16-column chunk, starting at chunk w / 4.
-//   warp 8     producer: the chunk sequence (tile, layer, chunk) into the
-//              ring, an mbarrier pair (full / empty) per slot.
+//   warp 8     producer: the slot sequence (tile, layer, chunk group) into
+//              the ring, an mbarrier pair (full / empty) per slot.
 //   warp 9     owns the TMEM allocation; one lane issues tcgen05.mma
-//              (M = 128, N = width, K = 16) per chunk, commits each to the
-//              slot's empty barrier and each layer to acc_full.
+//              (M = 128, N = width, K = 16) per chunk, commits each slot to
+//              its empty barrier and each layer to acc_full.
 // The weight sequence does not depend on the data, so the producer runs
 // ahead across layer and tile boundaries, bounded only by the ring depth.
 // Every wait is bounded; a timeout sets the error word and the shared abort
@@ -47,13 +52,15 @@ struct Net {
     int offWo, offBo;
     int in_pad, width, layers;
     int slots;                    // ring depth
+    int group;                    // K chunks per slot
     unsigned chunk_bytes;         // width * 16 * 2
+    unsigned slot_bytes;          // group * chunk_bytes
     unsigned a_bytes;             // 128 * max(in_pad, width) * 2
     unsigned tmem_cols;           // power of two >= max(32, width)
     unsigned p_floats;            // biases, output weights and bias: layers * width + width + 1
 };
 
-struct Ctl {                      // follows the A buffer and the ring
+struct alignas(16) Ctl {          // follows the A buffer and the ring
     uint64_t full[kMaxSlots], empty[kMaxSlots];
     uint64_t acc_full, a_ready, part_full, drain;
     float part[128];
@@ -61,10 +68,11 @@ struct Ctl {                      // follows the A buffer and the ring
     int abort;
 };
 
-// A buffer, weight ring, control block, then the FP32 biases and output layer
+// A buffer, weight ring, control block, then the FP32 halved biases and the
+// output layer (16-byte aligned: the control block's size is a multiple of 16)
 __host__ __device__ inline size_t smem_bytes(const Net &n)
 {
-    return (size_t)n.a_bytes + (size_t)n.slots * n.chunk_bytes + sizeof(Ctl) +
+    return (size_t)n.a_bytes + (size_t)n.slots * n.slot_bytes + sizeof(Ctl) +
            ((size_t)n.p_floats * 4 + 15) / 16 * 16;
 }
 
@@ -118,10 +126,11 @@ __device__ __forceinline__ void fail(Ctl &C, int *err)
 // z sigmoid(z) = h (1 + tanh h) with h = z / 2: one hardware tanh (relative
 // error about 2^-11, an absolute error of the result below 2^-12 |z|, the
 // order of the BF16 rounding that follows) instead of an exponential and a
-// reciprocal, which halves the special-function work of the epilogue
-__device__ __forceinline__ float silu(float z)
+// reciprocal, which halves the special-function work of the epilogue.  The
+// caller passes h = acc / 2 + bias / 2 (one FMA, the halved biases kept in
+// shared memory).
+__device__ __forceinline__ float silu_half(float h)
 {
-    const float h = 0.5f * z;
     float t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
     return fmaf(h, t, h);
@@ -258,12 +267,12 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *Abuf = smem;
     unsigned char *ring = smem + net.a_bytes;
-    Ctl &C = *reinterpret_cast<Ctl *>(ring + (size_t)net.slots * net.chunk_bytes);
+    Ctl &C = *reinterpret_cast<Ctl *>(ring + (size_t)net.slots * net.slot_bytes);
     float *Ps = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(&C) + sizeof(Ctl));
     volatile int *abort = &C.abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (rows + 127) / 128;
-    const int S = net.slots;
+    const int S = net.slots, G = net.group;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -279,12 +288,13 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
     }
     if (warp == kMmaWarp) tc::tmem_alloc(&C.tmem, net.tmem_cols);
     {
-        // biases of every layer, output weights and bias, read by the epilogue
+        // halved biases of every layer (the SiLU takes z / 2), output weights
+        // and bias, read by the epilogue
         const int W = net.width, LW = net.layers * W;
         for (int i = threadIdx.x; i < (int)net.p_floats; i += kThreads) {
             float v;
             if (i < LW)
-                v = net.params[net.offB0 + (size_t)(i / W) * (W * W + W) + i % W];
+                v = 0.5f * net.params[net.offB0 + (size_t)(i / W) * (W * W + W) + i % W];
             else if (i < LW + W)
                 v = net.params[net.offWo + i - LW];
             else
@@ -299,21 +309,27 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
-            uint32_t cnt = 0;
+            uint32_t cnt = 0, s = 0, phase = 0;   // slots filled, ring position, its wrap parity
             bool ok = true;
             for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
                 const unsigned char *src = net.wpack;
                 for (int l = 0; ok && l < net.layers; ++l) {
                     const int nch = in_of(net, l) / 16;
-                    for (int c = 0; c < nch; ++c, ++cnt, src += net.chunk_bytes) {
-                        const int s = (int)(cnt % S);
-                        if (!wait_or_abort(&C.empty[s], ((cnt / S) & 1u) ^ 1u, abort)) {
+                    for (int c = 0; c < nch; c += G) {
+                        const uint32_t bytes = (uint32_t)min(G, nch - c) * net.chunk_bytes;
+                        if (!wait_or_abort(&C.empty[s], phase ^ 1u, abort)) {
                             fail(C, err);
                             ok = false;
                             break;
                         }
-                        arrive_expect_tx(&C.full[s], net.chunk_bytes);
-                        bulk_copy(ring + (size_t)s * net.chunk_bytes, src, net.chunk_bytes, &C.full[s]);
+                        arrive_expect_tx(&C.full[s], bytes);
+                        bulk_copy(ring + (size_t)s * net.slot_bytes, src, bytes, &C.full[s]);
+                        src += bytes;
+                        ++cnt;
+                        if (++s == (uint32_t)S) {
+                            s = 0;
+                            phase ^= 1u;
+                        }
                     }
                 }
             }
@@ -324,10 +340,11 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
-            uint32_t cnt = 0, v = 0;
+            uint32_t s = 0, phase = 0, v = 0;
             bool ok = true;
             const uint32_t idesc = tc::idesc_bf16_f32(128, net.width);
-            const uint32_t a0 = tc::smem_u32(Abuf), r0 = tc::smem_u32(ring);
+            const uint32_t a0 = tc::smem_u32(Abuf);
+            const uint64_t bd0 = tc::smem_desc(tc::smem_u32(ring), 128u, 256u);
             for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
                 for (int l = 0; ok && l < net.layers; ++l) {
                     if (!wait_or_abort(&C.a_ready, (v++) & 1u, abort)) {
@@ -337,18 +354,27 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
                     }
                     tc::fence_after_sync();
                     const int K = in_of(net, l), nch = K / 16;
-                    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-                    for (int c = 0; c < nch; ++c, ++cnt) {
-                        const int s = (int)(cnt % S);
-                        if (!wait_or_abort(&C.full[s], (cnt / S) & 1u, abort)) {
+                    // descriptors of chunk 0 of A and of slot 0; a chunk
+                    // further on adds its byte offset / 16 to the address
+                    // field (shared addresses stay below 2^18 bytes: no carry)
+                    const uint64_t ad0 = tc::smem_desc(a0, 128u, (uint32_t)(K / 8) * 128u);
+                    for (int c = 0; c < nch; c += G) {
+                        if (!wait_or_abort(&C.full[s], phase, abort)) {
                             fail(C, err);
                             ok = false;
                             break;
                         }
-                        const uint64_t ad = tc::smem_desc(a0 + (uint32_t)c * 256u, 128u, sbo);
-                        const uint64_t bd = tc::smem_desc(r0 + (uint32_t)s * net.chunk_bytes, 128u, 256u);
-                        tc::mma_bf16(tmem, ad, bd, idesc, c > 0 ? 1u : 0u);
+                        const int g = min(G, nch - c);
+                        const uint64_t bd = bd0 + (uint64_t)((s * net.slot_bytes) >> 4);
+                        for (int j = 0; j < g; ++j)
+                            tc::mma_bf16(tmem, ad0 + (uint64_t)((c + j) * 16),
+                                         bd + (uint64_t)(j * (net.chunk_bytes >> 4)), idesc,
+                                         (c + j) > 0 ? 1u : 0u);
                         tc::mma_commit(&C.empty[s]);
+                        if (++s == (uint32_t)S) {
+                            s = 0;
+                            phase ^= 1u;
+                        }
                     }
                     if (ok) tc::mma_commit(&C.acc_full);
                 }
@@ -399,26 +425,35 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
                 }
                 tc::fence_after_sync();
                 const bool last = l == net.layers - 1;
-                const float *bias = Ps + l * W;
+                const float *hbias = Ps + l * W;
                 const uint32_t sbo = (uint32_t)(W / 8) * 128u;
                 // this thread's 16-column chunks cc = half, half + 2, ..., two
                 // loads in flight per wait
                 auto finish = [&](int cc, const uint32_t (&r)[16]) {
                     uint32_t pk[8];
+                    const float4 *hb = reinterpret_cast<const float4 *>(hbias + cc * 16);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        pk[i] = pack_bf16(silu(__uint_as_float(r[2 * i]) + bias[cc * 16 + 2 * i]),
-                                          silu(__uint_as_float(r[2 * i + 1]) + bias[cc * 16 + 2 * i + 1]));
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 b = hb[i];
+                        pk[2 * i] = pack_bf16(silu_half(fmaf(__uint_as_float(r[4 * i]), 0.5f, b.x)),
+                                              silu_half(fmaf(__uint_as_float(r[4 * i + 1]), 0.5f, b.y)));
+                        pk[2 * i + 1] =
+                            pack_bf16(silu_half(fmaf(__uint_as_float(r[4 * i + 2]), 0.5f, b.z)),
+                                      silu_half(fmaf(__uint_as_float(r[4 * i + 3]), 0.5f, b.w)));
+                    }
                     if (!last) {
                         unsigned char *dst = Abuf + (m >> 3) * sbo + (2 * cc) * 128 + (m & 7) * 16;
                         *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         *reinterpret_cast<uint4 *>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     } else {
+                        const float4 *wo = reinterpret_cast<const float4 *>(w_out + cc * 16);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            part = fmaf(__uint_as_float(pk[i] << 16), w_out[cc * 16 + 2 * i], part);
-                            part = fmaf(__uint_as_float(pk[i] & 0xffff0000u), w_out[cc * 16 + 2 * i + 1],
-                                        part);
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 w = wo[i];
+                            part = fmaf(__uint_as_float(pk[2 * i] << 16), w.x, part);
+                            part = fmaf(__uint_as_float(pk[2 * i] & 0xffff0000u), w.y, part);
+                            part = fmaf(__uint_as_float(pk[2 * i + 1] << 16), w.z, part);
+                            part = fmaf(__uint_as_float(pk[2 * i + 1] & 0xffff0000u), w.w, part);
                         }
                     }
                 };
