@@ -149,7 +149,9 @@ __device__ __forceinline__ int in_of(const Net &n, int l) { return l == 0 ? n.in
 struct InRows {
     const float *x;
     int in_dim;
-    __device__ __forceinline__ void operator()(int row, int g, float (&v)[8]) const
+    using Row = int;
+    __device__ __forceinline__ Row at(int row) const { return row; }
+    __device__ __forceinline__ void operator()(Row row, int g, float (&v)[8]) const
     {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -157,7 +159,7 @@ struct InRows {
             v[i] = k < in_dim ? x[(size_t)row * in_dim + k] : 0.f;
         }
     }
-    __device__ __forceinline__ size_t out(int row) const { return (size_t)row; }
+    __device__ __forceinline__ size_t out(Row row) const { return (size_t)row; }
 };
 
 // sin, cos of each joint of every rollout step of a set of arms that share
@@ -175,31 +177,33 @@ struct TrajSegs {
 struct InTrajSet {
     const float *traj;
     TrajSegs seg;
-    __device__ __forceinline__ int find(int row) const
+    struct Row {
+        int s, r;                 // segment, row within it
+    };
+    __device__ __forceinline__ Row at(int row) const
     {
         int s = 0;
         while (s + 1 < seg.n && row >= seg.row_start[s + 1]) ++s;
-        return s;
+        return Row{s, row - seg.row_start[s]};
     }
-    __device__ __forceinline__ void operator()(int row, int g, float (&v)[8]) const
+    // The features are rounded to BF16 (8 significant bits) before the first
+    // layer, so the fast sine and cosine (absolute error near 1e-6 for the
+    // joint ranges of an arm) change none beyond that rounding's last step.
+    __device__ __forceinline__ void operator()(Row w, int g, float (&v)[8]) const
     {
-        const int s = find(row), K = seg.K[s], dof = seg.dof[s];
-        const int r = row - seg.row_start[s], h = r / K, n = r - h * K;
-        const float *qh = traj + seg.off_khd[s] + (size_t)h * dof * K + n;
+        const int K = seg.K[w.s], dof = seg.dof[w.s];
+        const int h = w.r / K, n = w.r - h * K;
+        const float *qh = traj + seg.off_khd[w.s] + (size_t)h * dof * K + n;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int j = 4 * g + p;
             float sn = 0.f, cs = 0.f;
-            if (j < dof) sincosf(qh[(size_t)j * K], &sn, &cs);
+            if (j < dof) __sincosf(qh[(size_t)j * K], &sn, &cs);
             v[2 * p] = sn;
             v[2 * p + 1] = cs;
         }
     }
-    __device__ __forceinline__ size_t out(int row) const
-    {
-        const int s = find(row);
-        return (size_t)(seg.off_kh[s] + (row - seg.row_start[s]));
-    }
+    __device__ __forceinline__ size_t out(Row w) const { return (size_t)(seg.off_kh[w.s] + w.r); }
 };
 
 // Features of the arm-pair surrogate for every rollout step of arm a against
@@ -221,16 +225,20 @@ struct PairSegs {
 struct InPairSet {
     const float *traj, *plan;
     PairSegs seg;
-    __device__ __forceinline__ int find(int row) const
+    struct Row {
+        int s, r;                 // segment, row within it
+    };
+    __device__ __forceinline__ Row at(int row) const
     {
         int s = 0;
         while (s + 1 < seg.n && row >= seg.row_start[s + 1]) ++s;
-        return s;
+        return Row{s, row - seg.row_start[s]};
     }
-    __device__ __forceinline__ void operator()(int row, int g, float (&v)[8]) const
+    // fast sine and cosine, as for InTrajSet: the features are rounded to BF16
+    __device__ __forceinline__ void operator()(Row w, int g, float (&v)[8]) const
     {
-        const int s = find(row), K = seg.K[s], da = seg.da[s], db = seg.db[s];
-        const int r = row - seg.row_start[s], h = r / K, n = r - h * K;
+        const int s = w.s, K = seg.K[s], da = seg.da[s], db = seg.db[s];
+        const int r = w.r, h = r / K, n = r - h * K;
         const float *qa = traj + seg.off_khd[s] + (size_t)h * da * K + n;
         const float *qb = plan + seg.off_hd[s] + (size_t)min(h, seg.Hb[s] - 1) * db;
 #pragma unroll
@@ -238,9 +246,9 @@ struct InPairSet {
             const int f = 8 * g + p;                 // even: (sin, cos) pairs stay together
             float a = 0.f, b = 0.f;
             if (f < 2 * da) {
-                sincosf(qa[(size_t)(f >> 1) * K], &a, &b);
+                __sincosf(qa[(size_t)(f >> 1) * K], &a, &b);
             } else if (f < 2 * da + 2 * db) {
-                sincosf(qb[(f - 2 * da) >> 1], &a, &b);
+                __sincosf(qb[(f - 2 * da) >> 1], &a, &b);
             } else {
                 const int k = f - 2 * da - 2 * db;
                 a = k < 7 ? seg.pose[s][k] : 0.f;
@@ -250,16 +258,12 @@ struct InPairSet {
             v[p + 1] = b;
         }
     }
-    __device__ __forceinline__ size_t out(int row) const
-    {
-        const int s = find(row);
-        return (size_t)(seg.off_out[s] + (row - seg.row_start[s]));
-    }
+    __device__ __forceinline__ size_t out(Row w) const { return (size_t)(seg.off_out[w.s] + w.r); }
 };
 
-// Input functor interface: in(row, g, v) fills the 8 features 8g .. 8g+7 of
-// a valid row (row < rows), features at or beyond the input width 0; the
-// row's output goes to y[in.out(row)].
+// Input functor interface: in.at(row) locates a valid row (row < rows) once,
+// in(at, g, v) fills its 8 features 8g .. 8g+7, features at or beyond the
+// input width 0, and the row's output goes to y[in.out(at)].
 template <class In>
 __global__ void __launch_bounds__(kThreads, 2)
 k_mlp_fused(Net net, In in, int rows, float *y, int *err)
@@ -396,13 +400,14 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
         for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
             const int row = t * 128 + m;
             const bool valid = row < rows;
+            const typename In::Row at = in.at(valid ? row : 0);
             // features of this row into A (layout of K = in_pad)
             {
                 const uint32_t sbo = (uint32_t)(net.in_pad / 8) * 128u;
                 for (int g = half; g < net.in_pad / 8; g += 2) {
                     float v[8];
                     if (valid) {
-                        in(row, g, v);
+                        in(at, g, v);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) v[i] = 0.f;
@@ -484,7 +489,7 @@ k_mlp_fused(Net net, In in, int rows, float *y, int *err)
                     fail(C, err);
                     ok = false;
                 } else if (valid) {
-                    y[in.out(row)] = part + C.part[m] + b_out;
+                    y[in.out(at)] = part + C.part[m] + b_out;
                 }
             }
         }
