@@ -86,6 +86,8 @@ struct RolloutSmem {
     int2 *opairs;           // [kObstaclePairCap] the sub-batch's obstacle pairs left by the
                             // box tests: own sphere | other << 6 | set << 18, (r + B + r_p)^2
     int *opn;               // the count of opairs entries this sub-batch (by sub-batch parity)
+    const unsigned *need;   // [32] with an arm-pair surrogate: the neighbours each lane needs
+    const unsigned *skip;   // the neighbours no lane needs (this sub-batch's parity)
     float4 *sbox;           // [ns][2] per-sphere bounding box over the sub-batch: lo, hi
     float2 *sc;             // [dof][32] sin, cos of q_j + theta_j of the sub-batch's samples
     float4 *dh;             // [kMaxDof] the arm's DH rows (a, d, alpha, theta)
@@ -335,6 +337,53 @@ __device__ __forceinline__ void obstacle_pairs(const Params &P, const RolloutSme
     if (nc > 0) near_pairs<SPG>(P, S, list, nc, n_world, tw, tn, s0, cnt, lane, need_nb);
 }
 
+// With an arm-pair surrogate, a step whose predicted clearance to a
+// neighbour's plan is at least B + margin needs no exact pass for it (its
+// coordination term is zero); a plan published without joints always takes
+// the exact pass.  Warp g decides for neighbours g, g + 8, ... of the
+// samples n (lane): the loaded predictions and plan flags (pair_loads), then
+// the bits (pair_bits): a cleared bit in need[lane] for a neighbour the lane
+// does not need, a set bit in *skip for one no lane needs.  need starts at
+// all ones and skip at zero for every sub-batch.
+constexpr int kPairPerWarp = (MRS_MAX_ARMS + kGroups - 1) / kGroups;
+template <class Arm>
+__device__ __forceinline__ void pair_loads(const Params &P, const Dev &D, const Arm &A,
+                                           unsigned mask, int n_nb, int h, int n, int g,
+                                           float (&rv)[kPairPerWarp], int (&bv)[kPairPerWarp])
+{
+#pragma unroll
+    for (int k = 0; k < kPairPerWarp; ++k) {
+        const int nb = g + kGroups * k;
+        rv[k] = kInf;
+        bv[k] = 1;
+        if (nb < n_nb) {
+            const int ai = __fns(mask, 0, nb + 1);     // the arm of neighbour nb
+            if ((A.pair_mask >> ai) & 1u) {
+                bv[k] = D.board_valid[ai];
+                if (n < A.K)
+                    rv[k] = D.rhohat[A.off_kh * P.n_arms + (long long)ai * A.H * A.K +
+                                     (long long)h * A.K + n];
+            }
+        }
+    }
+}
+template <class Arm>
+__device__ __forceinline__ void pair_bits(const Params &P, const Arm &A, unsigned mask, int n_nb,
+                                          int n, int g, int lane, const float (&rv)[kPairPerWarp],
+                                          const int (&bv)[kPairPerWarp], unsigned *need,
+                                          unsigned *skip)
+{
+#pragma unroll
+    for (int k = 0; k < kPairPerWarp; ++k) {
+        const int nb = g + kGroups * k;
+        if (nb < n_nb && ((A.pair_mask >> __fns(mask, 0, nb + 1)) & 1u)) {
+            const bool nd = n < A.K && (bv[k] != 1 || rv[k] < P.B + A.pair_margin);
+            if (!nd) atomicAnd(&need[lane], ~(1u << nb));
+            if (!__any_sync(0xffffffffu, nd) && lane == 0) atomicOr(skip, 1u << nb);
+        }
+    }
+}
+
 template <int SPG>
 __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmHdr &A,
                                               const RolloutSmem &S, int h, int n, bool valid,
@@ -389,24 +438,10 @@ __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, con
         }
         *pose_out = pose_cost(F, S.goal, S.goal + 3, P.w_rot);
     }
-    // with an arm-pair surrogate, a step whose predicted clearance to a
-    // neighbour's plan is at least B + margin needs no exact pass for it
-    // (its coordination term is zero); a plan published without joints
-    // always takes the exact pass.  need_nb: the neighbours this lane needs
-    // (the same in every warp); skip_nb: those no lane needs.
-    unsigned need_nb = ~0u, skip_nb = 0u;
-    if (A.pair_mask) {
-        for (int nb = 0; nb < n_nb; ++nb) {
-            const int ai = S.nb_arm[nb];
-            if ((A.pair_mask >> ai) & 1u) {
-                const bool need = valid && (D.board_valid[ai] != 1 ||
-                                            D.rhohat[A.off_kh * P.n_arms + (long long)ai * A.H * K +
-                                                     (long long)h * K + n] < P.B + A.pair_margin);
-                if (!need) need_nb &= ~(1u << nb);
-                if (!__any_sync(0xffffffffu, need)) skip_nb |= 1u << nb;
-            }
-        }
-    }
+    // with an arm-pair surrogate, the neighbours this lane needs (the same in
+    // every warp) and those no lane needs, decided ahead (pair_bits)
+    const unsigned need_nb = A.pair_mask ? S.need[lane] : ~0u;
+    const unsigned skip_nb = A.pair_mask ? *S.skip : 0u;
     // the obstacle passes below need only the warp's own spheres and boxes:
     // they run before the barrier that publishes every group's centres to
     // the self pass, so a warp with a short kinematic chain spends the wait
@@ -573,6 +608,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     __shared__ float s_qn[kMaxDof * 32];   // the next sub-batch's joint angles, copied ahead
     __shared__ ArmHdr s_ah[2];    // the unit arm's scalars, by unit parity
     __shared__ int s_opn[2];      // obstacle pairs listed, by sub-batch parity
+    __shared__ unsigned s_need[2][32], s_skip[2];   // pair_bits, by sub-batch parity
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_world = D.world_n[0], n_aabb = D.world_n[1];
     const int ncw = (n_world + 7) >> 3;   // world clusters
@@ -581,7 +617,11 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
     // both minima buffers start at +inf; every sub-batch's cost stage resets
     // the entries it used, so they are +inf again when reused
     for (int k = threadIdx.x; k < 2 * red_stride; k += kRolloutThreads) S.red[k] = float_to_ordered(kInf);
-    if (threadIdx.x < 2) s_opn[threadIdx.x] = 0;
+    if (threadIdx.x < 2) {
+        s_opn[threadIdx.x] = 0;
+        s_skip[threadIdx.x] = 0u;
+    }
+    if (threadIdx.x < 64) s_need[threadIdx.x >> 5][threadIdx.x & 31] = ~0u;
     __shared__ __align__(8) uint64_t s_bar;   // completion of the plan-slice copies
     uint32_t bar_phase = 0;
     if (threadIdx.x == 0) {
@@ -724,6 +764,12 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             pdl_trigger();
         }
         if (g == 1 && ok) S.nb_alpha[tp * MRS_MAX_ARMS + pos] = D.alpha[T.arm * NA + lane];
+        if (A.pair_mask) {   // the unit's first sub-batch's neighbour masks
+            float rv[kPairPerWarp];
+            int bv[kPairPerWarp];
+            pair_loads(P, D, A, mask, nnb, h, T.n0 + lane, g, rv, bv);
+            pair_bits(P, A, mask, nnb, T.n0 + lane, g, lane, rv, bv, s_need[buf], &s_skip[buf]);
+        }
         {
             const int n = T.n0 + lane;
             const bool valid = n < A.K;
@@ -782,6 +828,8 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             Sb.red = S.red + buf * red_stride;
             Sb.sc = sc_base + buf * (kMaxDof * 32);
             Sb.opn = s_opn + buf;
+            Sb.need = s_need[buf];
+            Sb.skip = &s_skip[buf];
             const int n = T.n0 + sb * 32 + lane;
             const bool valid = n < AH.K;
             // warp 0 uses the sub-batch's stop / joint-limit terms in its cost
@@ -805,6 +853,7 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                               D.traj + AH.off_khd + ((long long)h * AH.dof + j) * AH.K +
                                   (valid_next ? n_next : 0));
             }
+            const bool pm = AH.pair_mask != 0u;
             float pose = 0.f;
             // the group routine of the arm's size (only the sizes the build holds)
 #define MRS_GROUP(SZ)                                                                          \
@@ -825,6 +874,21 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             }
 #undef MRS_GROUP
             if (g == kGroups - 1) s_pose[buf][lane] = pose;
+            if (pm) {
+                // every warp read this sub-batch's masks before the group's
+                // first barrier: reset for their next use, two sub-batches on
+                if (g == kGroups - 1) {
+                    s_need[buf][lane] = ~0u;
+                    if (lane == 0) s_skip[buf] = 0u;
+                }
+                if (next) {   // the next sub-batch's masks, behind this one's passes
+                    float prv[kPairPerWarp];
+                    int pbv[kPairPerWarp];
+                    pair_loads(P, D, AH, mask, n_nb, h, n + 32, g, prv, pbv);
+                    pair_bits(P, AH, mask, n_nb, n + 32, g, lane, prv, pbv, s_need[buf ^ 1],
+                              &s_skip[buf ^ 1]);
+                }
+            }
             if (next) {
                 float2 *sc = sc_base + (buf ^ 1) * (kMaxDof * 32);
                 cp_async_wait_all();
