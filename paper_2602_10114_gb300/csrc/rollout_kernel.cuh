@@ -384,6 +384,19 @@ __device__ __forceinline__ void pair_bits(const Params &P, const Arm &A, unsigne
     }
 }
 
+// pair_loads then pair_bits, out of line: the exact mode never calls it, so
+// that its code stays out of the hot loop's instruction footprint
+template <class Arm>
+__device__ __noinline__ void pair_masks(const Params &P, const Dev &D, const Arm &A, unsigned mask,
+                                        int n_nb, int h, int n, int g, int lane, unsigned *need,
+                                        unsigned *skip)
+{
+    float rv[kPairPerWarp];
+    int bv[kPairPerWarp];
+    pair_loads(P, D, A, mask, n_nb, h, n, g, rv, bv);
+    pair_bits(P, A, mask, n_nb, n, g, lane, rv, bv, need, skip);
+}
+
 template <int SPG>
 __device__ __forceinline__ void rollout_group(const Params &P, const Dev &D, const ArmHdr &A,
                                               const RolloutSmem &S, int h, int n, bool valid,
@@ -764,12 +777,8 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
             pdl_trigger();
         }
         if (g == 1 && ok) S.nb_alpha[tp * MRS_MAX_ARMS + pos] = D.alpha[T.arm * NA + lane];
-        if (A.pair_mask) {   // the unit's first sub-batch's neighbour masks
-            float rv[kPairPerWarp];
-            int bv[kPairPerWarp];
-            pair_loads(P, D, A, mask, nnb, h, T.n0 + lane, g, rv, bv);
-            pair_bits(P, A, mask, nnb, T.n0 + lane, g, lane, rv, bv, s_need[buf], &s_skip[buf]);
-        }
+        if (A.pair_mask)   // the unit's first sub-batch's neighbour masks
+            pair_masks(P, D, A, mask, nnb, h, T.n0 + lane, g, lane, s_need[buf], &s_skip[buf]);
         {
             const int n = T.n0 + lane;
             const bool valid = n < A.K;
@@ -881,13 +890,9 @@ __global__ void __launch_bounds__(kRolloutThreads, MB) k_rollout(Params P, Dev D
                     s_need[buf][lane] = ~0u;
                     if (lane == 0) s_skip[buf] = 0u;
                 }
-                if (next) {   // the next sub-batch's masks, behind this one's passes
-                    float prv[kPairPerWarp];
-                    int pbv[kPairPerWarp];
-                    pair_loads(P, D, AH, mask, n_nb, h, n + 32, g, prv, pbv);
-                    pair_bits(P, AH, mask, n_nb, n + 32, g, lane, prv, pbv, s_need[buf ^ 1],
-                              &s_skip[buf ^ 1]);
-                }
+                if (next)   // the next sub-batch's masks, behind this one's passes
+                    pair_masks(P, D, AH, mask, n_nb, h, n + 32, g, lane, s_need[buf ^ 1],
+                               &s_skip[buf ^ 1]);
             }
             if (next) {
                 float2 *sc = sc_base + (buf ^ 1) * (kMaxDof * 32);
